@@ -1,0 +1,242 @@
+/*
+ * lp.h -- C ABI of liblp.so, the GB300 (sm_103a) hot path of the Lagrangian
+ * particle (LP) method of Yuan, Zepeda Aguilar, Naitlho and Samulyak,
+ * "Massively-Parallel Lagrangian Particle Code and Applications" (Sec. 2).
+ *
+ * The library advances the compressible Euler equations in Lagrangian form
+ * (Sec. 2.1, Eqs. mass, momentum, energy, eos) for an ideal gas, one particle
+ * per fluid parcel, with the per-step algorithm of Sec. 2.2:
+ *   neighbour search on a space-filling-curve ordering   -> lp_build_neighbors
+ *   GFD least-squares derivatives (Eq. linear_system_axb) -> lp_gfd_derivs,
+ *                                                           lp_onesided_derivs
+ *   Lax-Wendroff / upwind rates, state estimator, limiter
+ *   blend and particle mover (Eq. timeIntegrate)          -> lp_step
+ *
+ * Conventions for every entry point
+ *   - Pointers named "device" are CUDA device pointers; "host" pointers are
+ *     ordinary host memory.  Particle and field buffers are owned by the caller
+ *     and never freed by the library.  The context owns its scratch (sort
+ *     buffers, cell tables, neighbour lists) and frees it in lp_destroy.
+ *   - Work is enqueued asynchronously on the given CUDA stream (0 = legacy
+ *     default stream).  Host-side argument errors return immediately without
+ *     enqueuing anything.  Conditions found on the device (capacity overflow,
+ *     ill-conditioned stencils, non-finite states) are accumulated in a device
+ *     status word that lp_get_stats reads; no entry point aborts or traps.
+ *   - A context must not be used from two host threads at once.
+ *   - Positions, state and time are float64 structure-of-arrays.
+ */
+#ifndef LP_H
+#define LP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lp_stream;   /* a cudaStream_t */
+
+typedef enum {
+    LP_OK = 0,
+    LP_ERR_ARG = 1,        /* invalid argument (null pointer, bad size or mode) */
+    LP_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    LP_ERR_CAPACITY = 3,   /* n exceeds the context capacity */
+    LP_ERR_ILLCOND = 4,    /* a stencil had no usable fit (see lp_stats) */
+    LP_ERR_NONFINITE = 5,  /* a non-finite state or time step was produced */
+    LP_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
+    LP_ERR_STATE = 7       /* entry point called in the wrong order */
+} lp_status;
+
+enum { LP_PREC_FP32 = 0,   /* fits in FP32 with FP64 redo of ill-conditioned stencils */
+       LP_PREC_FP64 = 1 }; /* every fit in FP64 */
+
+enum { LP_RADIUS_FIXED = 0,   /* j is a neighbour of i iff |x_j - x_i| <= radius */
+       LP_RADIUS_VOLUME = 1,  /* ... iff |x_j - x_i| <= kappa (m_i V_i)^(1/dim) */
+       LP_RADIUS_KSIDE = 2 }; /* 1D only: k_per_side nearest on each side */
+
+enum { LP_LIM_FLAGGED = 0,  /* phi(r_s) where the estimator flags, pure LW elsewhere */
+       LP_LIM_PAPER = 1,    /* phi(r_s) at every particle */
+       LP_LIM_LW = 2,       /* Lax-Wendroff only (phi = 1) */
+       LP_LIM_UW = 3 };     /* upwind only (phi = 0) */
+
+enum { LP_EST_PLAIN = 0,    /* state estimator of Sec. 2.1 */
+       LP_EST_MLP = 1 };    /* learned estimator, plain estimator as fallback */
+
+enum { LP_OUT_F32 = 0, LP_OUT_F64 = 1 };
+
+/*
+ * Method and layout parameters (host struct, copied by lp_create).
+ *   dim            1, 2 or 3.
+ *   precision      LP_PREC_*.
+ *   radius_mode    LP_RADIUS_*; radius / kappa as the mode needs.
+ *   k_max          neighbour capacity per particle, 1..64; nearer neighbours
+ *                  (by (d^2, id)) are kept when more lie inside the radius.
+ *   k_side         one-sided stencil size per half-space (Sec. 2.2 step 5
+ *                  uses 8 in 3D), 1..16.
+ *   k_per_side     LP_RADIUS_KSIDE only, 1..8.
+ *   gamma          ideal-gas exponent, > 1.
+ *   limiter, estimator   LP_LIM_*, LP_EST_*.
+ *   flat_eps, active_frac, s_ref[5]   state-estimator constants: a field whose
+ *                  one-sided derivatives d satisfy max|d| * ell <= flat_eps *
+ *                  max(|s|, s_ref) is treated as locally constant (r = 1); axes
+ *                  with max(|s_l|,|s_r|) < active_frac * (largest over axes) are
+ *                  ignored.  Field order V, u_1..u_dim, P.
+ *   tau32, tau64   FP32 fits whose min|R_kk|/max|R_kk| (column-scaled) falls
+ *                  below tau32 are redone in FP64; below tau64 (FP64) the
+ *                  second-order fit is replaced by the first-order one.
+ *   periodic[3], box_lo[3], box_hi[3]   periodic axes use the minimum image
+ *                  and wrap moved particles; a periodic box must be a cube.
+ *   n_fluid        particles whose id >= n_fluid are frozen boundary
+ *                  particles: neighbours of others, never updated or moved.
+ *   capacity       largest n any call will pass (scratch is sized for it).
+ *   max_level      finest cell level of the Morton cell tables (0 = automatic).
+ */
+typedef struct {
+    int32_t dim;
+    int32_t precision;
+    int32_t radius_mode;
+    int32_t k_max;
+    int32_t k_side;
+    int32_t k_per_side;
+    int32_t limiter;
+    int32_t estimator;
+    double gamma;
+    double radius;
+    double kappa;
+    double flat_eps;
+    double active_frac;
+    double s_ref[5];
+    double tau32;
+    double tau64;
+    int32_t periodic[3];
+    int32_t max_level;
+    double box_lo[3];
+    double box_hi[3];
+    int64_t n_fluid;
+    int64_t capacity;
+} lp_config;
+
+/* Caller-owned device particle arrays (SoA, float64; id uint32).  Unused axes
+ * (>= dim) may be NULL. */
+typedef struct {
+    int64_t n;
+    double *x[3];
+    double *V;        /* specific volume 1/rho */
+    double *u[3];
+    double *P;
+    double *m;        /* particle mass (never modified, only permuted) */
+    uint32_t *id;
+} lp_particles;
+
+/* Read-only view of the context-owned neighbour lists (device pointers),
+ * valid until the next call that rebuilds them. */
+typedef struct {
+    int64_t n;
+    int32_t k_max;             /* row stride of idx */
+    int32_t pad;
+    const uint32_t *count;     /* [n] list length, <= k_max */
+    const uint32_t *total;     /* [n] neighbours inside the radius before truncation */
+    const uint32_t *idx;       /* [n][k_max] indices into the permuted particle arrays,
+                                  in (d^2, id) order */
+    const double *d2min;       /* [n] squared distance of the nearest neighbour */
+    const uint64_t *keys;      /* [n] Morton keys of the permuted particles */
+} lp_neighbors;
+
+/* Counters accumulated since the last lp_reset_stats (host struct). */
+typedef struct {
+    double dt;                 /* last time step used */
+    int64_t steps;
+    int64_t n_flagged;         /* particle-steps flagged by the estimator */
+    int64_t n_fp64_redo;       /* FP32 fits redone in FP64 */
+    int64_t n_linear;          /* fits that fell back to first order */
+    int64_t n_nofit;           /* fits with no usable system (derivatives zero) */
+    int64_t n_overflow;        /* particles with more than k_max neighbours */
+    int64_t n_nonfinite;       /* non-finite states produced */
+    int64_t n_mlp_uncertain;   /* learned-estimator calls deferred to the plain one */
+    uint32_t max_count;        /* largest neighbour count seen */
+    uint32_t status;           /* OR of LP_ERR_* bits (1 << code) seen on the device */
+} lp_stats;
+
+typedef struct lp_ctx lp_ctx;
+
+/* Create a context for cfg (validated; LP_ERR_ARG on a bad field). Allocates
+ * scratch for cfg->capacity particles on the current CUDA device. */
+lp_status lp_create(const lp_config *cfg, lp_ctx **out);
+
+/* Free the context and its scratch. NULL is accepted. */
+lp_status lp_destroy(lp_ctx *ctx);
+
+/*
+ * Sec. 2.2 steps 2-4: Morton keys of the positions (the Z-curve order of
+ * Sec. 2.2 "Space-filling curve"), radix sort, permutation of every particle
+ * array IN PLACE into that order, cell tables, and the neighbour query
+ * {j != i : |x_j - x_i| <= R_i} ordered by (d^2, id) and truncated to k_max.
+ * FP64 distances with the fixed operation order ((dx*dx + dy*dy) + dz*dz)
+ * decide membership and order, so the lists are exact.
+ * out (host struct) receives the view of the lists.
+ */
+lp_status lp_build_neighbors(lp_ctx *ctx, lp_particles *p, lp_neighbors *out, lp_stream stream);
+
+/*
+ * Central second-order GFD derivatives (Sec. 2.1, Eq. linear_system_axb and its
+ * 1D/3D analogues) of nfields fields on the lists of the last
+ * lp_build_neighbors (whose permuted particles p must be).  fields: host array
+ * of nfields device pointers (float64 [n], in the permuted order).
+ * derivs: device [nfields][n][n_u] of out_dtype, n_u = 2/5/9 for dim 1/2/3,
+ * unknowns ordered (d_1.., d_11.., mixed d_12, d_13, d_23).
+ * status: optional device uint32 [n] of per-particle fit flags
+ * (1 linear fallback, 2 no fit, 8 FP64 redo).
+ */
+lp_status lp_gfd_derivs(lp_ctx *ctx, const lp_particles *p, const double *const *fields,
+                        int32_t nfields, int32_t out_dtype, void *derivs, uint32_t *status,
+                        lp_stream stream);
+
+/*
+ * One-sided first derivatives (Sec. 2.1, the left/right derivatives of the
+ * upwind scheme): for each axis k and side (0 left, 1 right) the first k_side
+ * list members with x_jk on that side are fitted to first order and component
+ * k kept; with fewer than dim members the central derivative is used.
+ * derivs: device float64 [n][dim][2][nfields].
+ */
+lp_status lp_onesided_derivs(lp_ctx *ctx, const lp_particles *p, const double *const *fields,
+                             int32_t nfields, double *derivs, lp_stream stream);
+
+/*
+ * One LP time step (Sec. 2.2 steps 2-6): neighbours, fits, Lax-Wendroff and
+ * upwind rates, state estimator, limiter blend
+ *   s^{n+1} = s^n + dt (UW - phi (UW - LW))
+ * and the mover x^{n+1} = x^n + dt (u^n + u^{n+1}) / 2 (Eq. timeIntegrate).
+ * p is permuted into Morton order and advanced in place.
+ *   dt > 0 : that step;  dt <= 0 : dt = cfl * min_i ell_i / c_i on the device
+ *            (ell_i nearest-neighbour distance, c_i = sqrt(gamma P_i V_i)).
+ *   t      : optional device float64 scalar, incremented by dt on the device.
+ *   diag   : optional device outputs (any may be NULL): flag uint8 [n],
+ *            phi float32 [n][nf], r float32 [n][nf] (nf = dim + 2).
+ */
+typedef struct {
+    uint8_t *flag;
+    float *phi;
+    float *r;
+} lp_step_diag;
+
+lp_status lp_step(lp_ctx *ctx, lp_particles *p, double dt, double cfl, double *t,
+                  const lp_step_diag *diag, lp_stream stream);
+
+/* Device time step of the last lp_step (device float64 scalar owned by ctx). */
+const double *lp_dt_device(lp_ctx *ctx);
+
+/* Synchronise `stream`, read the counters into *out (host). */
+lp_status lp_get_stats(lp_ctx *ctx, lp_stats *out, lp_stream stream);
+lp_status lp_reset_stats(lp_ctx *ctx, lp_stream stream);
+
+/* Human-readable name of a status code (static string). */
+const char *lp_status_string(lp_status s);
+
+/* Library version string (static). */
+const char *lp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP_H */

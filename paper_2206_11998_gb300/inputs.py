@@ -1,0 +1,206 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds initial conditions only -- none of the method's arithmetic
+(no neighbour radii, fits, rates or updates).  Both the CUDA path and the
+oracle read the same float64 arrays produced here.  Random numbers come from
+numpy's PCG64 generator with fixed seeds.
+
+A state is a dict::
+
+    x  : list of per-axis float64 arrays (positions)
+    V  : float64 specific volume 1/rho
+    u  : list of per-axis float64 arrays (velocity)
+    P  : float64 pressure
+    m  : float64 particle mass
+    id : uint32 particle id (0..n-1); ids >= n_fluid are frozen boundary particles
+    n_fluid : int
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _state(x, V, u, P, m, n_fluid=None):
+    n = V.shape[0]
+    return {
+        "x": [np.ascontiguousarray(a, np.float64) for a in x],
+        "V": np.ascontiguousarray(V, np.float64),
+        "u": [np.ascontiguousarray(a, np.float64) for a in u],
+        "P": np.ascontiguousarray(P, np.float64),
+        "m": np.ascontiguousarray(m, np.float64),
+        "id": np.arange(n, dtype=np.uint32),
+        "n_fluid": int(n if n_fluid is None else n_fluid),
+    }
+
+
+def sod_1d(n_left: int = 889, n_right: int = 111, ghosts: int = 8,
+           left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1)):
+    """Sod shock tube on [0, 1], discontinuity at 0.5; (rho, u, p) per side.
+
+    Particles sit at cell centres with spacing set by density so that masses are
+    (nearly) equal: dx = 0.5 / n_side, m = rho dx (889/111 approximates the 8:1
+    density ratio with 1000 particles).  ``ghosts`` frozen particles continue the
+    end spacing beyond each end with the end state.
+    """
+    rl, ul, pl = left
+    rr, ur, pr = right
+    dxl, dxr = 0.5 / n_left, 0.5 / n_right
+    xl = (np.arange(n_left) + 0.5) * dxl
+    xr = 0.5 + (np.arange(n_right) + 0.5) * dxr
+    gl = -(np.arange(ghosts) + 0.5) * dxl
+    gr = 1.0 + (np.arange(ghosts) + 0.5) * dxr
+    x = np.concatenate([xl, xr, gl, gr])
+    rho = np.concatenate([np.full(n_left, rl), np.full(n_right, rr), np.full(ghosts, rl), np.full(ghosts, rr)])
+    u = np.concatenate([np.full(n_left, ul), np.full(n_right, ur), np.full(ghosts, ul), np.full(ghosts, ur)])
+    p = np.concatenate([np.full(n_left, pl), np.full(n_right, pr), np.full(ghosts, pl), np.full(ghosts, pr)])
+    dx = np.concatenate([np.full(n_left, dxl), np.full(n_right, dxr), np.full(ghosts, dxl), np.full(ghosts, dxr)])
+    return _state([x], 1.0 / rho, [u], p, rho * dx, n_fluid=n_left + n_right)
+
+
+def jittered_lattice_3d(n_side: int = 100, h: float = 0.01, jitter: float = 0.2, seed: int = 1):
+    """Cubic lattice of n_side^3 points (cell centres of [0, n_side h)^3) with
+    independent uniform jitter in (-jitter h, jitter h) per axis."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = (np.arange(n_side) + 0.5) * h
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()])
+    pts = pts + rng.uniform(-jitter * h, jitter * h, size=pts.shape)
+    return [np.ascontiguousarray(p) for p in pts]
+
+
+def random_quadratic_3d(seed: int = 2):
+    """Coefficients (c, g, H) of f(x) = c + g.x + x^T H x / 2 with N(0,1) entries
+    (H symmetrised)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = rng.standard_normal()
+    g = rng.standard_normal(3)
+    A = rng.standard_normal((3, 3))
+    H = 0.5 * (A + A.T)
+    return float(c), g, H
+
+
+def quadratic_values(x, c, g, H):
+    """Values of the quadratic c + g.x + x^T H x / 2 at positions x (list of 3 arrays)."""
+    X = np.stack(x)
+    return c + g @ X + 0.5 * np.einsum("in,ij,jn->n", X, H, X)
+
+
+def gfd_lattice_workload(n_side: int = 100, h: float = 0.01, noise: float = 1e-6,
+                         seeds=(1, 2, 3), nfields: int = 1):
+    """Jittered lattice plus quadratic fields with additive N(0, noise^2).
+
+    Returns (x, fields, coeffs) where coeffs[f] = (c, g, H) of field f.
+    """
+    x = jittered_lattice_3d(n_side, h, 0.2, seeds[0])
+    fields, coeffs = [], []
+    rng = np.random.Generator(np.random.PCG64(seeds[2]))
+    for f in range(nfields):
+        c, g, H = random_quadratic_3d(seeds[1] + 100 * f)
+        v = quadratic_values(x, c, g, H)
+        if noise > 0:
+            v = v + rng.normal(0.0, noise, size=v.shape)
+        fields.append(np.ascontiguousarray(v))
+        coeffs.append((c, g, H))
+    return x, fields, coeffs
+
+
+GAS_CLOUD_SIGMA2 = 0.05          # particle positions ~ N(0, 0.05 I)
+GAS_CLOUD_GAMMA = 5.0 / 3.0
+
+
+def gas_cloud_3d(n: int = 2_000_000, seed: int = 4, gamma: float = GAS_CLOUD_GAMMA):
+    """Gaussian gas cloud at rest: rho = exp(-r^2/0.1), p = rho^gamma, u = 0.
+
+    Positions are drawn from N(0, 0.05 I) -- the normalised density -- and every
+    particle carries mass M/n with M = (0.1 pi)^(3/2) the total mass.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pts = rng.normal(0.0, np.sqrt(GAS_CLOUD_SIGMA2), size=(3, n))
+    r2 = (pts * pts).sum(axis=0)
+    rho = np.exp(-r2 / (2.0 * GAS_CLOUD_SIGMA2))
+    M = (2.0 * GAS_CLOUD_SIGMA2 * np.pi) ** 1.5
+    zeros = np.zeros(n)
+    return _state([pts[0], pts[1], pts[2]], 1.0 / rho, [zeros, zeros.copy(), zeros.copy()],
+                  rho ** gamma, np.full(n, M / n))
+
+
+def uniform_box_3d(n_side: int = 20, h: float = 0.05, jitter: float = 0.2, seed: int = 7,
+                   rho: float = 1.0, p: float = 1.0, vel=(0.0, 0.0, 0.0)):
+    """Jittered lattice with a constant state (uniform-flow and Galilean checks)."""
+    x = jittered_lattice_3d(n_side, h, jitter, seed)
+    n = x[0].shape[0]
+    m = np.full(n, rho * h ** 3)
+    return _state(x, np.full(n, 1.0 / rho), [np.full(n, float(v)) for v in vel], np.full(n, p), m)
+
+
+def smooth_wave_3d(n_side: int = 24, h: float = 1.0 / 24, jitter: float = 0.2, seed: int = 9,
+                   amp: float = 0.05):
+    """Jittered lattice on [0,1)^3 with a smooth, non-trivial state: every field
+    varies along every axis (used for step-parity tests)."""
+    x = jittered_lattice_3d(n_side, h, jitter, seed)
+    X, Y, Z = x
+    tp = 2.0 * np.pi
+    rho = 1.0 + amp * np.sin(tp * X) * np.cos(tp * Y) + 0.5 * amp * np.sin(tp * Z)
+    p = 1.0 + amp * np.cos(tp * X + 0.3) * np.sin(tp * Y + 0.2) * np.cos(tp * Z)
+    u = [amp * np.sin(tp * Y + 0.1), amp * np.cos(tp * Z) * np.sin(tp * X), amp * np.sin(tp * (X + Y))]
+    m = rho * h ** 3
+    return _state(x, 1.0 / rho, u, p, m)
+
+
+def kh_2d(n: int, amp: float, seed: int, rho_in: float = 2.0, rho_out: float = 1.0,
+          vel: float = 0.5, p0: float = 2.5):
+    """Doubly periodic Kelvin-Helmholtz shear layer on [0,1)^2.
+
+    rho = 2, u = +0.5 for |y - 0.5| < 0.25; rho = 1, u = -0.5 elsewhere; p = 2.5.
+    Particles are placed with number density proportional to rho (equal masses):
+    a fraction rho_in * 0.5 / (rho_in * 0.5 + rho_out * 0.5) of them uniformly in
+    the strip, the rest uniformly outside it.  v = amp sin(4 pi x) times a
+    Gaussian of width 0.05 around each interface.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f_in = rho_in * 0.5 / (rho_in * 0.5 + rho_out * 0.5)
+    n_in = int(round(n * f_in))
+    n_out = n - n_in
+    xi = rng.uniform(0.0, 1.0, n_in); yi = rng.uniform(0.25, 0.75, n_in)
+    xo = rng.uniform(0.0, 1.0, n_out); yo = rng.uniform(0.0, 0.5, n_out)
+    yo = np.where(yo < 0.25, yo, yo + 0.5)
+    x = np.concatenate([xi, xo]); y = np.concatenate([yi, yo])
+    inside = np.abs(y - 0.5) < 0.25
+    rho = np.where(inside, rho_in, rho_out)
+    u = np.where(inside, vel, -vel)
+    s = 0.05
+    v = amp * np.sin(4.0 * np.pi * x) * (np.exp(-((y - 0.25) ** 2) / (2 * s * s)) +
+                                          np.exp(-((y - 0.75) ** 2) / (2 * s * s)))
+    M = rho_in * 0.5 + rho_out * 0.5
+    return _state([x, y], 1.0 / rho, [u, v], np.full(n, p0), np.full(n, M / n))
+
+
+def kh_ensemble_sizes(n_sims: int = 256, lo: int = 10_000, hi: int = 200_000, seed: int = 6):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.integers(lo, hi + 1, size=n_sims)
+
+
+def kh_ensemble_amplitudes(n_sims: int = 256, base_seed: int = 5):
+    return np.array([np.random.Generator(np.random.PCG64(base_seed + k)).uniform(0.01, 0.05)
+                     for k in range(n_sims)])
+
+
+def field_scales(state):
+    """Root-mean-square magnitudes used as the estimator's reference scale per
+    field (V, u..., P).  Velocity fields that start at rest use the RMS sound
+    speed proxy sqrt(P V) as their scale."""
+    V, P = state["V"], state["P"]
+    cs = float(np.sqrt(np.mean(P * V)))
+    out = [float(np.sqrt(np.mean(V * V)))]
+    for a in state["u"]:
+        r = float(np.sqrt(np.mean(a * a)))
+        out.append(r if r > 0 else cs)
+    out.append(float(np.sqrt(np.mean(P * P))))
+    return out
+
+
+def take(state, order):
+    """State with particles reordered (ids travel with their particles)."""
+    out = {k: ([a[order] for a in v] if isinstance(v, list) else
+               (v[order] if isinstance(v, np.ndarray) else v)) for k, v in state.items()}
+    return out
