@@ -1,0 +1,413 @@
+"""Benchmark of the 3D LP step on GB300: particle-updates/s.
+
+Workload: the 3D ideal-gas (gamma = 5/3) Gaussian gas cloud, 2,000,000 equal-mass
+particles sampled from rho ~ exp(-r^2/0.1), p = rho^gamma, u = 0 (seeded,
+synthetic).  One step = the whole hot path through the C ABI lp_step: bounding
+cube, Morton keys, radix sort, gather, cell tables, neighbour query, CFL time
+step on the device, fused GFD fits + Lax-Wendroff/upwind rates + estimator +
+limiter blend + mover (FP32 fits, FP64 state, FP64 redo of ill-conditioned
+stencils).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle (the only
+reference this paper has) on bounded samples of the same workload.
+N > 1 (torchrun): independent replicas, one per GPU; no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s (3D LP step) at 1e-5 rel err vs FP64; % HBM roofline"
+UNIT = "particle-updates/s"
+N_PARTICLES = 2_000_000
+GAMMA = 5.0 / 3.0
+KAPPA = 2.2
+K_MAX = 64
+CFL = 0.4
+SEED = 4
+WORKLOAD = "gas-cloud-3d-2M"
+L2_FLUSH_BYTES = 256 << 20
+
+# algorithmic work per particle of the fused fit+update kernel (FP32 flops),
+# m = mean neighbour count, n = 9 unknowns, F = 5 fields, 2d = 6 half-spaces of
+# k = 8 rows with 3 unknowns:
+#   central Householder QR 2 m n^2 - 2 n^3 / 3, Q^T b and back substitution
+#   4 m n F, one refinement step 4 m n F, one-sided 6 (2 k 9 - 18 + 4 k 3 F),
+#   rates + estimator + blend ~ 500.
+def fit_flops_per_particle(m: float) -> float:
+    n, F = 9, 5
+    central = 2 * m * n * n - 2 * n ** 3 / 3 + 8 * m * n * F
+    onesided = 6 * (2 * 8 * 9 - 18 + 4 * 8 * 3 * F)
+    return central + onesided + 500.0
+
+
+# algorithmic DRAM bytes per particle of the memory-bound phases
+BYTES_PER_PARTICLE = {
+    "grid+keys": 24 + 8 + 24 + 12,          # extent read, m V read, positions read, key + index write
+    "radix-sort": 24,                       # per 8-bit pass: key + index read and written once
+    "gather": 76 + 76 + 64,                 # state read, sorted copy written, hi/lo split written
+    "cell-tables": 8 * 2,                   # sorted keys read (fill and clear)
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--particles", type=int, default=N_PARTICLES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_state(n, seed=SEED):
+    from paper_2206_11998_gb300 import inputs
+    return inputs.gas_cloud_3d(n, seed=seed, gamma=GAMMA)
+
+
+def config_dict(n, extra=None):
+    d = {"workload": WORKLOAD, "particles": n, "dim": 3, "gamma": GAMMA, "kappa": KAPPA, "k_max": K_MAX,
+         "cfl": CFL, "limiter": "flagged", "precision": "FP32 fits + FP64 state, FP64 redo",
+         "l2": "flushed between timed steps (256 MiB write); inputs also exceed L2",
+         "parallelism": "replicas"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(state, target_s, seed=0):
+    """Time the oracle's step on a bounded random sample of the workload's
+    particles (full state visible).  Returns (updates/s, cores, sample text)."""
+    import oracle
+    oracle.build()
+    from paper_2206_11998_gb300 import inputs
+    cfg = oracle.make_config(3, gamma=GAMMA, radius_mode=oracle.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
+                             k_side=8, limiter=oracle.LIM_FLAGGED, s_ref=inputs.field_scales(state))
+    n = state["V"].shape[0]
+    rng = np.random.default_rng(seed)
+    q0 = np.sort(rng.choice(n, 256, replace=False))
+    t0 = time.perf_counter()
+    oracle.step(cfg, state, 1e-4, query=q0)
+    t1 = time.perf_counter() - t0
+    q_n = int(min(n, max(256, 256 * target_s / max(t1, 1e-3))))
+    q = np.sort(rng.choice(n, q_n, replace=False))
+    t0 = time.perf_counter()
+    oracle.step(cfg, state, 1e-4, query=q)
+    dt = time.perf_counter() - t0
+    cores = oracle.num_threads()
+    return q_n / dt, cores, q_n, dt
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%s.csv" % os.environ.get("RANK", "0"))
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu is not None:
+                cmd += ["-i", str(self.gpu)]
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_index_for(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2206_11998_gb300 import build as b
+    from paper_2206_11998_gb300 import inputs, lp
+
+    rank, world, local = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    b.build()
+    n = args.particles
+    state = workload_state(n, seed=SEED + rank)
+    cfg = lp.make_config(3, n, precision=lp.PREC_FP32, radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
+                         k_side=8, gamma=GAMMA, limiter=lp.LIM_FLAGGED, s_ref=inputs.field_scales(state))
+    ctx = lp.Context(cfg)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        ps = lp.ParticleSet.from_state(state)
+        t_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            ctx.step(ps, dt=0.0, cfl=CFL, t=t_dev, stream=stream)
+        # mean neighbour count of the current lists (algorithmic work per particle)
+        cnt = ctx.export_neighbors(n, stream=stream)[0]
+        m_mean = float(cnt.double().mean().item())
+        stream.synchronize()
+        ctx.reset_stats(stream=stream)
+        ctx.phase_times(stream=stream)
+        ctx.set_profiling(True)
+        launches0 = ctx.stats(stream=stream)["kernel_launches"]
+        sampler = ClockSampler(gpu_index_for(local))
+        barrier()
+        sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            ctx.step(ps, dt=0.0, cfl=CFL, t=t_dev, stream=stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - wall0
+        barrier()
+        clocks = sampler.stop()
+        ctx.set_profiling(False)
+        phases = ctx.phase_times(stream=stream)
+        st = ctx.stats(stream=stream)
+        launches = st["kernel_launches"] - launches0
+        step_ms = [a.elapsed_time(bb) for a, bb in ev]
+        total_ms = sum(step_ms)
+
+        # end to end through the same C-ABI call with host buffers
+        e2e = run_e2e(ctx, state, n, args, stream, lp, torch, flush)
+
+    tot = torch.tensor([total_ms, e2e["ms"]], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(tot[0]), float(tot[1])
+    value = world * n * args.steps / (total_ms * 1e-3)
+    e2e_value = world * n * args.steps / (e2e_ms * 1e-3)
+
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s, FP32 CUDA cores
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    per_phase = {}
+    for name, (ms, nl) in phases.items():
+        if nl == 0 and ms == 0.0:
+            continue
+        entry = {"ms_per_step": ms / args.steps, "launches": nl, "share": ms / max(1e-9, sum(v[0] for v in phases.values()))}
+        if name in BYTES_PER_PARTICLE:
+            byts = BYTES_PER_PARTICLE[name] * n * (4 if name == "radix-sort" else 1)
+            gbs = byts / (ms / args.steps * 1e-3) / 1e9 if ms > 0 else None
+            entry.update({"bound": "hbm", "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_peak if gbs else None})
+        per_phase[name] = entry
+    fit_ms = phases["fit+update"][0] / args.steps
+    fit_launch_ms = phases["fit+update"][0] / max(1, phases["fit+update"][1])
+    flops = fit_flops_per_particle(m_mean) * n
+    achieved = flops / (fit_launch_ms * 1e-3) / 1e12
+    dominant = max(per_phase, key=lambda k: per_phase[k]["ms_per_step"])
+    roofline = {"kernel": "k_step<float,3> (fit+update)", "dominant_phase": dominant, "bound": "alu",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (sm_max, peak_kind),
+                "flops_per_particle": fit_flops_per_particle(m_mean), "mean_neighbors": m_mean,
+                "traffic": None}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, q_n, secs = oracle_sample_rate(state, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "oracle step of %d random particles of the 2M cloud (full state visible), %.1f s" % (q_n, secs)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(n, {"fit_ms_per_step": fit_ms, "wall_s_timed": wall,
+                                          "flagged_per_step": st["n_flagged"] / args.steps,
+                                          "fp64_redo_per_step": st["n_fp64_redo"] / args.steps}),
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                        "d2h_bytes_per_step": e2e["d2h"]},
+                "gpu_launches": launches, "clocks": clocks, "phases": per_phase}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(ctx, state, n, args, stream, lp, torch, flush):
+    """Each step: host (pinned) -> device copy of the state, lp_step, device ->
+    host copy of the new state; all inside the timed region."""
+    names = ["x0", "x1", "x2", "V", "u0", "u1", "u2", "P", "m"]
+    host = {}
+    for nm in names:
+        src = state["x"][int(nm[1])] if nm[0] == "x" else (state["u"][int(nm[1])] if nm[0] == "u" else state[nm])
+        host[nm] = torch.from_numpy(np.ascontiguousarray(src)).pin_memory()
+    host["id"] = torch.from_numpy(state["id"].astype(np.int32)).pin_memory()
+    dev = {k: torch.empty_like(v, device="cuda") for k, v in host.items()}
+    ps = lp.ParticleSet([dev["x0"], dev["x1"], dev["x2"]], dev["V"], [dev["u0"], dev["u1"], dev["u2"]], dev["P"],
+                        dev["m"], dev["id"])
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = h2d
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, min(args.warmup, 2))):
+            for k in host:
+                dev[k].copy_(host[k], non_blocking=True)
+            ctx.step(ps, dt=0.0, cfl=CFL, stream=stream)
+            for k in host:
+                host[k].copy_(dev[k], non_blocking=True)
+        stream.synchronize()
+        steps = max(1, min(args.steps, 10))
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b2 = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for k in host:
+                dev[k].copy_(host[k], non_blocking=True)
+            ctx.step(ps, dt=0.0, cfl=CFL, stream=stream)
+            for k in host:
+                host[k].copy_(dev[k], non_blocking=True)
+            b2.record(stream)
+            evs.append((a, b2))
+        stream.synchronize()
+    ms = sum(a.elapsed_time(b2) for a, b2 in evs) / steps * args.steps
+    return {"ms": ms, "h2d": h2d, "d2h": d2h}
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    n = args.particles
+    state = workload_state(n)
+    import oracle
+    oracle.build()
+    from paper_2206_11998_gb300 import inputs
+    cfg = oracle.make_config(3, gamma=GAMMA, radius_mode=oracle.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
+                             k_side=8, limiter=oracle.LIM_FLAGGED, s_ref=inputs.field_scales(state))
+    rng = np.random.default_rng(1)
+    # size one step's sample so that the whole run stays within a few minutes
+    budget_s = 150.0
+    probe = np.sort(rng.choice(n, 128, replace=False))
+    t0 = time.perf_counter()
+    oracle.step(cfg, state, 1e-4, query=probe)
+    per = (time.perf_counter() - t0) / 128
+    q_n = int(max(64, min(n, budget_s / max(1, args.steps + args.warmup) / max(per, 1e-7))))
+    times = []
+    for k in range(args.warmup + args.steps):
+        q = np.sort(rng.choice(n, q_n, replace=False))
+        t0 = time.perf_counter()
+        oracle.step(cfg, state, 1e-4, query=q)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = q_n / (ms * 1e-3)
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(n, {"reference": "FP64 CPU oracle (oracle/lp_oracle.c), OpenMP", "precision": "FP64 (oracle)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: oracle step of %d random particles of the 2M cloud" % q_n},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -155,6 +155,7 @@ typedef struct {
     int64_t n_mlp_uncertain;   /* learned-estimator calls deferred to the plain one */
     uint32_t max_count;        /* largest neighbour count seen */
     uint32_t status;           /* OR of LP_ERR_* bits (1 << code) seen on the device */
+    int64_t kernel_launches;   /* kernels this context launched (host-side count) */
 } lp_stats;
 
 typedef struct lp_ctx lp_ctx;
@@ -221,6 +222,35 @@ typedef struct {
 
 lp_status lp_step(lp_ctx *ctx, lp_particles *p, double dt, double cfl, double *t,
                   const lp_step_diag *diag, lp_stream stream);
+
+/*
+ * Copy the lists of the last lp_build_neighbors / lp_step into caller-owned
+ * device buffers (any may be NULL): count/total uint32 [n], idx uint32
+ * [n][k_max], d2min float64 [n], keys uint64 [n] (Morton keys of the permuted
+ * particles).  Enqueued on `stream`.
+ */
+lp_status lp_export_neighbors(lp_ctx *ctx, uint32_t *count, uint32_t *total, uint32_t *idx,
+                              double *d2min, uint64_t *keys, lp_stream stream);
+
+/*
+ * Synchronise `stream` and read the quantisation cube of the last build into
+ * host out[5] = {lo_0, lo_1, lo_2, L, finest level}: Morton coordinates are
+ * q_k = floor((x_k - lo_k) * 2^21 / L), clamped to [0, 2^21 - 1].
+ */
+lp_status lp_grid_info(lp_ctx *ctx, double *out, lp_stream stream);
+
+/*
+ * Phase timing.  With profiling on, every entry point records CUDA events on
+ * its stream around each phase; lp_phase_times synchronises the stream and
+ * adds, per phase, the elapsed milliseconds and launch count since the last
+ * reset into host out_ms[LP_NPHASES] / out_launches[LP_NPHASES] (either may be
+ * NULL), then clears them.  lp_phase_name(k) is the phase's static name.
+ */
+enum { LP_PH_GRID = 0, LP_PH_SORT = 1, LP_PH_GATHER = 2, LP_PH_TABLES = 3, LP_PH_QUERY = 4,
+       LP_PH_CFL = 5, LP_PH_FIT = 6, LP_PH_FIT64 = 7, LP_NPHASES = 8 };
+lp_status lp_set_profiling(lp_ctx *ctx, int32_t on);
+lp_status lp_phase_times(lp_ctx *ctx, double *out_ms, int64_t *out_launches, lp_stream stream);
+const char *lp_phase_name(int32_t phase);
 
 /* Device time step of the last lp_step (device float64 scalar owned by ctx). */
 const double *lp_dt_device(lp_ctx *ctx);

@@ -1,0 +1,632 @@
+// lp_api.cu -- the C ABI of liblp.so (include/lp.h): context management,
+// argument checks, and the order of the phases of one LP step (Sec. 2.2).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lp_fit_kern.cuh"
+
+using namespace lp;
+
+namespace {
+
+// misc device words: [0] dt_min bits, [1..8] extents, [16..16+MAX_LEVELS] level offsets
+constexpr int MISC_WORDS = 64;
+
+#define LP_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return LP_ERR_CUDA;             \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+void free_all(lp_ctx* c)
+{
+    void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist, c->sx[0], c->sx[1], c->sx[2],
+                    c->sV, c->su[0], c->su[1], c->su[2], c->sP, c->sm, c->sid, c->hx[0], c->hx[1], c->hx[2],
+                    c->lx[0], c->lx[1], c->lx[2], c->hf[0], c->hf[1], c->hf[2], c->hf[3], c->hf[4],
+                    c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->cells, c->nb_count, c->nb_total,
+                    c->nb_idx, c->nb_d2min, c->grid, c->dt_dev, c->dt_min, c->counters, c->redo_list};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+lp_status check_cfg(const lp_config* g)
+{
+    if (!g) return LP_ERR_ARG;
+    if (g->dim < 1 || g->dim > 3) return LP_ERR_ARG;
+    if (g->precision != LP_PREC_FP32 && g->precision != LP_PREC_FP64) return LP_ERR_ARG;
+    if (g->radius_mode < 0 || g->radius_mode > 2) return LP_ERR_ARG;
+    if (g->radius_mode == LP_RADIUS_KSIDE && (g->dim != 1 || g->k_per_side < 1 || g->k_per_side > 8 ||
+                                              g->k_max < 2 * g->k_per_side))
+        return LP_ERR_ARG;
+    if (g->radius_mode == LP_RADIUS_FIXED && !(g->radius > 0.0)) return LP_ERR_ARG;
+    if (g->radius_mode == LP_RADIUS_VOLUME && !(g->kappa > 0.0)) return LP_ERR_ARG;
+    if (g->k_max < 1 || g->k_max > KMAX) return LP_ERR_ARG;
+    if (g->k_side < 1 || g->k_side > 16) return LP_ERR_ARG;
+    if (!(g->gamma > 1.0)) return LP_ERR_ARG;
+    if (g->limiter < 0 || g->limiter > 3) return LP_ERR_ARG;
+    if (g->estimator != LP_EST_PLAIN) return LP_ERR_ARG;
+    if (g->capacity < 1 || g->capacity > (int64_t)0x7fffffff) return LP_ERR_ARG;
+    if (!(g->tau32 >= 0.0) || !(g->tau64 >= 0.0)) return LP_ERR_ARG;
+    double L = -1.0;
+    for (int k = 0; k < g->dim; ++k) {
+        if (!g->periodic[k]) continue;
+        double e = g->box_hi[k] - g->box_lo[k];
+        if (!(e > 0.0)) return LP_ERR_ARG;
+        if (L > 0.0 && e != L) return LP_ERR_ARG;   // a periodic box must be a cube
+        L = e;
+    }
+    if (g->max_level < 0 || g->max_level > 21) return LP_ERR_ARG;
+    return LP_OK;
+}
+
+lp_status check_particles(const lp_ctx* c, const lp_particles* p)
+{
+    if (!p) return LP_ERR_ARG;
+    if (p->n < 0) return LP_ERR_ARG;
+    if (p->n > c->cap) return LP_ERR_CAPACITY;
+    if (p->n == 0) return LP_OK;   // nothing is read or written
+    int d = c->dc.dim;
+    for (int k = 0; k < d; ++k)
+        if (!p->x[k] || !p->u[k]) return LP_ERR_ARG;
+    if (!p->V || !p->P || !p->m || !p->id) return LP_ERR_ARG;
+    return LP_OK;
+}
+
+__global__ void k_split_fields(int64_t n, int nf, const double* f0, const double* f1, const double* f2,
+                               const double* f3, const double* f4, float* h0, float* h1, float* h2, float* h3,
+                               float* h4, float* l0, float* l1, float* l2, float* l3, float* l4)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* f[5] = {f0, f1, f2, f3, f4};
+    float* h[5] = {h0, h1, h2, h3, h4};
+    float* l[5] = {l0, l1, l2, l3, l4};
+    for (int q = 0; q < nf; ++q) split(f[q][i], h[q][i], l[q][i]);
+}
+
+// dt = cfl * sqrt(min_i d2min_i / (gamma P_i V_i)) over fluid particles
+__global__ void k_cfl(int64_t n, DevCfg c, const double* d2min, const double* P, const double* V,
+                      const uint32_t* id, unsigned long long* dtmin)
+{
+    double best = INFINITY;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if ((int64_t)id[i] >= c.n_fluid) continue;
+        double d2 = d2min[i];
+        if (isinf(d2)) continue;
+        double cs2 = (c.gamma * P[i]) * V[i];
+        double v = d2 / cs2;
+        best = fmin(best, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best >= 0.0 && best < INFINITY)
+        atomicMin(dtmin, (unsigned long long)__double_as_longlong(best));
+}
+
+__global__ void k_dt_finalize(double cfl, double dt_fixed, const unsigned long long* dtmin, double* dt, double* t,
+                              unsigned long long* counters)
+{
+    double v;
+    if (dt_fixed > 0.0) v = dt_fixed;
+    else {
+        double m = __longlong_as_double((long long)*dtmin);
+        v = cfl * sqrt(m);
+    }
+    if (!(v > 0.0) || isinf(v) || isnan(v)) {
+        atomicOr(reinterpret_cast<unsigned int*>(counters + C_STATUS), ST_NONFINITE);
+        v = 0.0;
+    }
+    *dt = v;
+    if (t) *t += v;
+    counters[C_STEPS] += 1;
+}
+
+void fill_fit_args(lp_ctx* c, FitArgs& a, int64_t n)
+{
+    memset(&a, 0, sizeof(a));
+    a.c = c->dc;
+    a.n = n;
+    a.count = c->nb_count;
+    a.idx = c->nb_idx;
+    a.d2min = c->nb_d2min;
+    for (int k = 0; k < 3; ++k) {
+        int kk = k < c->dc.dim ? k : 0;
+        a.sx[k] = c->sx[kk];
+        a.hx[k] = c->hx[kk];
+        a.lx[k] = c->lx[kk];
+    }
+    for (int f = 0; f < 5; ++f) { a.fh[f] = c->hf[f]; a.fl[f] = c->lf[f]; }
+    a.sid = c->sid;
+    a.sm = c->sm;
+    a.counters = c->counters;
+    a.redo_list = c->redo_list;
+    a.list = nullptr;
+    a.list_len = c->counters + C_REDO_LEN;
+}
+
+constexpr int EV_PAIRS = LP_NPHASES * 4;
+
+cudaError_t flush_events(lp_ctx* c)
+{
+    for (int q = 0; q < c->ev_used; ++q) {
+        cudaError_t e = cudaEventSynchronize(c->ev[2 * q + 1]);
+        if (e != cudaSuccess) return e;
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, c->ev[2 * q], c->ev[2 * q + 1]);
+        if (e != cudaSuccess) return e;
+        c->phase_ms[c->ev_phase[q]] += ms;
+    }
+    c->ev_used = 0;
+    return cudaSuccess;
+}
+
+// phase bracket: counts launches always, records events when profiling
+struct Phase {
+    lp_ctx* c;
+    int ph;
+    int launches;
+    cudaStream_t s;
+    int slot;
+    Phase(lp_ctx* c_, int ph_, int launches_, cudaStream_t s_) : c(c_), ph(ph_), launches(launches_), s(s_), slot(-1)
+    {
+        c->launches += launches;
+        c->phase_launches[ph] += launches;
+        if (c->profiling) {
+            if (c->ev_used == EV_PAIRS) flush_events(c);
+            slot = c->ev_used++;
+            c->ev_phase[slot] = ph;
+            cudaEventRecord(c->ev[2 * slot], s);
+        }
+    }
+    ~Phase()
+    {
+        if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], s);
+    }
+};
+
+}  // namespace
+
+namespace lp {
+
+cudaError_t run_cfl(lp_ctx* c, int64_t n, double cfl, double dt_fixed, double* t, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(c->dt_min, 0x7f, sizeof(unsigned long long), s);   // large positive
+    if (e != cudaSuccess) return e;
+    if (dt_fixed <= 0.0 && n > 0) {
+        int64_t nb_ = (n + 255) / 256; unsigned blocks = (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
+        k_cfl<<<blocks, 256, 0, s>>>(n, c->dc, c->nb_d2min, c->sP, c->sV, c->sid, c->dt_min);
+    }
+    k_dt_finalize<<<1, 1, 0, s>>>(cfl, dt_fixed, c->dt_min, c->dt_dev, t, c->counters);
+    return cudaGetLastError();
+}
+
+}  // namespace lp
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* lp_version(void) { return "lp-gb300 0.1 (sm_103a)"; }
+
+const char* lp_status_string(lp_status s)
+{
+    switch (s) {
+    case LP_OK: return "ok";
+    case LP_ERR_ARG: return "invalid argument";
+    case LP_ERR_CUDA: return "CUDA runtime error";
+    case LP_ERR_CAPACITY: return "particle count exceeds context capacity";
+    case LP_ERR_ILLCOND: return "stencil without a usable fit";
+    case LP_ERR_NONFINITE: return "non-finite state or time step";
+    case LP_ERR_TIMEOUT: return "bounded device wait timed out";
+    case LP_ERR_STATE: return "entry point called out of order";
+    }
+    return "unknown status";
+}
+
+lp_status lp_create(const lp_config* cfg, lp_ctx** out)
+{
+    if (!out) return LP_ERR_ARG;
+    *out = nullptr;
+    lp_status st = check_cfg(cfg);
+    if (st != LP_OK) return st;
+    lp_ctx* c = (lp_ctx*)calloc(1, sizeof(lp_ctx));
+    if (!c) return LP_ERR_CUDA;
+    c->cfg = *cfg;
+    if (c->cfg.tau32 == 0.0) c->cfg.tau32 = 1e-3;
+    if (c->cfg.tau64 == 0.0) c->cfg.tau64 = 1e-12;
+    DevCfg& d = c->dc;
+    d.dim = cfg->dim;
+    d.precision = cfg->precision;
+    d.radius_mode = cfg->radius_mode;
+    d.k_max = cfg->k_max;
+    d.k_side = cfg->k_side;
+    d.k_per_side = cfg->k_per_side;
+    d.limiter = cfg->limiter;
+    d.estimator = cfg->estimator;
+    d.refine = 1;
+    d.gamma = cfg->gamma;
+    d.radius = cfg->radius;
+    d.kappa = cfg->kappa;
+    d.flat_eps = cfg->flat_eps;
+    d.active_frac = cfg->active_frac;
+    d.tau32 = c->cfg.tau32;
+    d.tau64 = c->cfg.tau64;
+    for (int f = 0; f < 5; ++f) d.s_ref[f] = cfg->s_ref[f];
+    for (int k = 0; k < 3; ++k) {
+        d.periodic[k] = k < cfg->dim ? cfg->periodic[k] : 0;
+        d.box_lo[k] = cfg->box_lo[k];
+        d.box_hi[k] = cfg->box_hi[k];
+        d.Lper[k] = cfg->box_hi[k] - cfg->box_lo[k];
+        d.Lper_h[k] = (float)d.Lper[k];
+        d.Lper_l[k] = (float)(d.Lper[k] - (double)d.Lper_h[k]);
+    }
+    d.n_fluid = cfg->n_fluid;
+    c->cap = cfg->capacity;
+    cudaGetDevice(&c->device);
+    // cell tables: levels 0..lmax_cap, 2^(dim l) entries each
+    int dim = cfg->dim;
+    if (dim == 1) c->lmax_cap = 0;
+    else c->lmax_cap = cfg->max_level > 0 ? cfg->max_level : (dim == 3 ? 9 : 13);
+    int64_t off = 0;
+    for (int l = 0; l <= MAX_LEVELS; ++l) {
+        c->level_off[l] = off;
+        if (l <= c->lmax_cap && dim > 1) off += (int64_t)1 << (dim * l);
+    }
+    c->table_entries = dim > 1 ? off : 1;
+    // sort bits: cells down to level lmax_cap (dim * lmax_cap bits under the top)
+    if (dim == 1) { c->sort_lo_bit = 0; c->sort_hi_bit = 64; }
+    else {
+        int top = dim * MORTON_BITS;
+        int need = dim * c->lmax_cap;
+        int passes = (need + 7) / 8;
+        c->sort_hi_bit = top;
+        c->sort_lo_bit = top - 8 * passes;
+        if (c->sort_lo_bit < 0) c->sort_lo_bit = 0;
+    }
+    int64_t n = c->cap;
+    c->hist_blocks = (n + 4095) / 4096;
+    bool ok = true;
+    auto A = [&](cudaError_t e) { if (e != cudaSuccess) ok = false; };
+    A(dalloc(&c->keys[0], n * 8)); A(dalloc(&c->keys[1], n * 8));
+    A(dalloc(&c->vals[0], n * 4)); A(dalloc(&c->vals[1], n * 4));
+    A(dalloc(&c->hist, (size_t)256 * c->hist_blocks * 4));
+    for (int k = 0; k < 3; ++k) {
+        if (k < dim) {
+            A(dalloc(&c->sx[k], n * 8)); A(dalloc(&c->su[k], n * 8));
+            A(dalloc(&c->hx[k], n * 4)); A(dalloc(&c->lx[k], n * 4));
+        }
+    }
+    A(dalloc(&c->sV, n * 8)); A(dalloc(&c->sP, n * 8)); A(dalloc(&c->sm, n * 8)); A(dalloc(&c->sid, n * 4));
+    for (int f = 0; f < 5; ++f) { A(dalloc(&c->hf[f], n * 4)); A(dalloc(&c->lf[f], n * 4)); }
+    A(dalloc(&c->cells, (size_t)c->table_entries * 8));
+    A(dalloc(&c->nb_count, n * 4)); A(dalloc(&c->nb_total, n * 4));
+    A(dalloc(&c->nb_idx, (size_t)n * cfg->k_max * 4)); A(dalloc(&c->nb_d2min, n * 8));
+    A(dalloc(&c->grid, sizeof(Grid))); A(dalloc(&c->dt_dev, 8));
+    A(dalloc(&c->dt_min, MISC_WORDS * 8)); A(dalloc(&c->counters, C_COUNT * 8));
+    A(dalloc(&c->redo_list, n * 4));
+    if (ok) {
+        A(cudaMemset(c->cells, 0, (size_t)c->table_entries * 8));
+        A(cudaMemset(c->counters, 0, C_COUNT * 8));
+        A(cudaMemset(c->dt_dev, 0, 8));
+        A(cudaMemcpy(c->dt_min + 16, c->level_off, sizeof(int64_t) * (MAX_LEVELS + 1), cudaMemcpyHostToDevice));
+        for (int q = 0; q < 2 * EV_PAIRS && ok; ++q) A(cudaEventCreate(&c->ev[q]));
+        A(cudaDeviceSynchronize());
+    }
+    if (!ok) {
+        free_all(c);
+        free(c);
+        return LP_ERR_CUDA;
+    }
+    *out = c;
+    return LP_OK;
+}
+
+lp_status lp_destroy(lp_ctx* c)
+{
+    if (!c) return LP_OK;
+    cudaDeviceSynchronize();
+    for (int q = 0; q < 2 * EV_PAIRS; ++q)
+        if (c->ev[q]) cudaEventDestroy(c->ev[q]);
+    free_all(c);
+    free(c);
+    return LP_OK;
+}
+
+static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
+{
+    int64_t n = p->n;
+    bool tables = c->dc.dim > 1;
+    if (c->tables_dirty) {   // clear the previous build's table entries
+        Phase ph(c, LP_PH_TABLES, tables && c->n_lists > 0 ? 1 : 0, s);
+        LP_CUDA(fill_tables(c, c->n_lists, true, s));
+        c->tables_dirty = 0;
+    }
+    c->n_lists = 0;
+    if (n == 0) return LP_OK;
+    {
+        Phase ph(c, LP_PH_GRID, 4, s);
+        LP_CUDA(build_grid(c, p, s));
+        LP_CUDA(make_keys(c, p, s));
+    }
+    {
+        Phase ph(c, LP_PH_SORT, 3 * radix_passes(c), s);
+        LP_CUDA(radix_sort(c, n, s));
+    }
+    {
+        Phase ph(c, LP_PH_GATHER, 1, s);
+        LP_CUDA(gather(c, p, s));
+    }
+    {
+        Phase ph(c, LP_PH_TABLES, tables ? 1 : 0, s);
+        LP_CUDA(fill_tables(c, n, false, s));
+        c->tables_dirty = tables ? 1 : 0;
+    }
+    {
+        Phase ph(c, LP_PH_QUERY, 1, s);
+        LP_CUDA(query_neighbors(c, n, s));
+    }
+    c->n_lists = n;
+    return LP_OK;
+}
+
+lp_status lp_build_neighbors(lp_ctx* c, lp_particles* p, lp_neighbors* out, lp_stream stream)
+{
+    if (!c) return LP_ERR_ARG;
+    lp_status st = check_particles(c, p);
+    if (st != LP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = build(c, p, s);
+    if (st != LP_OK) return st;
+    if (p->n > 0) {
+        Phase ph(c, LP_PH_GATHER, 1, s);
+        LP_CUDA(scatter_back(c, p, s));
+    }
+    if (out) {
+        out->n = p->n;
+        out->k_max = c->dc.k_max;
+        out->pad = 0;
+        out->count = c->nb_count;
+        out->total = c->nb_total;
+        out->idx = c->nb_idx;
+        out->d2min = c->nb_d2min;
+        out->keys = c->keys_sorted;
+    }
+    return LP_OK;
+}
+
+lp_status lp_gfd_derivs(lp_ctx* c, const lp_particles* p, const double* const* fields, int32_t nfields,
+                        int32_t out_dtype, void* derivs, uint32_t* status, lp_stream stream)
+{
+    if (!c || !p || !fields || !derivs || nfields < 1) return LP_ERR_ARG;
+    if (out_dtype != LP_OUT_F32 && out_dtype != LP_OUT_F64) return LP_ERR_ARG;
+    if (c->n_lists != p->n) return LP_ERR_STATE;
+    for (int f = 0; f < nfields; ++f)
+        if (!fields[f]) return LP_ERR_ARG;
+    int64_t n = p->n;
+    if (n == 0) return LP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dim = c->dc.dim;
+    bool fp32 = c->dc.precision == LP_PREC_FP32;
+    for (int f0 = 0; f0 < nfields;) {
+        int F = (dim == 3 && nfields - f0 == 1) ? 1 : 5;
+        int real = nfields - f0 < F ? nfields - f0 : F;
+        FitArgs a;
+        fill_fit_args(c, a, n);
+        for (int q = 0; q < 5; ++q) a.fd[q] = fields[f0 + (q < real ? q : 0)];
+        DerivOut o;
+        o.out = derivs;
+        o.out_f64 = out_dtype == LP_OUT_F64;
+        o.f_first = f0;
+        o.f_real = real;
+        o.status = status;
+        if (fp32) {
+            {
+                Phase ph(c, LP_PH_GATHER, 1, s);
+                k_split_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+                    n, real, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->hf[0], c->hf[1], c->hf[2], c->hf[3],
+                    c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4]);
+            }
+            for (int q = real; q < 5; ++q) { a.fh[q] = c->hf[0]; a.fl[q] = c->lf[0]; }
+            LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
+            {
+                Phase ph(c, LP_PH_FIT, 1, s);
+                LP_CUDA(launch_derivs_f32(dim, F, a, o, s));
+            }
+            a.list = c->redo_list;
+            Phase ph(c, LP_PH_FIT64, 1, s);
+            LP_CUDA(launch_derivs_f64(dim, F, a, o, s));
+        } else {
+            Phase ph(c, LP_PH_FIT64, 1, s);
+            LP_CUDA(launch_derivs_f64(dim, F, a, o, s));
+        }
+        f0 += real;
+    }
+    // the neighbour lists stay valid; the split copies of the state are
+    // rebuilt by the next lp_step
+    return LP_OK;
+}
+
+lp_status lp_onesided_derivs(lp_ctx* c, const lp_particles* p, const double* const* fields, int32_t nfields,
+                             double* derivs, lp_stream stream)
+{
+    if (!c || !p || !fields || !derivs || nfields < 1 || nfields > 5) return LP_ERR_ARG;
+    if (c->n_lists != p->n) return LP_ERR_STATE;
+    for (int f = 0; f < nfields; ++f)
+        if (!fields[f]) return LP_ERR_ARG;
+    int64_t n = p->n;
+    if (n == 0) return LP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dim = c->dc.dim;
+    FitArgs a;
+    fill_fit_args(c, a, n);
+    for (int q = 0; q < 5; ++q) a.fd[q] = fields[q < nfields ? q : 0];
+    if (c->dc.precision == LP_PREC_FP32) {
+        {
+            Phase ph(c, LP_PH_GATHER, 1, s);
+            k_split_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+                n, nfields, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->hf[0], c->hf[1], c->hf[2], c->hf[3],
+                c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4]);
+        }
+        for (int q = nfields; q < 5; ++q) { a.fh[q] = c->hf[0]; a.fl[q] = c->lf[0]; }
+        LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
+        {
+            Phase ph(c, LP_PH_FIT, 1, s);
+            LP_CUDA(launch_onesided_f32(dim, a, derivs, nfields, s));
+        }
+        a.list = c->redo_list;
+        Phase ph(c, LP_PH_FIT64, 1, s);
+        LP_CUDA(launch_onesided_f64(dim, a, derivs, nfields, s));
+    } else {
+        Phase ph(c, LP_PH_FIT64, 1, s);
+        LP_CUDA(launch_onesided_f64(dim, a, derivs, nfields, s));
+    }
+    return LP_OK;
+}
+
+lp_status lp_step(lp_ctx* c, lp_particles* p, double dt, double cfl, double* t, const lp_step_diag* diag,
+                  lp_stream stream)
+{
+    if (!c) return LP_ERR_ARG;
+    lp_status st = check_particles(c, p);
+    if (st != LP_OK) return st;
+    if (!(dt > 0.0) && !(cfl > 0.0)) return LP_ERR_ARG;
+    if (isnan(dt) || isinf(dt)) return LP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = build(c, p, s);
+    if (st != LP_OK) return st;
+    int64_t n = p->n;
+    {
+        Phase ph(c, LP_PH_CFL, (dt <= 0.0 && n > 0) ? 2 : 1, s);
+        LP_CUDA(run_cfl(c, n, cfl, dt, t, s));
+    }
+    if (n == 0) return LP_OK;
+    int dim = c->dc.dim;
+    FitArgs a;
+    fill_fit_args(c, a, n);
+    a.fd[0] = c->sV;
+    for (int k = 0; k < dim; ++k) a.fd[1 + k] = c->su[k];
+    a.fd[dim + 1] = c->sP;
+    for (int q = dim + 2; q < 5; ++q) a.fd[q] = c->sV;
+    StepOut o;
+    memset(&o, 0, sizeof(o));
+    for (int k = 0; k < 3; ++k) {
+        o.x[k] = p->x[k < dim ? k : 0];
+        o.u[k] = p->u[k < dim ? k : 0];
+    }
+    o.V = p->V; o.P = p->P; o.m = p->m; o.id = p->id;
+    if (diag) { o.flag = diag->flag; o.phi = diag->phi; o.r = diag->r; }
+    o.dt = c->dt_dev;
+    if (c->dc.precision == LP_PREC_FP32) {
+        LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
+        {
+            Phase ph(c, LP_PH_FIT, 1, s);
+            LP_CUDA(launch_step_f32(dim, a, o, s));
+        }
+        a.list = c->redo_list;
+        Phase ph(c, LP_PH_FIT64, 1, s);
+        LP_CUDA(launch_step_f64(dim, a, o, s));
+    } else {
+        Phase ph(c, LP_PH_FIT64, 1, s);
+        LP_CUDA(launch_step_f64(dim, a, o, s));
+    }
+    return LP_OK;
+}
+
+lp_status lp_export_neighbors(lp_ctx* c, uint32_t* count, uint32_t* total, uint32_t* idx, double* d2min,
+                              uint64_t* keys, lp_stream stream)
+{
+    if (!c) return LP_ERR_ARG;
+    int64_t n = c->n_lists;
+    if (n == 0) return LP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (count) LP_CUDA(cudaMemcpyAsync(count, c->nb_count, n * 4, cudaMemcpyDeviceToDevice, s));
+    if (total) LP_CUDA(cudaMemcpyAsync(total, c->nb_total, n * 4, cudaMemcpyDeviceToDevice, s));
+    if (idx) LP_CUDA(cudaMemcpyAsync(idx, c->nb_idx, (size_t)n * c->dc.k_max * 4, cudaMemcpyDeviceToDevice, s));
+    if (d2min) LP_CUDA(cudaMemcpyAsync(d2min, c->nb_d2min, n * 8, cudaMemcpyDeviceToDevice, s));
+    if (keys) LP_CUDA(cudaMemcpyAsync(keys, c->keys_sorted, n * 8, cudaMemcpyDeviceToDevice, s));
+    return LP_OK;
+}
+
+lp_status lp_grid_info(lp_ctx* c, double* out, lp_stream stream)
+{
+    if (!c || !out) return LP_ERR_ARG;
+    Grid g;
+    cudaStream_t s = (cudaStream_t)stream;
+    LP_CUDA(cudaMemcpyAsync(&g, c->grid, sizeof(Grid), cudaMemcpyDeviceToHost, s));
+    LP_CUDA(cudaStreamSynchronize(s));
+    out[0] = g.lo[0]; out[1] = g.lo[1]; out[2] = g.lo[2]; out[3] = g.L; out[4] = (double)g.lmax;
+    return LP_OK;
+}
+
+lp_status lp_set_profiling(lp_ctx* c, int32_t on)
+{
+    if (!c) return LP_ERR_ARG;
+    c->profiling = on ? 1 : 0;
+    return LP_OK;
+}
+
+lp_status lp_phase_times(lp_ctx* c, double* out_ms, int64_t* out_launches, lp_stream stream)
+{
+    if (!c) return LP_ERR_ARG;
+    LP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    LP_CUDA(flush_events(c));
+    for (int q = 0; q < LP_NPHASES; ++q) {
+        if (out_ms) out_ms[q] = c->phase_ms[q];
+        if (out_launches) out_launches[q] = c->phase_launches[q];
+        c->phase_ms[q] = 0.0;
+        c->phase_launches[q] = 0;
+    }
+    return LP_OK;
+}
+
+const char* lp_phase_name(int32_t ph)
+{
+    static const char* names[LP_NPHASES] = {"grid+keys", "radix-sort", "gather", "cell-tables",
+                                            "neighbor-query", "cfl", "fit+update", "fit+update-fp64"};
+    return (ph >= 0 && ph < LP_NPHASES) ? names[ph] : "unknown";
+}
+
+const double* lp_dt_device(lp_ctx* c) { return c ? c->dt_dev : nullptr; }
+
+lp_status lp_get_stats(lp_ctx* c, lp_stats* out, lp_stream stream)
+{
+    if (!c || !out) return LP_ERR_ARG;
+    unsigned long long h[C_COUNT];
+    double dt = 0.0;
+    cudaStream_t s = (cudaStream_t)stream;
+    LP_CUDA(cudaMemcpyAsync(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+    LP_CUDA(cudaMemcpyAsync(&dt, c->dt_dev, 8, cudaMemcpyDeviceToHost, s));
+    LP_CUDA(cudaStreamSynchronize(s));
+    memset(out, 0, sizeof(*out));
+    out->dt = dt;
+    out->steps = (int64_t)h[C_STEPS];
+    out->n_flagged = (int64_t)h[C_FLAGGED];
+    out->n_fp64_redo = (int64_t)h[C_FP64];
+    out->n_linear = (int64_t)h[C_LINEAR];
+    out->n_nofit = (int64_t)h[C_NOFIT];
+    out->n_overflow = (int64_t)h[C_OVERFLOW];
+    out->n_nonfinite = (int64_t)h[C_NONFINITE];
+    out->n_mlp_uncertain = (int64_t)h[C_MLP_UNCERTAIN];
+    out->max_count = (uint32_t)h[C_MAXCOUNT];
+    out->status = (uint32_t)h[C_STATUS];
+    out->kernel_launches = c->launches;
+    return LP_OK;
+}
+
+lp_status lp_reset_stats(lp_ctx* c, lp_stream stream)
+{
+    if (!c) return LP_ERR_ARG;
+    LP_CUDA(cudaMemsetAsync(c->counters, 0, C_COUNT * 8, (cudaStream_t)stream));
+    return LP_OK;
+}
+
+}  // extern "C"

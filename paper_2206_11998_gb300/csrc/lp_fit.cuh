@@ -1,0 +1,461 @@
+// lp_fit.cuh -- GFD least-squares fits and the LP update (Sec. 2.1), as
+// templates instantiated for FP32 (lp_fit_f32.cu) and FP64 (lp_fit_f64.cu).
+//
+// Schedule: one thread per particle.  The overdetermined GFD system of
+// Eq. linear_system_axb (and its 1D/3D analogues) is reduced to triangular form
+// by Givens rotations applied row by row as the neighbours stream in, so the
+// 9-column R, Q^T b for all fields and the running row live in registers; no
+// stencil is staged and no lane idles.  Columns are scaled by powers of two
+// (exact) so R is well scaled; min|R_kk|/max|R_kk| decides the FP64 redo (FP32)
+// or the first-order fallback (FP64).  The FP32 path forms offsets and field
+// differences from split (hi, lo) floats, accurate to a few ulp of the offset
+// itself.
+#pragma once
+
+#include "lp_internal.cuh"
+
+namespace lp {
+
+template <int DIM> struct NU { static constexpr int v = DIM == 1 ? 2 : (DIM == 2 ? 5 : 9); };
+
+template <typename T> __device__ inline T rsqrt_t(T x);
+template <> __device__ inline float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+// ---------------------------------------------------------------------------
+// row-by-row Givens least squares:  min || A x - B ||, A: rows x N, B: rows x F
+// ---------------------------------------------------------------------------
+template <typename T, int N, int F>
+struct Givens {
+    T R[N * (N + 1) / 2];
+    T Z[N][F];
+
+    __device__ static constexpr int id(int k, int l) { return k * N - (k * (k - 1)) / 2 + (l - k); }
+
+    __device__ void zero()
+    {
+#pragma unroll
+        for (int q = 0; q < N * (N + 1) / 2; ++q) R[q] = T(0);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+#pragma unroll
+            for (int f = 0; f < F; ++f) Z[k][f] = T(0);
+    }
+
+    __device__ void add(T (&a)[N], T (&b)[F])
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            T ak = a[k];
+            if (ak != T(0)) {
+                T rkk = R[id(k, k)];
+                T h2 = rkk * rkk + ak * ak;
+                T inv = rsqrt_t<T>(h2);
+                T cc = rkk * inv, ss = ak * inv;
+                R[id(k, k)] = h2 * inv;
+#pragma unroll
+                for (int l = k + 1; l < N; ++l) {
+                    T t = R[id(k, l)];
+                    R[id(k, l)] = cc * t + ss * a[l];
+                    a[l] = cc * a[l] - ss * t;
+                }
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    T t = Z[k][f];
+                    Z[k][f] = cc * t + ss * b[f];
+                    b[f] = cc * b[f] - ss * t;
+                }
+            }
+        }
+    }
+
+    __device__ T ratio() const
+    {
+        T lo = fabs(R[id(0, 0)]), hi = lo;
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+            T d = fabs(R[id(k, k)]);
+            lo = d < lo ? d : lo;
+            hi = d > hi ? d : hi;
+        }
+        return hi > T(0) ? lo / hi : T(0);
+    }
+
+    // x = R^{-1} Z
+    __device__ void solve(T (&x)[N][F]) const
+    {
+#pragma unroll
+        for (int k = N - 1; k >= 0; --k) {
+            T inv = T(1) / R[id(k, k)];
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                T s = Z[k][f];
+#pragma unroll
+                for (int l = k + 1; l < N; ++l) s -= R[id(k, l)] * x[l][f];
+                x[k][f] = s * inv;
+            }
+        }
+    }
+
+    // d = (R^T R)^{-1} g  (one correction step of the semi-normal equations)
+    __device__ void solve_normal(T (&g)[N][F]) const
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            T inv = T(1) / R[id(k, k)];
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                T s = g[k][f];
+#pragma unroll
+                for (int l = 0; l < k; ++l) s -= R[id(l, k)] * g[l][f];
+                g[k][f] = s * inv;
+            }
+        }
+#pragma unroll
+        for (int k = N - 1; k >= 0; --k) {
+            T inv = T(1) / R[id(k, k)];
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                T s = g[k][f];
+#pragma unroll
+                for (int l = k + 1; l < N; ++l) s -= R[id(k, l)] * g[l][f];
+                g[k][f] = s * inv;
+            }
+        }
+    }
+};
+
+// GFD row for scaled offset e (Eq. linear_system_axb order, 1D/3D analogues)
+template <typename T, int DIM>
+__device__ inline void gfd_row(const T (&e)[DIM], T (&a)[NU<DIM>::v])
+{
+    if (DIM == 1) {
+        a[0] = e[0];
+        a[1] = T(0.5) * e[0] * e[0];
+    } else if (DIM == 2) {
+        a[0] = e[0]; a[1] = e[1];
+        a[2] = T(0.5) * e[0] * e[0]; a[3] = T(0.5) * e[1] * e[1];
+        a[4] = e[0] * e[1];
+    } else {
+        a[0] = e[0]; a[1] = e[1]; a[2] = e[DIM > 2 ? 2 : 0];
+        a[3] = T(0.5) * e[0] * e[0]; a[4] = T(0.5) * e[1] * e[1];
+        a[5] = T(0.5) * e[DIM > 2 ? 2 : 0] * e[DIM > 2 ? 2 : 0];
+        a[6] = e[0] * e[1]; a[7] = e[0] * e[DIM > 2 ? 2 : 0]; a[8] = e[1] * e[DIM > 2 ? 2 : 0];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// neighbour data sources
+// ---------------------------------------------------------------------------
+struct FitArgs {
+    DevCfg c;
+    int64_t n;
+    int nf;
+    const uint32_t* count;
+    const uint32_t* idx;
+    const double* d2min;
+    const double* sx[3];
+    const float* hx[3];
+    const float* lx[3];
+    const double* fd[5];      // field values (FP64)
+    const float* fh[5];       // field hi/lo split
+    const float* fl[5];
+    const uint32_t* sid;
+    const double* sm;
+    unsigned long long* counters;
+    uint32_t* redo_list;      // FP32 pass: particles to redo in FP64
+    const uint32_t* list;     // FP64 pass over a list (null: all particles)
+    const unsigned long long* list_len;
+};
+
+template <typename T, int DIM, int F> struct Src;
+
+// FP32: offsets and differences from split hi/lo floats
+template <int DIM, int F>
+struct Src<float, DIM, F> {
+    const FitArgs& a;
+    int64_t i;
+    float hxi[DIM], lxi[DIM], hfi[F], lfi[F];
+    __device__ Src(const FitArgs& a_, int64_t i_) : a(a_), i(i_)
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { hxi[k] = a.hx[k][i]; lxi[k] = a.lx[k][i]; }
+#pragma unroll
+        for (int f = 0; f < F; ++f) { hfi[f] = a.fh[f][i]; lfi[f] = a.fl[f][i]; }
+    }
+    __device__ void off(uint32_t j, float (&d)[DIM]) const
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            float dh = a.hx[k][j] - hxi[k];
+            float dl = a.lx[k][j] - lxi[k];
+            if (a.c.periodic[k]) {
+                if (dh > 0.5f * a.c.Lper_h[k]) { dh -= a.c.Lper_h[k]; dl -= a.c.Lper_l[k]; }
+                else if (dh < -0.5f * a.c.Lper_h[k]) { dh += a.c.Lper_h[k]; dl += a.c.Lper_l[k]; }
+            }
+            d[k] = dh + dl;
+        }
+    }
+    __device__ void diff(uint32_t j, float (&b)[F]) const
+    {
+#pragma unroll
+        for (int f = 0; f < F; ++f) b[f] = (a.fh[f][j] - hfi[f]) + (a.fl[f][j] - lfi[f]);
+    }
+    // exact sign of the offset x_jk - x_ik (the oracle's definition)
+    __device__ int side(uint32_t j, int k) const
+    {
+        if (!a.c.periodic[k]) {
+            float hj = a.hx[k][j];
+            if (hj != hxi[k]) return hj > hxi[k] ? 1 : -1;
+            float lj = a.lx[k][j];
+            if (lj != lxi[k]) return lj > lxi[k] ? 1 : -1;
+        }
+        double d = offset64(a.c, k, a.sx[k][i], a.sx[k][j]);
+        return d > 0.0 ? 1 : (d < 0.0 ? -1 : 0);
+    }
+};
+
+// FP64: offsets and differences in FP64 (the oracle's operation order)
+template <int DIM, int F>
+struct Src<double, DIM, F> {
+    const FitArgs& a;
+    int64_t i;
+    double xi[DIM], fi[F];
+    __device__ Src(const FitArgs& a_, int64_t i_) : a(a_), i(i_)
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) xi[k] = a.sx[k][i];
+#pragma unroll
+        for (int f = 0; f < F; ++f) fi[f] = a.fd[f][i];
+    }
+    __device__ void off(uint32_t j, double (&d)[DIM]) const
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) d[k] = offset64(a.c, k, xi[k], a.sx[k][j]);
+    }
+    __device__ void diff(uint32_t j, double (&b)[F]) const
+    {
+#pragma unroll
+        for (int f = 0; f < F; ++f) b[f] = a.fd[f][j] - fi[f];
+    }
+    __device__ int side(uint32_t j, int k) const
+    {
+        double d = offset64(a.c, k, xi[k], a.sx[k][j]);
+        return d > 0.0 ? 1 : (d < 0.0 ? -1 : 0);
+    }
+};
+
+// power-of-two 1/S with S >= sqrt(d2)
+__device__ inline float inv_scale(float d2)
+{
+    if (!(d2 > 0.0f) || !isfinite(d2)) return 1.0f;
+    int e = (int)ceilf(0.5f * log2f(d2));
+    return ldexpf(1.0f, -e);
+}
+
+// Central second-order fit.  x[u][f] unscaled derivatives.  Returns 0 ok,
+// 1 ill-conditioned (ratio below tau), with x untouched.
+template <typename T, int DIM, int F>
+__device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau,
+                           bool refine, T (&x)[NU<DIM>::v][F])
+{
+    constexpr int N = NU<DIM>::v;
+    Givens<T, N, F> G;
+    G.zero();
+    for (int r = 0; r < cnt; ++r) {
+        uint32_t j = nb[r];
+        T d[DIM], a[N], b[F];
+        src.off(j, d);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) d[k] *= invS;
+        gfd_row<T, DIM>(d, a);
+        src.diff(j, b);
+        G.add(a, b);
+    }
+    if (!(G.ratio() >= tau) || cnt < N) return 1;
+    G.solve(x);
+    if (refine) {
+        T g[N][F];
+#pragma unroll
+        for (int u = 0; u < N; ++u)
+#pragma unroll
+            for (int f = 0; f < F; ++f) g[u][f] = T(0);
+        for (int r = 0; r < cnt; ++r) {
+            uint32_t j = nb[r];
+            T d[DIM], a[N], b[F];
+            src.off(j, d);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) d[k] *= invS;
+            gfd_row<T, DIM>(d, a);
+            src.diff(j, b);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                T res = b[f];
+#pragma unroll
+                for (int u = 0; u < N; ++u) res -= a[u] * x[u][f];
+#pragma unroll
+                for (int u = 0; u < N; ++u) g[u][f] += a[u] * res;
+            }
+        }
+        G.solve_normal(g);
+#pragma unroll
+        for (int u = 0; u < N; ++u)
+#pragma unroll
+            for (int f = 0; f < F; ++f) x[u][f] += g[u][f];
+    }
+    T s2 = invS * invS;
+#pragma unroll
+    for (int u = 0; u < N; ++u)
+#pragma unroll
+        for (int f = 0; f < F; ++f) x[u][f] *= (u < DIM ? invS : s2);
+    return 0;
+}
+
+// First-order fit on the whole list (fallback).  Returns 0 ok, 1 rank deficient.
+template <typename T, int DIM, int F>
+__device__ int linear_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau, T (&x)[DIM][F])
+{
+    Givens<T, DIM, F> G;
+    G.zero();
+    for (int r = 0; r < cnt; ++r) {
+        uint32_t j = nb[r];
+        T d[DIM], b[F];
+        src.off(j, d);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) d[k] *= invS;
+        src.diff(j, b);
+        G.add(d, b);
+    }
+    if (!(G.ratio() >= tau) || cnt < DIM) return 1;
+    G.solve(x);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+#pragma unroll
+        for (int f = 0; f < F; ++f) x[k][f] *= invS;
+    return 0;
+}
+
+// One-sided first derivatives along axis k (Sec. 2.1 left/right derivatives):
+// first k_side list members on each side, first-order fit, component k.
+// ok[s] = false where fewer than DIM members or rank deficient.  ill = true when
+// a system with enough members is below tau (FP32: redo in FP64).
+template <typename T, int DIM, int F>
+__device__ void onesided_axis(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, int k, int ks, T invS,
+                              T tau, T tau_rank, T (&out)[2][F], bool (&ok)[2], bool& ill)
+{
+    Givens<T, DIM, F> G[2];
+    G[0].zero();
+    G[1].zero();
+    int ns[2] = {0, 0};
+    for (int r = 0; r < cnt && (ns[0] < ks || ns[1] < ks); ++r) {
+        uint32_t j = nb[r];
+        int sg = src.side(j, k);
+        if (sg == 0) continue;
+        int s = sg > 0 ? 1 : 0;
+        if (ns[s] >= ks) continue;
+        T d[DIM], b[F];
+        src.off(j, d);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) d[q] *= invS;
+        src.diff(j, b);
+        if (s) G[1].add(d, b); else G[0].add(d, b);
+        ++ns[s];
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        ok[s] = false;
+        if (ns[s] < DIM) continue;
+        T rt = G[s].ratio();
+        if (!(rt >= tau_rank)) continue;              // rank deficient: central derivative
+        if (!(rt >= tau)) ill = true;                 // usable only in higher precision
+        T x[DIM][F];
+        G[s].solve(x);
+#pragma unroll
+        for (int f = 0; f < F; ++f) out[s][f] = x[k][f] * invS;
+        ok[s] = true;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// estimator, limiter, rates (Sec. 2.1)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline T phi_limiter(T r)
+{
+    if (isinf(r)) return T(0);
+    T sr = sqrt(r);
+    if (r <= T(1.5)) return T(1.25) * exp(T(1) - sr);
+    T q = sr - T(1);
+    return T(1.25) * exp(T(-4.5) * q * q);
+}
+
+template <typename T, int DIM>
+__device__ inline T estimator_r(const T (&sl)[DIM], const T (&sr)[DIM], T ell, T s_i, T s_ref, T flat_eps,
+                                T active_frac)
+{
+    T G = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        T g = fmax(fabs(sl[k]), fabs(sr[k]));
+        G = g > G ? g : G;
+    }
+    T S = fmax(fabs(s_i), s_ref);
+    if (G * ell <= flat_eps * S) return T(1);
+    T r = T(1);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        T g = fmax(fabs(sl[k]), fabs(sr[k]));
+        if (g < active_frac * G) continue;
+        T rk;
+        if (sl[k] * sr[k] <= T(0)) rk = T(INFINITY);
+        else rk = T(0.5) * (sr[k] / sl[k] + sl[k] / sr[k]);
+        r = rk > r ? rk : r;
+    }
+    return r;
+}
+
+// slot of d_c d_a in the second-order unknown ordering
+template <int DIM>
+__device__ constexpr int hess_slot(int c, int a)
+{
+    return c == a ? DIM + a : (DIM == 2 ? 4 : ((c < a ? c : a) == 0 ? ((c < a ? a : c) == 1 ? 6 : 7) : 8));
+}
+
+// Lax-Wendroff rates LW_s = s_t + dt/2 s_tt for an ideal gas (see the oracle
+// for the derivation from V_t = V div u, u_t = -V grad P, P_t = -gamma P div u).
+// cd[u][f] central derivatives, fields V, u_1..u_d, P.
+template <typename T, int DIM>
+__device__ inline void lw_rates(T gamma, T dt, T V, T P, const T (&cd)[NU<DIM>::v][DIM + 2], T (&lw)[DIM + 2])
+{
+    constexpr int FP = DIM + 1;
+    T divu = T(0), S2 = T(0), gVgP = T(0), lapP = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) divu += cd[a][1 + a];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) S2 += cd[b][1 + a] * cd[a][1 + b];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) gVgP += cd[k][0] * cd[k][FP];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) lapP += cd[DIM + k][FP];
+    T Vt = V * divu;
+    T Vtt = V * divu * divu - V * S2 - V * gVgP - V * V * lapP;
+    lw[0] = Vt + T(0.5) * dt * Vtt;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        T uPt = T(0), gdiv = T(0);
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) uPt += cd[i][1 + m] * cd[m][FP];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) gdiv += cd[hess_slot<DIM>(i, a)][1 + a];
+        T ut = -V * cd[i][FP];
+        T utt = (gamma - T(1)) * V * divu * cd[i][FP] + V * uPt + gamma * V * P * gdiv;
+        lw[1 + i] = ut + T(0.5) * dt * utt;
+    }
+    T Pt = -gamma * P * divu;
+    T Ptt = gamma * gamma * P * divu * divu + gamma * P * S2 + gamma * P * (gVgP + V * lapP);
+    lw[FP] = Pt + T(0.5) * dt * Ptt;
+}
+
+}  // namespace lp

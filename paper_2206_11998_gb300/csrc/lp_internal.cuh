@@ -1,0 +1,221 @@
+// lp_internal.cuh -- device-side building blocks shared by the liblp.so
+// translation units (never by the oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lp.h"
+
+namespace lp {
+
+constexpr int KMAX = 64;          // neighbour capacity compiled into the kernels
+constexpr int MORTON_BITS = 21;   // bits per axis of a Morton key (2D and 3D)
+constexpr int MAX_LEVELS = 22;    // cell levels 0..21
+constexpr int NB_WARPS = 8;       // warps per block of the neighbour query
+constexpr int NB_CAP = 2 * KMAX;  // candidate buffer per warp
+
+// status bits kept in the device status word (1 << lp_status)
+constexpr uint32_t ST_CAPACITY = 1u << LP_ERR_CAPACITY;
+constexpr uint32_t ST_ILLCOND = 1u << LP_ERR_ILLCOND;
+constexpr uint32_t ST_NONFINITE = 1u << LP_ERR_NONFINITE;
+constexpr uint32_t ST_ARG = 1u << LP_ERR_ARG;
+
+// per-particle fit flags (lp_gfd_derivs status output)
+constexpr uint32_t FIT_LINEAR = 1u, FIT_NONE = 2u, FIT_FP64 = 8u;
+
+// device counters (unsigned long long each)
+enum Counter {
+    C_FLAGGED = 0, C_FP64, C_LINEAR, C_NOFIT, C_OVERFLOW, C_NONFINITE, C_MLP_UNCERTAIN,
+    C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_COUNT
+};
+
+// method constants as the kernels see them
+struct DevCfg {
+    int dim, precision, radius_mode, k_max, k_side, k_per_side, limiter, estimator, refine;
+    int periodic[3];
+    double gamma, radius, kappa, flat_eps, active_frac, tau32, tau64;
+    double s_ref[5];
+    double box_lo[3], box_hi[3];
+    double Lper[3];       // box_hi - box_lo on periodic axes
+    float Lper_h[3], Lper_l[3];
+    int64_t n_fluid;
+};
+
+// grid parameters computed on the device every build
+struct Grid {
+    double lo[3];         // quantisation origin
+    double L;             // cube edge
+    double inv;           // 2^MORTON_BITS / L
+    int lmin, lmax;       // cell levels in use
+    int pad[2];
+};
+
+// ---------------------------------------------------------------------------
+// Morton helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__host__ __device__ inline uint64_t spread2(uint64_t v)
+{
+    v &= 0xffffffffull;
+    v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+    v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+    v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+template <int DIM>
+__host__ __device__ inline uint64_t morton(const uint32_t* q)
+{
+    if (DIM == 3) return spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+    if (DIM == 2) return spread2(q[0]) | (spread2(q[1]) << 1);
+    return q[0];
+}
+
+// total order of doubles as unsigned integers (-0 is mapped to +0)
+__device__ inline uint64_t order_key(double x)
+{
+    if (x == 0.0) x = 0.0;
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// ---------------------------------------------------------------------------
+// exact FP64 geometry, fixed operation order (no contraction)
+// ---------------------------------------------------------------------------
+__device__ inline double offset64(const DevCfg& c, int k, double xi, double xj)
+{
+    double dx = __dsub_rn(xj, xi);
+    if (c.periodic[k]) {
+        double L = c.Lper[k];
+        double h = __dmul_rn(0.5, L);
+        if (dx > h) dx = __dsub_rn(dx, L);
+        else if (dx < -h) dx = __dadd_rn(dx, L);
+    }
+    return dx;
+}
+
+// neighbour membership for squared distance d2 and w = m_i V_i
+__device__ inline bool inside64(const DevCfg& c, int dim, double d2, double w)
+{
+    if (c.radius_mode == LP_RADIUS_FIXED) {
+        double R2 = __dmul_rn(c.radius, c.radius);
+        return d2 <= R2;
+    }
+    double k2 = __dmul_rn(c.kappa, c.kappa);
+    double ww = __dmul_rn(w, w);
+    if (dim == 3) {
+        double k6 = __dmul_rn(__dmul_rn(k2, k2), k2);
+        return __dmul_rn(__dmul_rn(d2, d2), d2) <= __dmul_rn(k6, ww);
+    }
+    if (dim == 2) {
+        double k4 = __dmul_rn(k2, k2);
+        return __dmul_rn(d2, d2) <= __dmul_rn(k4, ww);
+    }
+    return d2 <= __dmul_rn(k2, ww);
+}
+
+// split a double into float hi + float lo (x ~ hi + lo)
+__device__ inline void split(double x, float& h, float& l)
+{
+    h = __double2float_rn(x);
+    l = __double2float_rn(__dsub_rn(x, (double)h));
+}
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+__device__ inline unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ inline void count_add(unsigned long long* ctr, int which, unsigned long long v)
+{
+    if (v) atomicAdd(ctr + which, v);
+}
+
+}  // namespace lp
+
+// ---------------------------------------------------------------------------
+// context (host-side object, device buffers)
+// ---------------------------------------------------------------------------
+struct lp_ctx {
+    lp_config cfg;
+    lp::DevCfg dc;
+    int64_t cap;
+    int device;
+    int lmax_cap;             // finest level a table is allocated for
+    int sort_lo_bit, sort_hi_bit;
+    int64_t level_off[lp::MAX_LEVELS + 1];
+    int64_t table_entries;
+    // sort
+    uint64_t* keys[2];
+    uint32_t* vals[2];
+    uint32_t* hist;           // [256][max_blocks]
+    int64_t hist_blocks;
+    // sorted copies of the state
+    double* sx[3];
+    double* sV;
+    double* su[3];
+    double* sP;
+    double* sm;
+    uint32_t* sid;
+    float* hx[3];
+    float* lx[3];
+    float* hf[5];
+    float* lf[5];
+    // cell tables, neighbour lists
+    unsigned long long* cells;
+    uint32_t* nb_count;
+    uint32_t* nb_total;
+    uint32_t* nb_idx;
+    double* nb_d2min;
+    uint64_t* keys_sorted;    // points at keys[0] or keys[1] after the sort
+    uint32_t* perm_sorted;    // matching permutation (sorted position -> input index)
+    // grid, time step, counters
+    lp::Grid* grid;
+    double* dt_dev;
+    unsigned long long* dt_min;   // bit pattern of min(d2 / c^2)
+    unsigned long long* counters;
+    uint32_t* redo_list;
+    int64_t n_lists;          // n of the last neighbour build (0: none)
+    int tables_dirty;         // tables hold entries of the last build
+    double reduce_min_w;
+    // launch accounting and optional phase timing
+    int64_t launches;
+    int profiling;
+    cudaEvent_t ev[2 * LP_NPHASES * 4];
+    int ev_used;                      // events recorded since the last read
+    int ev_phase[LP_NPHASES * 4];
+    double phase_ms[LP_NPHASES];
+    int64_t phase_launches[LP_NPHASES];
+};
+
+namespace lp {
+// launchers implemented in the .cu files
+cudaError_t build_grid(lp_ctx* c, const lp_particles* p, cudaStream_t s);
+cudaError_t make_keys(lp_ctx* c, const lp_particles* p, cudaStream_t s);
+int radix_passes(const lp_ctx* c);
+cudaError_t radix_sort(lp_ctx* c, int64_t n, cudaStream_t s);
+cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s);
+cudaError_t fill_tables(lp_ctx* c, int64_t n, bool clear, cudaStream_t s);
+cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s);
+cudaError_t scatter_back(lp_ctx* c, lp_particles* p, cudaStream_t s);
+cudaError_t split_fields(lp_ctx* c, int64_t n, const double* const* f, int nf, cudaStream_t s);
+cudaError_t run_derivs(lp_ctx* c, int64_t n, const double* const* f, int nf, int out_dtype,
+                       void* out, uint32_t* status, cudaStream_t s);
+cudaError_t run_onesided(lp_ctx* c, int64_t n, const double* const* f, int nf, double* out,
+                         cudaStream_t s);
+cudaError_t run_cfl(lp_ctx* c, int64_t n, double cfl, double dt_fixed, double* t, cudaStream_t s);
+cudaError_t run_step(lp_ctx* c, lp_particles* p, const lp_step_diag* diag, cudaStream_t s);
+}  // namespace lp

@@ -1,0 +1,383 @@
+// lp_sort.cu -- Sec. 2.2 steps 2-3 on the GPU: bounding cube, Morton (Z-curve)
+// keys, LSD radix sort, gather of the state into key order, and the per-level
+// cell tables that stand in for the paper's octree.
+#include "lp_internal.cuh"
+
+namespace lp {
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+__device__ inline void atomic_min_d(unsigned long long* a, double v) { atomicMin(a, (unsigned long long)order_key(v)); }
+__device__ inline void atomic_max_d(unsigned long long* a, double v) { atomicMax(a, (unsigned long long)order_key(v)); }
+
+__device__ inline double from_order_key(unsigned long long k)
+{
+    uint64_t b = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// ext[0..2] min x_k, ext[3..5] max x_k, ext[6] min w, ext[7] max w (order keys)
+__global__ void k_reduce_extent(int dim, int64_t n, const double* __restrict__ x0,
+                                const double* __restrict__ x1, const double* __restrict__ x2,
+                                const double* __restrict__ m, const double* __restrict__ V,
+                                unsigned long long* ext)
+{
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double wlo = INFINITY, whi = -INFINITY;
+    const double* xs[3] = {x0, x1, x2};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < dim; ++k) {
+            double v = xs[k][i];
+            lo[k] = fmin(lo[k], v);
+            hi[k] = fmax(hi[k], v);
+        }
+        double w = __dmul_rn(m[i], V[i]);
+        wlo = fmin(wlo, w);
+        whi = fmax(whi, w);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+        wlo = fmin(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
+        whi = fmax(whi, __shfl_xor_sync(0xffffffffu, whi, o));
+    }
+    if (lane_id() == 0) {
+        for (int k = 0; k < dim; ++k) {
+            atomic_min_d(ext + k, lo[k]);
+            atomic_max_d(ext + 3 + k, hi[k]);
+        }
+        atomic_min_d(ext + 6, wlo);
+        atomic_max_d(ext + 7, whi);
+    }
+}
+
+__global__ void k_init_extent(unsigned long long* ext)
+{
+    int t = threadIdx.x;
+    if (t < 8) ext[t] = (t < 3 || t == 6) ? ~0ull : 0ull;
+}
+
+// Bounding cube and the range of cell levels.  A particle of radius R queries
+// the finest level whose cell edge L / 2^l is at least R; lmax/lmin are those
+// levels for the smallest/largest radius present.
+__global__ void k_finalize_grid(DevCfg c, int lmax_cap, const unsigned long long* ext, Grid* g)
+{
+    double L = 0.0;
+    for (int k = 0; k < c.dim; ++k) {
+        double lo, ext_k;
+        if (c.periodic[k]) { lo = c.box_lo[k]; ext_k = c.Lper[k]; }
+        else { lo = from_order_key(ext[k]); ext_k = __dsub_rn(from_order_key(ext[3 + k]), lo); }
+        g->lo[k] = lo;
+        L = fmax(L, ext_k);
+    }
+    for (int k = c.dim; k < 3; ++k) g->lo[k] = 0.0;
+    if (!(L > 0.0)) L = 1.0;
+    g->L = L;
+    g->inv = __ddiv_rn(ldexp(1.0, MORTON_BITS), L);
+    double rmin, rmax;
+    if (c.radius_mode == LP_RADIUS_FIXED) { rmin = rmax = c.radius; }
+    else {
+        double wlo = from_order_key(ext[6]), whi = from_order_key(ext[7]);
+        rmin = c.kappa * pow(wlo, 1.0 / c.dim);
+        rmax = c.kappa * pow(whi, 1.0 / c.dim);
+    }
+    // margins wider than the per-particle float radius margin (1e-5) keep every
+    // particle's level inside [lmin, lmax]
+    rmin *= 1.0 - 1e-4;
+    rmax *= 1.0 + 1e-4;
+    int lmax = (int)floor(log2(L / rmin));
+    int lmin = (int)floor(log2(L / rmax));
+    lmax = max(0, min(lmax, lmax_cap));
+    lmin = max(0, min(lmin, lmax));
+    g->lmax = lmax;
+    g->lmin = lmin;
+}
+
+template <int DIM>
+__global__ void k_keys(int64_t n, const double* __restrict__ x0, const double* __restrict__ x1,
+                       const double* __restrict__ x2, const Grid* __restrict__ g,
+                       uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (DIM == 1) {
+        keys[i] = order_key(x0[i]);
+        vals[i] = (uint32_t)i;
+        return;
+    }
+    const double* xs[3] = {x0, x1, x2};
+    double inv = g->inv;
+    const double qmax = (double)((1u << MORTON_BITS) - 1u);
+    uint32_t q[3] = {0, 0, 0};
+    for (int k = 0; k < DIM; ++k) {
+        double t = __dmul_rn(__dsub_rn(xs[k][i], g->lo[k]), inv);
+        double f = floor(t);
+        uint32_t v;
+        if (!(f > 0.0)) v = 0;
+        else if (f >= qmax) v = (uint32_t)qmax;
+        else v = (uint32_t)f;
+        q[k] = v;
+    }
+    keys[i] = morton<DIM>(q);
+    vals[i] = (uint32_t)i;
+}
+
+// ---- LSD radix sort, 8-bit digits ----------------------------------------
+
+__global__ void k_rs_upsweep(int64_t n, const uint64_t* __restrict__ keys, int shift,
+                             uint32_t* __restrict__ counts, int64_t nblocks)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int64_t i = base + r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of counts[0..total) in one block of 1024 threads
+__global__ void k_rs_scan(uint32_t* counts, int64_t total)
+{
+    __shared__ uint32_t part[1024];
+    int t = threadIdx.x;
+    int64_t per = (total + 1023) / 1024;
+    int64_t b = t * per, e = min(total, b + per);
+    uint32_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += counts[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        uint32_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = t ? part[t - 1] : 0;
+    for (int64_t i = b; i < e; ++i) {
+        uint32_t c = counts[i];
+        counts[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+               uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
+               const uint32_t* __restrict__ counts, int64_t nblocks)
+{
+    __shared__ uint32_t off[256];
+    __shared__ uint32_t wc[RS_THREADS / 32][256];
+    int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    off[t] = counts[(int64_t)t * nblocks + blockIdx.x];
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        for (int d = lane; d < 256; d += 32) wc[w][d] = 0;
+        __syncthreads();
+        int64_t i = base + r * RS_THREADS + t;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0;
+        uint32_t val = valid ? vin[i] : 0;
+        uint32_t d = valid ? (uint32_t)((key >> shift) & 255u) : 256u + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && (__ffs(peers) - 1) == lane) wc[w][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = off[t];
+            for (int ww = 0; ww < RS_THREADS / 32; ++ww) {
+                uint32_t c = wc[ww][t];
+                wc[ww][t] = run;
+                run += c;
+            }
+            off[t] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = wc[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// gather the state into key order and split it into float hi/lo pairs
+template <int DIM>
+__global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_particles p,
+                         double* sx0, double* sx1, double* sx2, double* sV, double* su0, double* su1,
+                         double* su2, double* sP, double* sm, uint32_t* sid,
+                         float* hx0, float* hx1, float* hx2, float* lx0, float* lx1, float* lx2,
+                         float* hf0, float* hf1, float* hf2, float* hf3, float* hf4,
+                         float* lf0, float* lf1, float* lf2, float* lf3, float* lf4)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = perm[i];
+    double* sx[3] = {sx0, sx1, sx2};
+    double* su[3] = {su0, su1, su2};
+    float* hx[3] = {hx0, hx1, hx2};
+    float* lx[3] = {lx0, lx1, lx2};
+    float* hf[5] = {hf0, hf1, hf2, hf3, hf4};
+    float* lf[5] = {lf0, lf1, lf2, lf3, lf4};
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        double v = p.x[k][j];
+        sx[k][i] = v;
+        split(v, hx[k][i], lx[k][i]);
+    }
+    double V = p.V[j], P = p.P[j];
+    sV[i] = V;
+    sP[i] = P;
+    split(V, hf[0][i], lf[0][i]);
+    split(P, hf[DIM + 1][i], lf[DIM + 1][i]);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        double v = p.u[k][j];
+        su[k][i] = v;
+        split(v, hf[1 + k][i], lf[1 + k][i]);
+    }
+    sm[i] = p.m[j];
+    sid[i] = p.id[j];
+}
+
+// cell tables: entry = start | end << 32 of the key-sorted particles in the cell
+__global__ void k_tables(int dim, int64_t n, const uint64_t* __restrict__ keys, const Grid* __restrict__ g,
+                         const int64_t* __restrict__ level_off, unsigned long long* cells, int clear)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t k = keys[i];
+    uint64_t kp = i > 0 ? keys[i - 1] : 0;
+    uint64_t kn = i + 1 < n ? keys[i + 1] : 0;
+    uint32_t* half = reinterpret_cast<uint32_t*>(cells);
+    for (int l = g->lmin; l <= g->lmax; ++l) {
+        int sh = dim * (MORTON_BITS - l);
+        uint64_t c = k >> sh;
+        bool first = i == 0 || (kp >> sh) != c;
+        bool last = i + 1 == n || (kn >> sh) != c;
+        int64_t e = level_off[l] + (int64_t)c;
+        if (clear) {
+            if (first) cells[e] = 0ull;
+        } else {
+            if (first) half[2 * e] = (uint32_t)i;
+            if (last) half[2 * e + 1] = (uint32_t)(i + 1);
+        }
+    }
+}
+
+__global__ void k_scatter_back(int dim, int64_t n, lp_particles p, const double* sx0, const double* sx1,
+                               const double* sx2, const double* sV, const double* su0, const double* su1,
+                               const double* su2, const double* sP, const double* sm, const uint32_t* sid)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* sx[3] = {sx0, sx1, sx2};
+    const double* su[3] = {su0, su1, su2};
+    for (int k = 0; k < dim; ++k) {
+        p.x[k][i] = sx[k][i];
+        p.u[k][i] = su[k][i];
+    }
+    p.V[i] = sV[i];
+    p.P[i] = sP[i];
+    p.m[i] = sm[i];
+    p.id[i] = sid[i];
+}
+
+inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t build_grid(lp_ctx* c, const lp_particles* p, cudaStream_t s)
+{
+    unsigned long long* ext = c->dt_min + 1;   // 8 scratch words after dt_min
+    k_init_extent<<<1, 32, 0, s>>>(ext);
+    int64_t n = p->n;
+    int64_t nb_ = grid_for(n, 256); unsigned blocks = (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
+    if (blocks == 0) blocks = 1;
+    k_reduce_extent<<<blocks, 256, 0, s>>>(c->dc.dim, n, p->x[0], p->x[1] ? p->x[1] : p->x[0],
+                                           p->x[2] ? p->x[2] : p->x[0], p->m, p->V, ext);
+    k_finalize_grid<<<1, 1, 0, s>>>(c->dc, c->lmax_cap, ext, c->grid);
+    return cudaGetLastError();
+}
+
+cudaError_t make_keys(lp_ctx* c, const lp_particles* p, cudaStream_t s)
+{
+    int64_t n = p->n;
+    int dim = c->dc.dim;
+    const double* x1 = p->x[1] ? p->x[1] : p->x[0];
+    const double* x2 = p->x[2] ? p->x[2] : p->x[0];
+    unsigned gb = grid_for(n, 256);
+    if (dim == 3) k_keys<3><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, c->keys[0], c->vals[0]);
+    else if (dim == 2) k_keys<2><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, c->keys[0], c->vals[0]);
+    else k_keys<1><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, c->keys[0], c->vals[0]);
+    return cudaGetLastError();
+}
+
+int radix_passes(const lp_ctx* c) { return (c->sort_hi_bit - c->sort_lo_bit + 7) / 8; }
+
+cudaError_t radix_sort(lp_ctx* c, int64_t n, cudaStream_t s)
+{
+    int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
+    int cur = 0;
+    for (int sh = c->sort_lo_bit; sh < c->sort_hi_bit; sh += 8) {
+        k_rs_upsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, c->keys[cur], sh, c->hist, nblocks);
+        k_rs_scan<<<1, 1024, 0, s>>>(c->hist, 256 * nblocks);
+        k_rs_downsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, c->keys[cur], c->vals[cur], c->keys[cur ^ 1],
+                                                                c->vals[cur ^ 1], sh, c->hist, nblocks);
+        cur ^= 1;
+    }
+    c->keys_sorted = c->keys[cur];
+    c->perm_sorted = c->vals[cur];
+    return cudaGetLastError();
+}
+
+cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s)
+{
+    int64_t n = p->n;
+    int dim = c->dc.dim;
+    unsigned gb = grid_for(n, 256);
+    const uint32_t* perm = c->perm_sorted;
+    lp_particles q = *p;
+    for (int k = dim; k < 3; ++k) { q.x[k] = p->x[0]; q.u[k] = p->u[0]; }
+#define LP_GATHER_ARGS n, perm, q, c->sx[0], c->sx[1], c->sx[2], c->sV, c->su[0], c->su[1], c->su[2], c->sP, \
+        c->sm, c->sid, c->hx[0], c->hx[1], c->hx[2], c->lx[0], c->lx[1], c->lx[2], c->hf[0], c->hf[1],     \
+        c->hf[2], c->hf[3], c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4]
+    if (dim == 3) k_gather<3><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+    else if (dim == 2) k_gather<2><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+    else k_gather<1><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+#undef LP_GATHER_ARGS
+    return cudaGetLastError();
+}
+
+cudaError_t fill_tables(lp_ctx* c, int64_t n, bool clear, cudaStream_t s)
+{
+    if (c->dc.dim == 1 || n == 0) return cudaSuccess;
+    k_tables<<<grid_for(n, 256), 256, 0, s>>>(c->dc.dim, n, c->keys_sorted, c->grid,
+                                               reinterpret_cast<const int64_t*>(c->dt_min + 16), c->cells,
+                                               clear ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t scatter_back(lp_ctx* c, lp_particles* p, cudaStream_t s)
+{
+    int64_t n = p->n;
+    if (n == 0) return cudaSuccess;
+    lp_particles q = *p;
+    for (int k = c->dc.dim; k < 3; ++k) { q.x[k] = p->x[0]; q.u[k] = p->u[0]; }
+    k_scatter_back<<<grid_for(n, 256), 256, 0, s>>>(c->dc.dim, n, q, c->sx[0], c->sx[1], c->sx[2], c->sV, c->su[0],
+                                                     c->su[1], c->su[2], c->sP, c->sm, c->sid);
+    return cudaGetLastError();
+}
+
+}  // namespace lp

@@ -1,0 +1,291 @@
+"""ctypes binding of liblp.so (declared in include/lp.h).
+
+Argument marshalling only: every step of the LP hot path runs in the CUDA
+library.  PyTorch provides device memory (torch.cuda tensors) and streams.
+There is no CPU fallback: if liblp.so is missing or cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblp.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_ILLCOND, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(8)
+PREC_FP32, PREC_FP64 = 0, 1
+RADIUS_FIXED, RADIUS_VOLUME, RADIUS_KSIDE = 0, 1, 2
+LIM_FLAGGED, LIM_PAPER, LIM_LW, LIM_UW = 0, 1, 2, 3
+EST_PLAIN, EST_MLP = 0, 1
+OUT_F32, OUT_F64 = 0, 1
+
+EXPORTED = [
+    "lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs", "lp_step",
+    "lp_export_neighbors", "lp_grid_info", "lp_dt_device", "lp_get_stats", "lp_reset_stats",
+    "lp_status_string", "lp_version", "lp_set_profiling", "lp_phase_times", "lp_phase_name",
+]
+NPHASES = 8
+
+
+class LPError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = "%s: %s (%d)" % (where, _lib_or_none_status(code), code)
+        super().__init__(msg)
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("precision", C.c_int32), ("radius_mode", C.c_int32), ("k_max", C.c_int32),
+        ("k_side", C.c_int32), ("k_per_side", C.c_int32), ("limiter", C.c_int32), ("estimator", C.c_int32),
+        ("gamma", C.c_double), ("radius", C.c_double), ("kappa", C.c_double), ("flat_eps", C.c_double),
+        ("active_frac", C.c_double), ("s_ref", C.c_double * 5), ("tau32", C.c_double), ("tau64", C.c_double),
+        ("periodic", C.c_int32 * 3), ("max_level", C.c_int32),
+        ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
+        ("n_fluid", C.c_int64), ("capacity", C.c_int64),
+    ]
+
+
+class Particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p * 3), ("V", C.c_void_p), ("u", C.c_void_p * 3),
+                ("P", C.c_void_p), ("m", C.c_void_p), ("id", C.c_void_p)]
+
+
+class Neighbors(C.Structure):
+    _fields_ = [("n", C.c_int64), ("k_max", C.c_int32), ("pad", C.c_int32), ("count", C.c_void_p),
+                ("total", C.c_void_p), ("idx", C.c_void_p), ("d2min", C.c_void_p), ("keys", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("dt", C.c_double), ("steps", C.c_int64), ("n_flagged", C.c_int64),
+                ("n_fp64_redo", C.c_int64), ("n_linear", C.c_int64), ("n_nofit", C.c_int64),
+                ("n_overflow", C.c_int64), ("n_nonfinite", C.c_int64), ("n_mlp_uncertain", C.c_int64),
+                ("max_count", C.c_uint32), ("status", C.c_uint32), ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class StepDiag(C.Structure):
+    _fields_ = [("flag", C.c_void_p), ("phi", C.c_void_p), ("r", C.c_void_p)]
+
+
+_lib = None
+
+
+def _lib_or_none_status(code):
+    try:
+        return lib().lp_status_string(code).decode()
+    except Exception:
+        return "status"
+
+
+def lib():
+    """Load liblp.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblp.so not found at %s; build it with paper_2206_11998_gb300.build.build()"
+                               % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.lp_create.argtypes = [C.POINTER(Config), C.POINTER(C.c_void_p)]
+        L.lp_destroy.argtypes = [P]
+        L.lp_build_neighbors.argtypes = [P, C.POINTER(Particles), C.POINTER(Neighbors), P]
+        L.lp_gfd_derivs.argtypes = [P, C.POINTER(Particles), C.POINTER(C.c_void_p), C.c_int32, C.c_int32, P, P, P]
+        L.lp_onesided_derivs.argtypes = [P, C.POINTER(Particles), C.POINTER(C.c_void_p), C.c_int32, P, P]
+        L.lp_step.argtypes = [P, C.POINTER(Particles), C.c_double, C.c_double, P, C.POINTER(StepDiag), P]
+        L.lp_export_neighbors.argtypes = [P, P, P, P, P, P, P]
+        L.lp_grid_info.argtypes = [P, P, P]
+        L.lp_dt_device.argtypes = [P]
+        L.lp_dt_device.restype = C.c_void_p
+        L.lp_get_stats.argtypes = [P, C.POINTER(Stats), P]
+        L.lp_reset_stats.argtypes = [P, P]
+        L.lp_status_string.argtypes = [C.c_int]
+        L.lp_status_string.restype = C.c_char_p
+        L.lp_version.restype = C.c_char_p
+        L.lp_set_profiling.argtypes = [P, C.c_int32]
+        L.lp_phase_times.argtypes = [P, P, P, P]
+        L.lp_phase_name.argtypes = [C.c_int32]
+        L.lp_phase_name.restype = C.c_char_p
+        for name in ("lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs",
+                     "lp_step", "lp_export_neighbors", "lp_grid_info", "lp_get_stats", "lp_reset_stats",
+                     "lp_set_profiling", "lp_phase_times"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise LPError(rc, where)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def make_config(dim, capacity, precision=PREC_FP32, radius_mode=RADIUS_VOLUME, radius=0.0, kappa=2.2,
+                k_max=64, k_side=8, k_per_side=4, gamma=1.4, limiter=LIM_FLAGGED, estimator=EST_PLAIN,
+                flat_eps=1e-6, active_frac=0.1, s_ref=(0, 0, 0, 0, 0), tau32=1e-3, tau64=1e-12,
+                periodic=(0, 0, 0), box_lo=(0, 0, 0), box_hi=(1, 1, 1), n_fluid=2**62, max_level=0) -> Config:
+    c = Config()
+    c.dim, c.precision, c.radius_mode, c.k_max, c.k_side = dim, precision, radius_mode, k_max, k_side
+    c.k_per_side, c.limiter, c.estimator = k_per_side, limiter, estimator
+    c.gamma, c.radius, c.kappa, c.flat_eps, c.active_frac = gamma, radius, kappa, flat_eps, active_frac
+    for k in range(5):
+        c.s_ref[k] = float(s_ref[k]) if k < len(s_ref) else 0.0
+    c.tau32, c.tau64, c.max_level = tau32, tau64, max_level
+    for k in range(3):
+        c.periodic[k] = int(periodic[k])
+        c.box_lo[k] = float(box_lo[k])
+        c.box_hi[k] = float(box_hi[k])
+    c.n_fluid, c.capacity = int(n_fluid), int(capacity)
+    return c
+
+
+@dataclass
+class ParticleSet:
+    """Device SoA particle arrays (torch.cuda tensors) owned by the caller."""
+    x: list
+    V: object
+    u: list
+    P: object
+    m: object
+    id: object
+
+    @property
+    def n(self):
+        return int(self.V.shape[0])
+
+    @property
+    def dim(self):
+        return len(self.x)
+
+    @staticmethod
+    def from_state(state, device="cuda"):
+        import torch
+        t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        return ParticleSet([t(a) for a in state["x"]], t(state["V"]), [t(a) for a in state["u"]], t(state["P"]),
+                           t(state["m"]), t(state["id"].astype(np.int32), torch.int32))
+
+    def to_state(self, n_fluid=None):
+        g = lambda a: a.detach().cpu().numpy()
+        st = {"x": [g(a) for a in self.x], "V": g(self.V), "u": [g(a) for a in self.u], "P": g(self.P),
+              "m": g(self.m), "id": g(self.id).astype(np.uint32)}
+        if n_fluid is not None:
+            st["n_fluid"] = n_fluid
+        return st
+
+    def struct(self) -> Particles:
+        p = Particles()
+        p.n = self.n
+        for k in range(3):
+            p.x[k] = self.x[k].data_ptr() if k < self.dim else None
+            p.u[k] = self.u[k].data_ptr() if k < self.dim else None
+        p.V, p.P, p.m, p.id = self.V.data_ptr(), self.P.data_ptr(), self.m.data_ptr(), self.id.data_ptr()
+        return p
+
+
+class Context:
+    """An lp_ctx: method configuration plus device scratch for `capacity` particles."""
+
+    def __init__(self, cfg: Config):
+        self.cfg = cfg
+        h = C.c_void_p()
+        _check(lib().lp_create(C.byref(cfg), C.byref(h)), "lp_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_neighbors(self, ps: ParticleSet, stream=None) -> Neighbors:
+        p = ps.struct()
+        nb = Neighbors()
+        _check(lib().lp_build_neighbors(self.h, C.byref(p), C.byref(nb), _stream(stream)), "lp_build_neighbors")
+        return nb
+
+    def export_neighbors(self, n, stream=None):
+        import torch
+        k = self.cfg.k_max
+        dev = "cuda"
+        cnt = torch.empty(n, dtype=torch.int32, device=dev)
+        tot = torch.empty(n, dtype=torch.int32, device=dev)
+        idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+        d2 = torch.empty(n, dtype=torch.float64, device=dev)
+        keys = torch.empty(n, dtype=torch.int64, device=dev)
+        _check(lib().lp_export_neighbors(self.h, _ptr(cnt), _ptr(tot), _ptr(idx), _ptr(d2), _ptr(keys),
+                                         _stream(stream)), "lp_export_neighbors")
+        return cnt, tot, idx, d2, keys
+
+    def grid_info(self, stream=None):
+        out = (C.c_double * 5)()
+        _check(lib().lp_grid_info(self.h, out, _stream(stream)), "lp_grid_info")
+        return list(out)
+
+    def gfd_derivs(self, ps: ParticleSet, fields, out_dtype=OUT_F64, status=None, stream=None):
+        import torch
+        nu = {1: 2, 2: 5, 3: 9}[ps.dim]
+        out = torch.empty((len(fields), ps.n, nu), dtype=torch.float64 if out_dtype == OUT_F64 else torch.float32,
+                          device="cuda")
+        ptrs = (C.c_void_p * len(fields))(*[f.data_ptr() for f in fields])
+        p = ps.struct()
+        _check(lib().lp_gfd_derivs(self.h, C.byref(p), ptrs, len(fields), out_dtype, _ptr(out), _ptr(status),
+                                   _stream(stream)), "lp_gfd_derivs")
+        return out
+
+    def onesided_derivs(self, ps: ParticleSet, fields, stream=None):
+        import torch
+        out = torch.empty((ps.n, ps.dim, 2, len(fields)), dtype=torch.float64, device="cuda")
+        ptrs = (C.c_void_p * len(fields))(*[f.data_ptr() for f in fields])
+        p = ps.struct()
+        _check(lib().lp_onesided_derivs(self.h, C.byref(p), ptrs, len(fields), _ptr(out), _stream(stream)),
+               "lp_onesided_derivs")
+        return out
+
+    def step(self, ps: ParticleSet, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None, stream=None):
+        p = ps.struct()
+        d = StepDiag()
+        d.flag, d.phi, d.r = (_ptr(flag) if flag is not None else None, _ptr(phi) if phi is not None else None,
+                              _ptr(r) if r is not None else None)
+        _check(lib().lp_step(self.h, C.byref(p), float(dt), float(cfl), _ptr(t), C.byref(d), _stream(stream)),
+               "lp_step")
+
+    def stats(self, stream=None) -> dict:
+        s = Stats()
+        _check(lib().lp_get_stats(self.h, C.byref(s), _stream(stream)), "lp_get_stats")
+        return s.as_dict()
+
+    def reset_stats(self, stream=None):
+        _check(lib().lp_reset_stats(self.h, _stream(stream)), "lp_reset_stats")
+
+    def set_profiling(self, on=True):
+        _check(lib().lp_set_profiling(self.h, 1 if on else 0), "lp_set_profiling")
+
+    def phase_times(self, stream=None):
+        """{phase name: (milliseconds, launches)} since the last call."""
+        ms = (C.c_double * NPHASES)()
+        nl = (C.c_int64 * NPHASES)()
+        _check(lib().lp_phase_times(self.h, ms, nl, _stream(stream)), "lp_phase_times")
+        return {lib().lp_phase_name(k).decode(): (ms[k], nl[k]) for k in range(NPHASES)}
+
+    def dt_device_ptr(self):
+        return lib().lp_dt_device(self.h)

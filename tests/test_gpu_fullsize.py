@@ -1,0 +1,120 @@
+"""Parity at the benchmark's full size and launch configuration.
+
+The 3D gas cloud with 2,000,000 particles (the workload bench.py times) is
+advanced one step on the GPU with the CFL time step computed on the device.
+The oracle then evaluates, one particle at a time, the neighbour lists and the
+new state of a seeded sample of particles from the same full state, so the
+comparison is element by element on those samples.  Also: the Sod shock tube
+run to t = 0.2 on the GPU's FP64 path converges to the exact Riemann solution
+as closely as the oracle's own run does.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_11998_gb300 import inputs, lp
+from tests.gpu_util import ensure_built, normwise
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    oracle.build()
+
+
+def test_gas_cloud_2m_sampled_parity():
+    n = 2_000_000
+    st = inputs.gas_cloud_3d(n, seed=4)
+    sref = inputs.field_scales(st)
+    cfg = lp.make_config(3, n, precision=lp.PREC_FP32, kappa=2.2, k_max=64, k_side=8, gamma=5.0 / 3.0,
+                         limiter=lp.LIM_FLAGGED, s_ref=sref)
+    ctx = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    phi = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+    ctx.step(ps, dt=0.0, cfl=0.4, phi=phi)
+    torch.cuda.synchronize()
+    dt = ctx.stats()["dt"]
+    cnt, tot, idx, d2, keys = ctx.export_neighbors(n)
+    ids = ps.id.cpu().numpy().astype(np.int64)
+    pos = np.empty(n, np.int64)
+    pos[ids] = np.arange(n)
+    rng = np.random.default_rng(123)
+    q = np.sort(rng.choice(n, 400, replace=False))
+    # extremes of the distribution too: the outermost particles have the largest radii
+    r2 = st["x"][0] ** 2 + st["x"][1] ** 2 + st["x"][2] ** 2
+    q = np.unique(np.concatenate([q, np.argsort(r2)[-20:], np.argsort(r2)[:20]]))
+    ocfg = oracle.make_config(3, gamma=5.0 / 3.0, kappa=2.2, k_max=64, k_side=8, limiter=oracle.LIM_FLAGGED,
+                              s_ref=sref)
+    # neighbour lists of the samples, bit-exact
+    oidx, ocnt, otot, od2 = oracle.neighbors(ocfg, st["x"], st["V"], st["m"], st["id"], query=q)
+    cnt = cnt.cpu().numpy(); tot = tot.cpu().numpy(); idx = idx.cpu().numpy(); d2 = d2.cpu().numpy()
+    for r, pid in enumerate(q):
+        i = pos[pid]
+        assert np.array_equal(ids[idx[i, :cnt[i]]], oidx[r, :ocnt[r]]), pid
+        assert tot[i] == otot[r] and d2[i] == od2[r]
+    # new state of the samples, with the GPU's phi forced where a decision differs
+    o = oracle.step(ocfg, st, dt, query=q)
+    gphi = phi.cpu().numpy()[pos[q]]
+    diff = np.nonzero(np.abs(gphi - o["phi"]).max(axis=1) > 1e-3)[0]
+    assert len(diff) <= 4, len(diff)
+    if len(diff):
+        forced = np.full((len(q), 5), np.nan)
+        forced[diff] = gphi[diff]
+        o = oracle.step(ocfg, st, dt, query=q, forced_phi=forced)
+    V = ps.V.cpu().numpy()[pos[q]]
+    P = ps.P.cpu().numpy()[pos[q]]
+    assert normwise(V, o["V"]) < 1e-5
+    assert normwise(P, o["P"]) < 1e-5
+    for k in range(3):
+        u = ps.u[k].cpu().numpy()[pos[q]]
+        x = ps.x[k].cpu().numpy()[pos[q]]
+        assert normwise(u, o["u"][k]) < 1e-5, k
+        assert normwise(x, o["x"][k]) < 1e-12, k
+    ctx.close()
+
+
+def _sod_l1(state, n_fluid, t):
+    f = state["id"] < n_fluid
+    x = state["x"][0][f]
+    r, u, p = oracle.riemann_exact(1.4, (1, 0, 1), (0.125, 0, 0.1), 0.5, t, x)
+    return (np.mean(np.abs(1 / state["V"][f] - r)), np.mean(np.abs(state["u"][0][f] - u)),
+            np.mean(np.abs(state["P"][f] - p)))
+
+
+def test_sod_fp64_run_to_t02_converges():
+    golden = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "sod_oracle_l1.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            golden[k] = float(v)
+    st = inputs.sod_1d(889, 111)
+    n = st["V"].shape[0]
+    cfg = lp.make_config(1, n, precision=lp.PREC_FP64, radius_mode=lp.RADIUS_KSIDE, k_max=8, k_per_side=4,
+                         k_side=1, gamma=1.4, s_ref=inputs.field_scales(st), n_fluid=st["n_fluid"])
+    ctx = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    t, dt = 0.0, 0.0
+    while dt == 0.0 or 0.2 - t > 2.0 * dt:
+        ctx.step(ps, dt=0.0, cfl=0.4)     # CFL step computed on the device
+        dt = ctx.stats()["dt"]
+        t += dt
+    k = int(np.ceil((0.2 - t) / dt))      # land on t = 0.2 with k equal steps <= the CFL step
+    for _ in range(k):
+        ctx.step(ps, dt=(0.2 - t) / k if _ == 0 else h, cfl=0.4)
+        h = (0.2 - t) / k
+    t = 0.2
+    g = ps.to_state(st["n_fluid"])
+    e = _sod_l1(g, st["n_fluid"], t)
+    # the GPU's errors match the oracle's own run to within 10 %, and stay small
+    assert e[0] < 1.1 * golden["rho_l1"] + 1e-4
+    assert e[1] < 1.1 * golden["u_l1"] + 1e-4
+    assert e[2] < 1.1 * golden["p_l1"] + 1e-4
+    ctx.close()
