@@ -252,6 +252,37 @@ lp_status lp_set_profiling(lp_ctx *ctx, int32_t on);
 lp_status lp_phase_times(lp_ctx *ctx, double *out_ms, int64_t *out_launches, lp_stream stream);
 const char *lp_phase_name(int32_t phase);
 
+/*
+ * Morton keys of n positions and their sort order, computed without allocating
+ * any device memory.  The paper has no counterpart: this serves callers that
+ * cannot allocate device memory at the point they need the key order -- a host
+ * application whose own pool owns all device memory and forbids other
+ * allocations, or a latency-critical loop that cannot afford cudaMalloc's
+ * implicit device-wide synchronisation.
+ *
+ * Computes what lp_build_neighbors computes for its keys and order with a
+ * default configuration (non-periodic bounding cube, keys sorted by their cell
+ * bits down to level 9 in 3D / 13 in 2D, ties in input order; 1D: the exact
+ * order of x): keys_out[i] is the key of the i-th particle in sorted order and
+ * perm_out[i] its input index.  x0..x2: device float64 [n] (unused axes may be
+ * NULL); keys_out uint64 [n], perm_out uint32 [n]: caller-owned device buffers.
+ *
+ * Scratch: one fixed device array inside the library, sized for
+ * LP_NOALLOC_MAX_N particles (about 6 MiB), which every GPU that loads the
+ * library holds until the process exits.  n > LP_NOALLOC_MAX_N returns
+ * LP_ERR_CAPACITY without enqueuing anything.  The first call on a device looks
+ * up the array's device address (a one-time set-up per device, made with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array: calls whose work overlaps on the GPU (different streams,
+ * or different host threads) race and corrupt each other's results, so
+ * serialise them.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.
+ */
+#define LP_NOALLOC_MAX_N 262144
+lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double *x0, const double *x1,
+                               const double *x2, uint64_t *keys_out, uint32_t *perm_out,
+                               lp_stream stream);
+
 /* Device time step of the last lp_step (device float64 scalar owned by ctx). */
 const double *lp_dt_device(lp_ctx *ctx);
 

@@ -1,6 +1,10 @@
 // lp_sort.cu -- Sec. 2.2 steps 2-3 on the GPU: bounding cube, Morton (Z-curve)
 // keys, LSD radix sort, gather of the state into key order, and the per-level
 // cell tables that stand in for the paper's octree.
+#include <string.h>
+
+#include <mutex>
+
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -381,3 +385,119 @@ cudaError_t scatter_back(lp_ctx* c, lp_particles* p, cudaStream_t s)
 }
 
 }  // namespace lp
+
+// ---------------------------------------------------------------------------
+// Morton keys and sort order without any device allocation.
+//
+// Some callers cannot allocate device memory when they need the key order: a
+// host application that owns every byte of device memory through its own pool
+// and forbids other allocations, or a latency-critical loop where cudaMalloc's
+// implicit device-wide synchronisation is not acceptable.  This entry point
+// serves them: its scratch (key and index ping-pong buffers, digit histograms,
+// the extent words and the cube) lives in one fixed file-scope device array,
+// NOALLOC_MAX_N particles large, which every GPU that loads this library holds
+// until the process exits.  It reuses the sort kernels above; nothing else in
+// the library uses this array.
+// ---------------------------------------------------------------------------
+namespace lp {
+namespace {
+
+constexpr int64_t NOALLOC_MAX_N = LP_NOALLOC_MAX_N;
+constexpr int64_t NA_BLOCKS = (NOALLOC_MAX_N + RS_TILE - 1) / RS_TILE;
+// byte offsets inside the array (each 256-byte aligned)
+constexpr size_t NA_KEYS0 = 0;
+constexpr size_t NA_KEYS1 = NA_KEYS0 + 8 * NOALLOC_MAX_N;
+constexpr size_t NA_VALS0 = NA_KEYS1 + 8 * NOALLOC_MAX_N;
+constexpr size_t NA_VALS1 = NA_VALS0 + 4 * NOALLOC_MAX_N;
+constexpr size_t NA_HIST = NA_VALS1 + 4 * NOALLOC_MAX_N;
+constexpr size_t NA_EXT = NA_HIST + ((256 * NA_BLOCKS * 4 + 255) / 256) * 256;
+constexpr size_t NA_GRID = NA_EXT + 256;
+constexpr size_t NA_BYTES = NA_GRID + 256;
+
+static __device__ __align__(256) unsigned char noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex na_mutex;
+unsigned char* na_ptr[NA_MAX_DEVICES] = {};
+
+// Once per device, with that device current: the device address of the array.
+cudaError_t noalloc_setup(unsigned char** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(na_mutex);
+    if (!na_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        na_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = na_ptr[dev];
+    return cudaSuccess;
+}
+
+__global__ void k_copy_sorted(int64_t n, const uint64_t* __restrict__ ks, const uint32_t* __restrict__ vs,
+                              uint64_t* __restrict__ ko, uint32_t* __restrict__ vo)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) { ko[i] = ks[i]; vo[i] = vs[i]; }
+}
+
+}  // namespace
+}  // namespace lp
+
+extern "C" lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double* x0, const double* x1,
+                                          const double* x2, uint64_t* keys_out, uint32_t* perm_out,
+                                          lp_stream stream)
+{
+    using namespace lp;
+    if (dim < 1 || dim > 3 || n < 0 || !keys_out || !perm_out) return LP_ERR_ARG;
+    if (n > NOALLOC_MAX_N) return LP_ERR_CAPACITY;
+    if (n == 0) return LP_OK;
+    if (!x0 || (dim > 1 && !x1) || (dim > 2 && !x2)) return LP_ERR_ARG;
+    unsigned char* base = nullptr;
+    if (noalloc_setup(&base) != cudaSuccess) return LP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* keys[2] = {reinterpret_cast<uint64_t*>(base + NA_KEYS0), reinterpret_cast<uint64_t*>(base + NA_KEYS1)};
+    uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(base + NA_VALS0), reinterpret_cast<uint32_t*>(base + NA_VALS1)};
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + NA_HIST);
+    unsigned long long* ext = reinterpret_cast<unsigned long long*>(base + NA_EXT);
+    Grid* grid = reinterpret_cast<Grid*>(base + NA_GRID);
+    const double* p1 = x1 ? x1 : x0;
+    const double* p2 = x2 ? x2 : x0;
+    // the cube: same kernels and parameters as a default context (fixed radius 1,
+    // finest table level 9 in 3D, 13 in 2D); the radius only sets the level range
+    DevCfg dc;
+    memset(&dc, 0, sizeof(dc));
+    dc.dim = dim;
+    dc.radius_mode = LP_RADIUS_FIXED;
+    dc.radius = 1.0;
+    int lmax_cap = dim == 3 ? 9 : (dim == 2 ? 13 : 0);
+    int lo_bit = 0, hi_bit = 64;
+    if (dim > 1) {
+        hi_bit = dim * MORTON_BITS;
+        lo_bit = hi_bit - 8 * ((dim * lmax_cap + 7) / 8);
+    }
+    unsigned gb = grid_for(n, 256);
+    int64_t nb_ = gb;
+    unsigned rblocks = (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
+    k_init_extent<<<1, 32, 0, s>>>(ext);
+    k_reduce_extent<<<rblocks, 256, 0, s>>>(dim, n, x0, p1, p2, x0, x0, ext);
+    k_finalize_grid<<<1, 1, 0, s>>>(dc, lmax_cap, ext, grid);
+    if (dim == 3) k_keys<3><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, keys[0], vals[0]);
+    else if (dim == 2) k_keys<2><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, keys[0], vals[0]);
+    else k_keys<1><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, keys[0], vals[0]);
+    int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
+    int cur = 0;
+    for (int sh = lo_bit; sh < hi_bit; sh += 8) {
+        k_rs_upsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, keys[cur], sh, hist, nblocks);
+        k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * nblocks);
+        k_rs_downsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, keys[cur], vals[cur], keys[cur ^ 1],
+                                                                vals[cur ^ 1], sh, hist, nblocks);
+        cur ^= 1;
+    }
+    k_copy_sorted<<<gb, 256, 0, s>>>(n, keys[cur], vals[cur], keys_out, perm_out);
+    return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}

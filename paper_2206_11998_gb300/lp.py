@@ -27,7 +27,9 @@ EXPORTED = [
     "lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs", "lp_step",
     "lp_export_neighbors", "lp_grid_info", "lp_dt_device", "lp_get_stats", "lp_reset_stats",
     "lp_status_string", "lp_version", "lp_set_profiling", "lp_phase_times", "lp_phase_name",
+    "lp_sort_keys_noalloc",
 ]
+NOALLOC_MAX_N = 262144
 NPHASES = 8
 
 
@@ -112,6 +114,8 @@ def lib():
         L.lp_phase_times.argtypes = [P, P, P, P]
         L.lp_phase_name.argtypes = [C.c_int32]
         L.lp_phase_name.restype = C.c_char_p
+        L.lp_sort_keys_noalloc.argtypes = [C.c_int32, C.c_int64, P, P, P, P, P, P]
+        L.lp_sort_keys_noalloc.restype = C.c_int
         for name in ("lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs",
                      "lp_step", "lp_export_neighbors", "lp_grid_info", "lp_get_stats", "lp_reset_stats",
                      "lp_set_profiling", "lp_phase_times"):
@@ -195,6 +199,14 @@ class ParticleSet:
             p.u[k] = self.u[k].data_ptr() if k < self.dim else None
         p.V, p.P, p.m, p.id = self.V.data_ptr(), self.P.data_ptr(), self.m.data_ptr(), self.id.data_ptr()
         return p
+
+
+def sort_keys_noalloc(x, keys_out, perm_out, stream=None):
+    """Morton keys and sort order of positions x (list of device float64 tensors)
+    into caller buffers, with the library's fixed scratch (no allocation)."""
+    xs = [_ptr(a) for a in x] + [None] * (3 - len(x))
+    _check(lib().lp_sort_keys_noalloc(len(x), int(x[0].shape[0]), xs[0], xs[1], xs[2], _ptr(keys_out),
+                                      _ptr(perm_out), _stream(stream)), "lp_sort_keys_noalloc")
 
 
 class Context:
