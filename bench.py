@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--particles", type=int, default=N_PARTICLES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="gas-cloud", choices=["gas-cloud", "kh-ensemble"])
+    ap.add_argument("--sims", type=int, default=256)
     return ap.parse_args()
 
 
@@ -401,10 +403,122 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the batched ensemble: many independent 2D shear layers in one step
+# ---------------------------------------------------------------------------
+
+KH_GAMMA = 1.4
+
+
+def kh_states(nsim):
+    from paper_2206_11998_gb300 import inputs
+    sizes = inputs.kh_ensemble_sizes(nsim)
+    amps = inputs.kh_ensemble_amplitudes(nsim)
+    return [inputs.kh_2d(int(sizes[k]), float(amps[k]), seed=1000 + k) for k in range(nsim)]
+
+
+def kh_cfg(lp, n, nsim):
+    return lp.make_config(2, n, precision=lp.PREC_FP32, kappa=KAPPA, k_max=40, gamma=KH_GAMMA, periodic=(1, 1, 0),
+                          box_lo=(0, 0, 0), box_hi=(1, 1, 1), s_ref=(1.0, 0.5, 0.5, 2.5), max_sims=nsim,
+                          max_level=8)
+
+
+def run_ensemble(args):
+    """Batched: all simulations in one lp_step_batched, replayed from a CUDA
+    graph.  Unbatched comparison: one lp_step per simulation, each with its own
+    context, in a loop."""
+    import torch
+
+    from paper_2206_11998_gb300 import build as b
+    from paper_2206_11998_gb300 import lp
+
+    b.build()
+    torch.cuda.set_device(0)
+    nsim = args.sims
+    sims = kh_states(nsim)
+    sizes = np.array([s["V"].shape[0] for s in sims])
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offs[-1])
+    st = {k: np.concatenate([s[k] for s in sims]) for k in ("V", "P", "m")}
+    st["x"] = [np.concatenate([s["x"][a] for s in sims]) for a in range(2)]
+    st["u"] = [np.concatenate([s["u"][a] for s in sims]) for a in range(2)]
+    st["id"] = np.arange(n, dtype=np.uint32)
+    ctx = lp.Context(kh_cfg(lp, n, nsim))
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        ps = lp.ParticleSet.from_state(st)
+        offs_d = torch.as_tensor(offs, device="cuda")
+        t = torch.zeros(nsim, dtype=torch.float64, device="cuda")
+        ctx.step_batched(ps, offs_d, nsim, dt=0.0, cfl=CFL, t=t, stream=stream)
+        ctx.graph_capture(ps, offs_d, nsim, dt=0.0, cfl=CFL, t=t, stream=stream)
+        for _ in range(args.warmup):
+            ctx.graph_launch(stream=stream)
+        stream.synchronize()
+        l0 = ctx.stats(stream=stream)["kernel_launches"]
+        sampler = ClockSampler(gpu_index_for(0))
+        sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            ctx.graph_launch(stream=stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        clocks = sampler.stop()
+        launches = ctx.stats(stream=stream)["kernel_launches"] - l0
+        batched_ms = sum(a.elapsed_time(bb) for a, bb in ev) / args.steps
+        # per-phase times of one eager batched step
+        ctx.phase_times(stream=stream)
+        ctx.set_profiling(True)
+        ctx.step_batched(ps, offs_d, nsim, dt=0.0, cfl=CFL, t=t, stream=stream)
+        phases = ctx.phase_times(stream=stream)
+        ctx.set_profiling(False)
+    ctx.close()
+    del ps
+    # unbatched: one context per simulation, one lp_step each, in a loop
+    loop_ms = None
+    with torch.cuda.stream(stream):
+        ctxs, pss = [], []
+        for s in sims:
+            c = lp.Context(kh_cfg(lp, s["V"].shape[0], 1))
+            ctxs.append(c)
+            pss.append(lp.ParticleSet.from_state(s))
+        for c, p in zip(ctxs, pss):
+            c.step(p, dt=0.0, cfl=CFL, stream=stream)
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        bb = torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(reps):
+            for c, p in zip(ctxs, pss):
+                c.step(p, dt=0.0, cfl=CFL, stream=stream)
+        bb.record(stream)
+        stream.synchronize()
+        loop_ms = a.elapsed_time(bb) / reps
+        for c in ctxs:
+            c.close()
+    value = n * args.steps / (batched_ms * args.steps * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": batched_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "kh-ensemble-%d" % nsim, "particles": n, "dim": 2, "gamma": KH_GAMMA,
+                       "sizes": "U[10k, 200k] per simulation (seed 6)", "schedule": "batched, CUDA graph replay",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "unbatched": {"ms_per_step": loop_ms, "value": n / (loop_ms * 1e-3),
+                          "note": "one lp_step per simulation in a loop, one context each"},
+            "speedup_vs_unbatched": loop_ms / batched_ms, "gpu_launches": launches, "clocks": clocks,
+            "phases": {k: {"ms": v[0], "launches": v[1]} for k, v in phases.items() if v[1]}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "kh-ensemble":
+        run_ensemble(args)
     else:
         run_ours(args)
 

@@ -89,7 +89,16 @@ enum { LP_OUT_F32 = 0, LP_OUT_F64 = 1 };
  *   n_fluid        particles whose id >= n_fluid are frozen boundary
  *                  particles: neighbours of others, never updated or moved.
  *   capacity       largest n any call will pass (scratch is sized for it).
- *   max_level      finest cell level of the Morton cell tables (0 = automatic).
+ *   max_level      finest cell level of the Morton cell tables (0 = automatic, <= 17).
+ *   mlp_tau_lo     LP_EST_MLP: a particle whose learned flag probability is
+ *                  below this is treated as unflagged (pure Lax-Wendroff) without
+ *                  its one-sided fits; otherwise the plain estimator decides.
+ *   mlp_audit      LP_EST_MLP: also run the plain estimator on every particle and
+ *                  count the skipped particles it would have flagged (the miss
+ *                  count in lp_stats); the update still follows the learned call.
+ *   max_sims       most simulations one lp_step_batched call advances (0 or 1:
+ *                  one).  2D keys keep 21 bits per axis; 3D keys with several
+ *                  simulations keep min(21, (64 - ceil(log2 max_sims)) / 3).
  */
 typedef struct {
     int32_t dim;
@@ -114,6 +123,9 @@ typedef struct {
     double box_hi[3];
     int64_t n_fluid;
     int64_t capacity;
+    double mlp_tau_lo;
+    int32_t mlp_audit;
+    int32_t max_sims;
 } lp_config;
 
 /* Caller-owned device particle arrays (SoA, float64; id uint32).  Unused axes
@@ -135,7 +147,8 @@ typedef struct {
     int32_t k_max;             /* row stride of idx */
     int32_t pad;
     const uint32_t *count;     /* [n] list length, <= k_max */
-    const uint32_t *total;     /* [n] neighbours inside the radius before truncation */
+    const uint32_t *total;     /* [n] neighbours inside the radius before truncation,
+                                  saturated at 4 k_max */
     const uint32_t *idx;       /* [n][k_max] indices into the permuted particle arrays,
                                   in (d^2, id) order */
     const double *d2min;       /* [n] squared distance of the nearest neighbour */
@@ -156,6 +169,8 @@ typedef struct {
     uint32_t max_count;        /* largest neighbour count seen */
     uint32_t status;           /* OR of LP_ERR_* bits (1 << code) seen on the device */
     int64_t kernel_launches;   /* kernels this context launched (host-side count) */
+    int64_t n_mlp_skip;        /* particle-steps the learned estimator declared unflagged */
+    int64_t n_mlp_miss;        /* ... of which the plain estimator flags (audit mode) */
 } lp_stats;
 
 typedef struct lp_ctx lp_ctx;
@@ -212,12 +227,14 @@ lp_status lp_onesided_derivs(lp_ctx *ctx, const lp_particles *p, const double *c
  *            (ell_i nearest-neighbour distance, c_i = sqrt(gamma P_i V_i)).
  *   t      : optional device float64 scalar, incremented by dt on the device.
  *   diag   : optional device outputs (any may be NULL): flag uint8 [n],
- *            phi float32 [n][nf], r float32 [n][nf] (nf = dim + 2).
+ *            phi float32 [n][nf], r float32 [n][nf] (nf = dim + 2),
+ *            features float32 [n][8] (see lp_mlp_*).
  */
 typedef struct {
     uint8_t *flag;
     float *phi;
     float *r;
+    float *features;   /* float32 [n][8]: the learned estimator's inputs */
 } lp_step_diag;
 
 lp_status lp_step(lp_ctx *ctx, lp_particles *p, double dt, double cfl, double *t,
@@ -238,6 +255,36 @@ lp_status lp_export_neighbors(lp_ctx *ctx, uint32_t *count, uint32_t *total, uin
  * q_k = floor((x_k - lo_k) * 2^21 / L), clamped to [0, 2^21 - 1].
  */
 lp_status lp_grid_info(lp_ctx *ctx, double *out, lp_stream stream);
+
+/*
+ * Learned state estimator (no counterpart in the paper beyond the plain
+ * estimator it imitates): an 8 -> 32 (ReLU) -> 1 (sigmoid) network on eight
+ * dimensionless stencil features of each particle (from its central fit: the
+ * scaled |grad P|, |grad V|, |Hess P|, |Hess V|, divergence over sound speed,
+ * largest rise and fall of P over the neighbours, relative residual of the P
+ * fit; each transformed as log(1 + 10|f|), the divergence keeping its sign).
+ * BF16 weights with FP32 accumulation on the device, FP32 master weights.
+ * Parameters (LP_MLP_NPARAM floats): W1[32][8] row-major, b1[32], w2[32], b2.
+ *   lp_mlp_set_params   upload master weights (host), reset Adam.
+ *   lp_mlp_get_params   download master weights and/or the BF16 values (host).
+ *   lp_mlp_grad         loss and gradient of the mean class-weighted BCE
+ *                       (weight pos_weight on y = 1) over n samples X [n][8],
+ *                       y [n] (device), at the BF16 weights; grad [NPARAM] and
+ *                       loss [1] are device float32.
+ *   lp_mlp_adam_step    one Adam step (beta 0.9/0.999, eps 1e-8) with grad (device).
+ *   lp_mlp_train        minibatch Adam over the samples in order, `epochs` passes;
+ *                       epoch_loss (host, may be NULL) gets the mean batch loss.
+ *   lp_mlp_infer        probabilities p [n] (device) for features X.
+ */
+#define LP_MLP_NPARAM 321
+lp_status lp_mlp_set_params(lp_ctx *ctx, const float *params);
+lp_status lp_mlp_get_params(lp_ctx *ctx, float *master, float *bf16_as_float);
+lp_status lp_mlp_grad(lp_ctx *ctx, const float *X, const float *y, int64_t n, double pos_weight,
+                      float *grad, float *loss, lp_stream stream);
+lp_status lp_mlp_adam_step(lp_ctx *ctx, const float *grad, double lr, lp_stream stream);
+lp_status lp_mlp_train(lp_ctx *ctx, const float *X, const float *y, int64_t n, int32_t epochs,
+                       int32_t batch, double lr, double pos_weight, float *epoch_loss, lp_stream stream);
+lp_status lp_mlp_infer(lp_ctx *ctx, const float *X, int64_t n, float *p, lp_stream stream);
 
 /*
  * Phase timing.  With profiling on, every entry point records CUDA events on
@@ -283,7 +330,37 @@ lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double *x0, const d
                                const double *x2, uint64_t *keys_out, uint32_t *perm_out,
                                lp_stream stream);
 
-/* Device time step of the last lp_step (device float64 scalar owned by ctx). */
+/*
+ * One LP step of nsim independent simulations stored back to back in p: the
+ * particles of simulation s are [offsets[s], offsets[s+1]) (offsets: device
+ * int64 [nsim + 1], offsets[0] = 0, offsets[nsim] = p->n; nsim <= max_sims).
+ * One sort, one set of cell tables and one launch per phase serve all of
+ * them: a key carries its simulation above the Morton bits, so every
+ * simulation's particles stay at the same offsets after the step.  Each
+ * simulation has its own bounding cube and its own CFL step (dt <= 0); the
+ * periodic box of the configuration is shared.  t: optional device float64
+ * [nsim], advanced by each simulation's step.  Otherwise as lp_step.
+ */
+lp_status lp_step_batched(lp_ctx *ctx, lp_particles *p, const int64_t *offsets, int32_t nsim,
+                          double dt, double cfl, double *t, const lp_step_diag *diag,
+                          lp_stream stream);
+
+/*
+ * CUDA-graph form of a step.  lp_graph_capture records one lp_step_batched
+ * call (same arguments) on `stream` -- which must be a created stream, not the
+ * legacy default stream -- into an executable graph kept by the context, without
+ * running it; lp_graph_launch replays that step on `stream`.  The particle,
+ * offsets and t buffers are captured by address and must stay valid; the
+ * neighbour build of the previous step must already have run on this context
+ * (LP_ERR_STATE otherwise), because each step clears the cell-table entries of
+ * the one before.  Profiling must be off while capturing.
+ */
+lp_status lp_graph_capture(lp_ctx *ctx, lp_particles *p, const int64_t *offsets, int32_t nsim, double dt,
+                           double cfl, double *t, lp_stream stream);
+lp_status lp_graph_launch(lp_ctx *ctx, lp_stream stream);
+
+/* Device time step of the last lp_step (device float64 scalar owned by ctx;
+ * one per simulation after lp_step_batched). */
 const double *lp_dt_device(lp_ctx *ctx);
 
 /* Synchronise `stream`, read the counters into *out (host). */

@@ -58,7 +58,7 @@ class Config(C.Structure):
 
 
 def make_config(dim, gamma=1.4, radius_mode=RADIUS_VOLUME, radius=0.0, kappa=2.2, k_max=64,
-                k_side=8, k_per_side=4, limiter=LIM_FLAGGED, flat_eps=1e-6, active_frac=0.1,
+                k_side=8, k_per_side=4, limiter=LIM_FLAGGED, flat_eps=1e-6, active_frac=0.5,
                 s_ref=(0, 0, 0, 0, 0), periodic=(0, 0, 0), box_lo=(0, 0, 0), box_hi=(1, 1, 1),
                 rank_tol=1e-12, n_fluid=2**62) -> Config:
     c = Config()
@@ -105,6 +105,8 @@ def lib():
             L.lpo_riemann_star.argtypes = [C.c_double] * 7 + [_P, _P]
             L.lpo_riemann_star.restype = C.c_int
             L.lpo_riemann_exact.argtypes = [C.c_double] * 9 + [C.c_int64, _P, _P, _P, _P]
+            L.lpo_features.argtypes = [C.POINTER(Config), C.c_int64, _PP, _P, _PP, _P, _P, _P, C.c_int64, _P, _P]
+            L.lpo_features.restype = C.c_int
             L.lpo_mlp_forward.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_double, _P, _P]
             L.lpo_mlp_loss_grad.argtypes = [C.c_int64, _P, _P, C.c_double, _P, _P, _P, C.c_double,
                                             _P, _P, _P, _P]
@@ -250,6 +252,23 @@ def step(cfg: Config, state: dict, dt: float, query=None, forced_phi=None):
     if rc != 0:
         raise MemoryError("lpo_step failed")
     return {"x": xn, "V": Vn, "u": un, "P": Pn, "flag": flag, "phi": phi, "r": rr, "status": st}
+
+
+def features(cfg: Config, state: dict, query=None):
+    """The learned estimator's eight inputs for the query particles: [nq, 8]."""
+    xs = [_c(a, np.float64) for a in state["x"]]
+    us = [_c(a, np.float64) for a in state["u"]]
+    V = _c(state["V"], np.float64); P = _c(state["P"], np.float64)
+    m = _c(state["m"], np.float64); ids = _c(state["id"], np.uint32)
+    n = V.shape[0]
+    q = np.arange(n, dtype=np.int64) if query is None else _c(query, np.int64)
+    out = np.zeros((q.shape[0], 8))
+    px, k1 = _ptrs(xs); pu, k2 = _ptrs(us)
+    rc = lib().lpo_features(C.byref(cfg), n, px, _ptr(V), pu, _ptr(P), _ptr(m), _ptr(ids), q.shape[0], _ptr(q),
+                            _ptr(out))
+    if rc != 0:
+        raise MemoryError("lpo_features failed")
+    return out
 
 
 def phi(r: float) -> float:

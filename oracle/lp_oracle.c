@@ -77,6 +77,7 @@ typedef struct {
 #define LPO_ST_LINEAR_FALLBACK 1u   /* second-order system rank deficient: first-order fit used */
 #define LPO_ST_NO_FIT          2u   /* first-order system rank deficient too: derivatives zero */
 #define LPO_ST_OVERFLOW        4u   /* more than k_max neighbours inside the radius */
+#define LPO_ST_REJECTED        8u   /* update not admissible (V or P <= 0, non-finite): not applied */
 
 /* ------------------------------------------------------------------------ */
 /* Morton keys (Sec. 2.2, space-filling Z-curve)                              */
@@ -189,7 +190,8 @@ static int idx_cmp_x0(const void *a, const void *b)
  * Neighbour lists of the query particles q[0..nq-1] (indices into the inputs).
  *
  * out_idx[r*k_max + t] holds the t-th neighbour (input index) of query r in
- * (d2, id) order, out_count[r] = min(#inside, k_max), out_total[r] = #inside,
+ * (d2, id) order, out_count[r] = min(#inside, k_max),
+ * out_total[r] = min(#inside, 4 k_max) (the count saturates there),
  * out_d2min[r] = d2 of the nearest neighbour (INFINITY if none).
  *
  * 1D k-per-side mode (radius_mode 2): the k_per_side nearest with x_j < x_i and
@@ -275,7 +277,7 @@ int lpo_neighbors(const lpo_config *c, int64_t n, const double *const *x,
             for (int64_t t = 0; t < keep; ++t) out_idx[r * c->k_max + t] = buf[t].j;
             for (int64_t t = keep; t < c->k_max; ++t) out_idx[r * c->k_max + t] = -1;
             out_count[r] = (uint32_t)keep;
-            out_total[r] = (uint32_t)nc;
+            out_total[r] = (uint32_t)(nc < 4 * (int64_t)c->k_max ? nc : 4 * (int64_t)c->k_max);
             out_d2min[r] = nc > 0 ? buf[0].d2 : INFINITY;
         }
         free(buf);
@@ -697,6 +699,14 @@ int lpo_step(const lpo_config *c, int64_t n, const double *const *x, const doubl
             phi[f] = p;
             s1[f] = s0[f] + dt * (uw[f] - p * (uw[f] - lw[f]));
         }
+        /* safeguard (not in the paper): an update that leaves V or P non-positive
+         * or a field non-finite is not applied; the particle keeps its state */
+        int admissible = s1[0] > 0.0 && s1[dim + 1] > 0.0;
+        for (int f = 0; f < nf; ++f) admissible = admissible && isfinite(s1[f]);
+        if (!admissible) {
+            for (int f = 0; f < nf; ++f) s1[f] = s0[f];
+            st |= 8u;
+        }
         Vn[r] = s1[0];
         for (int k = 0; k < dim; ++k) un[k][r] = s1[1 + k];
         Pn[r] = s1[dim + 1];
@@ -883,6 +893,100 @@ void lpo_riemann_exact(double g, double rL, double uL, double pL, double rR, dou
         }
         rho[i] = r; vel[i] = uu; pre[i] = pp;
     }
+}
+
+/*
+ * The eight inputs of the learned state estimator for the query particles,
+ * from each particle's central fit (see central_fit), its nearest-neighbour
+ * distance ell, and the differences b_j = P_j - P_i over its list:
+ *   f0 = ell |grad P| / P          f1 = ell |grad V| / V
+ *   f2, f3 = for P and V: the largest, over axes k whose |d_k s| is at least
+ *            half the largest, of ell |d_kk s| / (|d_k s| + ell |d_kk s|)
+ *   f4 = ell div u / c, c = sqrt(gamma P V)
+ *   f5 = max_j b_j / P             f6 = -min_j b_j / P   (extremes include 0)
+ *   f7 = sqrt(sum_j res_j^2 / sum_j b_j^2), res = residual of the P fit
+ * each mapped to log(1 + 10 |f|), f4 keeping its sign.  out[r*8 + k].
+ */
+int lpo_features(const lpo_config *c, int64_t n, const double *const *x, const double *V,
+                 const double *const *u, const double *P, const double *m, const uint32_t *id,
+                 int64_t nq, const int64_t *q, double *out)
+{
+    int dim = c->dim, nf = dim + 2, nu = n_second(dim);
+    const double *F[LPO_MAXF];
+    F[0] = V;
+    for (int k = 0; k < dim; ++k) F[1 + k] = u[k];
+    F[dim + 1] = P;
+    int kmax = c->k_max;
+    uint32_t *cnt = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nq > 0 ? nq : 1));
+    uint32_t *tot = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nq > 0 ? nq : 1));
+    int64_t *nb = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nq > 0 ? nq : 1) * (size_t)kmax);
+    double *d2m = (double *)malloc(sizeof(double) * (size_t)(nq > 0 ? nq : 1));
+    if (!cnt || !tot || !nb || !d2m) { free(cnt); free(tot); free(nb); free(d2m); return -1; }
+    int rc = lpo_neighbors(c, n, x, V, m, id, nq, q, 1, cnt, tot, nb, d2m);
+    if (rc != 0) { free(cnt); free(tot); free(nb); free(d2m); return rc; }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < nq; ++r) {
+        int64_t i = q[r];
+        double cd[LPO_MAXF * LPO_MAXN];
+        const int64_t *lst = nb + r * kmax;
+        central_fit(c, x, F, nf, i, lst, (int)cnt[r], cd);
+        const double *dV = cd, *dP = cd + (dim + 1) * nu;
+        double gP = 0, gV = 0, hP = 0, hV = 0, divu = 0;
+        for (int k = 0; k < dim; ++k) {
+            gP += dP[k] * dP[k];
+            gV += dV[k] * dV[k];
+            hP += dP[dim + k] * dP[dim + k];
+            hV += dV[dim + k] * dV[dim + k];
+            divu += cd[(1 + k) * nu + k];
+        }
+        for (int s2 = 2 * dim; s2 < nu; ++s2) {
+            hP += 2.0 * dP[s2] * dP[s2];
+            hV += 2.0 * dV[s2] * dV[s2];
+        }
+        double bmin = 0, bmax = 0, ssb = 0, ssr = 0;
+        for (int t = 0; t < (int)cnt[r]; ++t) {
+            int64_t j = lst[t];
+            double d[3], row[LPO_MAXN];
+            for (int k = 0; k < dim; ++k) d[k] = offset(c, x, k, i, j);
+            gfd_row(dim, d, row);
+            double b = P[j] - P[i];
+            double fit = 0;
+            for (int s2 = 0; s2 < nu; ++s2) fit += row[s2] * dP[s2];
+            if (b < bmin) bmin = b;
+            if (b > bmax) bmax = b;
+            ssb += b * b;
+            ssr += (b - fit) * (b - fit);
+        }
+        double ell = sqrt(d2m[r]), Pi = P[i], Vi = V[i];
+        double cs = sqrt(c->gamma * Pi * Vi);
+        double f[8];
+        f[0] = ell * sqrt(gP) / Pi;
+        f[1] = ell * sqrt(gV) / Vi;
+        for (int w = 0; w < 2; ++w) {
+            const double *dd = w == 0 ? dP : dV;
+            double gmax = 0.0, best = 0.0;
+            for (int k = 0; k < dim; ++k) gmax = fmax(gmax, fabs(dd[k]));
+            for (int k = 0; k < dim; ++k) {
+                double g = fabs(dd[k]);
+                if (g < 0.5 * gmax) continue;
+                double h = ell * fabs(dd[dim + k]);
+                double rr = (g + h) > 0.0 ? h / (g + h) : 0.0;
+                best = fmax(best, rr);
+            }
+            f[2 + w] = best;
+        }
+        (void)hP; (void)hV;
+        f[4] = ell * divu / cs;
+        f[5] = bmax / Pi;
+        f[6] = -bmin / Pi;
+        f[7] = ssb > 0 ? sqrt(ssr / ssb) : 0.0;
+        for (int k = 0; k < 8; ++k) {
+            double t = log1p(10.0 * fabs(f[k]));
+            out[r * 8 + k] = (k == 4 && f[k] < 0) ? -t : t;
+        }
+    }
+    free(cnt); free(tot); free(nb); free(d2m);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -10,9 +10,6 @@ using namespace lp;
 
 namespace {
 
-// misc device words: [0] dt_min bits, [1..8] extents, [16..16+MAX_LEVELS] level offsets
-constexpr int MISC_WORDS = 64;
-
 #define LP_CUDA(call)                                          \
     do {                                                       \
         cudaError_t e_ = (call);                               \
@@ -32,8 +29,10 @@ void free_all(lp_ctx* c)
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist, c->sx[0], c->sx[1], c->sx[2],
                     c->sV, c->su[0], c->su[1], c->su[2], c->sP, c->sm, c->sid, c->hx[0], c->hx[1], c->hx[2],
                     c->lx[0], c->lx[1], c->lx[2], c->hf[0], c->hf[1], c->hf[2], c->hf[3], c->hf[4],
-                    c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->cells, c->nb_count, c->nb_total,
-                    c->nb_idx, c->nb_d2min, c->grid, c->dt_dev, c->dt_min, c->counters, c->redo_list};
+                    c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec, c->pos4, c->cells, c->nb_count, c->nb_total,
+                    c->nb_idx, c->nb_d2min, c->grid, c->dt_dev, c->dt_min, c->counters, c->redo_list,
+                    c->ext, c->grange, c->level_off_dev, c->sim_of,
+                    c->mlp_master, c->mlp_bf16, c->mlp_m1, c->mlp_m2, c->mlp_grad, c->mlp_loss};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -53,7 +52,10 @@ lp_status check_cfg(const lp_config* g)
     if (g->k_side < 1 || g->k_side > 16) return LP_ERR_ARG;
     if (!(g->gamma > 1.0)) return LP_ERR_ARG;
     if (g->limiter < 0 || g->limiter > 3) return LP_ERR_ARG;
-    if (g->estimator != LP_EST_PLAIN) return LP_ERR_ARG;
+    if (g->estimator != LP_EST_PLAIN && g->estimator != LP_EST_MLP) return LP_ERR_ARG;
+    if (g->estimator == LP_EST_MLP && (g->limiter != LP_LIM_FLAGGED || !(g->mlp_tau_lo >= 0.0) ||
+                                       !(g->mlp_tau_lo <= 1.0)))
+        return LP_ERR_ARG;
     if (g->capacity < 1 || g->capacity > (int64_t)0x7fffffff) return LP_ERR_ARG;
     if (!(g->tau32 >= 0.0) || !(g->tau64 >= 0.0)) return LP_ERR_ARG;
     double L = -1.0;
@@ -64,7 +66,9 @@ lp_status check_cfg(const lp_config* g)
         if (L > 0.0 && e != L) return LP_ERR_ARG;   // a periodic box must be a cube
         L = e;
     }
-    if (g->max_level < 0 || g->max_level > 21) return LP_ERR_ARG;
+    if (g->max_level < 0 || g->max_level > 17) return LP_ERR_ARG;
+    if (g->max_sims < 0 || g->max_sims > (1 << 20)) return LP_ERR_ARG;
+    if (g->max_sims > 1 && g->dim == 1) return LP_ERR_ARG;   // 1D keys are the raw order of x
     return LP_OK;
 }
 
@@ -83,50 +87,61 @@ lp_status check_particles(const lp_ctx* c, const lp_particles* p)
 
 __global__ void k_split_fields(int64_t n, int nf, const double* f0, const double* f1, const double* f2,
                                const double* f3, const double* f4, float* h0, float* h1, float* h2, float* h3,
-                               float* h4, float* l0, float* l1, float* l2, float* l3, float* l4)
+                               float* h4, float* l0, float* l1, float* l2, float* l3, float* l4, float4* rec)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double* f[5] = {f0, f1, f2, f3, f4};
     float* h[5] = {h0, h1, h2, h3, h4};
     float* l[5] = {l0, l1, l2, l3, l4};
-    for (int q = 0; q < nf; ++q) split(f[q][i], h[q][i], l[q][i]);
+    float* r = reinterpret_cast<float*>(rec + i * REC_F4);
+    for (int q = 0; q < nf; ++q) {
+        split(f[q][i], h[q][i], l[q][i]);
+        r[REC_FH + q] = h[q][i];
+        r[REC_FL + q] = l[q][i];
+    }
 }
 
-// dt = cfl * sqrt(min_i d2min_i / (gamma P_i V_i)) over fluid particles
+// dt_s = cfl * sqrt(min_i d2min_i / (gamma P_i V_i)) over the fluid particles of
+// simulation s (one simulation: a grid-stride loop; several: one particle per
+// thread, reduced over the warp when its particles share a simulation)
 __global__ void k_cfl(int64_t n, DevCfg c, const double* d2min, const double* P, const double* V,
-                      const uint32_t* id, unsigned long long* dtmin)
+                      const uint32_t* id, const uint64_t* keys, int key_shift, unsigned long long* dtmin)
 {
     double best = INFINITY;
+    uint32_t sim = 0;
+    bool many = c.nsim_max > 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if ((int64_t)id[i] >= c.n_fluid) continue;
-        double d2 = d2min[i];
-        if (isinf(d2)) continue;
-        double cs2 = (c.gamma * P[i]) * V[i];
-        double v = d2 / cs2;
-        best = fmin(best, v);
+        if (many) sim = (uint32_t)(keys[i] >> key_shift);
+        if ((int64_t)id[i] < c.n_fluid && !isinf(d2min[i])) {
+            double cs2 = (c.gamma * P[i]) * V[i];
+            best = fmin(best, d2min[i] / cs2);
+        }
+        if (many) break;
     }
-    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0 && best >= 0.0 && best < INFINITY)
-        atomicMin(dtmin, (unsigned long long)__double_as_longlong(best));
+    uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
+    if (__all_sync(0xffffffffu, sim == s0)) {
+        for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if ((threadIdx.x & 31) != 0) return;
+    }
+    if (best >= 0.0 && best < INFINITY) atomicMin(dtmin + sim, (unsigned long long)__double_as_longlong(best));
 }
 
-__global__ void k_dt_finalize(double cfl, double dt_fixed, const unsigned long long* dtmin, double* dt, double* t,
-                              unsigned long long* counters)
+__global__ void k_dt_finalize(int nsim, double cfl, double dt_fixed, const unsigned long long* dtmin, double* dt,
+                              double* t, unsigned long long* counters)
 {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsim) return;
     double v;
     if (dt_fixed > 0.0) v = dt_fixed;
-    else {
-        double m = __longlong_as_double((long long)*dtmin);
-        v = cfl * sqrt(m);
-    }
+    else v = cfl * sqrt(__longlong_as_double((long long)dtmin[s]));
     if (!(v > 0.0) || isinf(v) || isnan(v)) {
         atomicOr(reinterpret_cast<unsigned int*>(counters + C_STATUS), ST_NONFINITE);
         v = 0.0;
     }
-    *dt = v;
-    if (t) *t += v;
-    counters[C_STEPS] += 1;
+    dt[s] = v;
+    if (t) t[s] += v;
+    if (s == 0) counters[C_STEPS] += 1;
 }
 
 void fill_fit_args(lp_ctx* c, FitArgs& a, int64_t n)
@@ -144,12 +159,15 @@ void fill_fit_args(lp_ctx* c, FitArgs& a, int64_t n)
         a.lx[k] = c->lx[kk];
     }
     for (int f = 0; f < 5; ++f) { a.fh[f] = c->hf[f]; a.fl[f] = c->lf[f]; }
+    a.rec = c->rec;
     a.sid = c->sid;
     a.sm = c->sm;
     a.counters = c->counters;
     a.redo_list = c->redo_list;
     a.list = nullptr;
     a.list_len = c->counters + C_REDO_LEN;
+    a.keys = c->keys_sorted;
+    a.key_shift = c->dc.dim * c->dc.mbits;
 }
 
 constexpr int EV_PAIRS = LP_NPHASES * 4;
@@ -198,13 +216,17 @@ namespace lp {
 
 cudaError_t run_cfl(lp_ctx* c, int64_t n, double cfl, double dt_fixed, double* t, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(c->dt_min, 0x7f, sizeof(unsigned long long), s);   // large positive
+    int nsim = c->nsim;
+    cudaError_t e = cudaMemsetAsync(c->dt_min, 0x7f, sizeof(unsigned long long) * nsim, s);   // large positive
     if (e != cudaSuccess) return e;
     if (dt_fixed <= 0.0 && n > 0) {
-        int64_t nb_ = (n + 255) / 256; unsigned blocks = (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
-        k_cfl<<<blocks, 256, 0, s>>>(n, c->dc, c->nb_d2min, c->sP, c->sV, c->sid, c->dt_min);
+        int64_t nb_ = (n + 255) / 256;
+        unsigned blocks = nsim > 1 ? (unsigned)nb_ : (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
+        k_cfl<<<blocks, 256, 0, s>>>(n, c->dc, c->nb_d2min, c->sP, c->sV, c->sid, c->keys_sorted,
+                                     c->dc.dim * c->dc.mbits, c->dt_min);
     }
-    k_dt_finalize<<<1, 1, 0, s>>>(cfl, dt_fixed, c->dt_min, c->dt_dev, t, c->counters);
+    k_dt_finalize<<<(unsigned)((nsim + 127) / 128), 128, 0, s>>>(nsim, cfl, dt_fixed, c->dt_min, c->dt_dev, t,
+                                                                c->counters);
     return cudaGetLastError();
 }
 
@@ -253,6 +275,13 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     d.limiter = cfg->limiter;
     d.estimator = cfg->estimator;
     d.refine = 1;
+    d.mlp_tau_lo = (float)cfg->mlp_tau_lo;
+    d.mlp_audit = cfg->mlp_audit ? 1 : 0;
+    d.nsim_max = cfg->max_sims > 1 ? cfg->max_sims : 1;
+    int simbits = 0;
+    while ((1 << simbits) < d.nsim_max) ++simbits;
+    d.mbits = (cfg->dim == 3 && d.nsim_max > 1) ? (64 - simbits) / 3 : MORTON_BITS;
+    if (d.mbits > MORTON_BITS) d.mbits = MORTON_BITS;
     d.gamma = cfg->gamma;
     d.radius = cfg->radius;
     d.kappa = cfg->kappa;
@@ -274,19 +303,21 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     cudaGetDevice(&c->device);
     // cell tables: levels 0..lmax_cap, 2^(dim l) entries each
     int dim = cfg->dim;
+    bool batched = d.nsim_max > 1;
     if (dim == 1) c->lmax_cap = 0;
-    else c->lmax_cap = cfg->max_level > 0 ? cfg->max_level : (dim == 3 ? 9 : 13);
+    else c->lmax_cap = cfg->max_level > 0 ? cfg->max_level : (dim == 3 ? (batched ? 6 : 9) : (batched ? 8 : 13));
+    if (c->lmax_cap > d.mbits) c->lmax_cap = d.mbits;
     int64_t off = 0;
     for (int l = 0; l <= MAX_LEVELS; ++l) {
         c->level_off[l] = off;
-        if (l <= c->lmax_cap && dim > 1) off += (int64_t)1 << (dim * l);
+        if (l <= c->lmax_cap && dim > 1) off += (int64_t)d.nsim_max << (dim * l);
     }
     c->table_entries = dim > 1 ? off : 1;
-    // sort bits: cells down to level lmax_cap (dim * lmax_cap bits under the top)
+    // sort bits: the simulation and the cells down to level lmax_cap
     if (dim == 1) { c->sort_lo_bit = 0; c->sort_hi_bit = 64; }
     else {
-        int top = dim * MORTON_BITS;
-        int need = dim * c->lmax_cap;
+        int top = dim * d.mbits + simbits;
+        int need = dim * c->lmax_cap + simbits;
         int passes = (need + 7) / 8;
         c->sort_hi_bit = top;
         c->sort_lo_bit = top - 8 * passes;
@@ -307,17 +338,26 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     }
     A(dalloc(&c->sV, n * 8)); A(dalloc(&c->sP, n * 8)); A(dalloc(&c->sm, n * 8)); A(dalloc(&c->sid, n * 4));
     for (int f = 0; f < 5; ++f) { A(dalloc(&c->hf[f], n * 4)); A(dalloc(&c->lf[f], n * 4)); }
+    A(dalloc(&c->rec, (size_t)n * REC_F4 * sizeof(float4)));
+    A(dalloc(&c->pos4, (size_t)n * 2 * sizeof(float4)));
     A(dalloc(&c->cells, (size_t)c->table_entries * 8));
     A(dalloc(&c->nb_count, n * 4)); A(dalloc(&c->nb_total, n * 4));
     A(dalloc(&c->nb_idx, (size_t)n * cfg->k_max * 4)); A(dalloc(&c->nb_d2min, n * 8));
-    A(dalloc(&c->grid, sizeof(Grid))); A(dalloc(&c->dt_dev, 8));
-    A(dalloc(&c->dt_min, MISC_WORDS * 8)); A(dalloc(&c->counters, C_COUNT * 8));
+    int ns = d.nsim_max;
+    A(dalloc(&c->grid, sizeof(Grid) * ns)); A(dalloc(&c->dt_dev, 8 * ns));
+    A(dalloc(&c->dt_min, 8 * ns)); A(dalloc(&c->ext, 64 * (size_t)ns)); A(dalloc(&c->grange, 8));
+    A(dalloc(&c->level_off_dev, sizeof(int64_t) * (MAX_LEVELS + 1)));
+    A(dalloc(&c->sim_of, batched ? n * 4 : 4));
+    A(dalloc(&c->counters, C_COUNT * 8));
     A(dalloc(&c->redo_list, n * 4));
+    A(dalloc(&c->mlp_master, MLP_NPARAM * 4)); A(dalloc(&c->mlp_bf16, MLP_NPARAM * 2));
+    A(dalloc(&c->mlp_m1, MLP_NPARAM * 4)); A(dalloc(&c->mlp_m2, MLP_NPARAM * 4));
+    A(dalloc(&c->mlp_grad, MLP_NPARAM * 4)); A(dalloc(&c->mlp_loss, 4));
     if (ok) {
         A(cudaMemset(c->cells, 0, (size_t)c->table_entries * 8));
         A(cudaMemset(c->counters, 0, C_COUNT * 8));
-        A(cudaMemset(c->dt_dev, 0, 8));
-        A(cudaMemcpy(c->dt_min + 16, c->level_off, sizeof(int64_t) * (MAX_LEVELS + 1), cudaMemcpyHostToDevice));
+        A(cudaMemset(c->dt_dev, 0, 8 * ns));
+        A(cudaMemcpy(c->level_off_dev, c->level_off, sizeof(int64_t) * (MAX_LEVELS + 1), cudaMemcpyHostToDevice));
         for (int q = 0; q < 2 * EV_PAIRS && ok; ++q) A(cudaEventCreate(&c->ev[q]));
         A(cudaDeviceSynchronize());
     }
@@ -334,6 +374,8 @@ lp_status lp_destroy(lp_ctx* c)
 {
     if (!c) return LP_OK;
     cudaDeviceSynchronize();
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     for (int q = 0; q < 2 * EV_PAIRS; ++q)
         if (c->ev[q]) cudaEventDestroy(c->ev[q]);
     free_all(c);
@@ -353,7 +395,7 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
     c->n_lists = 0;
     if (n == 0) return LP_OK;
     {
-        Phase ph(c, LP_PH_GRID, 4, s);
+        Phase ph(c, LP_PH_GRID, 5 + (c->nsim > 1 ? 1 : 0), s);
         LP_CUDA(build_grid(c, p, s));
         LP_CUDA(make_keys(c, p, s));
     }
@@ -371,7 +413,7 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
         c->tables_dirty = tables ? 1 : 0;
     }
     {
-        Phase ph(c, LP_PH_QUERY, 1, s);
+        Phase ph(c, LP_PH_QUERY, c->dc.radius_mode == LP_RADIUS_KSIDE ? 1 : 2, s);
         LP_CUDA(query_neighbors(c, n, s));
     }
     c->n_lists = n;
@@ -381,6 +423,8 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
 lp_status lp_build_neighbors(lp_ctx* c, lp_particles* p, lp_neighbors* out, lp_stream stream)
 {
     if (!c) return LP_ERR_ARG;
+    c->nsim = 1;
+    c->offsets = nullptr;
     lp_status st = check_particles(c, p);
     if (st != LP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -433,7 +477,7 @@ lp_status lp_gfd_derivs(lp_ctx* c, const lp_particles* p, const double* const* f
                 Phase ph(c, LP_PH_GATHER, 1, s);
                 k_split_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
                     n, real, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->hf[0], c->hf[1], c->hf[2], c->hf[3],
-                    c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4]);
+                    c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec);
             }
             for (int q = real; q < 5; ++q) { a.fh[q] = c->hf[0]; a.fl[q] = c->lf[0]; }
             LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
@@ -474,7 +518,7 @@ lp_status lp_onesided_derivs(lp_ctx* c, const lp_particles* p, const double* con
             Phase ph(c, LP_PH_GATHER, 1, s);
             k_split_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
                 n, nfields, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->hf[0], c->hf[1], c->hf[2], c->hf[3],
-                c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4]);
+                c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec);
         }
         for (int q = nfields; q < 5; ++q) { a.fh[q] = c->hf[0]; a.fl[q] = c->lf[0]; }
         LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
@@ -492,13 +536,17 @@ lp_status lp_onesided_derivs(lp_ctx* c, const lp_particles* p, const double* con
     return LP_OK;
 }
 
-lp_status lp_step(lp_ctx* c, lp_particles* p, double dt, double cfl, double* t, const lp_step_diag* diag,
-                  lp_stream stream)
+lp_status lp_step_batched(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_t nsim, double dt, double cfl,
+                          double* t, const lp_step_diag* diag, lp_stream stream)
 {
     if (!c) return LP_ERR_ARG;
     lp_status st = check_particles(c, p);
     if (st != LP_OK) return st;
+    if (nsim < 1 || nsim > c->dc.nsim_max || (nsim > 1 && !offsets)) return LP_ERR_ARG;
+    c->nsim = nsim;
+    c->offsets = nsim > 1 ? offsets : nullptr;
     if (!(dt > 0.0) && !(cfl > 0.0)) return LP_ERR_ARG;
+    if (c->dc.estimator == LP_EST_MLP && !c->mlp_ready) return LP_ERR_STATE;
     if (isnan(dt) || isinf(dt)) return LP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     st = build(c, p, s);
@@ -523,7 +571,8 @@ lp_status lp_step(lp_ctx* c, lp_particles* p, double dt, double cfl, double* t, 
         o.u[k] = p->u[k < dim ? k : 0];
     }
     o.V = p->V; o.P = p->P; o.m = p->m; o.id = p->id;
-    if (diag) { o.flag = diag->flag; o.phi = diag->phi; o.r = diag->r; }
+    if (diag) { o.flag = diag->flag; o.phi = diag->phi; o.r = diag->r; o.features = diag->features; }
+    a.mlp_w = reinterpret_cast<const __nv_bfloat16*>(c->mlp_bf16);
     o.dt = c->dt_dev;
     if (c->dc.precision == LP_PREC_FP32) {
         LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
@@ -595,6 +644,44 @@ const char* lp_phase_name(int32_t ph)
     return (ph >= 0 && ph < LP_NPHASES) ? names[ph] : "unknown";
 }
 
+lp_status lp_step(lp_ctx* c, lp_particles* p, double dt, double cfl, double* t, const lp_step_diag* diag,
+                  lp_stream stream)
+{
+    return lp_step_batched(c, p, nullptr, 1, dt, cfl, t, diag, stream);
+}
+
+lp_status lp_graph_capture(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_t nsim, double dt, double cfl,
+                           double* t, lp_stream stream)
+{
+    if (!c || !p || !stream) return LP_ERR_ARG;
+    if (c->profiling) return LP_ERR_STATE;
+    if (c->n_lists != p->n || (c->dc.dim > 1 && !c->tables_dirty)) return LP_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    int64_t before = c->launches;
+    LP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    lp_status st = lp_step_batched(c, p, offsets, nsim, dt, cfl, t, nullptr, stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != LP_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return LP_ERR_CUDA;
+    c->graph = g;
+    if (cudaGraphInstantiate(&c->graph_exec, g, 0) != cudaSuccess) return LP_ERR_CUDA;
+    c->graph_launches = c->launches - before;
+    c->launches = before;           // nothing ran yet
+    return LP_OK;
+}
+
+lp_status lp_graph_launch(lp_ctx* c, lp_stream stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (!c->graph_exec) return LP_ERR_STATE;
+    LP_CUDA(cudaGraphLaunch(c->graph_exec, (cudaStream_t)stream));
+    c->launches += c->graph_launches;
+    return LP_OK;
+}
+
 const double* lp_dt_device(lp_ctx* c) { return c ? c->dt_dev : nullptr; }
 
 lp_status lp_get_stats(lp_ctx* c, lp_stats* out, lp_stream stream)
@@ -619,6 +706,8 @@ lp_status lp_get_stats(lp_ctx* c, lp_stats* out, lp_stream stream)
     out->max_count = (uint32_t)h[C_MAXCOUNT];
     out->status = (uint32_t)h[C_STATUS];
     out->kernel_launches = c->launches;
+    out->n_mlp_skip = (int64_t)h[C_MLP_SKIP];
+    out->n_mlp_miss = (int64_t)h[C_MLP_MISS];
     return LP_OK;
 }
 

@@ -13,6 +13,7 @@
 #pragma once
 
 #include "lp_internal.cuh"
+#include "lp_mlp.cuh"
 
 namespace lp {
 
@@ -160,35 +161,50 @@ struct FitArgs {
     const double* fd[5];      // field values (FP64)
     const float* fh[5];       // field hi/lo split
     const float* fl[5];
+    const float4* rec;        // packed fit records (positions and fields, hi/lo)
     const uint32_t* sid;
     const double* sm;
     unsigned long long* counters;
     uint32_t* redo_list;      // FP32 pass: particles to redo in FP64
     const uint32_t* list;     // FP64 pass over a list (null: all particles)
     const unsigned long long* list_len;
+    const __nv_bfloat16* mlp_w;   // learned-estimator weights (BF16)
+    const uint64_t* keys;         // key-sorted keys (simulation above bit key_shift)
+    int key_shift;
+};
+
+// statistics of the last field's differences b_j = s_j - s_i over the central
+// stencil: extremes, sum of squares, and the least-squares residual (the
+// learned estimator's inputs)
+template <typename T>
+struct FitStats {
+    T bmin, bmax, ssb, ssr;
 };
 
 template <typename T, int DIM, int F> struct Src;
 
-// FP32: offsets and differences from split hi/lo floats
+// FP32: offsets and differences from the packed hi/lo record of each neighbour
 template <int DIM, int F>
 struct Src<float, DIM, F> {
     const FitArgs& a;
     int64_t i;
-    float hxi[DIM], lxi[DIM], hfi[F], lfi[F];
-    __device__ Src(const FitArgs& a_, int64_t i_) : a(a_), i(i_)
+    float ri[4 * REC_F4];
+    __device__ Src(const FitArgs& a_, int64_t i_) : a(a_), i(i_) { load(i, ri); }
+    __device__ void load(int64_t j, float (&r)[4 * REC_F4]) const
     {
+        const float4* p = a.rec + j * REC_F4;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) { hxi[k] = a.hx[k][i]; lxi[k] = a.lx[k][i]; }
-#pragma unroll
-        for (int f = 0; f < F; ++f) { hfi[f] = a.fh[f][i]; lfi[f] = a.fl[f][i]; }
+        for (int q = 0; q < REC_F4; ++q) {
+            float4 v = __ldg(p + q);
+            r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+        }
     }
-    __device__ void off(uint32_t j, float (&d)[DIM]) const
+    __device__ void off_rec(const float (&r)[4 * REC_F4], float (&d)[DIM]) const
     {
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            float dh = a.hx[k][j] - hxi[k];
-            float dl = a.lx[k][j] - lxi[k];
+            float dh = r[REC_XH + k] - ri[REC_XH + k];
+            float dl = r[REC_XL + k] - ri[REC_XL + k];
             if (a.c.periodic[k]) {
                 if (dh > 0.5f * a.c.Lper_h[k]) { dh -= a.c.Lper_h[k]; dl -= a.c.Lper_l[k]; }
                 else if (dh < -0.5f * a.c.Lper_h[k]) { dh += a.c.Lper_h[k]; dl += a.c.Lper_l[k]; }
@@ -196,22 +212,45 @@ struct Src<float, DIM, F> {
             d[k] = dh + dl;
         }
     }
-    __device__ void diff(uint32_t j, float (&b)[F]) const
+    __device__ void fetch(uint32_t j, float (&d)[DIM], float (&b)[F]) const
     {
+        float r[4 * REC_F4];
+        load(j, r);
+        off_rec(r, d);
 #pragma unroll
-        for (int f = 0; f < F; ++f) b[f] = (a.fh[f][j] - hfi[f]) + (a.fl[f][j] - lfi[f]);
+        for (int f = 0; f < F; ++f) b[f] = (r[REC_FH + f] - ri[REC_FH + f]) + (r[REC_FL + f] - ri[REC_FL + f]);
     }
-    // exact sign of the offset x_jk - x_ik (the oracle's definition)
-    __device__ int side(uint32_t j, int k) const
+    __device__ void off(uint32_t j, float (&d)[DIM]) const
+    {
+        float r[4 * REC_F4];
+        load(j, r);
+        off_rec(r, d);
+    }
+    // exact sign of the offset x_jk - x_ik (the oracle's definition), with the
+    // record of j already loaded
+    __device__ int side_rec(const float (&r)[4 * REC_F4], uint32_t j, int k) const
     {
         if (!a.c.periodic[k]) {
-            float hj = a.hx[k][j];
-            if (hj != hxi[k]) return hj > hxi[k] ? 1 : -1;
-            float lj = a.lx[k][j];
-            if (lj != lxi[k]) return lj > lxi[k] ? 1 : -1;
+            float hj = r[REC_XH + k], hi = ri[REC_XH + k];
+            if (hj != hi) return hj > hi ? 1 : -1;
+            float lj = r[REC_XL + k], li = ri[REC_XL + k];
+            if (lj != li) return lj > li ? 1 : -1;
         }
         double d = offset64(a.c, k, a.sx[k][i], a.sx[k][j]);
         return d > 0.0 ? 1 : (d < 0.0 ? -1 : 0);
+    }
+    // side of j along axis k; when non-zero, also its offsets and differences
+    __device__ int fetch_side(uint32_t j, int k, float (&d)[DIM], float (&b)[F]) const
+    {
+        float r[4 * REC_F4];
+        load(j, r);
+        int sg = side_rec(r, j, k);
+        if (sg != 0) {
+            off_rec(r, d);
+#pragma unroll
+            for (int f = 0; f < F; ++f) b[f] = (r[REC_FH + f] - ri[REC_FH + f]) + (r[REC_FL + f] - ri[REC_FL + f]);
+        }
+        return sg;
     }
 };
 
@@ -238,10 +277,17 @@ struct Src<double, DIM, F> {
 #pragma unroll
         for (int f = 0; f < F; ++f) b[f] = a.fd[f][j] - fi[f];
     }
-    __device__ int side(uint32_t j, int k) const
+    __device__ void fetch(uint32_t j, double (&d)[DIM], double (&b)[F]) const
     {
-        double d = offset64(a.c, k, xi[k], a.sx[k][j]);
-        return d > 0.0 ? 1 : (d < 0.0 ? -1 : 0);
+        off(j, d);
+        diff(j, b);
+    }
+    __device__ int fetch_side(uint32_t j, int k, double (&d)[DIM], double (&b)[F]) const
+    {
+        double dk = offset64(a.c, k, xi[k], a.sx[k][j]);
+        int sg = dk > 0.0 ? 1 : (dk < 0.0 ? -1 : 0);
+        if (sg != 0) fetch(j, d, b);
+        return sg;
     }
 };
 
@@ -255,23 +301,31 @@ __device__ inline float inv_scale(float d2)
 
 // Central second-order fit.  x[u][f] unscaled derivatives.  Returns 0 ok,
 // 1 ill-conditioned (ratio below tau), with x untouched.
-template <typename T, int DIM, int F>
+template <typename T, int DIM, int F, bool STATS = false>
 __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau,
-                           bool refine, T (&x)[NU<DIM>::v][F])
+                           bool refine, T (&x)[NU<DIM>::v][F], FitStats<T>* st = nullptr)
 {
     constexpr int N = NU<DIM>::v;
     Givens<T, N, F> G;
     G.zero();
+    T bmin = T(0), bmax = T(0), ssb = T(0), ssr = T(0);
     for (int r = 0; r < cnt; ++r) {
         uint32_t j = nb[r];
         T d[DIM], a[N], b[F];
-        src.off(j, d);
+        src.fetch(j, d, b);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) d[k] *= invS;
         gfd_row<T, DIM>(d, a);
-        src.diff(j, b);
+        if (STATS) {
+            T bl = b[F - 1];
+            bmin = bl < bmin ? bl : bmin;
+            bmax = bl > bmax ? bl : bmax;
+            ssb += bl * bl;
+        }
         G.add(a, b);
+        if (STATS) ssr += b[F - 1] * b[F - 1];   // the row's leftover after the rotations
     }
+    if (STATS && st) { st->bmin = bmin; st->bmax = bmax; st->ssb = ssb; st->ssr = ssr; }
     if (!(G.ratio() >= tau) || cnt < N) return 1;
     G.solve(x);
     if (refine) {
@@ -283,11 +337,10 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
         for (int r = 0; r < cnt; ++r) {
             uint32_t j = nb[r];
             T d[DIM], a[N], b[F];
-            src.off(j, d);
+            src.fetch(j, d, b);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) d[k] *= invS;
             gfd_row<T, DIM>(d, a);
-            src.diff(j, b);
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 T res = b[f];
@@ -320,10 +373,9 @@ __device__ int linear_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt
     for (int r = 0; r < cnt; ++r) {
         uint32_t j = nb[r];
         T d[DIM], b[F];
-        src.off(j, d);
+        src.fetch(j, d, b);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) d[k] *= invS;
-        src.diff(j, b);
         G.add(d, b);
     }
     if (!(G.ratio() >= tau) || cnt < DIM) return 1;
@@ -349,15 +401,13 @@ __device__ void onesided_axis(const Src<T, DIM, F>& src, const uint32_t* nb, int
     int ns[2] = {0, 0};
     for (int r = 0; r < cnt && (ns[0] < ks || ns[1] < ks); ++r) {
         uint32_t j = nb[r];
-        int sg = src.side(j, k);
+        T d[DIM], b[F];
+        int sg = src.fetch_side(j, k, d, b);
         if (sg == 0) continue;
         int s = sg > 0 ? 1 : 0;
         if (ns[s] >= ks) continue;
-        T d[DIM], b[F];
-        src.off(j, d);
 #pragma unroll
         for (int q = 0; q < DIM; ++q) d[q] *= invS;
-        src.diff(j, b);
         if (s) G[1].add(d, b); else G[0].add(d, b);
         ++ns[s];
     }

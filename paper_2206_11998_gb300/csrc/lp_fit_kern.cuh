@@ -16,6 +16,7 @@ struct StepOut {
     uint8_t* flag;
     float* phi;
     float* r;
+    float* features;
     const double* dt;
 };
 
@@ -41,6 +42,50 @@ __device__ inline float last_d2(const Src<T, DIM, F>& src, const uint32_t* nb, i
     return (float)s;
 }
 
+// the eight inputs of the learned estimator (see lp_mlp_* in lp.h)
+template <typename T, int DIM>
+__device__ inline T curvature_ratio(const T (&cd)[NU<DIM>::v][DIM + 2], int f, T ell)
+{
+    // max over active axes (|d_k s| >= 1/2 of the largest) of
+    // ell |d_kk s| / (|d_k s| + ell |d_kk s|), in [0, 1]; 1 at an extremum
+    T gmax = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) gmax = fmax(gmax, fabs(cd[k][f]));
+    T best = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        T g = fabs(cd[k][f]);
+        if (g < T(0.5) * gmax) continue;
+        T h = ell * fabs(cd[DIM + k][f]);
+        T r = (g + h) > T(0) ? h / (g + h) : T(0);
+        best = fmax(best, r);
+    }
+    return best;
+}
+
+template <typename T, int DIM>
+__device__ inline void mlp_features(const T (&cd)[NU<DIM>::v][DIM + 2], const FitStats<T>& st, T ell, T V, T P,
+                                    T gamma, float (&x)[MLP_IN])
+{
+    constexpr int FP = DIM + 1;
+    T gP = T(0), gV = T(0), divu = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        gP += cd[k][FP] * cd[k][FP];
+        gV += cd[k][0] * cd[k][0];
+        divu += cd[k][1 + k];
+    }
+    T cs = sqrt(gamma * P * V);
+    x[0] = feat_t((float)(ell * sqrt(gP) / P));
+    x[1] = feat_t((float)(ell * sqrt(gV) / V));
+    x[2] = feat_t((float)curvature_ratio<T, DIM>(cd, FP, ell));
+    x[3] = feat_t((float)curvature_ratio<T, DIM>(cd, 0, ell));
+    x[4] = feat_ts((float)(ell * divu / cs));
+    x[5] = feat_t((float)(st.bmax / P));
+    x[6] = feat_t((float)(-st.bmin / P));
+    x[7] = feat_t((float)(st.ssb > T(0) ? sqrt(st.ssr / st.ssb) : T(0)));
+}
+
 // ---------------------------------------------------------------------------
 // one LP step for particle i (sorted index)
 // ---------------------------------------------------------------------------
@@ -50,7 +95,7 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     constexpr int F = DIM + 2;
     constexpr int N = NU<DIM>::v;
     const DevCfg& c = a.c;
-    const double dt = *o.dt;
+    const double dt = o.dt[c.nsim_max > 1 ? (a.keys[i] >> a.key_shift) : 0];
     // frozen boundary particles are copied through
     double s0[F];
     s0[0] = a.fd[0][i];
@@ -81,7 +126,8 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     const T tau_rank = (T)c.tau64;
 
     T cd[N][F];
-    if (central_fit<T, DIM, F>(src, nb, cnt, invS, tau, c.refine != 0, cd)) {
+    FitStats<T> fst = {T(0), T(0), T(0), T(0)};
+    if (central_fit<T, DIM, F, true>(src, nb, cnt, invS, tau, c.refine != 0, cd, &fst)) {
         if (IsF32<T>::v) { push_redo(a, i); return; }
         T lin[DIM][F];
 #pragma unroll
@@ -98,18 +144,43 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
             atomicAdd(a.counters + C_NOFIT, 1ull);
         }
     }
+    // learned estimator: below mlp_tau_lo the particle is unflagged and its
+    // one-sided fits are skipped (unless auditing against the plain estimator)
+    bool mlp_skip = false;
+    if (o.features || c.estimator == LP_EST_MLP) {
+        float xf[MLP_IN];
+        mlp_features<T, DIM>(cd, fst, (T)sqrt(a.d2min[i]), (T)s0[0], (T)s0[F - 1], (T)c.gamma, xf);
+        if (o.features)
+#pragma unroll
+            for (int k = 0; k < MLP_IN; ++k) o.features[i * MLP_IN + k] = xf[k];
+        if (c.estimator == LP_EST_MLP) {
+            mlp_skip = mlp_prob(xf, a.mlp_w) < c.mlp_tau_lo;
+            warp_count(a.counters, C_MLP_SKIP, mlp_skip);
+            warp_count(a.counters, C_MLP_UNCERTAIN, !mlp_skip);
+        }
+    }
+    const bool plain = !mlp_skip || c.mlp_audit;
     // one-sided derivatives os[k][s][f]
     T os[DIM][2][F];
     bool ill = false;
+    if (plain) {
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        T out[2][F];
-        bool ok[2];
-        onesided_axis<T, DIM, F>(src, nb, cnt, k, c.k_side, invS, tau, tau_rank, out, ok, ill);
+        for (int k = 0; k < DIM; ++k) {
+            T out[2][F];
+            bool ok[2];
+            onesided_axis<T, DIM, F>(src, nb, cnt, k, c.k_side, invS, tau, tau_rank, out, ok, ill);
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+            for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int f = 0; f < F; ++f) os[k][s][f] = ok[s] ? out[s][f] : cd[k][f];
+                for (int f = 0; f < F; ++f) os[k][s][f] = ok[s] ? out[s][f] : cd[k][f];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int f = 0; f < F; ++f) os[k][s][f] = cd[k][f];
     }
     if (IsF32<T>::v && ill) { push_redo(a, i); return; }
 
@@ -142,11 +213,17 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
         T sl[DIM], sr[DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) { sl[k] = os[k][0][f]; sr[k] = os[k][1][f]; }
-        rs[f] = estimator_r<T, DIM>(sl, sr, ell, (T)s0[f], (T)c.s_ref[f], (T)c.flat_eps, (T)c.active_frac);
+        rs[f] = plain ? estimator_r<T, DIM>(sl, sr, ell, (T)s0[f], (T)c.s_ref[f], (T)c.flat_eps, (T)c.active_frac)
+                      : T(1);
         any = any || rs[f] > T(1.5);
     }
+    warp_count(a.counters, C_MLP_MISS, mlp_skip && any);
+    if (mlp_skip) {               // the learned call stands; the audit counts misses
+        any = false;
+#pragma unroll
+        for (int f = 0; f < F; ++f) rs[f] = T(1);
+    }
     double s1[F];
-    bool finite = true;
 #pragma unroll
     for (int f = 0; f < F; ++f) {
         T p;
@@ -158,9 +235,19 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
         }
         T rate = uw[f] - p * (uw[f] - lw[f]);
         s1[f] = __dadd_rn(s0[f], __dmul_rn(dt, (double)rate));   // no contraction: the oracle's rounding
-        finite = finite && isfinite(s1[f]);
         if (o.phi) o.phi[i * F + f] = (float)p;
         if (o.r) o.r[i * F + f] = (float)rs[f];
+    }
+    // safeguard: an update that leaves V or P non-positive or any field non-finite
+    // is not applied; the particle keeps its state and is counted
+    bool admissible = s1[0] > 0.0 && s1[F - 1] > 0.0;
+#pragma unroll
+    for (int f = 0; f < F; ++f) admissible = admissible && isfinite(s1[f]);
+    if (!admissible) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) s1[f] = s0[f];
+        atomicAdd(a.counters + C_NONFINITE, 1ull);
+        atomicOr(reinterpret_cast<unsigned int*>(a.counters + C_STATUS), ST_NONFINITE);
     }
     // mover, Eq. timeIntegrate
 #pragma unroll
@@ -178,11 +265,7 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     o.m[i] = a.sm[i];
     o.id[i] = idi;
     if (o.flag) o.flag[i] = any ? 1 : 0;
-    if (any) atomicAdd(a.counters + C_FLAGGED, 1ull);
-    if (!finite) {
-        atomicAdd(a.counters + C_NONFINITE, 1ull);
-        atomicOr(reinterpret_cast<unsigned int*>(a.counters + C_STATUS), ST_NONFINITE);
-    }
+    warp_count(a.counters, C_FLAGGED, any);
 }
 
 template <typename T, int DIM>

@@ -10,10 +10,14 @@
 namespace lp {
 
 constexpr int KMAX = 64;          // neighbour capacity compiled into the kernels
-constexpr int MORTON_BITS = 21;   // bits per axis of a Morton key (2D and 3D)
+constexpr int MORTON_BITS = 21;   // bits per axis of a Morton key (one simulation)
 constexpr int MAX_LEVELS = 22;    // cell levels 0..21
-constexpr int NB_WARPS = 8;       // warps per block of the neighbour query
+constexpr int NB_WARPS = 6;       // warps per block of the neighbour query (static smem <= 48 KB)
 constexpr int NB_CAP = 2 * KMAX;  // candidate buffer per warp
+// packed fit record: floats [0,3) position hi, [3,6) position lo,
+// [6,11) field hi, [11,16) field lo (fields V, u_1..u_d, P)
+constexpr int REC_F4 = 4;
+constexpr int REC_XH = 0, REC_XL = 3, REC_FH = 6, REC_FL = 11;
 
 // status bits kept in the device status word (1 << lp_status)
 constexpr uint32_t ST_CAPACITY = 1u << LP_ERR_CAPACITY;
@@ -27,12 +31,16 @@ constexpr uint32_t FIT_LINEAR = 1u, FIT_NONE = 2u, FIT_FP64 = 8u;
 // device counters (unsigned long long each)
 enum Counter {
     C_FLAGGED = 0, C_FP64, C_LINEAR, C_NOFIT, C_OVERFLOW, C_NONFINITE, C_MLP_UNCERTAIN,
-    C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_COUNT
+    C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_MLP_SKIP, C_MLP_MISS, C_COUNT
 };
 
 // method constants as the kernels see them
 struct DevCfg {
     int dim, precision, radius_mode, k_max, k_side, k_per_side, limiter, estimator, refine;
+    int mlp_audit;
+    float mlp_tau_lo;
+    int mbits;            // bits per axis of the Morton part of a key
+    int nsim_max;         // simulations per batched call (1: a single simulation)
     int periodic[3];
     double gamma, radius, kappa, flat_eps, active_frac, tau32, tau64;
     double s_ref[5];
@@ -46,9 +54,10 @@ struct DevCfg {
 struct Grid {
     double lo[3];         // quantisation origin
     double L;             // cube edge
-    double inv;           // 2^MORTON_BITS / L
+    double inv;           // 2^mbits / L
     int lmin, lmax;       // cell levels in use
-    int pad[2];
+    float lo_h[3], lo_l[3];   // origin as float hi/lo (FP32 query set-up)
+    float inv_f, L_f;
 };
 
 // ---------------------------------------------------------------------------
@@ -144,6 +153,14 @@ __device__ inline void count_add(unsigned long long* ctr, int which, unsigned lo
     if (v) atomicAdd(ctr + which, v);
 }
 
+// one atomic per warp: counts the active lanes with pred set
+__device__ inline void warp_count(unsigned long long* ctr, int which, bool pred)
+{
+    unsigned m = __activemask();
+    unsigned b = __ballot_sync(m, pred);
+    if (b && (int)(threadIdx.x & 31u) == __ffs(m) - 1) atomicAdd(ctr + which, (unsigned long long)__popc(b));
+}
+
 }  // namespace lp
 
 // ---------------------------------------------------------------------------
@@ -174,6 +191,8 @@ struct lp_ctx {
     float* lx[3];
     float* hf[5];
     float* lf[5];
+    float4* rec;              // packed per-particle fit record, REC_F4 float4 each
+    float4* pos4;             // [n][2] position hi / lo as float4 (neighbour query)
     // cell tables, neighbour lists
     unsigned long long* cells;
     uint32_t* nb_count;
@@ -183,14 +202,33 @@ struct lp_ctx {
     uint64_t* keys_sorted;    // points at keys[0] or keys[1] after the sort
     uint32_t* perm_sorted;    // matching permutation (sorted position -> input index)
     // grid, time step, counters
-    lp::Grid* grid;
-    double* dt_dev;
-    unsigned long long* dt_min;   // bit pattern of min(d2 / c^2)
+    lp::Grid* grid;               // one per simulation
+    double* dt_dev;               // one per simulation
+    unsigned long long* dt_min;   // per simulation: bit pattern of min(d2 / c^2)
+    unsigned long long* ext;      // per simulation: 8 extent words
+    int* grange;                  // [2] table levels in use over all simulations
+    int64_t* level_off_dev;
+    uint32_t* sim_of;             // simulation of each particle (input order)
+    const int64_t* offsets;       // batched call: device [nsim + 1] (null: one simulation)
+    int nsim;                     // simulations of the current call
     unsigned long long* counters;
     uint32_t* redo_list;
     int64_t n_lists;          // n of the last neighbour build (0: none)
     int tables_dirty;         // tables hold entries of the last build
     double reduce_min_w;
+    // learned estimator: FP32 master weights, BF16 copy used by the kernels, Adam
+    float* mlp_master;
+    void* mlp_bf16;
+    float* mlp_m1;
+    float* mlp_m2;
+    float* mlp_grad;
+    float* mlp_loss;
+    int64_t mlp_step;
+    int mlp_ready;
+    // captured step
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    int64_t graph_launches;       // kernels in one replay
     // launch accounting and optional phase timing
     int64_t launches;
     int profiling;

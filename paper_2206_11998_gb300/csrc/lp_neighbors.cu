@@ -21,12 +21,14 @@ constexpr float TOL_T = 4e-6f;   // relative gap below which two entries are re-
 struct QueryArgs {
     DevCfg c;
     int64_t n;
-    const Grid* g;
+    const Grid* g;            // one per simulation
+    const uint64_t* keys;     // key-sorted keys: simulation = key >> (dim mbits)
     const int64_t* level_off;
     const unsigned long long* cells;
     const double* sx[3];
     const float* hx[3];
     const float* lx[3];
+    const float4* pos4;       // [n][2]: position hi (xyz, 0), lo (xyz, 0)
     const double* sm;
     const double* sV;
     const uint32_t* sid;
@@ -47,6 +49,9 @@ __device__ inline double exact_d2(const QueryArgs& a, int64_t i, int64_t j)
     return d2;
 }
 
+constexpr int FCAP = 256;          // cells per frontier (current / next) per warp
+constexpr uint32_t DESC_MIN = 64;  // cells with more particles than this are split into children
+
 struct WarpBuf {
     unsigned long long key[NB_CAP];   // float bits of d2 << 32 | id
     uint32_t j[NB_CAP];
@@ -54,9 +59,34 @@ struct WarpBuf {
     uint32_t tie[NB_CAP / 32];        // bit e: entry e is within rounding of entry e-1
     uint32_t cstart[32];
     uint32_t cexcl[32];
+    unsigned long long front[2][FCAP];   // packed (level, unwrapped cell coordinates)
 };
 
 __device__ inline float key_d2(unsigned long long k) { return __uint_as_float((uint32_t)(k >> 32)); }
+
+// frontier cell: level l in bits 58..62; per axis k the wrapped coordinate
+// w_k in [0, 2^l) (17 bits at 17k) and the periodic image shift s_k in
+// {-1, 0, 1} (2 bits at 51 + 2k); the unwrapped coordinate is w_k + s_k 2^l.
+// A child keeps the shift: 2 (w + s 2^l) + b = (2w + b) + s 2^(l+1).
+__device__ inline unsigned long long pack_cell(int l, const int (&w)[3], const int (&sh)[3])
+{
+    unsigned long long e = (unsigned long long)l << 58;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e |= (unsigned long long)(w[k] & 0x1ffff) << (17 * k);
+        e |= (unsigned long long)(max(-1, min(1, sh[k])) + 1) << (51 + 2 * k);
+    }
+    return e;
+}
+__device__ inline void unpack_cell(unsigned long long e, int& l, int (&w)[3], int (&sh)[3])
+{
+    l = (int)((e >> 58) & 31u);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        w[k] = (int)((e >> (17 * k)) & 0x1ffffull);
+        sh[k] = (int)((e >> (51 + 2 * k)) & 3ull) - 1;
+    }
+}
 
 // Sort buf[0..m) by (d2, id) exactly; returns nothing, buffer sorted in place.
 template <int DIM>
@@ -126,6 +156,18 @@ __device__ void sort_exact(const QueryArgs& a, WarpBuf& b, int m, int64_t i)
     __syncwarp();
 }
 
+// Octree-style traversal of the per-level cell tables.  Cells start at the
+// finest level whose edge is >= R (at most 3 per axis) and are classified
+// lane-parallel from their box distances (in quantised units, with margins
+// that cover the float rounding):
+//   outside the radius                         -> skipped
+//   nearest point beyond the current k_max-th distance (no kept neighbour
+//   possible): entirely inside -> counted whole; otherwise counted by scanning
+//   or split
+//   large (> DESC_MIN particles, finer level available) -> split into children
+//   otherwise                                  -> candidates scanned
+// Split cells go to the next frontier, processed once the current one is done,
+// so the k_max-th distance found so far prunes them.
 template <int DIM>
 __global__ void __launch_bounds__(NB_WARPS * 32) k_query(QueryArgs a)
 {
@@ -136,146 +178,262 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_query(QueryArgs a)
     int64_t i = (int64_t)blockIdx.x * NB_WARPS + w;
     if (i >= a.n) return;
     const DevCfg& c = a.c;
-    const Grid& g = *a.g;
+    const int mb = c.mbits;
+    const uint64_t sim = c.nsim_max > 1 ? (a.keys[i] >> (DIM * mb)) : 0ull;
+    const Grid& g = a.g[sim];
     unsigned lt = (1u << lane) - 1u;
 
-    // own position and radius
-    double xi[3];
-    float hxi[3], lxi[3];
+    // own position and radius, all in FP32 (FP64 warp instructions are costly
+    // on this part: one occupies a sub-partition's FP64 pipe for ~64 cycles)
+    float hxi[3], lxi[3], tq[3];
+    const float inv = g.inv_f;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) { xi[k] = a.sx[k][i]; hxi[k] = a.hx[k][i]; lxi[k] = a.lx[k][i]; }
-    double wi = __dmul_rn(a.sm[i], a.sV[i]);
+    for (int k = 0; k < DIM; ++k) {
+        hxi[k] = a.hx[k][i]; lxi[k] = a.lx[k][i];
+        tq[k] = ((hxi[k] - g.lo_h[k]) + (lxi[k] - g.lo_l[k])) * inv;   // quantised units, error < 1
+    }
     float Rf;
     if (c.radius_mode == LP_RADIUS_FIXED) Rf = (float)c.radius;
     else {
-        float wf = (float)wi;
+        float wf = (float)a.sm[i] * (float)a.sV[i];
+        if (!(wf > 0.0f)) wf = 0.0f;
         float r = DIM == 3 ? cbrtf(wf) : (DIM == 2 ? sqrtf(wf) : wf);
         Rf = (float)c.kappa * r;
     }
+    if (!(Rf >= 0.0f) || isinf(Rf)) Rf = 0.0f;   // non-finite volume: no neighbours
     float R2f = (c.radius_mode == LP_RADIUS_FIXED) ? (float)(c.radius * c.radius) : Rf * Rf;
     float Rc = Rf * (1.0f + 1e-5f);
+    const float Rq = Rc * inv;
+    const float Rout = Rf * inv * (1.0f + 2e-5f) + 2.0f;   // boxes beyond: no neighbour
+    const float Rin = Rf * inv * (1.0f - 2e-5f) - 2.0f;    // boxes within: all neighbours
+    if (lane == 0) {   // the minimum image needs R < L/2 on periodic axes
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+            if (c.periodic[k] && 2.0f * Rq >= ldexpf(1.0f, mb))
+                atomicOr(reinterpret_cast<unsigned int*>(a.counters + C_STATUS), ST_ARG);
+    }
 
-    // level: finest with cell edge L / 2^l >= Rc
-    float Lf = (float)g.L;
-    int l = (int)floorf(log2f(Lf / Rc));
-    while (l > 0 && ldexpf(Lf, -l) < Rc) --l;
-    l = max(g.lmin, min(l, g.lmax));
-    double scale = ldexp(g.inv, -(MORTON_BITS - l));   // cells per unit length at level l
-    long long ncell_axis = 1ll << l;
-
+    // start level: finest with cell edge L / 2^l >= Rc / 2 (at most 5 cells per axis)
+    float Lf = g.L_f;
+    float Rh = 0.5f * Rc;
+    int l0 = Rh > 0.0f ? (int)floorf(log2f(Lf / Rh)) : g.lmax;
+    while (l0 > 0 && ldexpf(Lf, -l0) < Rh) --l0;
+    l0 = max(g.lmin, min(l0, g.lmax));
+    long long ncell_axis = 1ll << l0;
+    const float cell_scale = ldexpf(1.0f, -(mb - l0));
     long long clo[3] = {0, 0, 0};
     int nc[3] = {1, 1, 1};
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-        double lo_t = floor(__dmul_rn(__dsub_rn(__dsub_rn(xi[k], (double)Rc), g.lo[k]), scale));
-        double hi_t = floor(__dmul_rn(__dsub_rn(__dadd_rn(xi[k], (double)Rc), g.lo[k]), scale));
-        long long a0 = (long long)lo_t, a1 = (long long)hi_t;
+        long long a0 = (long long)floorf((tq[k] - Rq - 2.0f) * cell_scale);
+        long long a1 = (long long)floorf((tq[k] + Rq + 2.0f) * cell_scale);
         if (!c.periodic[k]) {
             a0 = max(0ll, min(a0, ncell_axis - 1));
             a1 = max(0ll, min(a1, ncell_axis - 1));
-            clo[k] = a0;
-            nc[k] = (int)(a1 - a0 + 1);
-        } else {
-            long long span = a1 - a0 + 1;
-            if (span > ncell_axis) span = ncell_axis;
-            clo[k] = a0;
-            nc[k] = (int)span;
+        } else if (a1 - a0 + 1 > ncell_axis) {
+            a1 = a0 + ncell_axis - 1;
         }
+        clo[k] = a0;
+        nc[k] = (int)(a1 - a0 + 1);
     }
     int ncells = nc[0] * nc[1] * nc[2];
-    if (ncells > 32) {   // cannot happen with cell edge >= radius; recorded, never silent
+    if (ncells > FCAP) {   // cannot happen with cell edge >= radius / 2; recorded, never silent
         if (lane == 0) atomicOr(reinterpret_cast<unsigned int*>(a.counters + C_STATUS), ST_ILLCOND);
-        ncells = 32;
+        ncells = FCAP;
     }
-
-    // cell ranges, one lane per cell
-    uint32_t cs = 0, cn = 0;
-    if ((int)lane < ncells) {
-        int t = lane;
-        uint32_t q[3] = {0, 0, 0};
+    for (int t = lane; t < ncells; t += 32) {
+        int u = t;
+        int wv[3] = {0, 0, 0}, shv[3] = {0, 0, 0};
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            long long v = clo[k] + (t % nc[k]);
-            t /= nc[k];
-            if (c.periodic[k]) v = ((v % ncell_axis) + ncell_axis) % ncell_axis;
-            q[k] = (uint32_t)v;
+            long long v = clo[k] + (u % nc[k]);     // unwrapped (periodic axes: within one period)
+            u /= nc[k];
+            long long wr = ((v % ncell_axis) + ncell_axis) % ncell_axis;
+            wv[k] = (int)wr;
+            shv[k] = (int)((v - wr) / ncell_axis);
         }
-        uint64_t code = morton<DIM>(q);
-        unsigned long long e = a.cells[a.level_off[l] + (int64_t)code];
-        cs = (uint32_t)e;
-        uint32_t ce = (uint32_t)(e >> 32);
-        cn = ce > cs ? ce - cs : 0;
+        b.front[0][t] = pack_cell(l0, wv, shv);
     }
-    uint32_t incl = cn;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((int)lane >= o) incl += v;
-    }
-    uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-    b.cstart[lane] = cs;
-    b.cexcl[lane] = incl - cn;
     __syncwarp();
 
+    const uint32_t total_cap = 4u * (uint32_t)c.k_max;   // the count before truncation saturates here
     int m = 0;                     // entries in the buffer
-    uint32_t inside_total = 0;
-    float cut = INFINITY;          // entries beyond this can no longer be kept
-    int nce = min(ncells, 32);
-    for (uint32_t base = 0; base < T; base += 32) {
-        if (m > NB_CAP - 32) {
-            sort_exact<DIM>(a, b, m, i);
-            m = min(m, c.k_max);
-            if (m == c.k_max) cut = key_d2(b.key[m - 1]) * (1.0f + TOL_T);
-        }
-        uint32_t t = base + lane;
-        bool in = false;
-        bool keep = false;
-        float d2f = 0.0f;
-        uint32_t j = 0;
-        if (t < T) {
-            int lo = 0, hi = nce - 1;      // last cell with cexcl <= t
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
+    uint32_t whole = 0;            // particles of cells counted whole (per lane)
+    uint32_t scanned_in = 0;       // scanned candidates inside the radius (warp-uniform)
+    float cut = INFINITY;          // entries beyond this (float d2) can no longer be kept
+    float cutq = INFINITY;         // the same distance in quantised units, with margin
+    int cur = 0, ncur = ncells;
+    while (ncur > 0) {
+        int nnext = 0;
+        for (int base0 = 0; base0 < ncur; base0 += 32) {
+            uint32_t counted = scanned_in;
+            {
+                uint32_t wsum = whole;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+                counted += wsum;
             }
-            j = b.cstart[lo] + (t - b.cexcl[lo]);
-            if ((int64_t)j != i) {
+            const bool count_done = counted >= total_cap;   // further cells matter only if keepable
+            // ---- classify one batch of cells, one lane per cell
+            int e = base0 + (int)lane;
+            uint32_t cs = 0, cn = 0;
+            int act = 0;           // 0 nothing to scan, 1 scan, 2 scan for the count only, 3 split
+            bool beyond = false;   // no particle of the cell can be kept
+            int l = 0, wv[3] = {0, 0, 0}, shv[3] = {0, 0, 0};
+            if (e < ncur) {
+                unpack_cell(b.front[cur][e], l, wv, shv);
+                uint32_t q[3] = {0, 0, 0};
+                float size = ldexpf(1.0f, mb - l);
+                float period = ldexpf(1.0f, mb);
+                float dmin2 = 0.0f, dmax2 = 0.0f;
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) {
-                    float dh = a.hx[k][j] - hxi[k];
-                    float dl = a.lx[k][j] - lxi[k];
-                    if (c.periodic[k]) {
-                        if (dh > 0.5f * c.Lper_h[k]) { dh -= c.Lper_h[k]; dl -= c.Lper_l[k]; }
-                        else if (dh < -0.5f * c.Lper_h[k]) { dh += c.Lper_h[k]; dl += c.Lper_l[k]; }
-                    }
-                    float d = dh + dl;
-                    d2f = fmaf(d, d, d2f);
+                    q[k] = (uint32_t)wv[k];
+                    float lo = (float)wv[k] * size + (float)shv[k] * period, hi = lo + size;
+                    float dn = fmaxf(0.0f, fmaxf(lo - tq[k], tq[k] - hi));
+                    float df = fmaxf(tq[k] - lo, hi - tq[k]);
+                    dmin2 += dn * dn;
+                    dmax2 += df * df;
                 }
-                if (d2f <= R2f * (1.0f - TOL_R)) in = true;
-                else if (d2f <= R2f * (1.0f + TOL_R)) in = inside64(c, DIM, exact_d2<DIM>(a, i, j), wi);
-                keep = in && d2f <= cut;
+                uint64_t code = (sim << (DIM * l)) | morton<DIM>(q);
+                unsigned long long ent = a.cells[a.level_off[l] + (int64_t)code];
+                cs = (uint32_t)ent;
+                uint32_t ce = (uint32_t)(ent >> 32);
+                cn = ce > cs ? ce - cs : 0;
+                float dmin = sqrtf(dmin2), dmax = sqrtf(dmax2);
+                bool splittable = cn > DESC_MIN && l < g.lmax;
+                beyond = dmin > cutq;
+                if (cn == 0 || dmin >= Rout) act = 0;
+                else if (beyond && (count_done || dmax <= Rin)) {
+                    if (!count_done) whole += cn;
+                    act = 0;
+                }
+                else if (splittable) act = 3;
+                else act = beyond ? 2 : 1;
             }
+            // ---- split cells: children into the next frontier; a cell that does
+            // not fit waits there unsplit; with no room at all it is scanned
+            const int nchild = 1 << DIM;
+            unsigned sm_ = __ballot_sync(0xffffffffu, act == 3);
+            int room = (FCAP - nnext) / nchild;
+            int nsplit = min(__popc(sm_), max(room, 0));
+            if (act == 3) {
+                int rank = __popc(sm_ & lt);
+                if (rank < room) {
+                    int pos = nnext + rank * nchild;
+                    for (int ch = 0; ch < nchild; ++ch) {
+                        int cw[3] = {2 * wv[0] + (ch & 1), DIM > 1 ? 2 * wv[1] + ((ch >> 1) & 1) : 0,
+                                     DIM > 2 ? 2 * wv[2] + ((ch >> 2) & 1) : 0};
+                        b.front[cur ^ 1][pos + ch] = pack_cell(l + 1, cw, shv);
+                    }
+                    act = 0;
+                }
+            }
+            int after = nnext + nsplit * nchild;
+            unsigned wait_ = __ballot_sync(0xffffffffu, act == 3);
+            if (act == 3) {
+                int rank = __popc(wait_ & lt);
+                if (after + rank < FCAP) {
+                    b.front[cur ^ 1][after + rank] = pack_cell(l, wv, shv);
+                    act = 0;
+                } else {
+                    act = beyond ? 2 : 1;
+                }
+            }
+            nnext = min(FCAP, after + __popc(wait_));
+            // ---- scanned cells: flatten their candidates over the lanes
+            uint32_t cnt = (act == 1 || act == 2) ? cn : 0;
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += v;
+            }
+            uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned co = __ballot_sync(0xffffffffu, act == 2);
+            b.cstart[lane] = cs;
+            b.cexcl[lane] = incl - cnt;
+            __syncwarp();
+            for (uint32_t base = 0; base < T; base += 32) {
+                if (m > NB_CAP - 32) {
+                    sort_exact<DIM>(a, b, m, i);
+                    m = min(m, c.k_max);
+                    if (m == c.k_max) {
+                        cut = key_d2(b.key[m - 1]) * (1.0f + TOL_T);
+                        cutq = sqrtf(cut) * inv * (1.0f + 2e-5f) + 1.0f;
+                    }
+                }
+                uint32_t t = base + lane;
+                bool in = false, keep = false;
+                float d2f = 0.0f;
+                uint32_t j = 0;
+                if (t < T) {
+                    int lo = 0, hi = 31;       // the last cell with cexcl <= t
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
+                    }
+                    j = b.cstart[lo] + (t - b.cexcl[lo]);
+                    bool count_only = (co >> lo) & 1u;
+                    if ((int64_t)j != i) {
+                        float4 ph = __ldg(a.pos4 + 2 * (int64_t)j), pl = __ldg(a.pos4 + 2 * (int64_t)j + 1);
+                        float hj[3] = {ph.x, ph.y, ph.z}, lj[3] = {pl.x, pl.y, pl.z};
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) {
+                            float dh = hj[k] - hxi[k];
+                            float dl = lj[k] - lxi[k];
+                            if (c.periodic[k]) {
+                                if (dh > 0.5f * c.Lper_h[k]) { dh -= c.Lper_h[k]; dl -= c.Lper_l[k]; }
+                                else if (dh < -0.5f * c.Lper_h[k]) { dh += c.Lper_h[k]; dl += c.Lper_l[k]; }
+                            }
+                            float d = dh + dl;
+                            d2f = fmaf(d, d, d2f);
+                        }
+                        if (d2f <= R2f * (1.0f - TOL_R)) in = true;
+                        else if (d2f <= R2f * (1.0f + TOL_R))
+                            in = inside64(c, DIM, exact_d2<DIM>(a, i, j), __dmul_rn(a.sm[i], a.sV[i]));
+                        keep = in && !count_only && d2f <= cut;
+                    }
+                }
+                scanned_in += __popc(__ballot_sync(0xffffffffu, in));
+                unsigned km = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    int pos = m + __popc(km & lt);
+                    b.key[pos] = ((unsigned long long)__float_as_uint(d2f) << 32) | a.sid[j];
+                    b.j[pos] = j;
+                }
+                m += __popc(km);
+                __syncwarp();
+            }
+            __syncwarp();
         }
-        inside_total += __popc(__ballot_sync(0xffffffffu, in));
-        unsigned km = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            int pos = m + __popc(km & lt);
-            b.key[pos] = ((unsigned long long)__float_as_uint(d2f) << 32) | a.sid[j];
-            b.j[pos] = j;
-        }
-        m += __popc(km);
+        cur ^= 1;
+        ncur = nnext;
         __syncwarp();
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) whole += __shfl_xor_sync(0xffffffffu, whole, o);
+    uint32_t inside_total = whole + scanned_in;
     sort_exact<DIM>(a, b, m, i);
     int cnt = min(m, c.k_max);
     for (int e = lane; e < cnt; e += 32) a.idx[i * (int64_t)c.k_max + e] = b.j[e];
     if (lane == 0) {
         a.count[i] = (uint32_t)cnt;
-        a.total[i] = inside_total;
-        a.d2min[i] = cnt > 0 ? exact_d2<DIM>(a, i, b.j[0]) : INFINITY;
+        a.total[i] = min(inside_total, total_cap);
         if (inside_total > (uint32_t)c.k_max) atomicAdd(a.counters + C_OVERFLOW, 1ull);
         atomicMax(a.counters + C_MAXCOUNT, (unsigned long long)inside_total);
     }
+}
+
+// exact FP64 squared distance to the first (nearest) list entry, one thread per
+// particle
+template <int DIM>
+__global__ void k_d2min(QueryArgs a)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    uint32_t cnt = a.count[i];
+    a.d2min[i] = cnt > 0 ? exact_d2<DIM>(a, i, a.idx[i * (int64_t)a.c.k_max]) : INFINITY;
 }
 
 // 1D, k nearest per side on the exactly x-ordered particles
@@ -341,12 +499,14 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     a.c = c->dc;
     a.n = n;
     a.g = c->grid;
-    a.level_off = reinterpret_cast<const int64_t*>(c->dt_min + 16);
+    a.keys = c->keys_sorted;
+    a.level_off = c->level_off_dev;
     a.cells = c->cells;
     for (int k = 0; k < 3; ++k) {
         int kk = k < c->dc.dim ? k : 0;
         a.sx[k] = c->sx[kk]; a.hx[k] = c->hx[kk]; a.lx[k] = c->lx[kk];
     }
+    a.pos4 = c->pos4;
     a.sm = c->sm; a.sV = c->sV; a.sid = c->sid;
     a.count = c->nb_count; a.total = c->nb_total; a.idx = c->nb_idx; a.d2min = c->nb_d2min;
     a.counters = c->counters;
@@ -354,9 +514,10 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
         k_query_kside<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
     } else {
         unsigned blocks = (unsigned)((n + NB_WARPS - 1) / NB_WARPS);
-        if (c->dc.dim == 3) k_query<3><<<blocks, NB_WARPS * 32, 0, s>>>(a);
-        else if (c->dc.dim == 2) k_query<2><<<blocks, NB_WARPS * 32, 0, s>>>(a);
-        else k_query<1><<<blocks, NB_WARPS * 32, 0, s>>>(a);
+        unsigned tb = (unsigned)((n + 255) / 256);
+        if (c->dc.dim == 3) { k_query<3><<<blocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<3><<<tb, 256, 0, s>>>(a); }
+        else if (c->dc.dim == 2) { k_query<2><<<blocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<2><<<tb, 256, 0, s>>>(a); }
+        else { k_query<1><<<blocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<1><<<tb, 256, 0, s>>>(a); }
     }
     return cudaGetLastError();
 }

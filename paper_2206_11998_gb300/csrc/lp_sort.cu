@@ -24,54 +24,83 @@ __device__ inline double from_order_key(unsigned long long k)
     return __longlong_as_double((long long)b);
 }
 
-// ext[0..2] min x_k, ext[3..5] max x_k, ext[6] min w, ext[7] max w (order keys)
+// ext[8 s + 0..2] min x_k, [8 s + 3..5] max x_k, [8 s + 6] min w, [8 s + 7] max w
+// (order keys) of simulation s.  One simulation: grid-stride accumulation and a
+// warp reduction; several: one particle per thread, reduced over the warp when
+// the warp's particles share a simulation (they are stored by simulation).
 __global__ void k_reduce_extent(int dim, int64_t n, const double* __restrict__ x0,
                                 const double* __restrict__ x1, const double* __restrict__ x2,
                                 const double* __restrict__ m, const double* __restrict__ V,
-                                unsigned long long* ext)
+                                const uint32_t* __restrict__ sim_of, unsigned long long* ext)
 {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     double wlo = INFINITY, whi = -INFINITY;
     const double* xs[3] = {x0, x1, x2};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        for (int k = 0; k < dim; ++k) {
-            double v = xs[k][i];
-            lo[k] = fmin(lo[k], v);
-            hi[k] = fmax(hi[k], v);
+    uint32_t sim = 0;
+    if (!sim_of) {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            for (int k = 0; k < dim; ++k) {
+                double v = xs[k][i];
+                lo[k] = fmin(lo[k], v);
+                hi[k] = fmax(hi[k], v);
+            }
+            double w = __dmul_rn(m[i], V[i]);
+            wlo = fmin(wlo, w);
+            whi = fmax(whi, w);
         }
-        double w = __dmul_rn(m[i], V[i]);
-        wlo = fmin(wlo, w);
-        whi = fmax(whi, w);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        for (int k = 0; k < 3; ++k) {
-            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    } else {
+        int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (i < n) {
+            sim = sim_of[i];
+            for (int k = 0; k < dim; ++k) { lo[k] = xs[k][i]; hi[k] = lo[k]; }
+            wlo = whi = __dmul_rn(m[i], V[i]);
+        } else {
+            sim = 0xffffffffu;
         }
-        wlo = fmin(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
-        whi = fmax(whi, __shfl_xor_sync(0xffffffffu, whi, o));
     }
-    if (lane_id() == 0) {
-        for (int k = 0; k < dim; ++k) {
-            atomic_min_d(ext + k, lo[k]);
-            atomic_max_d(ext + 3 + k, hi[k]);
+    uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
+    bool uniform = __all_sync(0xffffffffu, sim == s0 || sim == 0xffffffffu);
+    if (uniform) {
+        for (int o = 16; o > 0; o >>= 1) {
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            }
+            wlo = fmin(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
+            whi = fmax(whi, __shfl_xor_sync(0xffffffffu, whi, o));
         }
-        atomic_min_d(ext + 6, wlo);
-        atomic_max_d(ext + 7, whi);
+        if (lane_id() != 0 || s0 == 0xffffffffu) return;
+        sim = s0;
+    } else if (sim == 0xffffffffu) {
+        return;
     }
+    unsigned long long* e = ext + 8 * (int64_t)sim;
+    for (int k = 0; k < dim; ++k) {
+        atomic_min_d(e + k, lo[k]);
+        atomic_max_d(e + 3 + k, hi[k]);
+    }
+    atomic_min_d(e + 6, wlo);
+    atomic_max_d(e + 7, whi);
 }
 
-__global__ void k_init_extent(unsigned long long* ext)
+__global__ void k_init_extent(unsigned long long* ext, int nsim)
 {
-    int t = threadIdx.x;
-    if (t < 8) ext[t] = (t < 3 || t == 6) ? ~0ull : 0ull;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 8 * nsim) {
+        int w = t & 7;
+        ext[t] = (w < 3 || w == 6) ? ~0ull : 0ull;
+    }
 }
 
 // Bounding cube and the range of cell levels.  A particle of radius R queries
 // the finest level whose cell edge L / 2^l is at least R; lmax/lmin are those
 // levels for the smallest/largest radius present.
-__global__ void k_finalize_grid(DevCfg c, int lmax_cap, const unsigned long long* ext, Grid* g)
+__global__ void k_finalize_grid(DevCfg c, int lmax_cap, int nsim, const unsigned long long* ext_all, Grid* grids)
 {
+    int sim = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sim >= nsim) return;
+    const unsigned long long* ext = ext_all + 8 * sim;
+    Grid* g = grids + sim;
     double L = 0.0;
     for (int k = 0; k < c.dim; ++k) {
         double lo, ext_k;
@@ -83,7 +112,10 @@ __global__ void k_finalize_grid(DevCfg c, int lmax_cap, const unsigned long long
     for (int k = c.dim; k < 3; ++k) g->lo[k] = 0.0;
     if (!(L > 0.0)) L = 1.0;
     g->L = L;
-    g->inv = __ddiv_rn(ldexp(1.0, MORTON_BITS), L);
+    g->inv = __ddiv_rn(ldexp(1.0, c.mbits), L);
+    for (int k = 0; k < 3; ++k) split(g->lo[k], g->lo_h[k], g->lo_l[k]);
+    g->inv_f = (float)g->inv;
+    g->L_f = (float)L;
     double rmin, rmax;
     if (c.radius_mode == LP_RADIUS_FIXED) { rmin = rmax = c.radius; }
     else {
@@ -95,6 +127,8 @@ __global__ void k_finalize_grid(DevCfg c, int lmax_cap, const unsigned long long
     // particle's level inside [lmin, lmax]
     rmin *= 1.0 - 1e-4;
     rmax *= 1.0 + 1e-4;
+    if (!(rmin > 0.0)) rmin = L * ldexp(1.0, -lmax_cap);   // empty or degenerate simulation
+    if (!(rmax > 0.0) || isinf(rmax)) rmax = L;
     int lmax = (int)floor(log2(L / rmin));
     int lmin = (int)floor(log2(L / rmax));
     lmax = max(0, min(lmax, lmax_cap));
@@ -103,9 +137,23 @@ __global__ void k_finalize_grid(DevCfg c, int lmax_cap, const unsigned long long
     g->lmin = lmin;
 }
 
+// table levels in use over all simulations
+__global__ void k_grid_range(int nsim, const Grid* grids, int* grange)
+{
+    int lo = 1 << 20, hi = 0;
+    for (int s = 0; s < nsim; ++s) {
+        lo = min(lo, grids[s].lmin);
+        hi = max(hi, grids[s].lmax);
+    }
+    grange[0] = lo;
+    grange[1] = hi;
+}
+
+// key = simulation << (DIM mbits) | Morton code of the quantised position
 template <int DIM>
 __global__ void k_keys(int64_t n, const double* __restrict__ x0, const double* __restrict__ x1,
-                       const double* __restrict__ x2, const Grid* __restrict__ g,
+                       const double* __restrict__ x2, const Grid* __restrict__ grids,
+                       const uint32_t* __restrict__ sim_of, int mbits,
                        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -116,8 +164,10 @@ __global__ void k_keys(int64_t n, const double* __restrict__ x0, const double* _
         return;
     }
     const double* xs[3] = {x0, x1, x2};
+    uint32_t sim = sim_of ? sim_of[i] : 0u;
+    const Grid* g = grids + sim;
     double inv = g->inv;
-    const double qmax = (double)((1u << MORTON_BITS) - 1u);
+    const double qmax = (double)((1u << mbits) - 1u);
     uint32_t q[3] = {0, 0, 0};
     for (int k = 0; k < DIM; ++k) {
         double t = __dmul_rn(__dsub_rn(xs[k][i], g->lo[k]), inv);
@@ -128,7 +178,7 @@ __global__ void k_keys(int64_t n, const double* __restrict__ x0, const double* _
         else v = (uint32_t)f;
         q[k] = v;
     }
-    keys[i] = morton<DIM>(q);
+    keys[i] = ((uint64_t)sim << (DIM * mbits)) | morton<DIM>(q);
     vals[i] = (uint32_t)i;
 }
 
@@ -223,11 +273,14 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_partic
                          double* su2, double* sP, double* sm, uint32_t* sid,
                          float* hx0, float* hx1, float* hx2, float* lx0, float* lx1, float* lx2,
                          float* hf0, float* hf1, float* hf2, float* hf3, float* hf4,
-                         float* lf0, float* lf1, float* lf2, float* lf3, float* lf4)
+                         float* lf0, float* lf1, float* lf2, float* lf3, float* lf4, float4* rec, float4* pos4)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t j = perm[i];
+    float r[4 * REC_F4];
+#pragma unroll
+    for (int q = 0; q < 4 * REC_F4; ++q) r[q] = 0.0f;
     double* sx[3] = {sx0, sx1, sx2};
     double* su[3] = {su0, su1, su2};
     float* hx[3] = {hx0, hx1, hx2};
@@ -238,26 +291,35 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_partic
     for (int k = 0; k < DIM; ++k) {
         double v = p.x[k][j];
         sx[k][i] = v;
-        split(v, hx[k][i], lx[k][i]);
+        split(v, r[REC_XH + k], r[REC_XL + k]);
+        hx[k][i] = r[REC_XH + k];
+        lx[k][i] = r[REC_XL + k];
     }
     double V = p.V[j], P = p.P[j];
     sV[i] = V;
     sP[i] = P;
-    split(V, hf[0][i], lf[0][i]);
-    split(P, hf[DIM + 1][i], lf[DIM + 1][i]);
+    split(V, r[REC_FH], r[REC_FL]);
+    split(P, r[REC_FH + DIM + 1], r[REC_FL + DIM + 1]);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         double v = p.u[k][j];
         su[k][i] = v;
-        split(v, hf[1 + k][i], lf[1 + k][i]);
+        split(v, r[REC_FH + 1 + k], r[REC_FL + 1 + k]);
     }
+#pragma unroll
+    for (int f = 0; f < DIM + 2; ++f) { hf[f][i] = r[REC_FH + f]; lf[f][i] = r[REC_FL + f]; }
+#pragma unroll
+    for (int q = 0; q < REC_F4; ++q) rec[i * REC_F4 + q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    pos4[2 * i] = make_float4(r[REC_XH], r[REC_XH + 1], r[REC_XH + 2], 0.0f);
+    pos4[2 * i + 1] = make_float4(r[REC_XL], r[REC_XL + 1], r[REC_XL + 2], 0.0f);
     sm[i] = p.m[j];
     sid[i] = p.id[j];
 }
 
 // cell tables: entry = start | end << 32 of the key-sorted particles in the cell
-__global__ void k_tables(int dim, int64_t n, const uint64_t* __restrict__ keys, const Grid* __restrict__ g,
-                         const int64_t* __restrict__ level_off, unsigned long long* cells, int clear)
+__global__ void k_tables(int dim, int mbits, int64_t n, const uint64_t* __restrict__ keys,
+                         const int* __restrict__ grange, const int64_t* __restrict__ level_off,
+                         unsigned long long* cells, int clear)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -265,8 +327,8 @@ __global__ void k_tables(int dim, int64_t n, const uint64_t* __restrict__ keys, 
     uint64_t kp = i > 0 ? keys[i - 1] : 0;
     uint64_t kn = i + 1 < n ? keys[i + 1] : 0;
     uint32_t* half = reinterpret_cast<uint32_t*>(cells);
-    for (int l = g->lmin; l <= g->lmax; ++l) {
-        int sh = dim * (MORTON_BITS - l);
+    for (int l = grange[0]; l <= grange[1]; ++l) {
+        int sh = dim * (mbits - l);
         uint64_t c = k >> sh;
         bool first = i == 0 || (kp >> sh) != c;
         bool last = i + 1 == n || (kn >> sh) != c;
@@ -300,18 +362,37 @@ __global__ void k_scatter_back(int dim, int64_t n, lp_particles p, const double*
 
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+__global__ void k_sim_of(int64_t n, const int64_t* __restrict__ offsets, int nsim, uint32_t* __restrict__ sim_of)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nsim - 1;          // last simulation whose offset is <= i
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    sim_of[i] = (uint32_t)lo;
+}
+
 }  // namespace
 
 cudaError_t build_grid(lp_ctx* c, const lp_particles* p, cudaStream_t s)
 {
-    unsigned long long* ext = c->dt_min + 1;   // 8 scratch words after dt_min
-    k_init_extent<<<1, 32, 0, s>>>(ext);
     int64_t n = p->n;
-    int64_t nb_ = grid_for(n, 256); unsigned blocks = (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
+    int nsim = c->nsim;
+    const uint32_t* sim_of = nullptr;
+    if (nsim > 1) {
+        k_sim_of<<<grid_for(n, 256), 256, 0, s>>>(n, c->offsets, nsim, c->sim_of);
+        sim_of = c->sim_of;
+    }
+    k_init_extent<<<(unsigned)((8 * nsim + 255) / 256), 256, 0, s>>>(c->ext, nsim);
+    int64_t nb_ = grid_for(n, 256);
+    unsigned blocks = nsim > 1 ? (unsigned)nb_ : (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
     if (blocks == 0) blocks = 1;
     k_reduce_extent<<<blocks, 256, 0, s>>>(c->dc.dim, n, p->x[0], p->x[1] ? p->x[1] : p->x[0],
-                                           p->x[2] ? p->x[2] : p->x[0], p->m, p->V, ext);
-    k_finalize_grid<<<1, 1, 0, s>>>(c->dc, c->lmax_cap, ext, c->grid);
+                                           p->x[2] ? p->x[2] : p->x[0], p->m, p->V, sim_of, c->ext);
+    k_finalize_grid<<<(unsigned)((nsim + 127) / 128), 128, 0, s>>>(c->dc, c->lmax_cap, nsim, c->ext, c->grid);
+    k_grid_range<<<1, 1, 0, s>>>(nsim, c->grid, c->grange);
     return cudaGetLastError();
 }
 
@@ -321,10 +402,12 @@ cudaError_t make_keys(lp_ctx* c, const lp_particles* p, cudaStream_t s)
     int dim = c->dc.dim;
     const double* x1 = p->x[1] ? p->x[1] : p->x[0];
     const double* x2 = p->x[2] ? p->x[2] : p->x[0];
+    const uint32_t* sim_of = c->nsim > 1 ? c->sim_of : nullptr;
+    int mb = c->dc.mbits;
     unsigned gb = grid_for(n, 256);
-    if (dim == 3) k_keys<3><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, c->keys[0], c->vals[0]);
-    else if (dim == 2) k_keys<2><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, c->keys[0], c->vals[0]);
-    else k_keys<1><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, c->keys[0], c->vals[0]);
+    if (dim == 3) k_keys<3><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, sim_of, mb, c->keys[0], c->vals[0]);
+    else if (dim == 2) k_keys<2><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, sim_of, mb, c->keys[0], c->vals[0]);
+    else k_keys<1><<<gb, 256, 0, s>>>(n, p->x[0], x1, x2, c->grid, sim_of, mb, c->keys[0], c->vals[0]);
     return cudaGetLastError();
 }
 
@@ -356,7 +439,7 @@ cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s)
     for (int k = dim; k < 3; ++k) { q.x[k] = p->x[0]; q.u[k] = p->u[0]; }
 #define LP_GATHER_ARGS n, perm, q, c->sx[0], c->sx[1], c->sx[2], c->sV, c->su[0], c->su[1], c->su[2], c->sP, \
         c->sm, c->sid, c->hx[0], c->hx[1], c->hx[2], c->lx[0], c->lx[1], c->lx[2], c->hf[0], c->hf[1],     \
-        c->hf[2], c->hf[3], c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4]
+        c->hf[2], c->hf[3], c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec, c->pos4
     if (dim == 3) k_gather<3><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
     else if (dim == 2) k_gather<2><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
     else k_gather<1><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
@@ -367,9 +450,8 @@ cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s)
 cudaError_t fill_tables(lp_ctx* c, int64_t n, bool clear, cudaStream_t s)
 {
     if (c->dc.dim == 1 || n == 0) return cudaSuccess;
-    k_tables<<<grid_for(n, 256), 256, 0, s>>>(c->dc.dim, n, c->keys_sorted, c->grid,
-                                               reinterpret_cast<const int64_t*>(c->dt_min + 16), c->cells,
-                                               clear ? 1 : 0);
+    k_tables<<<grid_for(n, 256), 256, 0, s>>>(c->dc.dim, c->dc.mbits, n, c->keys_sorted, c->grange,
+                                               c->level_off_dev, c->cells, clear ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -474,6 +556,8 @@ extern "C" lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double* 
     dc.dim = dim;
     dc.radius_mode = LP_RADIUS_FIXED;
     dc.radius = 1.0;
+    dc.mbits = MORTON_BITS;
+    dc.nsim_max = 1;
     int lmax_cap = dim == 3 ? 9 : (dim == 2 ? 13 : 0);
     int lo_bit = 0, hi_bit = 64;
     if (dim > 1) {
@@ -483,12 +567,12 @@ extern "C" lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double* 
     unsigned gb = grid_for(n, 256);
     int64_t nb_ = gb;
     unsigned rblocks = (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
-    k_init_extent<<<1, 32, 0, s>>>(ext);
-    k_reduce_extent<<<rblocks, 256, 0, s>>>(dim, n, x0, p1, p2, x0, x0, ext);
-    k_finalize_grid<<<1, 1, 0, s>>>(dc, lmax_cap, ext, grid);
-    if (dim == 3) k_keys<3><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, keys[0], vals[0]);
-    else if (dim == 2) k_keys<2><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, keys[0], vals[0]);
-    else k_keys<1><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, keys[0], vals[0]);
+    k_init_extent<<<1, 32, 0, s>>>(ext, 1);
+    k_reduce_extent<<<rblocks, 256, 0, s>>>(dim, n, x0, p1, p2, x0, x0, nullptr, ext);
+    k_finalize_grid<<<1, 1, 0, s>>>(dc, lmax_cap, 1, ext, grid);
+    if (dim == 3) k_keys<3><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
+    else if (dim == 2) k_keys<2><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
+    else k_keys<1><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
     int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
     int cur = 0;
     for (int sh = lo_bit; sh < hi_bit; sh += 8) {

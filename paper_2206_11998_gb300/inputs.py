@@ -108,17 +108,32 @@ GAS_CLOUD_SIGMA2 = 0.05          # particle positions ~ N(0, 0.05 I)
 GAS_CLOUD_GAMMA = 5.0 / 3.0
 
 
-def gas_cloud_3d(n: int = 2_000_000, seed: int = 4, gamma: float = GAS_CLOUD_GAMMA):
+def gas_cloud_3d(n: int = 2_000_000, seed: int = 4, gamma: float = GAS_CLOUD_GAMMA, r_max_sigma: float = 4.0):
     """Gaussian gas cloud at rest: rho = exp(-r^2/0.1), p = rho^gamma, u = 0.
 
-    Positions are drawn from N(0, 0.05 I) -- the normalised density -- and every
-    particle carries mass M/n with M = (0.1 pi)^(3/2) the total mass.
+    Positions are drawn from N(0, 0.05 I) -- the normalised density -- truncated
+    to r <= r_max_sigma * sigma (sigma = sqrt(0.05); rejected draws are redrawn
+    from the same stream), and every particle carries mass M/n with M the mass of
+    the truncated cloud.  The truncation keeps the edge at a density contrast of
+    about exp(-r_max_sigma^2 / 2) instead of a handful of far, isolated particles.
     """
+    import math
     rng = np.random.Generator(np.random.PCG64(seed))
-    pts = rng.normal(0.0, np.sqrt(GAS_CLOUD_SIGMA2), size=(3, n))
+    sig = np.sqrt(GAS_CLOUD_SIGMA2)
+    rmax2 = (r_max_sigma * sig) ** 2 if r_max_sigma else np.inf
+    parts, have = [], 0
+    while have < n:
+        draw = rng.normal(0.0, sig, size=(3, max(1024, int((n - have) * 1.01) + 64)))
+        keep = draw[:, (draw * draw).sum(axis=0) <= rmax2]
+        parts.append(keep)
+        have += keep.shape[1]
+    pts = np.concatenate(parts, axis=1)[:, :n]
     r2 = (pts * pts).sum(axis=0)
     rho = np.exp(-r2 / (2.0 * GAS_CLOUD_SIGMA2))
-    M = (2.0 * GAS_CLOUD_SIGMA2 * np.pi) ** 1.5
+    a = r_max_sigma if r_max_sigma else np.inf
+    inside = 1.0 if not np.isfinite(a) else (math.erf(a / math.sqrt(2.0)) -
+                                              math.sqrt(2.0 / math.pi) * a * math.exp(-a * a / 2.0))
+    M = (2.0 * GAS_CLOUD_SIGMA2 * np.pi) ** 1.5 * inside
     zeros = np.zeros(n)
     return _state([pts[0], pts[1], pts[2]], 1.0 / rho, [zeros, zeros.copy(), zeros.copy()],
                   rho ** gamma, np.full(n, M / n))

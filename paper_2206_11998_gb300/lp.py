@@ -27,8 +27,11 @@ EXPORTED = [
     "lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs", "lp_step",
     "lp_export_neighbors", "lp_grid_info", "lp_dt_device", "lp_get_stats", "lp_reset_stats",
     "lp_status_string", "lp_version", "lp_set_profiling", "lp_phase_times", "lp_phase_name",
-    "lp_sort_keys_noalloc",
+    "lp_sort_keys_noalloc", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step",
+    "lp_mlp_train", "lp_mlp_infer", "lp_step_batched", "lp_graph_capture", "lp_graph_launch",
 ]
+MLP_IN, MLP_H = 8, 32
+MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H + 1
 NOALLOC_MAX_N = 262144
 NPHASES = 8
 
@@ -49,6 +52,7 @@ class Config(C.Structure):
         ("periodic", C.c_int32 * 3), ("max_level", C.c_int32),
         ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("n_fluid", C.c_int64), ("capacity", C.c_int64),
+        ("mlp_tau_lo", C.c_double), ("mlp_audit", C.c_int32), ("max_sims", C.c_int32),
     ]
 
 
@@ -66,14 +70,15 @@ class Stats(C.Structure):
     _fields_ = [("dt", C.c_double), ("steps", C.c_int64), ("n_flagged", C.c_int64),
                 ("n_fp64_redo", C.c_int64), ("n_linear", C.c_int64), ("n_nofit", C.c_int64),
                 ("n_overflow", C.c_int64), ("n_nonfinite", C.c_int64), ("n_mlp_uncertain", C.c_int64),
-                ("max_count", C.c_uint32), ("status", C.c_uint32), ("kernel_launches", C.c_int64)]
+                ("max_count", C.c_uint32), ("status", C.c_uint32), ("kernel_launches", C.c_int64),
+                ("n_mlp_skip", C.c_int64), ("n_mlp_miss", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class StepDiag(C.Structure):
-    _fields_ = [("flag", C.c_void_p), ("phi", C.c_void_p), ("r", C.c_void_p)]
+    _fields_ = [("flag", C.c_void_p), ("phi", C.c_void_p), ("r", C.c_void_p), ("features", C.c_void_p)]
 
 
 _lib = None
@@ -101,6 +106,13 @@ def lib():
         L.lp_gfd_derivs.argtypes = [P, C.POINTER(Particles), C.POINTER(C.c_void_p), C.c_int32, C.c_int32, P, P, P]
         L.lp_onesided_derivs.argtypes = [P, C.POINTER(Particles), C.POINTER(C.c_void_p), C.c_int32, P, P]
         L.lp_step.argtypes = [P, C.POINTER(Particles), C.c_double, C.c_double, P, C.POINTER(StepDiag), P]
+        L.lp_step_batched.argtypes = [P, C.POINTER(Particles), P, C.c_int32, C.c_double, C.c_double, P,
+                                      C.POINTER(StepDiag), P]
+        L.lp_step_batched.restype = C.c_int
+        L.lp_graph_capture.argtypes = [P, C.POINTER(Particles), P, C.c_int32, C.c_double, C.c_double, P, P]
+        L.lp_graph_capture.restype = C.c_int
+        L.lp_graph_launch.argtypes = [P, P]
+        L.lp_graph_launch.restype = C.c_int
         L.lp_export_neighbors.argtypes = [P, P, P, P, P, P, P]
         L.lp_grid_info.argtypes = [P, P, P]
         L.lp_dt_device.argtypes = [P]
@@ -116,6 +128,15 @@ def lib():
         L.lp_phase_name.restype = C.c_char_p
         L.lp_sort_keys_noalloc.argtypes = [C.c_int32, C.c_int64, P, P, P, P, P, P]
         L.lp_sort_keys_noalloc.restype = C.c_int
+        L.lp_mlp_set_params.argtypes = [P, P]
+        L.lp_mlp_get_params.argtypes = [P, P, P]
+        L.lp_mlp_grad.argtypes = [P, P, P, C.c_int64, C.c_double, P, P, P]
+        L.lp_mlp_adam_step.argtypes = [P, P, C.c_double, P]
+        L.lp_mlp_train.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_double, P, P]
+        L.lp_mlp_infer.argtypes = [P, P, C.c_int64, P, P]
+        for name in ("lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step", "lp_mlp_train",
+                     "lp_mlp_infer"):
+            getattr(L, name).restype = C.c_int
         for name in ("lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs",
                      "lp_step", "lp_export_neighbors", "lp_grid_info", "lp_get_stats", "lp_reset_stats",
                      "lp_set_profiling", "lp_phase_times"):
@@ -141,8 +162,9 @@ def _ptr(t):
 
 def make_config(dim, capacity, precision=PREC_FP32, radius_mode=RADIUS_VOLUME, radius=0.0, kappa=2.2,
                 k_max=64, k_side=8, k_per_side=4, gamma=1.4, limiter=LIM_FLAGGED, estimator=EST_PLAIN,
-                flat_eps=1e-6, active_frac=0.1, s_ref=(0, 0, 0, 0, 0), tau32=1e-3, tau64=1e-12,
-                periodic=(0, 0, 0), box_lo=(0, 0, 0), box_hi=(1, 1, 1), n_fluid=2**62, max_level=0) -> Config:
+                flat_eps=1e-6, active_frac=0.5, s_ref=(0, 0, 0, 0, 0), tau32=1e-3, tau64=1e-12,
+                periodic=(0, 0, 0), box_lo=(0, 0, 0), box_hi=(1, 1, 1), n_fluid=2**62, max_level=0,
+                mlp_tau_lo=0.05, mlp_audit=0, max_sims=1) -> Config:
     c = Config()
     c.dim, c.precision, c.radius_mode, c.k_max, c.k_side = dim, precision, radius_mode, k_max, k_side
     c.k_per_side, c.limiter, c.estimator = k_per_side, limiter, estimator
@@ -155,6 +177,7 @@ def make_config(dim, capacity, precision=PREC_FP32, radius_mode=RADIUS_VOLUME, r
         c.box_lo[k] = float(box_lo[k])
         c.box_hi[k] = float(box_hi[k])
     c.n_fluid, c.capacity = int(n_fluid), int(capacity)
+    c.mlp_tau_lo, c.mlp_audit, c.max_sims = float(mlp_tau_lo), int(mlp_audit), int(max_sims)
     return c
 
 
@@ -199,6 +222,14 @@ class ParticleSet:
             p.u[k] = self.u[k].data_ptr() if k < self.dim else None
         p.V, p.P, p.m, p.id = self.V.data_ptr(), self.P.data_ptr(), self.m.data_ptr(), self.id.data_ptr()
         return p
+
+
+def mlp_init_params(seed):
+    """He-initialised parameters (W1, b1 = 0, w2, b2 = 0) from a seeded generator."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W1 = rng.normal(0.0, np.sqrt(2.0 / MLP_IN), size=(MLP_H, MLP_IN))
+    w2 = rng.normal(0.0, np.sqrt(1.0 / MLP_H), size=MLP_H)
+    return np.concatenate([W1.ravel(), np.zeros(MLP_H), w2, [0.0]]).astype(np.float32)
 
 
 def sort_keys_noalloc(x, keys_out, perm_out, stream=None):
@@ -273,13 +304,35 @@ class Context:
                "lp_onesided_derivs")
         return out
 
-    def step(self, ps: ParticleSet, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None, stream=None):
+    def step(self, ps: ParticleSet, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None, features=None,
+             stream=None):
         p = ps.struct()
         d = StepDiag()
         d.flag, d.phi, d.r = (_ptr(flag) if flag is not None else None, _ptr(phi) if phi is not None else None,
                               _ptr(r) if r is not None else None)
+        d.features = _ptr(features) if features is not None else None
         _check(lib().lp_step(self.h, C.byref(p), float(dt), float(cfl), _ptr(t), C.byref(d), _stream(stream)),
                "lp_step")
+
+    def step_batched(self, ps: ParticleSet, offsets, nsim, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None,
+                     features=None, stream=None):
+        """One step of nsim simulations stored back to back; offsets: device int64 [nsim + 1]."""
+        p = ps.struct()
+        d = StepDiag()
+        d.flag, d.phi, d.r = (_ptr(flag) if flag is not None else None, _ptr(phi) if phi is not None else None,
+                              _ptr(r) if r is not None else None)
+        d.features = _ptr(features) if features is not None else None
+        _check(lib().lp_step_batched(self.h, C.byref(p), _ptr(offsets), int(nsim), float(dt), float(cfl), _ptr(t),
+                                     C.byref(d), _stream(stream)), "lp_step_batched")
+
+    def graph_capture(self, ps: ParticleSet, offsets=None, nsim=1, dt=0.0, cfl=0.4, t=None, stream=None):
+        """Capture one (batched) step into a CUDA graph on `stream` (a created stream)."""
+        self._graph_ps = ps.struct()      # the captured addresses must stay alive
+        _check(lib().lp_graph_capture(self.h, C.byref(self._graph_ps), _ptr(offsets), int(nsim), float(dt),
+                                      float(cfl), _ptr(t), _stream(stream)), "lp_graph_capture")
+
+    def graph_launch(self, stream=None):
+        _check(lib().lp_graph_launch(self.h, _stream(stream)), "lp_graph_launch")
 
     def stats(self, stream=None) -> dict:
         s = Stats()
@@ -288,6 +341,44 @@ class Context:
 
     def reset_stats(self, stream=None):
         _check(lib().lp_reset_stats(self.h, _stream(stream)), "lp_reset_stats")
+
+    # ---- learned estimator -------------------------------------------------
+    def mlp_set_params(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == MLP_NPARAM
+        _check(lib().lp_mlp_set_params(self.h, a.ctypes.data_as(C.c_void_p)), "lp_mlp_set_params")
+
+    def mlp_get_params(self):
+        """(FP32 master weights, BF16 weights as float32) on the host."""
+        m = np.zeros(MLP_NPARAM, np.float32)
+        b = np.zeros(MLP_NPARAM, np.float32)
+        _check(lib().lp_mlp_get_params(self.h, m.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p)),
+               "lp_mlp_get_params")
+        return m, b
+
+    def mlp_grad(self, X, y, pos_weight, stream=None):
+        import torch
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        _check(lib().lp_mlp_grad(self.h, _ptr(X), _ptr(y), int(X.shape[0]), float(pos_weight), _ptr(g), _ptr(loss),
+                                 _stream(stream)), "lp_mlp_grad")
+        return g, loss
+
+    def mlp_adam_step(self, grad, lr, stream=None):
+        _check(lib().lp_mlp_adam_step(self.h, _ptr(grad), float(lr), _stream(stream)), "lp_mlp_adam_step")
+
+    def mlp_train(self, X, y, epochs, batch, lr, pos_weight, stream=None):
+        losses = np.zeros(epochs, np.float32)
+        _check(lib().lp_mlp_train(self.h, _ptr(X), _ptr(y), int(X.shape[0]), int(epochs), int(batch), float(lr),
+                                  float(pos_weight), losses.ctypes.data_as(C.c_void_p), _stream(stream)),
+               "lp_mlp_train")
+        return losses
+
+    def mlp_infer(self, X, stream=None):
+        import torch
+        p = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        _check(lib().lp_mlp_infer(self.h, _ptr(X), int(X.shape[0]), _ptr(p), _stream(stream)), "lp_mlp_infer")
+        return p
 
     def set_profiling(self, on=True):
         _check(lib().lp_set_profiling(self.h, 1 if on else 0), "lp_set_profiling")

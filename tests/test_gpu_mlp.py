@@ -1,0 +1,137 @@
+"""The learned state estimator on the GPU against the FP64 oracle.
+
+The GPU evaluates the network with BF16 weights and FP32 accumulation; the
+oracle evaluates the same BF16-rounded weights in FP64.  So the comparison
+isolates the FP32 accumulation: probabilities agree to ~1e-6 absolute,
+gradients to ~1e-5 relative (normwise over the parameters: each gradient entry
+is a sum of n products accumulated in FP32, error ~ sqrt(n) u).  Adam's update
+is compared with the oracle's FP64 update from the same gradient.  Features
+exported by an FP64-path step equal the oracle's definition to ~1e-9; FP32-path
+features to the FP32 fit's accuracy.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_11998_gb300 import inputs, lp
+from tests.gpu_util import by_id, ensure_built
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    oracle.build()
+
+
+def _unpack(p):
+    p = np.asarray(p, np.float64)
+    W1 = p[:256].reshape(32, 8)
+    return W1, p[256:288], p[288:320], float(p[320])
+
+
+def _ctx():
+    cfg = lp.make_config(3, 16, radius_mode=lp.RADIUS_FIXED, radius=0.1, k_max=8)
+    return lp.Context(cfg)
+
+
+def test_forward_and_gradient_match_oracle():
+    ctx = _ctx()
+    ctx.mlp_set_params(lp.mlp_init_params(3))
+    _, wb = ctx.mlp_get_params()
+    rng = np.random.default_rng(5)
+    n = 5003
+    X = rng.normal(0.0, 1.0, size=(n, 8)).astype(np.float32)
+    y = (rng.uniform(size=n) < 0.3).astype(np.float32)
+    Xd = torch.as_tensor(X, device="cuda")
+    yd = torch.as_tensor(y, device="cuda")
+    p = ctx.mlp_infer(Xd).cpu().numpy()
+    W1, b1, w2, b2 = _unpack(wb)
+    z, po = oracle.mlp_forward(X.astype(np.float64), W1, b1, w2, b2)
+    assert np.abs(p - po).max() < 2e-6
+    g, loss = ctx.mlp_grad(Xd, yd, 2.5)
+    g = g.cpu().numpy().astype(np.float64)
+    L, gW1, gb1, gw2, gb2 = oracle.mlp_loss_grad(X.astype(np.float64), y.astype(np.float64), 2.5, W1, b1, w2, b2)
+    go = np.concatenate([gW1.ravel(), gb1, gw2, [gb2]])
+    assert abs(float(loss.cpu()[0]) - L) < 1e-5 * abs(L)
+    assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
+    ctx.close()
+
+
+def test_adam_step_matches_oracle():
+    ctx = _ctx()
+    p0 = lp.mlp_init_params(7)
+    ctx.mlp_set_params(p0)
+    rng = np.random.default_rng(8)
+    g = rng.normal(0.0, 0.1, size=lp.MLP_NPARAM).astype(np.float32)
+    w = p0.astype(np.float64).copy()
+    mo = np.zeros_like(w); ve = np.zeros_like(w)
+    for t in (1, 2):
+        ctx.mlp_adam_step(torch.as_tensor(g, device="cuda"), 1e-3)
+        oracle.adam(w, g.astype(np.float64), mo, ve, t, 1e-3)
+    master, wb = ctx.mlp_get_params()
+    assert np.abs(master - w).max() < 1e-6
+    # the BF16 copy is the master rounded to BF16 (8 significant bits)
+    assert np.all(np.abs(wb - master) <= np.abs(master) * 2.0 ** -8 + 1e-30)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(lp.PREC_FP64, 1e-9), (lp.PREC_FP32, 2e-3)])
+def test_features_match_oracle(prec, tol):
+    st = inputs.smooth_wave_3d(12, 1.0 / 12)
+    n = st["V"].shape[0]
+    cfg = lp.make_config(3, n, precision=prec, kappa=2.2, k_max=64, gamma=1.4, s_ref=inputs.field_scales(st))
+    ctx = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    feats = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    ctx.step(ps, dt=1e-3, features=feats)
+    ids = ps.id.cpu().numpy().astype(np.int64)
+    g = by_id(ids, feats.cpu().numpy())
+    ocfg = oracle.make_config(3, gamma=1.4, kappa=2.2, k_max=64)
+    o = oracle.features(ocfg, st)
+    # FP32 storage of the features bounds the FP64 path at ~1e-7 relative
+    err = np.abs(g - o) / (1.0 + np.abs(o))
+    assert err.max() < max(tol, 3e-7), err.max()
+    ctx.close()
+
+
+def _training_set(n=200_000, steps=3, seed=11):
+    """Features and plain-estimator flags of the gas cloud's own plain steps."""
+    st = inputs.gas_cloud_3d(n, seed=seed)
+    cfg = lp.make_config(3, n, kappa=2.2, k_max=64, gamma=5.0 / 3.0, s_ref=inputs.field_scales(st))
+    ctx = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    Xs, ys = [], []
+    for _ in range(steps):
+        feats = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+        flag = torch.empty(n, dtype=torch.uint8, device="cuda")
+        ctx.step(ps, dt=0.0, cfl=0.4, features=feats, flag=flag)
+        Xs.append(feats)
+        ys.append(flag.float())
+    ctx.close()
+    return torch.cat(Xs), torch.cat(ys), st
+
+
+def test_training_reduces_loss_and_separates_flags():
+    X, y, _ = _training_set()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    perm = torch.randperm(X.shape[0], device="cuda", generator=g)
+    X, y = X[perm].contiguous(), y[perm].contiguous()
+    ctx = _ctx()
+    ctx.mlp_set_params(lp.mlp_init_params(1))
+    pos = float((y == 0).sum() / max(1, int((y == 1).sum())))
+    losses = ctx.mlp_train(X, y, epochs=30, batch=8192, lr=1e-2, pos_weight=pos)
+    assert losses[-1] < 0.85 * losses[0], losses
+    p = ctx.mlp_infer(X).cpu().numpy()
+    yy = y.cpu().numpy() > 0.5
+    # skipping below tau drops a large share of particles while missing few flags
+    tau = 0.05
+    skip = p < tau
+    miss = (skip & yy).sum() / max(1, yy.sum())
+    assert skip.mean() > 0.2, skip.mean()
+    assert miss < 0.02, miss
+    ctx.close()

@@ -43,7 +43,8 @@ def brute_lists(x, V, m, ids, mode, radius, kappa, k_max, periodic=(0, 0, 0), L=
         ok[i] = False
         js = np.nonzero(ok)[0]
         order = np.lexsort((ids[js], d2[js]))
-        out.append((js[order][:k_max], len(js), d2[js][order][0] if len(js) else np.inf))
+        # the count before truncation saturates at 4 k_max
+        out.append((js[order][:k_max], min(len(js), 4 * k_max), d2[js][order][0] if len(js) else np.inf))
     return out
 
 
@@ -71,6 +72,7 @@ def test_volume_radius_3d_with_truncation(oracle_lib):
     cfg = oracle.make_config(3, radius_mode=oracle.RADIUS_VOLUME, kappa=2.2, k_max=24)
     b = brute_lists(st["x"], st["V"], st["m"], st["id"], oracle.RADIUS_VOLUME, 0, 2.2, 24)
     assert max(t for _, t, _ in b) > 24        # truncation exercised
+    assert max(t for _, t, _ in b) == 96       # and the saturated count
     check(cfg, st, b)
 
 
