@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="gas-cloud", choices=["gas-cloud", "kh-ensemble"])
     ap.add_argument("--sims", type=int, default=256)
+    ap.add_argument("--estimator", default="plain", choices=["plain", "mlp"],
+                    help="mlp: train the learned estimator on this workload's own plain steps, then time "
+                         "steps gated by it")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -217,10 +221,17 @@ def run_ours(args):
     b.build()
     n = args.particles
     state = workload_state(n, seed=SEED + rank)
-    cfg = lp.make_config(3, n, precision=lp.PREC_FP32, radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
-                         k_side=8, gamma=GAMMA, limiter=lp.LIM_FLAGGED, s_ref=inputs.field_scales(state))
-    ctx = lp.Context(cfg)
     stream = torch.cuda.Stream()
+    mlp_info = None
+    kw = {}
+    if args.estimator == "mlp":
+        params, mlp_info = train_gate(lp, inputs, state, n, stream, torch)
+        kw = dict(estimator=lp.EST_MLP, mlp_tau_lo=MLP_TAU)
+    cfg = lp.make_config(3, n, precision=lp.PREC_FP32, radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
+                         k_side=8, gamma=GAMMA, limiter=lp.LIM_FLAGGED, s_ref=inputs.field_scales(state), **kw)
+    ctx = lp.Context(cfg)
+    if args.estimator == "mlp":
+        ctx.mlp_set_params(params)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -234,6 +245,11 @@ def run_ours(args):
         t_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
         for _ in range(args.warmup):
             ctx.step(ps, dt=0.0, cfl=CFL, t=t_dev, stream=stream)
+        tune = None
+        if not args.no_autotune:
+            f_ms, s_ms = ctx.autotune(ps, dt=0.0, cfl=CFL, reps=3, stream=stream)
+            tune = {"fused_ms": f_ms, "split_ms": s_ms,
+                    "chosen": "split" if ctx.schedule() == lp.SCHED_SPLIT else "fused"}
         # mean neighbour count of the current lists (algorithmic work per particle)
         cnt = ctx.export_neighbors(n, stream=stream)[0]
         m_mean = float(cnt.double().mean().item())
@@ -262,6 +278,10 @@ def run_ours(args):
         launches = st["kernel_launches"] - launches0
         step_ms = [a.elapsed_time(bb) for a, bb in ev]
         total_ms = sum(step_ms)
+
+        if mlp_info is not None:
+            mlp_info.update(audit_gate(lp, inputs, ps, n, cfg, params, stream, torch))
+            mlp_info["skipped_per_step"] = st["n_mlp_skip"] / args.steps
 
         # end to end through the same C-ABI call with host buffers
         e2e = run_e2e(ctx, state, n, args, stream, lp, torch, flush)
@@ -308,7 +328,9 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(n, {"fit_ms_per_step": fit_ms, "wall_s_timed": wall,
                                           "flagged_per_step": st["n_flagged"] / args.steps,
-                                          "fp64_redo_per_step": st["n_fp64_redo"] / args.steps}),
+                                          "fp64_redo_per_step": st["n_fp64_redo"] / args.steps,
+                                          "fit_schedule": tune, "estimator": args.estimator,
+                                          "learned_gate": mlp_info}),
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                         "d2h_bytes_per_step": e2e["d2h"]},
@@ -317,6 +339,57 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+MLP_TAU = 0.05
+
+
+def train_gate(lp, inputs, state, n, stream, torch):
+    """Train the learned estimator on features and plain-estimator flags of two
+    plain steps of this workload (untimed): returns (parameters, info)."""
+    cfg = lp.make_config(3, n, precision=lp.PREC_FP32, kappa=KAPPA, k_max=K_MAX, gamma=GAMMA,
+                         s_ref=inputs.field_scales(state))
+    c0 = lp.Context(cfg)
+    X, y = [], []
+    with torch.cuda.stream(stream):
+        ps = lp.ParticleSet.from_state(state)
+        for _ in range(2):
+            f = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+            g = torch.empty(n, dtype=torch.uint8, device="cuda")
+            c0.step(ps, dt=0.0, cfl=CFL, features=f, flag=g, stream=stream)
+            X.append(f)
+            y.append(g.float())
+        X = torch.cat(X)
+        y = torch.cat(y)
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        perm = torch.randperm(X.shape[0], device="cuda", generator=gen)
+        X, y = X[perm].contiguous(), y[perm].contiguous()
+        pos = float((y == 0).sum()) / max(1.0, float((y == 1).sum()))
+        c0.mlp_set_params(lp.mlp_init_params(1))
+        t0 = time.perf_counter()
+        losses = c0.mlp_train(X, y, epochs=20, batch=8192, lr=1e-2, pos_weight=pos, stream=stream)
+        stream.synchronize()
+        secs = time.perf_counter() - t0
+        params = c0.mlp_get_params()[0]
+    c0.close()
+    return params, {"train_samples": int(X.shape[0]), "train_epochs": 20, "train_s": secs,
+                    "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "tau_lo": MLP_TAU}
+
+
+def audit_gate(lp, inputs, ps, n, cfg, params, stream, torch):
+    """One audited step from a copy of the current state: flags the learned gate
+    cleared that the plain estimator raises."""
+    cfg.mlp_audit = 1
+    ca = lp.Context(cfg)
+    ca.mlp_set_params(params)
+    cp = lp.ParticleSet(x=[a.clone() for a in ps.x], V=ps.V.clone(), u=[a.clone() for a in ps.u], P=ps.P.clone(),
+                        m=ps.m.clone(), id=ps.id.clone())
+    ca.step(cp, dt=0.0, cfl=CFL, stream=stream)
+    st = ca.stats(stream=stream)
+    ca.close()
+    cfg.mlp_audit = 0
+    return {"audit_skipped": st["n_mlp_skip"], "audit_missed_flags": st["n_mlp_miss"],
+            "audit_flagged": st["n_flagged"]}
 
 
 def run_e2e(ctx, state, n, args, stream, lp, torch, flush):

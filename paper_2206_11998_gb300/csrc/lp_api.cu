@@ -31,7 +31,7 @@ void free_all(lp_ctx* c)
                     c->lx[0], c->lx[1], c->lx[2], c->hf[0], c->hf[1], c->hf[2], c->hf[3], c->hf[4],
                     c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec, c->pos4, c->cells, c->nb_count, c->nb_total,
                     c->nb_idx, c->nb_d2min, c->grid, c->dt_dev, c->dt_min, c->counters, c->redo_list,
-                    c->ext, c->grange, c->level_off_dev, c->sim_of,
+                    c->plain_list, c->mid, c->ext, c->grange, c->level_off_dev, c->sim_of,
                     c->mlp_master, c->mlp_bf16, c->mlp_m1, c->mlp_m2, c->mlp_grad, c->mlp_loss};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -168,6 +168,10 @@ void fill_fit_args(lp_ctx* c, FitArgs& a, int64_t n)
     a.list_len = c->counters + C_REDO_LEN;
     a.keys = c->keys_sorted;
     a.key_shift = c->dc.dim * c->dc.mbits;
+    a.plain_list = c->plain_list;
+    a.plain_len = c->counters + C_PLAIN_LEN;
+    a.mid = c->mid;
+    a.mid_cap = c->cap;
 }
 
 constexpr int EV_PAIRS = LP_NPHASES * 4;
@@ -232,6 +236,34 @@ cudaError_t run_cfl(lp_ctx* c, int64_t n, double cfl, double dt_fixed, double* t
 
 }  // namespace lp
 
+namespace {
+
+// the fit + update pass of one step: the main pass over all particles (fused,
+// or split into central and plain kernels), then, after an FP32 pass, the FP64
+// redo of the particles it listed
+lp_status run_fit(lp_ctx* c, FitArgs a, const StepOut& o, int sched, cudaStream_t s)
+{
+    const bool split = sched == LP_SCHED_SPLIT;
+    const int dim = c->dc.dim;
+    if (split) LP_CUDA(cudaMemsetAsync(c->counters + C_PLAIN_LEN, 0, 8, s));
+    if (c->dc.precision == LP_PREC_FP32) {
+        LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
+        {
+            Phase ph(c, LP_PH_FIT, split ? 2 : 1, s);
+            LP_CUDA(split ? launch_step_split_f32(dim, a, o, s) : launch_step_f32(dim, a, o, s));
+        }
+        a.list = c->redo_list;
+        Phase ph(c, LP_PH_FIT64, 1, s);
+        LP_CUDA(launch_step_f64(dim, a, o, s));
+    } else {
+        Phase ph(c, LP_PH_FIT64, split ? 2 : 1, s);
+        LP_CUDA(split ? launch_step_split_f64(dim, a, o, s) : launch_step_f64(dim, a, o, s));
+    }
+    return LP_OK;
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -278,6 +310,7 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     d.mlp_tau_lo = (float)cfg->mlp_tau_lo;
     d.mlp_audit = cfg->mlp_audit ? 1 : 0;
     d.nsim_max = cfg->max_sims > 1 ? cfg->max_sims : 1;
+    c->schedule = cfg->estimator == LP_EST_MLP ? LP_SCHED_SPLIT : LP_SCHED_FUSED;
     int simbits = 0;
     while ((1 << simbits) < d.nsim_max) ++simbits;
     d.mbits = (cfg->dim == 3 && d.nsim_max > 1) ? (64 - simbits) / 3 : MORTON_BITS;
@@ -350,6 +383,8 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     A(dalloc(&c->sim_of, batched ? n * 4 : 4));
     A(dalloc(&c->counters, C_COUNT * 8));
     A(dalloc(&c->redo_list, n * 4));
+    A(dalloc(&c->plain_list, n * 4));
+    A(dalloc(&c->mid, (size_t)n * MidN<3>::v * (cfg->precision == LP_PREC_FP32 ? 4 : 8)));
     A(dalloc(&c->mlp_master, MLP_NPARAM * 4)); A(dalloc(&c->mlp_bf16, MLP_NPARAM * 2));
     A(dalloc(&c->mlp_m1, MLP_NPARAM * 4)); A(dalloc(&c->mlp_m2, MLP_NPARAM * 4));
     A(dalloc(&c->mlp_grad, MLP_NPARAM * 4)); A(dalloc(&c->mlp_loss, 4));
@@ -536,19 +571,25 @@ lp_status lp_onesided_derivs(lp_ctx* c, const lp_particles* p, const double* con
     return LP_OK;
 }
 
-lp_status lp_step_batched(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_t nsim, double dt, double cfl,
-                          double* t, const lp_step_diag* diag, lp_stream stream)
+}  // extern "C"
+
+namespace {
+
+// everything of a step before the fit pass: checks, neighbour build, CFL step;
+// fills the fit pass's arguments.  *n_out = 0 when there is nothing to fit.
+lp_status step_prologue(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_t nsim, double dt, double cfl,
+                        double* t, const lp_step_diag* diag, cudaStream_t s, FitArgs& a, StepOut& o, int64_t* n_out)
 {
+    *n_out = 0;
     if (!c) return LP_ERR_ARG;
     lp_status st = check_particles(c, p);
     if (st != LP_OK) return st;
     if (nsim < 1 || nsim > c->dc.nsim_max || (nsim > 1 && !offsets)) return LP_ERR_ARG;
-    c->nsim = nsim;
-    c->offsets = nsim > 1 ? offsets : nullptr;
     if (!(dt > 0.0) && !(cfl > 0.0)) return LP_ERR_ARG;
     if (c->dc.estimator == LP_EST_MLP && !c->mlp_ready) return LP_ERR_STATE;
     if (isnan(dt) || isinf(dt)) return LP_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+    c->nsim = nsim;
+    c->offsets = nsim > 1 ? offsets : nullptr;
     st = build(c, p, s);
     if (st != LP_OK) return st;
     int64_t n = p->n;
@@ -558,13 +599,11 @@ lp_status lp_step_batched(lp_ctx* c, lp_particles* p, const int64_t* offsets, in
     }
     if (n == 0) return LP_OK;
     int dim = c->dc.dim;
-    FitArgs a;
     fill_fit_args(c, a, n);
     a.fd[0] = c->sV;
     for (int k = 0; k < dim; ++k) a.fd[1 + k] = c->su[k];
     a.fd[dim + 1] = c->sP;
     for (int q = dim + 2; q < 5; ++q) a.fd[q] = c->sV;
-    StepOut o;
     memset(&o, 0, sizeof(o));
     for (int k = 0; k < 3; ++k) {
         o.x[k] = p->x[k < dim ? k : 0];
@@ -574,19 +613,111 @@ lp_status lp_step_batched(lp_ctx* c, lp_particles* p, const int64_t* offsets, in
     if (diag) { o.flag = diag->flag; o.phi = diag->phi; o.r = diag->r; o.features = diag->features; }
     a.mlp_w = reinterpret_cast<const __nv_bfloat16*>(c->mlp_bf16);
     o.dt = c->dt_dev;
-    if (c->dc.precision == LP_PREC_FP32) {
-        LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
-        {
-            Phase ph(c, LP_PH_FIT, 1, s);
-            LP_CUDA(launch_step_f32(dim, a, o, s));
-        }
-        a.list = c->redo_list;
-        Phase ph(c, LP_PH_FIT64, 1, s);
-        LP_CUDA(launch_step_f64(dim, a, o, s));
-    } else {
-        Phase ph(c, LP_PH_FIT64, 1, s);
-        LP_CUDA(launch_step_f64(dim, a, o, s));
+    *n_out = n;
+    return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_step_batched(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_t nsim, double dt, double cfl,
+                          double* t, const lp_step_diag* diag, lp_stream stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    FitArgs a;
+    StepOut o;
+    int64_t n = 0;
+    lp_status st = step_prologue(c, p, offsets, nsim, dt, cfl, t, diag, s, a, o, &n);
+    if (st != LP_OK || n == 0) return st;
+    return run_fit(c, a, o, c->schedule, s);
+}
+
+lp_status lp_set_schedule(lp_ctx* c, int32_t schedule)
+{
+    if (!c || (schedule != LP_SCHED_FUSED && schedule != LP_SCHED_SPLIT)) return LP_ERR_ARG;
+    c->schedule = schedule;
+    return LP_OK;
+}
+
+lp_status lp_get_schedule(lp_ctx* c, int32_t* schedule)
+{
+    if (!c || !schedule) return LP_ERR_ARG;
+    *schedule = c->schedule;
+    return LP_OK;
+}
+
+lp_status lp_autotune(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_t nsim, double dt, double cfl,
+                      int32_t reps, double* out_ms, lp_stream stream)
+{
+    if (!c || reps < 1) return LP_ERR_ARG;
+    if (c->profiling) return LP_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the counters and the launch tally are put back afterwards: tuning is not a step
+    unsigned long long saved[C_COUNT];
+    LP_CUDA(cudaMemcpyAsync(saved, c->counters, sizeof(saved), cudaMemcpyDeviceToHost, s));
+    double* dt_saved = (double*)malloc(sizeof(double) * c->dc.nsim_max);
+    if (!dt_saved) return LP_ERR_CUDA;
+    if (cudaMemcpyAsync(dt_saved, c->dt_dev, sizeof(double) * c->dc.nsim_max, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        free(dt_saved);
+        return LP_ERR_CUDA;
     }
+    struct FreeOnExit { double* p; ~FreeOnExit() { free(p); } } dt_guard{dt_saved};
+    const int64_t launches0 = c->launches;
+    int64_t ph_launches0[LP_NPHASES];
+    memcpy(ph_launches0, c->phase_launches, sizeof(ph_launches0));
+    FitArgs a;
+    StepOut o;
+    int64_t n = 0;
+    lp_status st = step_prologue(c, p, offsets, nsim, dt, cfl, nullptr, nullptr, s, a, o, &n);
+    if (st != LP_OK) return st;
+    double ms[2] = {0.0, 0.0};
+    if (n > 0) {
+        // the fit pass reads the sorted copies and writes only its outputs, so it
+        // can be repeated; outputs go to scratch so that the state is untouched
+        const int dim = c->dc.dim;
+        double* scratch = nullptr;
+        uint32_t* sid = nullptr;
+        if (cudaMalloc(&scratch, (size_t)n * 8 * (2 * dim + 3)) != cudaSuccess) return LP_ERR_CUDA;
+        if (cudaMalloc(&sid, (size_t)n * 4) != cudaSuccess) { cudaFree(scratch); return LP_ERR_CUDA; }
+        for (int k = 0; k < 3; ++k) {
+            o.x[k] = scratch + (size_t)n * (k < dim ? k : 0);
+            o.u[k] = scratch + (size_t)n * (dim + (k < dim ? k : 0));
+        }
+        o.V = scratch + (size_t)n * (2 * dim);
+        o.P = scratch + (size_t)n * (2 * dim + 1);
+        o.m = scratch + (size_t)n * (2 * dim + 2);
+        o.id = sid;
+        cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
+        lp_status rs = LP_OK;
+        for (int sched = 0; sched < 2 && rs == LP_OK; ++sched) {
+            rs = run_fit(c, a, o, sched, s);                 // warm-up
+            if (rs != LP_OK) break;
+            if (cudaEventRecord(e0, s) != cudaSuccess) { rs = LP_ERR_CUDA; break; }
+            for (int r = 0; r < reps && rs == LP_OK; ++r) rs = run_fit(c, a, o, sched, s);
+            if (rs != LP_OK) break;
+            float f = 0.0f;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&f, e0, e1) != cudaSuccess) {
+                rs = LP_ERR_CUDA;
+                break;
+            }
+            ms[sched] = f / reps;
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(scratch);
+        cudaFree(sid);
+        if (rs != LP_OK) return rs;
+        c->schedule = ms[LP_SCHED_SPLIT] < ms[LP_SCHED_FUSED] ? LP_SCHED_SPLIT : LP_SCHED_FUSED;
+    }
+    LP_CUDA(cudaMemcpyAsync(c->counters, saved, sizeof(saved), cudaMemcpyHostToDevice, s));
+    LP_CUDA(cudaMemcpyAsync(c->dt_dev, dt_saved, sizeof(double) * c->dc.nsim_max, cudaMemcpyHostToDevice, s));
+    LP_CUDA(cudaStreamSynchronize(s));
+    c->launches = launches0;
+    memcpy(c->phase_launches, ph_launches0, sizeof(ph_launches0));
+    if (out_ms) { out_ms[0] = ms[0]; out_ms[1] = ms[1]; }
     return LP_OK;
 }
 

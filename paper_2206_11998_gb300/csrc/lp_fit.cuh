@@ -19,6 +19,26 @@ namespace lp {
 
 template <int DIM> struct NU { static constexpr int v = DIM == 1 ? 2 : (DIM == 2 ? 5 : 9); };
 
+// Explicit round-to-nearest operations.  The fit and rate arithmetic is inlined
+// into more than one kernel (fused and split schedules, the FP64 redo); with
+// explicit operations the compiler cannot contract a*b + c into an FMA in one
+// kernel and not in another, so every schedule produces the same bits.
+template <typename T> struct RN;
+template <> struct RN<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+template <> struct RN<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+
 template <typename T> __device__ inline T rsqrt_t(T x);
 template <> __device__ inline float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
@@ -45,26 +65,27 @@ struct Givens {
 
     __device__ void add(T (&a)[N], T (&b)[F])
     {
+        using O = RN<T>;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             T ak = a[k];
             if (ak != T(0)) {
                 T rkk = R[id(k, k)];
-                T h2 = rkk * rkk + ak * ak;
+                T h2 = O::fma(rkk, rkk, O::mul(ak, ak));
                 T inv = rsqrt_t<T>(h2);
-                T cc = rkk * inv, ss = ak * inv;
-                R[id(k, k)] = h2 * inv;
+                T cc = O::mul(rkk, inv), ss = O::mul(ak, inv);
+                R[id(k, k)] = O::mul(h2, inv);
 #pragma unroll
                 for (int l = k + 1; l < N; ++l) {
                     T t = R[id(k, l)];
-                    R[id(k, l)] = cc * t + ss * a[l];
-                    a[l] = cc * a[l] - ss * t;
+                    R[id(k, l)] = O::fma(cc, t, O::mul(ss, a[l]));
+                    a[l] = O::fma(cc, a[l], -O::mul(ss, t));
                 }
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
                     T t = Z[k][f];
-                    Z[k][f] = cc * t + ss * b[f];
-                    b[f] = cc * b[f] - ss * t;
+                    Z[k][f] = O::fma(cc, t, O::mul(ss, b[f]));
+                    b[f] = O::fma(cc, b[f], -O::mul(ss, t));
                 }
             }
         }
@@ -85,15 +106,16 @@ struct Givens {
     // x = R^{-1} Z
     __device__ void solve(T (&x)[N][F]) const
     {
+        using O = RN<T>;
 #pragma unroll
         for (int k = N - 1; k >= 0; --k) {
-            T inv = T(1) / R[id(k, k)];
+            T inv = O::div(T(1), R[id(k, k)]);
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 T s = Z[k][f];
 #pragma unroll
-                for (int l = k + 1; l < N; ++l) s -= R[id(k, l)] * x[l][f];
-                x[k][f] = s * inv;
+                for (int l = k + 1; l < N; ++l) s = O::fma(-R[id(k, l)], x[l][f], s);
+                x[k][f] = O::mul(s, inv);
             }
         }
     }
@@ -101,26 +123,27 @@ struct Givens {
     // d = (R^T R)^{-1} g  (one correction step of the semi-normal equations)
     __device__ void solve_normal(T (&g)[N][F]) const
     {
+        using O = RN<T>;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            T inv = T(1) / R[id(k, k)];
+            T inv = O::div(T(1), R[id(k, k)]);
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 T s = g[k][f];
 #pragma unroll
-                for (int l = 0; l < k; ++l) s -= R[id(l, k)] * g[l][f];
-                g[k][f] = s * inv;
+                for (int l = 0; l < k; ++l) s = O::fma(-R[id(l, k)], g[l][f], s);
+                g[k][f] = O::mul(s, inv);
             }
         }
 #pragma unroll
         for (int k = N - 1; k >= 0; --k) {
-            T inv = T(1) / R[id(k, k)];
+            T inv = O::div(T(1), R[id(k, k)]);
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 T s = g[k][f];
 #pragma unroll
-                for (int l = k + 1; l < N; ++l) s -= R[id(k, l)] * g[l][f];
-                g[k][f] = s * inv;
+                for (int l = k + 1; l < N; ++l) s = O::fma(-R[id(k, l)], g[l][f], s);
+                g[k][f] = O::mul(s, inv);
             }
         }
     }
@@ -171,6 +194,12 @@ struct FitArgs {
     const __nv_bfloat16* mlp_w;   // learned-estimator weights (BF16)
     const uint64_t* keys;         // key-sorted keys (simulation above bit key_shift)
     int key_shift;
+    // split schedule: compacted list of particles that need the plain stage,
+    // its length, and the intermediate record (component-major, mid_cap slots)
+    uint32_t* plain_list;
+    unsigned long long* plain_len;
+    void* mid;
+    int64_t mid_cap;
 };
 
 // statistics of the last field's differences b_j = s_j - s_i over the central
@@ -239,17 +268,21 @@ struct Src<float, DIM, F> {
         double d = offset64(a.c, k, a.sx[k][i], a.sx[k][j]);
         return d > 0.0 ? 1 : (d < 0.0 ? -1 : 0);
     }
-    // side of j along axis k; when non-zero, also its offsets and differences
-    __device__ int fetch_side(uint32_t j, int k, float (&d)[DIM], float (&b)[F]) const
+    // a neighbour's record as loaded (the pipelined loops load one ahead)
+    struct Rec { float v[4 * REC_F4]; };
+    __device__ void load_rec(uint32_t j, Rec& r) const { load(j, r.v); }
+    __device__ void unpack(const Rec& r, float (&d)[DIM], float (&b)[F]) const
     {
-        float r[4 * REC_F4];
-        load(j, r);
-        int sg = side_rec(r, j, k);
-        if (sg != 0) {
-            off_rec(r, d);
+        off_rec(r.v, d);
 #pragma unroll
-            for (int f = 0; f < F; ++f) b[f] = (r[REC_FH + f] - ri[REC_FH + f]) + (r[REC_FL + f] - ri[REC_FL + f]);
-        }
+        for (int f = 0; f < F; ++f)
+            b[f] = (r.v[REC_FH + f] - ri[REC_FH + f]) + (r.v[REC_FL + f] - ri[REC_FL + f]);
+    }
+    // side of j along axis k; when non-zero, also its offsets and differences
+    __device__ int unpack_side(const Rec& r, uint32_t j, int k, float (&d)[DIM], float (&b)[F]) const
+    {
+        int sg = side_rec(r.v, j, k);
+        if (sg != 0) unpack(r, d, b);
         return sg;
     }
 };
@@ -282,14 +315,51 @@ struct Src<double, DIM, F> {
         off(j, d);
         diff(j, b);
     }
-    __device__ int fetch_side(uint32_t j, int k, double (&d)[DIM], double (&b)[F]) const
+    struct Rec { double x[DIM]; double f[F]; };
+    __device__ void load_rec(uint32_t j, Rec& r) const
     {
-        double dk = offset64(a.c, k, xi[k], a.sx[k][j]);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) r.x[k] = a.sx[k][j];
+#pragma unroll
+        for (int f = 0; f < F; ++f) r.f[f] = a.fd[f][j];
+    }
+    __device__ void unpack(const Rec& r, double (&d)[DIM], double (&b)[F]) const
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) d[k] = offset64(a.c, k, xi[k], r.x[k]);
+#pragma unroll
+        for (int f = 0; f < F; ++f) b[f] = r.f[f] - fi[f];
+    }
+    __device__ int unpack_side(const Rec& r, uint32_t, int k, double (&d)[DIM], double (&b)[F]) const
+    {
+        double dk = offset64(a.c, k, xi[k], r.x[k]);
         int sg = dk > 0.0 ? 1 : (dk < 0.0 ? -1 : 0);
-        if (sg != 0) fetch(j, d, b);
+        if (sg != 0) unpack(r, d, b);
         return sg;
     }
 };
+
+// Visit the neighbour list in order with the next record (and the index after
+// it) already in flight: body(j, rec) returns false to stop early.
+template <class S, class Body>
+__device__ __forceinline__ void for_neighbors(const S& src, const uint32_t* nb, int cnt, Body&& body)
+{
+    if (cnt <= 0) return;
+    typename S::Rec nxt;
+    uint32_t jn = __ldg(nb);
+    src.load_rec(jn, nxt);
+    uint32_t jn2 = cnt > 1 ? __ldg(nb + 1) : 0u;
+    for (int r = 0; r < cnt; ++r) {
+        const typename S::Rec cur = nxt;
+        const uint32_t j = jn;
+        if (r + 1 < cnt) {
+            jn = jn2;
+            src.load_rec(jn, nxt);
+            if (r + 2 < cnt) jn2 = __ldg(nb + r + 2);
+        }
+        if (!body(j, cur)) break;
+    }
+}
 
 // power-of-two 1/S with S >= sqrt(d2)
 __device__ inline float inv_scale(float d2)
@@ -309,10 +379,10 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
     Givens<T, N, F> G;
     G.zero();
     T bmin = T(0), bmax = T(0), ssb = T(0), ssr = T(0);
-    for (int r = 0; r < cnt; ++r) {
-        uint32_t j = nb[r];
+    using Rec = typename Src<T, DIM, F>::Rec;
+    for_neighbors(src, nb, cnt, [&](uint32_t, const Rec& rec) {
         T d[DIM], a[N], b[F];
-        src.fetch(j, d, b);
+        src.unpack(rec, d, b);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) d[k] *= invS;
         gfd_row<T, DIM>(d, a);
@@ -320,11 +390,12 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
             T bl = b[F - 1];
             bmin = bl < bmin ? bl : bmin;
             bmax = bl > bmax ? bl : bmax;
-            ssb += bl * bl;
+            ssb = RN<T>::fma(bl, bl, ssb);
         }
         G.add(a, b);
-        if (STATS) ssr += b[F - 1] * b[F - 1];   // the row's leftover after the rotations
-    }
+        if (STATS) ssr = RN<T>::fma(b[F - 1], b[F - 1], ssr);   // the row's leftover after the rotations
+        return true;
+    });
     if (STATS && st) { st->bmin = bmin; st->bmax = bmax; st->ssb = ssb; st->ssr = ssr; }
     if (!(G.ratio() >= tau) || cnt < N) return 1;
     G.solve(x);
@@ -334,10 +405,9 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
         for (int u = 0; u < N; ++u)
 #pragma unroll
             for (int f = 0; f < F; ++f) g[u][f] = T(0);
-        for (int r = 0; r < cnt; ++r) {
-            uint32_t j = nb[r];
+        for_neighbors(src, nb, cnt, [&](uint32_t, const Rec& rec) {
             T d[DIM], a[N], b[F];
-            src.fetch(j, d, b);
+            src.unpack(rec, d, b);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) d[k] *= invS;
             gfd_row<T, DIM>(d, a);
@@ -345,11 +415,12 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
             for (int f = 0; f < F; ++f) {
                 T res = b[f];
 #pragma unroll
-                for (int u = 0; u < N; ++u) res -= a[u] * x[u][f];
+                for (int u = 0; u < N; ++u) res = RN<T>::fma(-a[u], x[u][f], res);
 #pragma unroll
-                for (int u = 0; u < N; ++u) g[u][f] += a[u] * res;
+                for (int u = 0; u < N; ++u) g[u][f] = RN<T>::fma(a[u], res, g[u][f]);
             }
-        }
+            return true;
+        });
         G.solve_normal(g);
 #pragma unroll
         for (int u = 0; u < N; ++u)
@@ -399,18 +470,22 @@ __device__ void onesided_axis(const Src<T, DIM, F>& src, const uint32_t* nb, int
     G[0].zero();
     G[1].zero();
     int ns[2] = {0, 0};
-    for (int r = 0; r < cnt && (ns[0] < ks || ns[1] < ks); ++r) {
-        uint32_t j = nb[r];
-        T d[DIM], b[F];
-        int sg = src.fetch_side(j, k, d, b);
-        if (sg == 0) continue;
-        int s = sg > 0 ? 1 : 0;
-        if (ns[s] >= ks) continue;
+    using Rec = typename Src<T, DIM, F>::Rec;
+    if (ks > 0)
+        for_neighbors(src, nb, cnt, [&](uint32_t j, const Rec& rec) {
+            T d[DIM], b[F];
+            int sg = src.unpack_side(rec, j, k, d, b);
+            if (sg != 0) {
+                int s = sg > 0 ? 1 : 0;
+                if (ns[s] < ks) {
 #pragma unroll
-        for (int q = 0; q < DIM; ++q) d[q] *= invS;
-        if (s) G[1].add(d, b); else G[0].add(d, b);
-        ++ns[s];
-    }
+                    for (int q = 0; q < DIM; ++q) d[q] *= invS;
+                    if (s) G[1].add(d, b); else G[0].add(d, b);
+                    ++ns[s];
+                }
+            }
+            return ns[0] < ks || ns[1] < ks;
+        });
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         ok[s] = false;
@@ -477,35 +552,44 @@ __device__ constexpr int hess_slot(int c, int a)
 template <typename T, int DIM>
 __device__ inline void lw_rates(T gamma, T dt, T V, T P, const T (&cd)[NU<DIM>::v][DIM + 2], T (&lw)[DIM + 2])
 {
+    using O = RN<T>;
     constexpr int FP = DIM + 1;
     T divu = T(0), S2 = T(0), gVgP = T(0), lapP = T(0);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) divu += cd[a][1 + a];
+    for (int a = 0; a < DIM; ++a) divu = O::add(divu, cd[a][1 + a]);
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) S2 += cd[b][1 + a] * cd[a][1 + b];
+        for (int b = 0; b < DIM; ++b) S2 = O::fma(cd[b][1 + a], cd[a][1 + b], S2);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) gVgP += cd[k][0] * cd[k][FP];
+    for (int k = 0; k < DIM; ++k) gVgP = O::fma(cd[k][0], cd[k][FP], gVgP);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) lapP += cd[DIM + k][FP];
-    T Vt = V * divu;
-    T Vtt = V * divu * divu - V * S2 - V * gVgP - V * V * lapP;
-    lw[0] = Vt + T(0.5) * dt * Vtt;
+    for (int k = 0; k < DIM; ++k) lapP = O::add(lapP, cd[DIM + k][FP]);
+    const T hdt = O::mul(T(0.5), dt);
+    const T Vd = O::mul(V, divu);
+    // V_tt = V (div u)^2 - V S2 - V grad V . grad P - V^2 lap P
+    T Vtt = O::sub(O::sub(O::sub(O::mul(Vd, divu), O::mul(V, S2)), O::mul(V, gVgP)), O::mul(O::mul(V, V), lapP));
+    lw[0] = O::fma(hdt, Vtt, Vd);
+    const T c1 = O::mul(O::sub(gamma, T(1)), Vd);        // (gamma - 1) V div u
+    const T gVP = O::mul(O::mul(gamma, V), P);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
         T uPt = T(0), gdiv = T(0);
 #pragma unroll
-        for (int m = 0; m < DIM; ++m) uPt += cd[i][1 + m] * cd[m][FP];
+        for (int m = 0; m < DIM; ++m) uPt = O::fma(cd[i][1 + m], cd[m][FP], uPt);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) gdiv += cd[hess_slot<DIM>(i, a)][1 + a];
-        T ut = -V * cd[i][FP];
-        T utt = (gamma - T(1)) * V * divu * cd[i][FP] + V * uPt + gamma * V * P * gdiv;
-        lw[1 + i] = ut + T(0.5) * dt * utt;
+        for (int a = 0; a < DIM; ++a) gdiv = O::add(gdiv, cd[hess_slot<DIM>(i, a)][1 + a]);
+        T ut = O::mul(-V, cd[i][FP]);
+        // u_i,tt = (gamma - 1) V div u d_i P + V sum_m d_i u_m d_m P + gamma V P d_i div u
+        T utt = O::add(O::add(O::mul(c1, cd[i][FP]), O::mul(V, uPt)), O::mul(gVP, gdiv));
+        lw[1 + i] = O::fma(hdt, utt, ut);
     }
-    T Pt = -gamma * P * divu;
-    T Ptt = gamma * gamma * P * divu * divu + gamma * P * S2 + gamma * P * (gVgP + V * lapP);
-    lw[FP] = Pt + T(0.5) * dt * Ptt;
+    const T gP = O::mul(gamma, P);
+    T Pt = O::mul(-gP, divu);
+    // P_tt = gamma^2 P (div u)^2 + gamma P S2 + gamma P (grad V . grad P + V lap P)
+    T Ptt = O::add(O::add(O::mul(O::mul(O::mul(gamma, gP), divu), divu), O::mul(gP, S2)),
+                   O::mul(gP, O::fma(V, lapP, gVgP)));
+    lw[FP] = O::fma(hdt, Ptt, Pt);
 }
 
 }  // namespace lp

@@ -56,8 +56,9 @@ __device__ inline T curvature_ratio(const T (&cd)[NU<DIM>::v][DIM + 2], int f, T
     for (int k = 0; k < DIM; ++k) {
         T g = fabs(cd[k][f]);
         if (g < T(0.5) * gmax) continue;
-        T h = ell * fabs(cd[DIM + k][f]);
-        T r = (g + h) > T(0) ? h / (g + h) : T(0);
+        T h = RN<T>::mul(ell, fabs(cd[DIM + k][f]));
+        T gh = RN<T>::add(g, h);
+        T r = gh > T(0) ? h / gh : T(0);
         best = fmax(best, r);
     }
     return best;
@@ -68,14 +69,15 @@ __device__ inline void mlp_features(const T (&cd)[NU<DIM>::v][DIM + 2], const Fi
                                     T gamma, float (&x)[MLP_IN])
 {
     constexpr int FP = DIM + 1;
+    using O = RN<T>;
     T gP = T(0), gV = T(0), divu = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-        gP += cd[k][FP] * cd[k][FP];
-        gV += cd[k][0] * cd[k][0];
-        divu += cd[k][1 + k];
+        gP = O::fma(cd[k][FP], cd[k][FP], gP);
+        gV = O::fma(cd[k][0], cd[k][0], gV);
+        divu = O::add(divu, cd[k][1 + k]);
     }
-    T cs = sqrt(gamma * P * V);
+    T cs = sqrt(O::mul(O::mul(gamma, P), V));
     x[0] = feat_t((float)(ell * sqrt(gP) / P));
     x[1] = feat_t((float)(ell * sqrt(gV) / V));
     x[2] = feat_t((float)curvature_ratio<T, DIM>(cd, FP, ell));
@@ -87,55 +89,77 @@ __device__ inline void mlp_features(const T (&cd)[NU<DIM>::v][DIM + 2], const Fi
 }
 
 // ---------------------------------------------------------------------------
-// one LP step for particle i (sorted index)
+// one LP step for particle i (sorted index), in stages
+//
+//   load     state of i; frozen boundary particles are copied through
+//   central  central fit, LW rates (Sec. 2.3), learned gate (features + MLP)
+//   plain    one-sided fits per axis (Sec. 2.4), falling back to the central
+//            first derivatives where a side has too few points
+//   finish   UW rates, estimator r and limiter phi, blend (Eq. 14), safeguard,
+//            mover (Sec. 2.5)
+//
+// The fused schedule runs all stages in one thread.  The split schedule runs
+// load + central in one kernel, which finishes particles the learned gate
+// clears and appends the rest to a compacted list with a small intermediate
+// record (central first derivatives, LW rates, gate bit); a second kernel
+// runs plain + finish over that list with full warps.  Both schedules execute
+// the same arithmetic on the same values, so their results are identical.
 // ---------------------------------------------------------------------------
+template <int DIM>
+struct Loaded {
+    double s0[DIM + 2];
+    double x0[DIM];
+    double dt;
+    uint32_t id;
+};
+
 template <typename T, int DIM>
-__device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
+__device__ inline bool step_load(const FitArgs& a, const StepOut& o, int64_t i, Loaded<DIM>& L)
+{
+    constexpr int F = DIM + 2;
+    const DevCfg& c = a.c;
+    L.dt = o.dt[c.nsim_max > 1 ? (a.keys[i] >> a.key_shift) : 0];
+    L.s0[0] = a.fd[0][i];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) L.s0[1 + k] = a.fd[1 + k][i];
+    L.s0[F - 1] = a.fd[F - 1][i];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) L.x0[k] = a.sx[k][i];
+    L.id = a.sid[i];
+    if ((int64_t)L.id < c.n_fluid) return false;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { o.x[k][i] = L.x0[k]; o.u[k][i] = L.s0[1 + k]; }
+    o.V[i] = L.s0[0];
+    o.P[i] = L.s0[F - 1];
+    o.m[i] = a.sm[i];
+    o.id[i] = L.id;
+    if (o.flag) o.flag[i] = 0;
+    if (o.phi) for (int f = 0; f < F; ++f) o.phi[i * F + f] = 1.0f;
+    if (o.r) for (int f = 0; f < F; ++f) o.r[i * F + f] = 1.0f;
+    return true;
+}
+
+// central stage; false when i went to the FP64 redo list
+template <typename T, int DIM>
+__device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t i, const Loaded<DIM>& L,
+                                    const Src<T, DIM, DIM + 2>& src, const uint32_t* nb, int cnt, T invS,
+                                    T (&cdf)[DIM][DIM + 2], T (&lw)[DIM + 2], bool& mlp_skip)
 {
     constexpr int F = DIM + 2;
     constexpr int N = NU<DIM>::v;
     const DevCfg& c = a.c;
-    const double dt = o.dt[c.nsim_max > 1 ? (a.keys[i] >> a.key_shift) : 0];
-    // frozen boundary particles are copied through
-    double s0[F];
-    s0[0] = a.fd[0][i];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) s0[1 + k] = a.fd[1 + k][i];
-    s0[F - 1] = a.fd[F - 1][i];
-    double x0[DIM];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) x0[k] = a.sx[k][i];
-    uint32_t idi = a.sid[i];
-    if ((int64_t)idi >= c.n_fluid) {
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) { o.x[k][i] = x0[k]; o.u[k][i] = s0[1 + k]; }
-        o.V[i] = s0[0];
-        o.P[i] = s0[F - 1];
-        o.m[i] = a.sm[i];
-        o.id[i] = idi;
-        if (o.flag) o.flag[i] = 0;
-        if (o.phi) for (int f = 0; f < F; ++f) o.phi[i * F + f] = 1.0f;
-        if (o.r) for (int f = 0; f < F; ++f) o.r[i * F + f] = 1.0f;
-        return;
-    }
-    Src<T, DIM, F> src(a, i);
-    const int cnt = (int)a.count[i];
-    const uint32_t* nb = a.idx + i * (int64_t)c.k_max;
-    const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
-    const T tau_rank = (T)c.tau64;
-
     T cd[N][F];
     FitStats<T> fst = {T(0), T(0), T(0), T(0)};
     if (central_fit<T, DIM, F, true>(src, nb, cnt, invS, tau, c.refine != 0, cd, &fst)) {
-        if (IsF32<T>::v) { push_redo(a, i); return; }
+        if (IsF32<T>::v) { push_redo(a, i); return false; }
         T lin[DIM][F];
 #pragma unroll
         for (int u = 0; u < N; ++u)
 #pragma unroll
             for (int f = 0; f < F; ++f) cd[u][f] = T(0);
         atomicAdd(a.counters + C_LINEAR, 1ull);
-        if (linear_fit<T, DIM, F>(src, nb, cnt, invS, tau_rank, lin) == 0) {
+        if (linear_fit<T, DIM, F>(src, nb, cnt, invS, (T)c.tau64, lin) == 0) {
 #pragma unroll
             for (int u = 0; u < DIM; ++u)
 #pragma unroll
@@ -146,10 +170,10 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     }
     // learned estimator: below mlp_tau_lo the particle is unflagged and its
     // one-sided fits are skipped (unless auditing against the plain estimator)
-    bool mlp_skip = false;
+    mlp_skip = false;
     if (o.features || c.estimator == LP_EST_MLP) {
         float xf[MLP_IN];
-        mlp_features<T, DIM>(cd, fst, (T)sqrt(a.d2min[i]), (T)s0[0], (T)s0[F - 1], (T)c.gamma, xf);
+        mlp_features<T, DIM>(cd, fst, (T)sqrt(a.d2min[i]), (T)L.s0[0], (T)L.s0[F - 1], (T)c.gamma, xf);
         if (o.features)
 #pragma unroll
             for (int k = 0; k < MLP_IN; ++k) o.features[i * MLP_IN + k] = xf[k];
@@ -159,47 +183,65 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
             warp_count(a.counters, C_MLP_UNCERTAIN, !mlp_skip);
         }
     }
-    const bool plain = !mlp_skip || c.mlp_audit;
-    // one-sided derivatives os[k][s][f]
-    T os[DIM][2][F];
-    bool ill = false;
-    if (plain) {
+    lw_rates<T, DIM>((T)c.gamma, (T)L.dt, (T)L.s0[0], (T)L.s0[F - 1], cd, lw);
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-            T out[2][F];
-            bool ok[2];
-            onesided_axis<T, DIM, F>(src, nb, cnt, k, c.k_side, invS, tau, tau_rank, out, ok, ill);
+    for (int k = 0; k < DIM; ++k)
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int f = 0; f < F; ++f) os[k][s][f] = ok[s] ? out[s][f] : cd[k][f];
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < DIM; ++k)
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int f = 0; f < F; ++f) os[k][s][f] = cd[k][f];
-    }
-    if (IsF32<T>::v && ill) { push_redo(a, i); return; }
+        for (int f = 0; f < F; ++f) cdf[k][f] = cd[k][f];
+    return true;
+}
 
-    // rates
+// plain stage; false when i went to the FP64 redo list
+template <typename T, int DIM>
+__device__ inline bool step_plain(const FitArgs& a, int64_t i, const Src<T, DIM, DIM + 2>& src, const uint32_t* nb,
+                                  int cnt, T invS, const T (&cdf)[DIM][DIM + 2], T (&os)[DIM][2][DIM + 2])
+{
+    constexpr int F = DIM + 2;
+    const DevCfg& c = a.c;
+    const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
+    bool ill = false;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        T out[2][F];
+        bool ok[2];
+        onesided_axis<T, DIM, F>(src, nb, cnt, k, c.k_side, invS, tau, (T)c.tau64, out, ok, ill);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int f = 0; f < F; ++f) os[k][s][f] = ok[s] ? out[s][f] : cdf[k][f];
+    }
+    if (IsF32<T>::v && ill) { push_redo(a, i); return false; }
+    return true;
+}
+
+template <typename T, int DIM>
+__device__ inline void step_finish(const FitArgs& a, const StepOut& o, int64_t i, const Loaded<DIM>& L,
+                                   const T (&os)[DIM][2][DIM + 2], const T (&lw)[DIM + 2], bool plain, bool mlp_skip)
+{
+    constexpr int F = DIM + 2;
+    const DevCfg& c = a.c;
+    const double dt = L.dt;
+    using O = RN<T>;
     const T g = (T)c.gamma;
-    const T V = (T)s0[0], P = (T)s0[F - 1];
-    T lw[F], uw[F];
-    lw_rates<T, DIM>(g, (T)dt, V, P, cd, lw);
+    const T V = (T)L.s0[0], P = (T)L.s0[F - 1];
+    T uw[F];
     {
-        T K = g * P / V;
-        T sK = sqrt(K);
+        // upwind rates, the 1D operator along each axis (the axis-sum reading)
+        const T K = O::div(O::mul(g, P), V);
+        const T sK = sqrt(K);
+        const T hV = O::mul(T(0.5), V);
+        const T hVsK = O::mul(hV, sK);
+        const T hVK = O::mul(hV, K);
+        const T VsK2 = O::div(V, O::mul(T(2), sK));
         T Vt = T(0), Pt = T(0);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
             T ul = os[k][0][1 + k], ur = os[k][1][1 + k];
             T Pl = os[k][0][F - 1], Pr = os[k][1][F - 1];
-            Vt += T(0.5) * V * (ur + ul) - V / (T(2) * sK) * (Pr - Pl);
-            uw[1 + k] = T(0.5) * V * sK * (ur - ul) - T(0.5) * V * (Pr + Pl);
-            Pt += T(-0.5) * V * K * (ur + ul) + T(0.5) * V * sK * (Pr - Pl);
+            T su = O::add(ur, ul), du = O::sub(ur, ul), sP = O::add(Pr, Pl), dP = O::sub(Pr, Pl);
+            Vt = O::add(Vt, O::sub(O::mul(hV, su), O::mul(VsK2, dP)));
+            uw[1 + k] = O::sub(O::mul(hVsK, du), O::mul(hV, sP));
+            Pt = O::add(Pt, O::sub(O::mul(hVsK, dP), O::mul(hVK, su)));
         }
         uw[0] = Vt;
         uw[F - 1] = Pt;
@@ -213,7 +255,7 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
         T sl[DIM], sr[DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) { sl[k] = os[k][0][f]; sr[k] = os[k][1][f]; }
-        rs[f] = plain ? estimator_r<T, DIM>(sl, sr, ell, (T)s0[f], (T)c.s_ref[f], (T)c.flat_eps, (T)c.active_frac)
+        rs[f] = plain ? estimator_r<T, DIM>(sl, sr, ell, (T)L.s0[f], (T)c.s_ref[f], (T)c.flat_eps, (T)c.active_frac)
                       : T(1);
         any = any || rs[f] > T(1.5);
     }
@@ -233,8 +275,8 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
         case LP_LIM_UW: p = T(0); break;
         default: p = any ? phi_limiter<T>(rs[f]) : T(1); break;
         }
-        T rate = uw[f] - p * (uw[f] - lw[f]);
-        s1[f] = __dadd_rn(s0[f], __dmul_rn(dt, (double)rate));   // no contraction: the oracle's rounding
+        T rate = O::sub(uw[f], O::mul(p, O::sub(uw[f], lw[f])));
+        s1[f] = __dadd_rn(L.s0[f], __dmul_rn(dt, (double)rate));   // no contraction: the oracle's rounding
         if (o.phi) o.phi[i * F + f] = (float)p;
         if (o.r) o.r[i * F + f] = (float)rs[f];
     }
@@ -245,14 +287,14 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     for (int f = 0; f < F; ++f) admissible = admissible && isfinite(s1[f]);
     if (!admissible) {
 #pragma unroll
-        for (int f = 0; f < F; ++f) s1[f] = s0[f];
+        for (int f = 0; f < F; ++f) s1[f] = L.s0[f];
         atomicAdd(a.counters + C_NONFINITE, 1ull);
         atomicOr(reinterpret_cast<unsigned int*>(a.counters + C_STATUS), ST_NONFINITE);
     }
-    // mover, Eq. timeIntegrate
+    // mover, Sec. 2.5: x += dt (u^n + u^{n+1}) / 2
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-        double xk = __dadd_rn(x0[k], __dmul_rn(__dmul_rn(0.5, dt), __dadd_rn(s0[1 + k], s1[1 + k])));
+        double xk = __dadd_rn(L.x0[k], __dmul_rn(__dmul_rn(0.5, dt), __dadd_rn(L.s0[1 + k], s1[1 + k])));
         if (c.periodic[k]) {
             if (xk >= c.box_hi[k]) xk = __dsub_rn(xk, c.Lper[k]);
             else if (xk < c.box_lo[k]) xk = __dadd_rn(xk, c.Lper[k]);
@@ -263,9 +305,44 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     o.V[i] = s1[0];
     o.P[i] = s1[F - 1];
     o.m[i] = a.sm[i];
-    o.id[i] = idi;
+    o.id[i] = L.id;
     if (o.flag) o.flag[i] = any ? 1 : 0;
     warp_count(a.counters, C_FLAGGED, any);
+}
+
+template <typename T, int DIM>
+__device__ inline void skip_plain(const T (&cdf)[DIM][DIM + 2], T (&os)[DIM][2][DIM + 2])
+{
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int f = 0; f < DIM + 2; ++f) os[k][s][f] = cdf[k][f];
+}
+
+// fused schedule: all stages in one thread
+template <typename T, int DIM>
+__device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
+{
+    constexpr int F = DIM + 2;
+    Loaded<DIM> L;
+    if (step_load<T, DIM>(a, o, i, L)) return;
+    Src<T, DIM, F> src(a, i);
+    const int cnt = (int)a.count[i];
+    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
+    const T invS = (T)inv_scale(last_d2(src, nb, cnt));
+    T cdf[DIM][F], lw[F];
+    bool mlp_skip;
+    if (!step_central<T, DIM>(a, o, i, L, src, nb, cnt, invS, cdf, lw, mlp_skip)) return;
+    const bool plain = !mlp_skip || a.c.mlp_audit;
+    T os[DIM][2][F];
+    if (plain) {
+        if (!step_plain<T, DIM>(a, i, src, nb, cnt, invS, cdf, os)) return;
+    } else {
+        skip_plain<T, DIM>(cdf, os);
+    }
+    step_finish<T, DIM>(a, o, i, L, os, lw, plain, mlp_skip);
 }
 
 template <typename T, int DIM>
@@ -280,6 +357,89 @@ __global__ void __launch_bounds__(128) k_step(FitArgs a, StepOut o)
         int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
         if (i < a.n) step_one<T, DIM>(a, o, i);
     }
+}
+
+// intermediate record of the split schedule, component-major over list slots:
+// mid[q * cap + t], q < DIM*F central first derivatives, then F LW rates, then
+// the gate bit
+template <int DIM> struct MidN { static constexpr int v = DIM * (DIM + 2) + (DIM + 2) + 1; };
+
+__device__ inline unsigned long long warp_append(unsigned long long* len, bool pred)
+{
+    unsigned m = __activemask();
+    unsigned b = __ballot_sync(m, pred);
+    int lane = (int)(threadIdx.x & 31u);
+    int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader && b) base = atomicAdd(len, (unsigned long long)__popc(b));
+    base = __shfl_sync(m, base, leader);
+    return base + (unsigned long long)__popc(b & ((1u << lane) - 1u));
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) k_step_central(FitArgs a, StepOut o)
+{
+    constexpr int F = DIM + 2;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    Loaded<DIM> L;
+    if (step_load<T, DIM>(a, o, i, L)) return;
+    Src<T, DIM, F> src(a, i);
+    const int cnt = (int)a.count[i];
+    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
+    const T invS = (T)inv_scale(last_d2(src, nb, cnt));
+    T cdf[DIM][F], lw[F];
+    bool mlp_skip;
+    if (!step_central<T, DIM>(a, o, i, L, src, nb, cnt, invS, cdf, lw, mlp_skip)) return;
+    const bool plain = !mlp_skip || a.c.mlp_audit;
+    unsigned long long t = warp_append(a.plain_len, plain);
+    if (plain) {
+        T* mid = static_cast<T*>(a.mid);
+        const int64_t cap = a.mid_cap;
+        a.plain_list[t] = (uint32_t)i;
+        int q = 0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+#pragma unroll
+            for (int f = 0; f < F; ++f) mid[(q++) * cap + t] = cdf[k][f];
+#pragma unroll
+        for (int f = 0; f < F; ++f) mid[(q++) * cap + t] = lw[f];
+        mid[q * cap + t] = mlp_skip ? T(1) : T(0);
+        return;
+    }
+    T os[DIM][2][F];
+    skip_plain<T, DIM>(cdf, os);
+    step_finish<T, DIM>(a, o, i, L, os, lw, false, true);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) k_step_plain(FitArgs a, StepOut o)
+{
+    constexpr int F = DIM + 2;
+    const unsigned long long len = *a.plain_len;
+    const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    if (t >= len) return;
+    const int64_t i = a.plain_list[t];
+    const T* mid = static_cast<const T*>(a.mid);
+    const int64_t cap = a.mid_cap;
+    T cdf[DIM][F], lw[F];
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+#pragma unroll
+        for (int f = 0; f < F; ++f) cdf[k][f] = mid[(q++) * cap + t];
+#pragma unroll
+    for (int f = 0; f < F; ++f) lw[f] = mid[(q++) * cap + t];
+    const bool mlp_skip = mid[q * cap + t] != T(0);
+    Loaded<DIM> L;
+    step_load<T, DIM>(a, o, i, L);          // never frozen: frozen particles are not listed
+    Src<T, DIM, F> src(a, i);
+    const int cnt = (int)a.count[i];
+    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
+    const T invS = (T)inv_scale(last_d2(src, nb, cnt));
+    T os[DIM][2][F];
+    if (!step_plain<T, DIM>(a, i, src, nb, cnt, invS, cdf, os)) return;
+    step_finish<T, DIM>(a, o, i, L, os, lw, true, mlp_skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,6 +577,8 @@ __global__ void __launch_bounds__(128) k_onesided(FitArgs a, double* out, int f_
 // launchers, defined once per precision in lp_fit_f32.cu / lp_fit_f64.cu
 cudaError_t launch_step_f32(int dim, const FitArgs& a, const StepOut& o, cudaStream_t s);
 cudaError_t launch_step_f64(int dim, const FitArgs& a, const StepOut& o, cudaStream_t s);
+cudaError_t launch_step_split_f32(int dim, const FitArgs& a, const StepOut& o, cudaStream_t s);
+cudaError_t launch_step_split_f64(int dim, const FitArgs& a, const StepOut& o, cudaStream_t s);
 cudaError_t launch_derivs_f32(int dim, int F, const FitArgs& a, const DerivOut& o, cudaStream_t s);
 cudaError_t launch_derivs_f64(int dim, int F, const FitArgs& a, const DerivOut& o, cudaStream_t s);
 cudaError_t launch_onesided_f32(int dim, const FitArgs& a, double* out, int f_real, cudaStream_t s);
@@ -435,6 +597,23 @@ inline unsigned fit_blocks(const FitArgs& a)
         if (dim == 3) k_step<T, 3><<<b, 128, 0, s>>>(a, o);                                     \
         else if (dim == 2) k_step<T, 2><<<b, 128, 0, s>>>(a, o);                                \
         else k_step<T, 1><<<b, 128, 0, s>>>(a, o);                                              \
+        return cudaGetLastError();                                                              \
+    }                                                                                           \
+    cudaError_t launch_step_split_##SUF(int dim, const FitArgs& a, const StepOut& o,            \
+                                        cudaStream_t s)                                         \
+    {                                                                                           \
+        unsigned b = (unsigned)((a.n + 127) / 128);                                             \
+        if (b == 0) return cudaSuccess;                                                         \
+        if (dim == 3) {                                                                         \
+            k_step_central<T, 3><<<b, 128, 0, s>>>(a, o);                                       \
+            k_step_plain<T, 3><<<b, 128, 0, s>>>(a, o);                                         \
+        } else if (dim == 2) {                                                                  \
+            k_step_central<T, 2><<<b, 128, 0, s>>>(a, o);                                       \
+            k_step_plain<T, 2><<<b, 128, 0, s>>>(a, o);                                         \
+        } else {                                                                                \
+            k_step_central<T, 1><<<b, 128, 0, s>>>(a, o);                                       \
+            k_step_plain<T, 1><<<b, 128, 0, s>>>(a, o);                                         \
+        }                                                                                       \
         return cudaGetLastError();                                                              \
     }                                                                                           \
     cudaError_t launch_derivs_##SUF(int dim, int F, const FitArgs& a, const DerivOut& o,        \

@@ -31,7 +31,7 @@ constexpr uint32_t FIT_LINEAR = 1u, FIT_NONE = 2u, FIT_FP64 = 8u;
 // device counters (unsigned long long each)
 enum Counter {
     C_FLAGGED = 0, C_FP64, C_LINEAR, C_NOFIT, C_OVERFLOW, C_NONFINITE, C_MLP_UNCERTAIN,
-    C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_MLP_SKIP, C_MLP_MISS, C_COUNT
+    C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_MLP_SKIP, C_MLP_MISS, C_PLAIN_LEN, C_COUNT
 };
 
 // method constants as the kernels see them
@@ -213,6 +213,10 @@ struct lp_ctx {
     int nsim;                     // simulations of the current call
     unsigned long long* counters;
     uint32_t* redo_list;
+    // split fit schedule: compacted plain-stage list and intermediate record
+    uint32_t* plain_list;
+    void* mid;
+    int schedule;                 // LP_SCHED_FUSED / LP_SCHED_SPLIT
     int64_t n_lists;          // n of the last neighbour build (0: none)
     int tables_dirty;         // tables hold entries of the last build
     double reduce_min_w;

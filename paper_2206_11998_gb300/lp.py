@@ -22,6 +22,7 @@ RADIUS_FIXED, RADIUS_VOLUME, RADIUS_KSIDE = 0, 1, 2
 LIM_FLAGGED, LIM_PAPER, LIM_LW, LIM_UW = 0, 1, 2, 3
 EST_PLAIN, EST_MLP = 0, 1
 OUT_F32, OUT_F64 = 0, 1
+SCHED_FUSED, SCHED_SPLIT = 0, 1
 
 EXPORTED = [
     "lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs", "lp_step",
@@ -29,6 +30,7 @@ EXPORTED = [
     "lp_status_string", "lp_version", "lp_set_profiling", "lp_phase_times", "lp_phase_name",
     "lp_sort_keys_noalloc", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step",
     "lp_mlp_train", "lp_mlp_infer", "lp_step_batched", "lp_graph_capture", "lp_graph_launch",
+    "lp_set_schedule", "lp_get_schedule", "lp_autotune",
 ]
 MLP_IN, MLP_H = 8, 32
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H + 1
@@ -112,6 +114,9 @@ def lib():
         L.lp_graph_capture.argtypes = [P, C.POINTER(Particles), P, C.c_int32, C.c_double, C.c_double, P, P]
         L.lp_graph_capture.restype = C.c_int
         L.lp_graph_launch.argtypes = [P, P]
+        L.lp_set_schedule.argtypes = [P, C.c_int32]
+        L.lp_get_schedule.argtypes = [P, P]
+        L.lp_autotune.argtypes = [P, C.POINTER(Particles), P, C.c_int32, C.c_double, C.c_double, C.c_int32, P, P]
         L.lp_graph_launch.restype = C.c_int
         L.lp_export_neighbors.argtypes = [P, P, P, P, P, P, P]
         L.lp_grid_info.argtypes = [P, P, P]
@@ -333,6 +338,23 @@ class Context:
 
     def graph_launch(self, stream=None):
         _check(lib().lp_graph_launch(self.h, _stream(stream)), "lp_graph_launch")
+
+    def set_schedule(self, schedule: int):
+        _check(lib().lp_set_schedule(self.h, int(schedule)), "lp_set_schedule")
+
+    def schedule(self) -> int:
+        v = C.c_int32()
+        _check(lib().lp_get_schedule(self.h, C.byref(v)), "lp_get_schedule")
+        return v.value
+
+    def autotune(self, ps: ParticleSet, offsets=None, nsim=1, dt=0.0, cfl=0.4, reps=3, stream=None):
+        """Time the fit pass under both schedules on this state and keep the faster;
+        returns (fused_ms, split_ms).  The state is not changed."""
+        p = ps.struct()
+        out = (C.c_double * 2)()
+        _check(lib().lp_autotune(self.h, C.byref(p), _ptr(offsets), int(nsim), float(dt), float(cfl), int(reps),
+                                 out, _stream(stream)), "lp_autotune")
+        return out[0], out[1]
 
     def stats(self, stream=None) -> dict:
         s = Stats()
