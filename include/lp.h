@@ -85,7 +85,8 @@ enum { LP_OUT_F32 = 0, LP_OUT_F64 = 1 };
  *                  below tau32 are redone in FP64; below tau64 (FP64) the
  *                  second-order fit is replaced by the first-order one.
  *   periodic[3], box_lo[3], box_hi[3]   periodic axes use the minimum image
- *                  and wrap moved particles; a periodic box must be a cube.
+ *                  and wrap moved particles; a periodic box must be a cube and
+ *                  periodic on all dim axes (LP_ERR_ARG otherwise).
  *   n_fluid        particles whose id >= n_fluid are frozen boundary
  *                  particles: neighbours of others, never updated or moved.
  *   capacity       largest n any call will pass (scratch is sized for it).
@@ -171,6 +172,8 @@ typedef struct {
     int64_t kernel_launches;   /* kernels this context launched (host-side count) */
     int64_t n_mlp_skip;        /* particle-steps the learned estimator declared unflagged */
     int64_t n_mlp_miss;        /* ... of which the plain estimator flags (audit mode) */
+    int64_t n_query_fallback;  /* particles of the last neighbour build listed by the warp-per-particle
+                                  query (more than 64 neighbours, or a tile spread over too many cells) */
 } lp_stats;
 
 typedef struct lp_ctx lp_ctx;

@@ -59,6 +59,9 @@ lp_status check_cfg(const lp_config* g)
     if (g->capacity < 1 || g->capacity > (int64_t)0x7fffffff) return LP_ERR_ARG;
     if (!(g->tau32 >= 0.0) || !(g->tau64 >= 0.0)) return LP_ERR_ARG;
     double L = -1.0;
+    int nper = 0;
+    for (int k = 0; k < g->dim; ++k) nper += g->periodic[k] ? 1 : 0;
+    if (nper != 0 && nper != g->dim) return LP_ERR_ARG;   // periodic on every axis or on none
     for (int k = 0; k < g->dim; ++k) {
         if (!g->periodic[k]) continue;
         double e = g->box_hi[k] - g->box_lo[k];
@@ -394,6 +397,7 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
         A(cudaMemset(c->dt_dev, 0, 8 * ns));
         A(cudaMemcpy(c->level_off_dev, c->level_off, sizeof(int64_t) * (MAX_LEVELS + 1), cudaMemcpyHostToDevice));
         for (int q = 0; q < 2 * EV_PAIRS && ok; ++q) A(cudaEventCreate(&c->ev[q]));
+        A(query_init());
         A(cudaDeviceSynchronize());
     }
     if (!ok) {
@@ -448,7 +452,7 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
         c->tables_dirty = tables ? 1 : 0;
     }
     {
-        Phase ph(c, LP_PH_QUERY, c->dc.radius_mode == LP_RADIUS_KSIDE ? 1 : 2, s);
+        Phase ph(c, LP_PH_QUERY, c->dc.radius_mode == LP_RADIUS_KSIDE ? 1 : (c->dc.dim == 1 ? 2 : 3), s);
         LP_CUDA(query_neighbors(c, n, s));
     }
     c->n_lists = n;
@@ -839,6 +843,7 @@ lp_status lp_get_stats(lp_ctx* c, lp_stats* out, lp_stream stream)
     out->kernel_launches = c->launches;
     out->n_mlp_skip = (int64_t)h[C_MLP_SKIP];
     out->n_mlp_miss = (int64_t)h[C_MLP_MISS];
+    out->n_query_fallback = (int64_t)h[C_QFB_LEN];
     return LP_OK;
 }
 

@@ -31,7 +31,7 @@ constexpr uint32_t FIT_LINEAR = 1u, FIT_NONE = 2u, FIT_FP64 = 8u;
 // device counters (unsigned long long each)
 enum Counter {
     C_FLAGGED = 0, C_FP64, C_LINEAR, C_NOFIT, C_OVERFLOW, C_NONFINITE, C_MLP_UNCERTAIN,
-    C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_MLP_SKIP, C_MLP_MISS, C_PLAIN_LEN, C_COUNT
+    C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_MLP_SKIP, C_MLP_MISS, C_PLAIN_LEN, C_QFB_LEN, C_COUNT
 };
 
 // method constants as the kernels see them
@@ -252,6 +252,7 @@ cudaError_t radix_sort(lp_ctx* c, int64_t n, cudaStream_t s);
 cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s);
 cudaError_t fill_tables(lp_ctx* c, int64_t n, bool clear, cudaStream_t s);
 cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s);
+cudaError_t query_init();   // once per context: kernel attributes
 cudaError_t scatter_back(lp_ctx* c, lp_particles* p, cudaStream_t s);
 cudaError_t split_fields(lp_ctx* c, int64_t n, const double* const* f, int nf, cudaStream_t s);
 cudaError_t run_derivs(lp_ctx* c, int64_t n, const double* const* f, int nf, int out_dtype,

@@ -37,6 +37,12 @@ struct QueryArgs {
     uint32_t* idx;
     double* d2min;
     unsigned long long* counters;
+    // the per-particle kernel runs over this list (null: every particle)
+    const uint32_t* list;
+    const unsigned long long* list_len;
+    // the tile kernel appends the particles it leaves here
+    uint32_t* fb_list;
+    unsigned long long* fb_len;
 };
 
 template <int DIM>
@@ -169,14 +175,9 @@ __device__ void sort_exact(const QueryArgs& a, WarpBuf& b, int m, int64_t i)
 // Split cells go to the next frontier, processed once the current one is done,
 // so the k_max-th distance found so far prunes them.
 template <int DIM>
-__global__ void __launch_bounds__(NB_WARPS * 32) k_query(QueryArgs a)
+__device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
 {
-    __shared__ WarpBuf bufs[NB_WARPS];
     unsigned lane = lane_id();
-    int w = threadIdx.x >> 5;
-    WarpBuf& b = bufs[w];
-    int64_t i = (int64_t)blockIdx.x * NB_WARPS + w;
-    if (i >= a.n) return;
     const DevCfg& c = a.c;
     const int mb = c.mbits;
     const uint64_t sim = c.nsim_max > 1 ? (a.keys[i] >> (DIM * mb)) : 0ull;
@@ -423,6 +424,522 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_query(QueryArgs a)
         if (inside_total > (uint32_t)c.k_max) atomicAdd(a.counters + C_OVERFLOW, 1ull);
         atomicMax(a.counters + C_MAXCOUNT, (unsigned long long)inside_total);
     }
+    __syncwarp();
+}
+
+// warp per particle: every particle, or the particles of a list
+template <int DIM>
+__global__ void __launch_bounds__(NB_WARPS * 32) k_query(QueryArgs a)
+{
+    __shared__ WarpBuf bufs[NB_WARPS];
+    const int w = threadIdx.x >> 5;
+    WarpBuf& b = bufs[w];
+    if (a.list) {
+        const unsigned long long len = *a.list_len;
+        for (unsigned long long t = (unsigned long long)blockIdx.x * NB_WARPS + w; t < len;
+             t += (unsigned long long)gridDim.x * NB_WARPS)
+            query_one<DIM>(a, b, (int64_t)a.list[t]);
+    } else {
+        const int64_t i = (int64_t)blockIdx.x * NB_WARPS + w;
+        if (i < a.n) query_one<DIM>(a, b, i);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile kernel: one warp per 32 consecutive particles in key order.  The tile
+// is cut into groups where consecutive particles lie more than TQ_GAP radii
+// apart (jumps of the Morton curve) or belong to different simulations; each
+// group is a compact region of space.  For a group:
+//   1. the cells of one level (edge >= half the group's largest radius) within
+//      reach of the group's bounding box are classified lane-parallel and the
+//      non-empty ones compacted;
+//   2. their particles are staged 32 at a time in shared memory as positions
+//      relative to the group's first particle, and every lane tests each staged
+//      candidate against its own particle with a margin that covers the
+//      rounding of the relative coordinates (a prefilter: no neighbour is
+//      lost), keeping the index of each hit in its own column of a shared list;
+//   3. per particle, the warp recomputes the hits' distances exactly as the
+//      per-particle kernel does (float hi/lo offsets; FP64 inside the rounding
+//      band of the radius), sorts (float d2, index) with a register bitonic
+//      network, re-orders near-tie runs by (FP64 d2, id) and writes the row.
+// Particles with more than TQ_CAP hits, and groups whose region spans too many
+// cells or candidates, are left to the per-particle kernel.
+// ---------------------------------------------------------------------------
+constexpr int TQ_WARPS = 4;
+constexpr int TQ_CAP = KMAX;          // prefilter hits a lane keeps
+constexpr int TQ_PAD = 33;            // column stride: a row read across lanes is conflict-free
+constexpr int TQ_CELLS_MAX = 4096;    // cells a group's region may span
+constexpr uint32_t TQ_CAND_MAX = 4096;   // candidates a group may test
+constexpr int TQ_KC = 256;            // non-empty cells a group may keep
+constexpr float TQ_GAP = 2.0f;        // in radii
+
+struct TileBuf {
+    uint32_t kj[TQ_CAP][TQ_PAD];      // prefilter hits, one column per lane
+    unsigned long long kc[TQ_KC];     // kept cells: start | count << 32
+    float4 cr[32];                    // staged candidates: relative position, index bits in w
+    uint32_t cstart[32], cexcl[32];
+};
+
+__device__ inline float warp_minf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ inline float warp_maxf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ inline void list_append(const QueryArgs& a, bool pred, uint32_t v)
+{
+    unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (!m) return;
+    unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.fb_len, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (pred) a.fb_list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+// own position (hi, lo), quantised position, radius terms of particle i
+template <int DIM>
+struct TileLane {
+    float hx[3], lx[3], tq[3];
+    float Rf, R2f, Rq, Rout;
+};
+
+template <int DIM, bool PER>
+__device__ inline void tile_lane(const QueryArgs& a, const Grid& g, int64_t i, TileLane<DIM>& t)
+{
+    const DevCfg& c = a.c;
+    const float inv = g.inv_f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { t.hx[k] = 0.0f; t.lx[k] = 0.0f; t.tq[k] = 0.0f; }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        t.hx[k] = a.hx[k][i]; t.lx[k] = a.lx[k][i];
+        t.tq[k] = ((t.hx[k] - g.lo_h[k]) + (t.lx[k] - g.lo_l[k])) * inv;
+    }
+    float Rf;
+    if (c.radius_mode == LP_RADIUS_FIXED) Rf = (float)c.radius;
+    else {
+        float wf = (float)a.sm[i] * (float)a.sV[i];
+        if (!(wf > 0.0f)) wf = 0.0f;
+        float r = DIM == 3 ? cbrtf(wf) : (DIM == 2 ? sqrtf(wf) : wf);
+        Rf = (float)c.kappa * r;
+    }
+    if (!(Rf >= 0.0f) || isinf(Rf)) Rf = 0.0f;
+    t.Rf = Rf;
+    t.R2f = (c.radius_mode == LP_RADIUS_FIXED) ? (float)(c.radius * c.radius) : Rf * Rf;
+    t.Rq = Rf * (1.0f + 1e-5f) * inv;
+    t.Rout = Rf * inv * (1.0f + 2e-5f) + 2.0f;
+}
+
+// float offset x_j - x_i along k from hi/lo parts (minimum image): the
+// per-particle kernel's arithmetic, so both give the same float d2
+template <bool PER>
+__device__ inline float split_offset(const DevCfg& c, int k, float hj, float lj, float hi, float li)
+{
+    float dh = hj - hi;
+    float dl = lj - li;
+    if (PER && c.periodic[k]) {
+        if (dh > 0.5f * c.Lper_h[k]) { dh -= c.Lper_h[k]; dl -= c.Lper_l[k]; }
+        else if (dh < -0.5f * c.Lper_h[k]) { dh += c.Lper_h[k]; dl += c.Lper_l[k]; }
+    }
+    return dh + dl;
+}
+
+// one (key, index) compare-exchange partner step of the bitonic network
+__device__ inline void bitonic_take(uint32_t& key, uint32_t& j, uint32_t pk, uint32_t pj, bool take_min)
+{
+    const bool mine_smaller = key < pk || (key == pk && j < pj);
+    if (take_min != mine_smaller) { key = pk; j = pj; }
+}
+
+// ascending sort of P = 32 * W (W = 1 or 2) (key, index) pairs, element
+// e = lane + 32 s held by lane in (key[s], j[s])
+template <int W>
+__device__ inline void bitonic_sort(uint32_t (&key)[2], uint32_t (&j)[2])
+{
+    const unsigned lane = lane_id();
+    constexpr int P = 32 * W;
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            if (jj >= 32) {                  // partner in the other register of this lane
+                const bool up = ((lane & (unsigned)k) == 0u);     // k = 64: always ascending
+                const bool sw = (key[0] > key[1] || (key[0] == key[1] && j[0] > j[1])) == up;
+                if (sw) {
+                    uint32_t t = key[0]; key[0] = key[1]; key[1] = t;
+                    t = j[0]; j[0] = j[1]; j[1] = t;
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < W; ++s) {
+                    const unsigned e = lane + 32u * s;
+                    const uint32_t pk = __shfl_xor_sync(0xffffffffu, key[s], jj);
+                    const uint32_t pj = __shfl_xor_sync(0xffffffffu, j[s], jj);
+                    const bool lower = (e & (unsigned)jj) == 0u;
+                    const bool up = (e & (unsigned)k) == 0u;
+                    bitonic_take(key[s], j[s], pk, pj, lower == up);
+                }
+            }
+        }
+    }
+}
+
+// one group of lanes of the tile (act); all 32 lanes take part
+template <int DIM, bool PER>
+__device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, uint64_t sim)
+{
+    const unsigned lane = lane_id();
+    const DevCfg& c = a.c;
+    const int mb = c.mbits;
+    const Grid& g = a.g[sim];
+    TileLane<DIM> me;
+    if (act) tile_lane<DIM, PER>(a, g, i, me);
+    else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { me.hx[k] = 0.0f; me.lx[k] = 0.0f; me.tq[k] = 0.0f; }
+        me.Rf = me.R2f = me.Rq = me.Rout = 0.0f;
+    }
+    if (PER && act) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+            if (c.periodic[k] && 2.0f * me.Rq >= ldexpf(1.0f, mb))
+                atomicOr(reinterpret_cast<unsigned int*>(a.counters + C_STATUS), ST_ARG);
+    }
+    // bounding box of the group and its largest radius (quantised units)
+    float bmin[3] = {0.0f, 0.0f, 0.0f}, bmax[3] = {0.0f, 0.0f, 0.0f};
+    float ext = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        bmin[k] = warp_minf(act ? me.tq[k] : INFINITY);
+        bmax[k] = warp_maxf(act ? me.tq[k] : -INFINITY);
+        ext = fmaxf(ext, bmax[k] - bmin[k]);
+    }
+    const float Rqm = warp_maxf(act ? me.Rq : 0.0f);
+    const float Routm = warp_maxf(act ? me.Rout : 0.0f);
+    // finest table level whose cell edge 2^(mb - l) is at least half the radius
+    const float Rh = 0.5f * Rqm;
+    int l0 = g.lmax;
+    while (l0 > g.lmin && ldexpf(1.0f, mb - l0) < Rh) --l0;
+    const float size = ldexpf(1.0f, mb - l0);
+    const float scale = ldexpf(1.0f, l0 - mb);
+    const float period = ldexpf(1.0f, mb);
+    const int naxis = 1 << l0;
+    int clo[3] = {0, 0, 0}, nc[3] = {1, 1, 1};
+    bool full[3] = {false, false, false};   // the region wraps a whole period on this axis
+    long long ncells = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        float lo_f = fmaxf(-16777216.0f, fminf(16777216.0f, (bmin[k] - Rqm - 2.0f) * scale));
+        float hi_f = fmaxf(-16777216.0f, fminf(16777216.0f, (bmax[k] + Rqm + 2.0f) * scale));
+        int a0 = (int)floorf(lo_f), a1 = (int)floorf(hi_f);
+        if (!PER || !c.periodic[k]) {
+            a0 = max(0, min(a0, naxis - 1));
+            a1 = max(0, min(a1, naxis - 1));
+        } else if (a1 - a0 + 1 > naxis) {
+            // each cell once, at one of its images -- not necessarily the one
+            // nearest the box, so this axis takes no part in the pruning
+            a1 = a0 + naxis - 1;
+            full[k] = true;
+        }
+        clo[k] = a0;
+        nc[k] = a1 - a0 + 1;
+        ncells = nc[k] < 1 ? 0 : ncells * nc[k];
+    }
+    if (ncells > TQ_CELLS_MAX) {      // a scattered group: per particle instead
+        list_append(a, act, (uint32_t)i);
+        return;
+    }
+    const int nct = (int)ncells;
+
+    // ---- 1. kept non-empty cells, compacted
+    const unsigned lt = (1u << lane) - 1u;
+    int nk = 0;
+    uint32_t ncand = 0;
+    bool over = false;
+    for (int base0 = 0; base0 < nct && !over; base0 += 32) {
+        const int e = base0 + (int)lane;
+        uint32_t cs = 0, cn = 0;
+        if (e < nct) {
+            int u = e;
+            uint32_t q[3] = {0u, 0u, 0u};
+            float dmin2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const int v = clo[k] + u % nc[k];
+                u /= nc[k];
+                const int wr = v & (naxis - 1);
+                const int sh = (v - wr) >> l0;          // periodic image (0 on other axes)
+                const float lo = (float)wr * size + (float)sh * period;
+                const float dn = full[k] ? 0.0f : fmaxf(0.0f, fmaxf(lo - bmax[k], bmin[k] - (lo + size)));
+                dmin2 += dn * dn;
+                q[k] = (uint32_t)wr;
+            }
+            if (sqrtf(dmin2) < Routm) {
+                const uint64_t code = (sim << (DIM * l0)) | morton<DIM>(q);
+                const unsigned long long ent = a.cells[a.level_off[l0] + (int64_t)code];
+                cs = (uint32_t)ent;
+                const uint32_t ce = (uint32_t)(ent >> 32);
+                cn = ce > cs ? ce - cs : 0;
+            }
+        }
+        const unsigned km = __ballot_sync(0xffffffffu, cn > 0);
+        ncand += __reduce_add_sync(0xffffffffu, cn);
+        if (nk + __popc(km) > TQ_KC || ncand > TQ_CAND_MAX) { over = true; break; }
+        if (cn > 0) b.kc[nk + __popc(km & lt)] = (unsigned long long)cs | ((unsigned long long)cn << 32);
+        nk += __popc(km);
+    }
+    if (over) {                       // a dense region under a wide group: per particle instead
+        list_append(a, act, (uint32_t)i);
+        return;
+    }
+    __syncwarp();
+
+    // ---- 2. prefilter: candidates relative to the group's first particle
+    const int lead = __ffs(__ballot_sync(0xffffffffu, act)) - 1;
+    float oh[3], ol[3], ri[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        oh[k] = __shfl_sync(0xffffffffu, me.hx[k], lead);
+        ol[k] = __shfl_sync(0xffffffffu, me.lx[k], lead);
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) ri[k] = split_offset<PER>(c, k, me.hx[k], me.lx[k], oh[k], ol[k]);
+    // rounding margin of the relative coordinates: each is within 2^-23 |r| of
+    // the split value and |r| <= E / sqrt(dim) per axis, so the prefilter's d2
+    // is within 2^-24 (7 d2 + 8 E |d|) of the true one; a true neighbour has
+    // d2 <= R^2 <= R2f (1 + TOL_R), hence d2_prefilter <= thr
+    float E = (ext + Rqm + size + 4.0f) / g.inv_f;
+    if (PER) E = fmaxf(E, g.L_f);
+    E *= DIM == 3 ? 1.7320508f : (DIM == 2 ? 1.4142136f : 1.0f);
+    const float thr = me.R2f * (1.0f + TOL_R) + ldexpf(me.R2f + 4.0f * E * me.Rf, -20);
+    float halfL[3], Lh[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { Lh[k] = c.Lper_h[k]; halfL[k] = 0.5f * c.Lper_h[k]; }
+    uint32_t cnt = 0;                 // prefilter hits of this lane
+    for (int c0 = 0; c0 < nk; c0 += 32) {
+        uint32_t cs = 0, cn = 0;
+        if (c0 + (int)lane < nk) {
+            const unsigned long long ent = b.kc[c0 + lane];
+            cs = (uint32_t)ent;
+            cn = (uint32_t)(ent >> 32);
+        }
+        uint32_t incl = cn;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += v;
+        }
+        const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+        b.cstart[lane] = cs;
+        b.cexcl[lane] = incl - cn;
+        __syncwarp();
+        for (uint32_t base = 0; base < T; base += 32) {
+            const uint32_t t = base + lane;
+            if (t < T) {
+                int lo = 0, hi = 31;                  // the last cell with cexcl <= t
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                const uint32_t j = b.cstart[lo] + (t - b.cexcl[lo]);
+                const float4 ph = __ldg(a.pos4 + 2 * (int64_t)j);
+                const float4 pl = __ldg(a.pos4 + 2 * (int64_t)j + 1);
+                float4 r;
+                r.x = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
+                r.y = DIM > 1 ? split_offset<PER>(c, 1, ph.y, pl.y, oh[1], ol[1]) : 0.0f;
+                r.z = DIM > 2 ? split_offset<PER>(c, 2, ph.z, pl.z, oh[2], ol[2]) : 0.0f;
+                r.w = __uint_as_float(j);
+                b.cr[lane] = r;
+            }
+            __syncwarp();
+            const int nb = (int)min(32u, T - base);
+            if (act) {
+#pragma unroll 4
+                for (int qq = 0; qq < nb; ++qq) {
+                    const float4 r = b.cr[qq];
+                    float d[3] = {r.x - ri[0], r.y - ri[1], r.z - ri[2]};
+                    if (PER) {
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k)
+                            if (c.periodic[k]) {
+                                if (d[k] > halfL[k]) d[k] -= Lh[k];
+                                else if (d[k] < -halfL[k]) d[k] += Lh[k];
+                            }
+                    }
+                    float d2 = d[0] * d[0];
+                    if (DIM > 1) d2 = fmaf(d[1], d[1], d2);
+                    if (DIM > 2) d2 = fmaf(d[2], d[2], d2);
+                    const uint32_t j = __float_as_uint(r.w);
+                    if (d2 <= thr && (int64_t)j != i) {
+                        if (cnt < (uint32_t)TQ_CAP) b.kj[cnt][lane] = j;
+                        ++cnt;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+
+    // ---- 3. per particle: exact membership, order, row
+    const bool mine = act && cnt <= (uint32_t)TQ_CAP;
+    list_append(a, act && !mine, (uint32_t)i);
+    const uint32_t kmax = (uint32_t)c.k_max;
+    uint32_t mx = 0, novf = 0;
+    unsigned todo = __ballot_sync(0xffffffffu, mine);
+    while (todo) {
+        const int p = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int m = (int)__shfl_sync(0xffffffffu, cnt, p);
+        const int64_t ip = i - (int64_t)lane + p;
+        float ph_[3], pl_[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ph_[k] = __shfl_sync(0xffffffffu, me.hx[k], p);
+            pl_[k] = __shfl_sync(0xffffffffu, me.lx[k], p);
+        }
+        const float pR2 = __shfl_sync(0xffffffffu, me.R2f, p);
+        uint32_t key[2] = {0xffffffffu, 0xffffffffu}, jv[2] = {0xffffffffu, 0xffffffffu};
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int e = (int)lane + 32 * s;
+            if (e < m) {
+                const uint32_t j = b.kj[e][p];
+                const float4 qh = __ldg(a.pos4 + 2 * (int64_t)j);
+                const float4 ql = __ldg(a.pos4 + 2 * (int64_t)j + 1);
+                const float hj[3] = {qh.x, qh.y, qh.z}, lj[3] = {ql.x, ql.y, ql.z};
+                float d2f = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) {
+                    const float dd = split_offset<PER>(c, k, hj[k], lj[k], ph_[k], pl_[k]);
+                    d2f = fmaf(dd, dd, d2f);
+                }
+                bool in = d2f <= pR2 * (1.0f - TOL_R);
+                if (!in && d2f <= pR2 * (1.0f + TOL_R))
+                    in = inside64(c, DIM, exact_d2<DIM>(a, ip, j), __dmul_rn(a.sm[ip], a.sV[ip]));
+                if (in) { key[s] = __float_as_uint(d2f); jv[s] = j; }
+            }
+        }
+        const uint32_t nin = (uint32_t)(__popc(__ballot_sync(0xffffffffu, key[0] != 0xffffffffu)) +
+                                        __popc(__ballot_sync(0xffffffffu, key[1] != 0xffffffffu)));
+        if (m <= 32) bitonic_sort<1>(key, jv);
+        else bitonic_sort<2>(key, jv);
+        // runs of entries within rounding of their predecessor: exact order
+        unsigned tie[2];
+        {
+            const uint32_t prev0 = __shfl_up_sync(0xffffffffu, key[0], 1);
+            const uint32_t last0 = __shfl_sync(0xffffffffu, key[0], 31);
+            const uint32_t prev1 = __shfl_up_sync(0xffffffffu, key[1], 1);
+            const uint32_t pk0 = prev0, pk1 = lane == 0 ? last0 : prev1;
+            const bool t0 = lane > 0 && lane < nin &&
+                            __uint_as_float(key[0]) <= __uint_as_float(pk0) * (1.0f + TOL_T);
+            const bool t1 = lane + 32 < nin && __uint_as_float(key[1]) <= __uint_as_float(pk1) * (1.0f + TOL_T);
+            tie[0] = __ballot_sync(0xffffffffu, t0);
+            tie[1] = __ballot_sync(0xffffffffu, t1);
+        }
+        if (tie[0] | tie[1]) {
+            // sorted indices to the column, runs re-sorted there by lane 0
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                if ((int)lane + 32 * s < (int)nin) b.kj[lane + 32 * s][p] = jv[s];
+            __syncwarp();
+            if (lane == 0) {
+                int e = 1;
+                while (e < (int)nin) {
+                    if (!((tie[e >> 5] >> (e & 31)) & 1u)) { ++e; continue; }
+                    const int s0 = e - 1;
+                    int f = e + 1;
+                    while (f < (int)nin && ((tie[f >> 5] >> (f & 31)) & 1u)) ++f;
+                    for (int qq = s0 + 1; qq < f; ++qq) {
+                        const uint32_t jq = b.kj[qq][p];
+                        const double dq = exact_d2<DIM>(a, ip, jq);
+                        const uint32_t iq = a.sid[jq];
+                        int r = qq - 1;
+                        while (r >= s0) {
+                            const uint32_t jr = b.kj[r][p];
+                            const double dr = exact_d2<DIM>(a, ip, jr);
+                            if (dr < dq || (dr == dq && a.sid[jr] < iq)) break;
+                            b.kj[r + 1][p] = jr;
+                            --r;
+                        }
+                        b.kj[r + 1][p] = jq;
+                    }
+                    e = f;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                if ((int)lane + 32 * s < (int)nin) jv[s] = b.kj[lane + 32 * s][p];
+            __syncwarp();
+        }
+        const uint32_t keep = min(nin, kmax);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            if (lane + 32u * s < keep) a.idx[ip * (int64_t)kmax + lane + 32 * s] = jv[s];
+        if (lane == 0) {
+            a.count[ip] = keep;
+            a.total[ip] = min(nin, 4u * kmax);
+        }
+        mx = max(mx, nin);
+        novf += nin > kmax ? 1u : 0u;
+    }
+    if (lane == 0) {
+        if (novf) atomicAdd(a.counters + C_OVERFLOW, (unsigned long long)novf);
+        if (mx) atomicMax(a.counters + C_MAXCOUNT, (unsigned long long)mx);
+    }
+    __syncwarp();
+}
+
+template <int DIM, bool PER>
+__global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile(QueryArgs a)
+{
+    extern __shared__ __align__(16) unsigned char tq_smem[];
+    TileBuf& b = reinterpret_cast<TileBuf*>(tq_smem)[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    const int64_t i0 = ((int64_t)blockIdx.x * TQ_WARPS + (threadIdx.x >> 5)) * 32;
+    if (i0 >= a.n) return;                      // whole warp
+    const int64_t i = i0 + lane;
+    const bool valid = i < a.n;
+    const int mb = a.c.mbits;
+    const uint64_t mysim = (valid && a.c.nsim_max > 1) ? (a.keys[i] >> (DIM * mb)) : 0ull;
+    // groups: a new one starts at lane 0, at a change of simulation, and after
+    // a jump of more than TQ_GAP radii between consecutive particles
+    float tq[3] = {0.0f, 0.0f, 0.0f}, Rq = 0.0f;
+    if (valid) {
+        TileLane<DIM> t;
+        tile_lane<DIM, PER>(a, a.g[mysim], i, t);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tq[k] = t.tq[k];
+        Rq = t.Rq;
+    }
+    const uint64_t psim = __shfl_up_sync(0xffffffffu, mysim, 1);
+    const float pRq = __shfl_up_sync(0xffffffffu, Rq, 1);
+    float gap2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float d = tq[k] - __shfl_up_sync(0xffffffffu, tq[k], 1);
+        gap2 = fmaf(d, d, gap2);
+    }
+    const float lim = TQ_GAP * fmaxf(Rq, pRq);
+    const unsigned starts = __ballot_sync(0xffffffffu, valid && (lane == 0 || psim != mysim || !(gap2 <= lim * lim)));
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    unsigned rest = starts;
+    while (rest) {                              // the groups, in turn
+        const int s0 = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const int s1 = rest ? __ffs(rest) - 1 : 32;
+        const unsigned grp = vmask & ((s1 == 32 ? 0xffffffffu : ((1u << s1) - 1u)) & ~((1u << s0) - 1u));
+        const uint64_t sim = __shfl_sync(0xffffffffu, mysim, s0);
+        tile_group<DIM, PER>(a, b, i, ((grp >> lane) & 1u) != 0u, sim);
+    }
 }
 
 // exact FP64 squared distance to the first (nearest) list entry, one thread per
@@ -510,16 +1027,51 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     a.sm = c->sm; a.sV = c->sV; a.sid = c->sid;
     a.count = c->nb_count; a.total = c->nb_total; a.idx = c->nb_idx; a.d2min = c->nb_d2min;
     a.counters = c->counters;
+    a.list = nullptr;
+    a.list_len = nullptr;
+    a.fb_list = c->redo_list;                  // capacity n: each particle is appended at most once
+    a.fb_len = c->counters + C_QFB_LEN;
     if (c->dc.radius_mode == LP_RADIUS_KSIDE) {
         k_query_kside<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
-    } else {
-        unsigned blocks = (unsigned)((n + NB_WARPS - 1) / NB_WARPS);
-        unsigned tb = (unsigned)((n + 255) / 256);
-        if (c->dc.dim == 3) { k_query<3><<<blocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<3><<<tb, 256, 0, s>>>(a); }
-        else if (c->dc.dim == 2) { k_query<2><<<blocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<2><<<tb, 256, 0, s>>>(a); }
-        else { k_query<1><<<blocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<1><<<tb, 256, 0, s>>>(a); }
+        return cudaGetLastError();
     }
+    const int dim = c->dc.dim;
+    const unsigned tb = (unsigned)((n + 255) / 256);
+    if (dim == 1) {
+        k_query<1><<<(unsigned)((n + NB_WARPS - 1) / NB_WARPS), NB_WARPS * 32, 0, s>>>(a);
+        k_d2min<1><<<tb, 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    // tiles first; the particles they leave go to the per-particle kernel
+    cudaError_t e = cudaMemsetAsync(c->counters + C_QFB_LEN, 0, 8, s);
+    if (e != cudaSuccess) return e;
+    const bool per = c->dc.periodic[0] || c->dc.periodic[1] || c->dc.periodic[2];
+    const int64_t tiles = (n + 31) / 32;
+    const unsigned tblocks = (unsigned)((tiles + TQ_WARPS - 1) / TQ_WARPS);
+    const size_t smem = sizeof(TileBuf) * TQ_WARPS;
+    if (dim == 3) {
+        if (per) k_query_tile<3, true><<<tblocks, TQ_WARPS * 32, smem, s>>>(a);
+        else k_query_tile<3, false><<<tblocks, TQ_WARPS * 32, smem, s>>>(a);
+    } else {
+        if (per) k_query_tile<2, true><<<tblocks, TQ_WARPS * 32, smem, s>>>(a);
+        else k_query_tile<2, false><<<tblocks, TQ_WARPS * 32, smem, s>>>(a);
+    }
+    a.list = c->redo_list;
+    a.list_len = c->counters + C_QFB_LEN;
+    const unsigned fblocks = 152u * 4u;
+    if (dim == 3) { k_query<3><<<fblocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<3><<<tb, 256, 0, s>>>(a); }
+    else { k_query<2><<<fblocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<2><<<tb, 256, 0, s>>>(a); }
     return cudaGetLastError();
+}
+
+cudaError_t query_init()
+{
+    const int smem = (int)(sizeof(TileBuf) * TQ_WARPS);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_query_tile<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_query_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_query_tile<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_query_tile<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 }  // namespace lp

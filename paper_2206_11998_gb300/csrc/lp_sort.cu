@@ -92,9 +92,10 @@ __global__ void k_init_extent(unsigned long long* ext, int nsim)
     }
 }
 
-// Bounding cube and the range of cell levels.  A particle of radius R queries
-// the finest level whose cell edge L / 2^l is at least R; lmax/lmin are those
-// levels for the smallest/largest radius present.
+// Bounding cube and the range of cell levels.  lmin is the finest level whose
+// cell edge L / 2^l is at least the largest radius present; lmax the finest
+// whose edge is at least half the smallest radius (the queries use cells down
+// to half a radius).
 __global__ void k_finalize_grid(DevCfg c, int lmax_cap, int nsim, const unsigned long long* ext_all, Grid* grids)
 {
     int sim = blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,7 +130,7 @@ __global__ void k_finalize_grid(DevCfg c, int lmax_cap, int nsim, const unsigned
     rmax *= 1.0 + 1e-4;
     if (!(rmin > 0.0)) rmin = L * ldexp(1.0, -lmax_cap);   // empty or degenerate simulation
     if (!(rmax > 0.0) || isinf(rmax)) rmax = L;
-    int lmax = (int)floor(log2(L / rmin));
+    int lmax = (int)floor(log2(2.0 * L / rmin));
     int lmin = (int)floor(log2(L / rmax));
     lmax = max(0, min(lmax, lmax_cap));
     lmin = max(0, min(lmin, lmax));

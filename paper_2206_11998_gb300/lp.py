@@ -73,7 +73,7 @@ class Stats(C.Structure):
                 ("n_fp64_redo", C.c_int64), ("n_linear", C.c_int64), ("n_nofit", C.c_int64),
                 ("n_overflow", C.c_int64), ("n_nonfinite", C.c_int64), ("n_mlp_uncertain", C.c_int64),
                 ("max_count", C.c_uint32), ("status", C.c_uint32), ("kernel_launches", C.c_int64),
-                ("n_mlp_skip", C.c_int64), ("n_mlp_miss", C.c_int64)]
+                ("n_mlp_skip", C.c_int64), ("n_mlp_miss", C.c_int64), ("n_query_fallback", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

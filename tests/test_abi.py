@@ -46,8 +46,12 @@ def test_host_side_argument_errors_without_gpu():
     assert L.lp_create(ctypes.byref(bad), ctypes.byref(h)) == lp.ERR_ARG
     bad = lp.make_config(2, 100, periodic=(1, 1, 0), box_hi=(1.0, 2.0, 1.0))   # non-cubic periodic box
     assert L.lp_create(ctypes.byref(bad), ctypes.byref(h)) == lp.ERR_ARG
+    bad = lp.make_config(2, 100, periodic=(1, 0, 0))   # periodic on some axes only
+    assert L.lp_create(ctypes.byref(bad), ctypes.byref(h)) == lp.ERR_ARG
     bad = lp.make_config(3, 100, radius_mode=lp.RADIUS_KSIDE)   # k-per-side is 1D only
     assert L.lp_create(ctypes.byref(bad), ctypes.byref(h)) == lp.ERR_ARG
     assert L.lp_create(None, ctypes.byref(h)) == lp.ERR_ARG
+    assert L.lp_set_schedule(None, lp.SCHED_SPLIT) == lp.ERR_ARG
+    assert L.lp_autotune(None, None, None, 1, 0.0, 0.4, 1, None, None) == lp.ERR_ARG
     assert L.lp_destroy(None) == lp.OK
     assert L.lp_status_string(lp.ERR_CAPACITY).decode().startswith("particle count")

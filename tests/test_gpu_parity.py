@@ -118,6 +118,31 @@ def test_neighbor_overflow_truncates_exactly():
     _check_lists(ctx, ps, st, _oracle_cfg(cfg))
     s = ctx.stats()
     assert s["n_overflow"] > 6000
+    # more than 64 in reach: those lists come from the warp-per-particle kernel
+    assert s["n_query_fallback"] > 1000
+    ctx.close()
+
+
+def test_neighbor_lists_scattered_tiles():
+    """Two far-apart clusters and a sprinkle of isolated points: tiles of 32
+    consecutive particles that straddle them span too many cells and are left
+    to the per-particle kernel; every list is still the oracle's."""
+    rng = np.random.default_rng(12)
+    a = rng.uniform(0.0, 0.05, size=(3, 1000))
+    b = rng.uniform(0.0, 0.05, size=(3, 1013)) + 0.9
+    c = rng.uniform(0.0, 1.0, size=(3, 45))
+    x = np.concatenate([a, b, c], axis=1)
+    n = x.shape[1]
+    st = {"x": [x[0].copy(), x[1].copy(), x[2].copy()], "V": np.ones(n), "u": [np.zeros(n)] * 3, "P": np.ones(n),
+          "m": np.ones(n), "id": np.arange(n, dtype=np.uint32), "n_fluid": n}
+    cfg = lp.make_config(3, n, radius_mode=lp.RADIUS_FIXED, radius=0.012, k_max=64)
+    ctx = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    ctx.build_neighbors(ps)
+    torch.cuda.synchronize()
+    _check_lists(ctx, ps, st, _oracle_cfg(cfg))
+    s = ctx.stats()
+    assert 0 < s["n_query_fallback"] < n
     ctx.close()
 
 
