@@ -78,6 +78,8 @@ def parse():
                     help="mlp: train the learned estimator on this workload's own plain steps, then time "
                          "steps gated by it")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="fp64: every fit and rate in FP64 (the plain FP64 GPU form)")
     return ap.parse_args()
 
 
@@ -227,7 +229,8 @@ def run_ours(args):
     if args.estimator == "mlp":
         params, mlp_info = train_gate(lp, inputs, state, n, stream, torch)
         kw = dict(estimator=lp.EST_MLP, mlp_tau_lo=MLP_TAU)
-    cfg = lp.make_config(3, n, precision=lp.PREC_FP32, radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
+    prec = lp.PREC_FP64 if args.precision == "fp64" else lp.PREC_FP32
+    cfg = lp.make_config(3, n, precision=prec, radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
                          k_side=8, gamma=GAMMA, limiter=lp.LIM_FLAGGED, s_ref=inputs.field_scales(state), **kw)
     ctx = lp.Context(cfg)
     if args.estimator == "mlp":
@@ -307,8 +310,9 @@ def run_ours(args):
             gbs = byts / (ms / args.steps * 1e-3) / 1e9 if ms > 0 else None
             entry.update({"bound": "hbm", "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_peak if gbs else None})
         per_phase[name] = entry
-    fit_ms = phases["fit+update"][0] / args.steps
-    fit_launch_ms = phases["fit+update"][0] / max(1, phases["fit+update"][1])
+    fit_phase = "fit+update" if args.precision == "fp32" else "fit+update-fp64"
+    fit_ms = phases[fit_phase][0] / args.steps
+    fit_launch_ms = phases[fit_phase][0] / max(1, phases[fit_phase][1])
     flops = fit_flops_per_particle(m_mean) * n
     achieved = flops / (fit_launch_ms * 1e-3) / 1e12
     dominant = max(per_phase, key=lambda k: per_phase[k]["ms_per_step"])
@@ -325,8 +329,11 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+                "data": "synthetic",
                 "config": config_dict(n, {"fit_ms_per_step": fit_ms, "wall_s_timed": wall,
+                                          "precision": ("FP32 fits + FP64 state, FP64 redo" if args.precision == "fp32"
+                                                        else "FP64 fits, rates and state"),
                                           "flagged_per_step": st["n_flagged"] / args.steps,
                                           "fp64_redo_per_step": st["n_fp64_redo"] / args.steps,
                                           "fit_schedule": tune, "estimator": args.estimator,

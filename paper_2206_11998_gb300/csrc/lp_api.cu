@@ -365,7 +365,7 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     auto A = [&](cudaError_t e) { if (e != cudaSuccess) ok = false; };
     A(dalloc(&c->keys[0], n * 8)); A(dalloc(&c->keys[1], n * 8));
     A(dalloc(&c->vals[0], n * 4)); A(dalloc(&c->vals[1], n * 4));
-    A(dalloc(&c->hist, (size_t)256 * c->hist_blocks * 4));
+    A(dalloc(&c->hist, (size_t)256 * (c->hist_blocks + 1) * 4));   // block counts + digit totals
     for (int k = 0; k < 3; ++k) {
         if (k < dim) {
             A(dalloc(&c->sx[k], n * 8)); A(dalloc(&c->su[k], n * 8));

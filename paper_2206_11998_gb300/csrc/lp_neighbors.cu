@@ -659,48 +659,47 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
     }
     const int nct = (int)ncells;
 
-    // ---- 1. kept non-empty cells, compacted
-    const unsigned lt = (1u << lane) - 1u;
-    int nk = 0;
-    uint32_t ncand = 0;
-    bool over = false;
-    for (int base0 = 0; base0 < nct && !over; base0 += 32) {
-        const int e = base0 + (int)lane;
-        uint32_t cs = 0, cn = 0;
-        if (e < nct) {
-            int u = e;
-            uint32_t q[3] = {0u, 0u, 0u};
-            float dmin2 = 0.0f;
+    // one lane per cell: the key-order range of cell e if it is within reach of the box
+    auto cell_range = [&](int e, uint32_t& cs, uint32_t& cn) {
+        cs = 0;
+        cn = 0;
+        if (e >= nct) return;
+        int u = e;
+        uint32_t q[3] = {0u, 0u, 0u};
+        float dmin2 = 0.0f;
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) {
-                const int v = clo[k] + u % nc[k];
-                u /= nc[k];
-                const int wr = v & (naxis - 1);
-                const int sh = (v - wr) >> l0;          // periodic image (0 on other axes)
-                const float lo = (float)wr * size + (float)sh * period;
-                const float dn = full[k] ? 0.0f : fmaxf(0.0f, fmaxf(lo - bmax[k], bmin[k] - (lo + size)));
-                dmin2 += dn * dn;
-                q[k] = (uint32_t)wr;
-            }
-            if (sqrtf(dmin2) < Routm) {
-                const uint64_t code = (sim << (DIM * l0)) | morton<DIM>(q);
-                const unsigned long long ent = a.cells[a.level_off[l0] + (int64_t)code];
-                cs = (uint32_t)ent;
-                const uint32_t ce = (uint32_t)(ent >> 32);
-                cn = ce > cs ? ce - cs : 0;
-            }
+        for (int k = 0; k < DIM; ++k) {
+            const int v = clo[k] + u % nc[k];
+            u /= nc[k];
+            const int wr = v & (naxis - 1);
+            const int sh = (v - wr) >> l0;          // periodic image (0 on other axes)
+            const float lo = (float)wr * size + (float)sh * period;
+            const float dn = full[k] ? 0.0f : fmaxf(0.0f, fmaxf(lo - bmax[k], bmin[k] - (lo + size)));
+            dmin2 += dn * dn;
+            q[k] = (uint32_t)wr;
         }
-        const unsigned km = __ballot_sync(0xffffffffu, cn > 0);
-        ncand += __reduce_add_sync(0xffffffffu, cn);
-        if (nk + __popc(km) > TQ_KC || ncand > TQ_CAND_MAX) { over = true; break; }
-        if (cn > 0) b.kc[nk + __popc(km & lt)] = (unsigned long long)cs | ((unsigned long long)cn << 32);
-        nk += __popc(km);
+        if (sqrtf(dmin2) < Routm) {
+            const uint64_t code = (sim << (DIM * l0)) | morton<DIM>(q);
+            const unsigned long long ent = a.cells[a.level_off[l0] + (int64_t)code];
+            cs = (uint32_t)ent;
+            const uint32_t ce = (uint32_t)(ent >> 32);
+            cn = ce > cs ? ce - cs : 0;
+        }
+    };
+    // ---- 1. the group's candidate count; a dense region under a wide group
+    // is cheaper per particle
+    {
+        uint32_t ncand = 0;
+        for (int base0 = 0; base0 < nct && ncand <= TQ_CAND_MAX; base0 += 32) {
+            uint32_t cs, cn;
+            cell_range(base0 + (int)lane, cs, cn);
+            ncand += __reduce_add_sync(0xffffffffu, cn);
+        }
+        if (ncand > TQ_CAND_MAX) {
+            list_append(a, act, (uint32_t)i);
+            return;
+        }
     }
-    if (over) {                       // a dense region under a wide group: per particle instead
-        list_append(a, act, (uint32_t)i);
-        return;
-    }
-    __syncwarp();
 
     // ---- 2. prefilter: candidates relative to the group's first particle
     const int lead = __ffs(__ballot_sync(0xffffffffu, act)) - 1;
@@ -724,68 +723,91 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
 #pragma unroll
     for (int k = 0; k < 3; ++k) { Lh[k] = c.Lper_h[k]; halfL[k] = 0.5f * c.Lper_h[k]; }
     uint32_t cnt = 0;                 // prefilter hits of this lane
-    for (int c0 = 0; c0 < nk; c0 += 32) {
-        uint32_t cs = 0, cn = 0;
-        if (c0 + (int)lane < nk) {
-            const unsigned long long ent = b.kc[c0 + lane];
-            cs = (uint32_t)ent;
-            cn = (uint32_t)(ent >> 32);
-        }
-        uint32_t incl = cn;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += v;
-        }
-        const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-        b.cstart[lane] = cs;
-        b.cexcl[lane] = incl - cn;
-        __syncwarp();
-        for (uint32_t base = 0; base < T; base += 32) {
-            const uint32_t t = base + lane;
-            if (t < T) {
-                int lo = 0, hi = 31;                  // the last cell with cexcl <= t
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
-                }
-                const uint32_t j = b.cstart[lo] + (t - b.cexcl[lo]);
-                const float4 ph = __ldg(a.pos4 + 2 * (int64_t)j);
-                const float4 pl = __ldg(a.pos4 + 2 * (int64_t)j + 1);
-                float4 r;
-                r.x = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
-                r.y = DIM > 1 ? split_offset<PER>(c, 1, ph.y, pl.y, oh[1], ol[1]) : 0.0f;
-                r.z = DIM > 2 ? split_offset<PER>(c, 2, ph.z, pl.z, oh[2], ol[2]) : 0.0f;
-                r.w = __uint_as_float(j);
-                b.cr[lane] = r;
+    // candidates of the compacted cells b.kc[0..nk), 32 cells at a time
+    auto scan_kept = [&](int nk) {
+        for (int c0 = 0; c0 < nk; c0 += 32) {
+            uint32_t cs = 0, cn = 0;
+            if (c0 + (int)lane < nk) {
+                const unsigned long long ent = b.kc[c0 + lane];
+                cs = (uint32_t)ent;
+                cn = (uint32_t)(ent >> 32);
             }
+            uint32_t incl = cn;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += v;
+            }
+            const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+            b.cstart[lane] = cs;
+            b.cexcl[lane] = incl - cn;
             __syncwarp();
-            const int nb = (int)min(32u, T - base);
-            if (act) {
+            for (uint32_t base = 0; base < T; base += 32) {
+                const uint32_t t = base + lane;
+                if (t < T) {
+                    int lo = 0, hi = 31;                  // the last cell with cexcl <= t
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
+                    }
+                    const uint32_t j = b.cstart[lo] + (t - b.cexcl[lo]);
+                    const float4 ph = __ldg(a.pos4 + 2 * (int64_t)j);
+                    const float4 pl = __ldg(a.pos4 + 2 * (int64_t)j + 1);
+                    float4 r;
+                    r.x = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
+                    r.y = DIM > 1 ? split_offset<PER>(c, 1, ph.y, pl.y, oh[1], ol[1]) : 0.0f;
+                    r.z = DIM > 2 ? split_offset<PER>(c, 2, ph.z, pl.z, oh[2], ol[2]) : 0.0f;
+                    r.w = __uint_as_float(j);
+                    b.cr[lane] = r;
+                }
+                __syncwarp();
+                const int nb = (int)min(32u, T - base);
+                if (act) {
 #pragma unroll 4
-                for (int qq = 0; qq < nb; ++qq) {
-                    const float4 r = b.cr[qq];
-                    float d[3] = {r.x - ri[0], r.y - ri[1], r.z - ri[2]};
-                    if (PER) {
+                    for (int qq = 0; qq < nb; ++qq) {
+                        const float4 r = b.cr[qq];
+                        float d[3] = {r.x - ri[0], r.y - ri[1], r.z - ri[2]};
+                        if (PER) {
 #pragma unroll
-                        for (int k = 0; k < DIM; ++k)
-                            if (c.periodic[k]) {
-                                if (d[k] > halfL[k]) d[k] -= Lh[k];
-                                else if (d[k] < -halfL[k]) d[k] += Lh[k];
-                            }
-                    }
-                    float d2 = d[0] * d[0];
-                    if (DIM > 1) d2 = fmaf(d[1], d[1], d2);
-                    if (DIM > 2) d2 = fmaf(d[2], d[2], d2);
-                    const uint32_t j = __float_as_uint(r.w);
-                    if (d2 <= thr && (int64_t)j != i) {
-                        if (cnt < (uint32_t)TQ_CAP) b.kj[cnt][lane] = j;
-                        ++cnt;
+                            for (int k = 0; k < DIM; ++k)
+                                if (c.periodic[k]) {
+                                    if (d[k] > halfL[k]) d[k] -= Lh[k];
+                                    else if (d[k] < -halfL[k]) d[k] += Lh[k];
+                                }
+                        }
+                        float d2 = d[0] * d[0];
+                        if (DIM > 1) d2 = fmaf(d[1], d[1], d2);
+                        if (DIM > 2) d2 = fmaf(d[2], d[2], d2);
+                        const uint32_t j = __float_as_uint(r.w);
+                        if (d2 <= thr && (int64_t)j != i) {
+                            if (cnt < (uint32_t)TQ_CAP) b.kj[cnt][lane] = j;
+                            ++cnt;
+                        }
                     }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
+    };
+    // classify again, compacting the non-empty cells; scan whenever the
+    // buffer of kept cells would overflow, and at the end
+    {
+        const unsigned lt = (1u << lane) - 1u;
+        int nk = 0;
+        for (int base0 = 0; base0 < nct; base0 += 32) {
+            uint32_t cs, cn;
+            cell_range(base0 + (int)lane, cs, cn);
+            const unsigned km = __ballot_sync(0xffffffffu, cn > 0);
+            if (nk + __popc(km) > TQ_KC) {
+                __syncwarp();
+                scan_kept(nk);
+                nk = 0;
+            }
+            if (cn > 0) b.kc[nk + __popc(km & lt)] = (unsigned long long)cs | ((unsigned long long)cn << 32);
+            nk += __popc(km);
+        }
+        __syncwarp();
+        scan_kept(nk);
     }
 
     // ---- 3. per particle: exact membership, order, row
@@ -794,10 +816,31 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
     const uint32_t kmax = (uint32_t)c.k_max;
     uint32_t mx = 0, novf = 0;
     unsigned todo = __ballot_sync(0xffffffffu, mine);
-    while (todo) {
-        const int p = __ffs(todo) - 1;
+    // the hits of the next particle are loaded while the current one is sorted
+    uint32_t fj[2] = {0u, 0u};
+    float4 fh[2], fl[2];
+    auto fetch = [&](int p, int m) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int e = (int)lane + 32 * s;
+            if (e < m) {
+                fj[s] = b.kj[e][p];
+                fh[s] = __ldg(a.pos4 + 2 * (int64_t)fj[s]);
+                fl[s] = __ldg(a.pos4 + 2 * (int64_t)fj[s] + 1);
+            }
+        }
+    };
+    int pn = todo ? __ffs(todo) - 1 : -1;
+    int mn = pn >= 0 ? (int)__shfl_sync(0xffffffffu, cnt, pn) : 0;
+    if (pn >= 0) fetch(pn, mn);
+    while (pn >= 0) {
+        const int p = pn, m = mn;
         todo &= todo - 1;
-        const int m = (int)__shfl_sync(0xffffffffu, cnt, p);
+        const uint32_t cj[2] = {fj[0], fj[1]};
+        const float4 ch[2] = {fh[0], fh[1]}, cl[2] = {fl[0], fl[1]};
+        pn = todo ? __ffs(todo) - 1 : -1;
+        mn = pn >= 0 ? (int)__shfl_sync(0xffffffffu, cnt, pn) : 0;
+        if (pn >= 0) fetch(pn, mn);
         const int64_t ip = i - (int64_t)lane + p;
         float ph_[3], pl_[3];
 #pragma unroll
@@ -811,9 +854,9 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         for (int s = 0; s < 2; ++s) {
             const int e = (int)lane + 32 * s;
             if (e < m) {
-                const uint32_t j = b.kj[e][p];
-                const float4 qh = __ldg(a.pos4 + 2 * (int64_t)j);
-                const float4 ql = __ldg(a.pos4 + 2 * (int64_t)j + 1);
+                const uint32_t j = cj[s];
+                const float4 qh = ch[s];
+                const float4 ql = cl[s];
                 const float hj[3] = {qh.x, qh.y, qh.z}, lj[3] = {ql.x, ql.y, ql.z};
                 float d2f = 0.0f;
 #pragma unroll

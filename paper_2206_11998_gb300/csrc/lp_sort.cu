@@ -200,70 +200,111 @@ __global__ void k_rs_upsweep(int64_t n, const uint64_t* __restrict__ keys, int s
     counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of counts[0..total) in one block of 1024 threads
-__global__ void k_rs_scan(uint32_t* counts, int64_t total)
+// Per digit d (one block each): exclusive scan of the block counts
+// counts[d * nblocks + b] along b, in place, and the digit's total in totals[d].
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* counts, int64_t nblocks, uint32_t* totals)
 {
-    __shared__ uint32_t part[1024];
-    int t = threadIdx.x;
-    int64_t per = (total + 1023) / 1024;
-    int64_t b = t * per, e = min(total, b + per);
-    uint32_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += counts[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        uint32_t v = t >= o ? part[t - o] : 0;
+    __shared__ uint32_t wsum[32];
+    uint32_t* row = counts + (int64_t)blockIdx.x * nblocks;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t carry = 0;
+    for (int64_t b0 = 0; b0 < nblocks; b0 += 1024) {
+        const int64_t b = b0 + t;
+        const uint32_t v = b < nblocks ? row[b] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        part[t] += v;
+        if (w == 0) {
+            uint32_t z = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            wsum[lane] = z;                    // inclusive over warps
+        }
+        __syncthreads();
+        const uint32_t before = (w ? wsum[w - 1] : 0u) + x - v;
+        if (b < nblocks) row[b] = carry + before;
+        carry += wsum[31];
         __syncthreads();
     }
-    uint32_t run = t ? part[t - 1] : 0;
-    for (int64_t i = b; i < e; ++i) {
-        uint32_t c = counts[i];
-        counts[i] = run;
-        run += c;
-    }
+    if (t == 0) totals[blockIdx.x] = carry;
 }
 
+// Scatter of one tile of RS_TILE keys: each warp ranks its 512 consecutive keys
+// round by round (match on the digit), the warps' digit counts are scanned
+// once per tile, and every key goes to digit base + block offset + rank.
 __global__ void __launch_bounds__(RS_THREADS)
 k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
-               const uint32_t* __restrict__ counts, int64_t nblocks)
+               const uint32_t* __restrict__ counts, const uint32_t* __restrict__ totals, int64_t nblocks)
 {
-    __shared__ uint32_t off[256];
-    __shared__ uint32_t wc[RS_THREADS / 32][256];
-    int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    off[t] = counts[(int64_t)t * nblocks + blockIdx.x];
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    unsigned lt = (1u << lane) - 1u;
+    constexpr int NW = RS_THREADS / 32;
+    __shared__ uint32_t wc[NW][256];
+    __shared__ uint32_t dbase[256];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    // digit bases: exclusive scan of the 256 digit totals
+    {
+        const uint32_t v = totals[t];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wc[0][w] = x;
+        __syncthreads();
+        uint32_t add = 0;
+        for (int ww = 0; ww < w; ++ww) add += wc[0][ww];
+        dbase[t] = add + x - v + counts[(int64_t)t * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+    for (int d = lane; d < 256; d += 32) wc[w][d] = 0;
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (32 * RS_ITEMS);
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t key[RS_ITEMS];
+    uint32_t val[RS_ITEMS], loc[RS_ITEMS];
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
-        for (int d = lane; d < 256; d += 32) wc[w][d] = 0;
-        __syncthreads();
-        int64_t i = base + r * RS_THREADS + t;
-        bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0;
-        uint32_t val = valid ? vin[i] : 0;
-        uint32_t d = valid ? (uint32_t)((key >> shift) & 255u) : 256u + lane;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & lt);
-        if (valid && (__ffs(peers) - 1) == lane) wc[w][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = off[t];
-            for (int ww = 0; ww < RS_THREADS / 32; ++ww) {
-                uint32_t c = wc[ww][t];
-                wc[ww][t] = run;
-                run += c;
-            }
-            off[t] = run;
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : 0ull;
+        val[r] = valid ? vin[i] : 0u;
+        const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & 255u) : 256u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const bool leader = (__ffs(peers) - 1) == lane;
+        loc[r] = valid ? wc[w][d] + __popc(peers & lt) : 0u;
+        __syncwarp();
+        if (valid && leader) wc[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // per digit: offsets of the warps' runs in tile order
+        uint32_t run = dbase[t];
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) {
+            const uint32_t c = wc[ww][t];
+            wc[ww][t] = run;
+            run += c;
         }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = wc[w][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        if (i < n) {
+            const uint32_t d = (uint32_t)((key[r] >> shift) & 255u);
+            const uint32_t pos = wc[w][d] + loc[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
         }
-        __syncthreads();
     }
 }
 
@@ -419,10 +460,11 @@ cudaError_t radix_sort(lp_ctx* c, int64_t n, cudaStream_t s)
     int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
     int cur = 0;
     for (int sh = c->sort_lo_bit; sh < c->sort_hi_bit; sh += 8) {
+        uint32_t* totals = c->hist + 256 * nblocks;
         k_rs_upsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, c->keys[cur], sh, c->hist, nblocks);
-        k_rs_scan<<<1, 1024, 0, s>>>(c->hist, 256 * nblocks);
+        k_rs_scan<<<256, 1024, 0, s>>>(c->hist, nblocks, totals);
         k_rs_downsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, c->keys[cur], c->vals[cur], c->keys[cur ^ 1],
-                                                                c->vals[cur ^ 1], sh, c->hist, nblocks);
+                                                                c->vals[cur ^ 1], sh, c->hist, totals, nblocks);
         cur ^= 1;
     }
     c->keys_sorted = c->keys[cur];
@@ -493,7 +535,7 @@ constexpr size_t NA_KEYS1 = NA_KEYS0 + 8 * NOALLOC_MAX_N;
 constexpr size_t NA_VALS0 = NA_KEYS1 + 8 * NOALLOC_MAX_N;
 constexpr size_t NA_VALS1 = NA_VALS0 + 4 * NOALLOC_MAX_N;
 constexpr size_t NA_HIST = NA_VALS1 + 4 * NOALLOC_MAX_N;
-constexpr size_t NA_EXT = NA_HIST + ((256 * NA_BLOCKS * 4 + 255) / 256) * 256;
+constexpr size_t NA_EXT = NA_HIST + ((256 * (NA_BLOCKS + 1) * 4 + 255) / 256) * 256;   // counts + digit totals
 constexpr size_t NA_GRID = NA_EXT + 256;
 constexpr size_t NA_BYTES = NA_GRID + 256;
 
@@ -578,9 +620,9 @@ extern "C" lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double* 
     int cur = 0;
     for (int sh = lo_bit; sh < hi_bit; sh += 8) {
         k_rs_upsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, keys[cur], sh, hist, nblocks);
-        k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * nblocks);
+        k_rs_scan<<<256, 1024, 0, s>>>(hist, nblocks, hist + 256 * nblocks);
         k_rs_downsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, keys[cur], vals[cur], keys[cur ^ 1],
-                                                                vals[cur ^ 1], sh, hist, nblocks);
+                                                                vals[cur ^ 1], sh, hist, hist + 256 * nblocks, nblocks);
         cur ^= 1;
     }
     k_copy_sorted<<<gb, 256, 0, s>>>(n, keys[cur], vals[cur], keys_out, perm_out);
