@@ -228,7 +228,7 @@ def run_ours(args):
     kw = {}
     if args.estimator == "mlp":
         params, mlp_info = train_gate(lp, inputs, state, n, stream, torch)
-        kw = dict(estimator=lp.EST_MLP, mlp_tau_lo=MLP_TAU)
+        kw = dict(estimator=lp.EST_MLP, mlp_tau_lo=mlp_info["tau_lo"])
     prec = lp.PREC_FP64 if args.precision == "fp64" else lp.PREC_FP32
     cfg = lp.make_config(3, n, precision=prec, radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
                          k_side=8, gamma=GAMMA, limiter=lp.LIM_FLAGGED, s_ref=inputs.field_scales(state), **kw)
@@ -250,9 +250,10 @@ def run_ours(args):
             ctx.step(ps, dt=0.0, cfl=CFL, t=t_dev, stream=stream)
         tune = None
         if not args.no_autotune:
-            f_ms, s_ms = ctx.autotune(ps, dt=0.0, cfl=CFL, reps=3, stream=stream)
-            tune = {"fused_ms": f_ms, "split_ms": s_ms,
-                    "chosen": "split" if ctx.schedule() == lp.SCHED_SPLIT else "fused"}
+            tune = ctx.autotune(ps, dt=0.0, cfl=CFL, reps=3, stream=stream)
+            sch = ctx.schedule()
+            tune["chosen"] = ("split" if sch & lp.SCHED_SPLIT else "fused") + (
+                "+query-warp" if sch & lp.SCHED_QUERY_WARP else "+query-tiles")
         # mean neighbour count of the current lists (algorithmic work per particle)
         cnt = ctx.export_neighbors(n, stream=stream)[0]
         m_mean = float(cnt.double().mean().item())
@@ -348,7 +349,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-MLP_TAU = 0.05
+MLP_MISS = 0.01   # share of the training set's flags the gate threshold may clear
 
 
 def train_gate(lp, inputs, state, n, stream, torch):
@@ -378,9 +379,13 @@ def train_gate(lp, inputs, state, n, stream, torch):
         stream.synchronize()
         secs = time.perf_counter() - t0
         params = c0.mlp_get_params()[0]
+        # threshold calibrated on the training set: MLP_MISS of its flags fall below it
+        p = c0.mlp_infer(X, stream=stream)
+        tau = float(torch.quantile(p[y > 0.5].float(), MLP_MISS).item())
     c0.close()
     return params, {"train_samples": int(X.shape[0]), "train_epochs": 20, "train_s": secs,
-                    "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "tau_lo": MLP_TAU}
+                    "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "tau_lo": tau,
+                    "calibrated_miss": MLP_MISS}
 
 
 def audit_gate(lp, inputs, ps, n, cfg, params, stream, torch):
@@ -531,6 +536,12 @@ def run_ensemble(args):
         offs_d = torch.as_tensor(offs, device="cuda")
         t = torch.zeros(nsim, dtype=torch.float64, device="cuda")
         ctx.step_batched(ps, offs_d, nsim, dt=0.0, cfl=CFL, t=t, stream=stream)
+        tune = None
+        if not args.no_autotune:
+            tune = ctx.autotune(ps, offs_d, nsim, dt=0.0, cfl=CFL, reps=2, stream=stream)
+            sch = ctx.schedule()
+            tune["chosen"] = ("split" if sch & lp.SCHED_SPLIT else "fused") + (
+                "+query-warp" if sch & lp.SCHED_QUERY_WARP else "+query-tiles")
         ctx.graph_capture(ps, offs_d, nsim, dt=0.0, cfl=CFL, t=t, stream=stream)
         for _ in range(args.warmup):
             ctx.graph_launch(stream=stream)
@@ -585,6 +596,7 @@ def run_ensemble(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "kh-ensemble-%d" % nsim, "particles": n, "dim": 2, "gamma": KH_GAMMA,
                        "sizes": "U[10k, 200k] per simulation (seed 6)", "schedule": "batched, CUDA graph replay",
+                       "autotune": tune,
                        "l2": "flushed between timed steps (256 MiB write)"},
             "unbatched": {"ms_per_step": loop_ms, "value": n / (loop_ms * 1e-3),
                           "note": "one lp_step per simulation in a loop, one context each"},

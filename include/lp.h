@@ -363,33 +363,42 @@ lp_status lp_graph_capture(lp_ctx *ctx, lp_particles *p, const int64_t *offsets,
 lp_status lp_graph_launch(lp_ctx *ctx, lp_stream stream);
 
 /*
- * Schedule of the fit + update pass (no counterpart in the paper: an
- * implementation choice with identical results).
- *   LP_SCHED_FUSED  one kernel runs the whole per-particle update (central
- *                   fit, LW rates, one-sided fits, estimator, blend, mover).
- *   LP_SCHED_SPLIT  a first kernel runs the central fit, the LW rates and the
- *                   learned gate, finishes the particles the gate clears, and
- *                   appends the rest (with their central first derivatives and
- *                   LW rates) to a compacted list; a second kernel runs the
- *                   one-sided fits, estimator and blend over that list.  Pays
- *                   off when the learned estimator clears many particles.
- * The default is SPLIT with the learned estimator, FUSED otherwise.  A graph
- * captured by lp_graph_capture keeps the schedule it was captured with.
+ * Schedules (no counterpart in the paper: implementation choices with
+ * identical results), as bit flags.
+ *   fit + update pass:
+ *     LP_SCHED_FUSED  one kernel runs the whole per-particle update (central
+ *                     fit, LW rates, one-sided fits, estimator, blend, mover).
+ *     LP_SCHED_SPLIT  a first kernel runs the central fit, the LW rates and the
+ *                     learned gate, finishes the particles the gate clears, and
+ *                     appends the rest (with their central first derivatives
+ *                     and LW rates) to a compacted list; a second kernel runs
+ *                     the one-sided fits, estimator and blend over that list.
+ *   neighbour query:
+ *     (default)            one warp per 32 key-ordered particles (tiles), with
+ *                          the per-particle kernel for the particles a tile
+ *                          leaves (more than 64 neighbours, scattered groups).
+ *     LP_SCHED_QUERY_WARP  one warp per particle for every particle.
+ * The default is SPLIT with the learned estimator, FUSED otherwise, and tiles.
+ * A graph captured by lp_graph_capture keeps the schedule it was captured with.
  */
 #define LP_SCHED_FUSED 0
 #define LP_SCHED_SPLIT 1
-lp_status lp_set_schedule(lp_ctx *ctx, int32_t schedule);   /* LP_ERR_ARG on an unknown value */
+#define LP_SCHED_QUERY_WARP 2
+lp_status lp_set_schedule(lp_ctx *ctx, int32_t schedule);   /* LP_ERR_ARG on unknown bits */
 lp_status lp_get_schedule(lp_ctx *ctx, int32_t *schedule);
 
 /*
  * Autotuner: runs the neighbour build and CFL step of lp_step_batched (same
- * arguments; t is not advanced), then times the fit pass under each schedule
- * (`reps` timed launches after one warm-up, CUDA events on `stream`), selects
- * the faster, and writes the two mean times in milliseconds to out_ms[0]
- * (FUSED) and out_ms[1] (SPLIT) when out_ms (host, 2 doubles) is not null.
- * The particle state is not changed (the timed passes write to scratch
- * buffers the call allocates and frees); the counters, the device time steps
- * (lp_dt_device) and the launch tally are restored.  Synchronises `stream`.  LP_ERR_STATE while profiling is on.
+ * arguments; t is not advanced), then times the neighbour query under each
+ * query schedule and the fit pass under each fit schedule (`reps` timed
+ * launches after one warm-up, CUDA events on `stream`), selects the faster of
+ * each, and writes the mean times in milliseconds to out_ms[0] (fit FUSED),
+ * out_ms[1] (fit SPLIT), out_ms[2] (query tiles), out_ms[3] (query per
+ * particle) when out_ms (host, 4 doubles) is not null.  The particle state is
+ * not changed (the timed fit passes write to scratch buffers the call
+ * allocates and frees); the counters, the device time steps (lp_dt_device) and
+ * the launch tally are restored.  Synchronises `stream`.  LP_ERR_STATE while
+ * profiling is on.
  */
 lp_status lp_autotune(lp_ctx *ctx, lp_particles *p, const int64_t *offsets, int32_t nsim, double dt, double cfl,
                       int32_t reps, double *out_ms, lp_stream stream);

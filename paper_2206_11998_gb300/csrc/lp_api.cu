@@ -27,9 +27,7 @@ cudaError_t dalloc(P** p, size_t bytes)
 void free_all(lp_ctx* c)
 {
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist, c->sx[0], c->sx[1], c->sx[2],
-                    c->sV, c->su[0], c->su[1], c->su[2], c->sP, c->sm, c->sid, c->hx[0], c->hx[1], c->hx[2],
-                    c->lx[0], c->lx[1], c->lx[2], c->hf[0], c->hf[1], c->hf[2], c->hf[3], c->hf[4],
-                    c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec, c->pos4, c->cells, c->nb_count, c->nb_total,
+                    c->sV, c->su[0], c->su[1], c->su[2], c->sP, c->sm, c->sid, c->rec, c->pos4, c->cells, c->nb_count, c->nb_total,
                     c->nb_idx, c->nb_d2min, c->grid, c->dt_dev, c->dt_min, c->counters, c->redo_list,
                     c->plain_list, c->mid, c->ext, c->grange, c->level_off_dev, c->sim_of,
                     c->mlp_master, c->mlp_bf16, c->mlp_m1, c->mlp_m2, c->mlp_grad, c->mlp_loss};
@@ -89,20 +87,13 @@ lp_status check_particles(const lp_ctx* c, const lp_particles* p)
 }
 
 __global__ void k_split_fields(int64_t n, int nf, const double* f0, const double* f1, const double* f2,
-                               const double* f3, const double* f4, float* h0, float* h1, float* h2, float* h3,
-                               float* h4, float* l0, float* l1, float* l2, float* l3, float* l4, float4* rec)
+                               const double* f3, const double* f4, float4* rec)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double* f[5] = {f0, f1, f2, f3, f4};
-    float* h[5] = {h0, h1, h2, h3, h4};
-    float* l[5] = {l0, l1, l2, l3, l4};
     float* r = reinterpret_cast<float*>(rec + i * REC_F4);
-    for (int q = 0; q < nf; ++q) {
-        split(f[q][i], h[q][i], l[q][i]);
-        r[REC_FH + q] = h[q][i];
-        r[REC_FL + q] = l[q][i];
-    }
+    for (int q = 0; q < nf; ++q) split(f[q][i], r[REC_FH + q], r[REC_FL + q]);
 }
 
 // dt_s = cfl * sqrt(min_i d2min_i / (gamma P_i V_i)) over the fluid particles of
@@ -158,10 +149,7 @@ void fill_fit_args(lp_ctx* c, FitArgs& a, int64_t n)
     for (int k = 0; k < 3; ++k) {
         int kk = k < c->dc.dim ? k : 0;
         a.sx[k] = c->sx[kk];
-        a.hx[k] = c->hx[kk];
-        a.lx[k] = c->lx[kk];
     }
-    for (int f = 0; f < 5; ++f) { a.fh[f] = c->hf[f]; a.fl[f] = c->lf[f]; }
     a.rec = c->rec;
     a.sid = c->sid;
     a.sm = c->sm;
@@ -246,7 +234,7 @@ namespace {
 // redo of the particles it listed
 lp_status run_fit(lp_ctx* c, FitArgs a, const StepOut& o, int sched, cudaStream_t s)
 {
-    const bool split = sched == LP_SCHED_SPLIT;
+    const bool split = (sched & LP_SCHED_SPLIT) != 0;
     const int dim = c->dc.dim;
     if (split) LP_CUDA(cudaMemsetAsync(c->counters + C_PLAIN_LEN, 0, 8, s));
     if (c->dc.precision == LP_PREC_FP32) {
@@ -321,6 +309,9 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     d.gamma = cfg->gamma;
     d.radius = cfg->radius;
     d.kappa = cfg->kappa;
+    d.radius_f = (float)cfg->radius;
+    d.radius2_f = (float)(cfg->radius * cfg->radius);
+    d.kappa_f = (float)cfg->kappa;
     d.flat_eps = cfg->flat_eps;
     d.active_frac = cfg->active_frac;
     d.tau32 = c->cfg.tau32;
@@ -369,11 +360,9 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     for (int k = 0; k < 3; ++k) {
         if (k < dim) {
             A(dalloc(&c->sx[k], n * 8)); A(dalloc(&c->su[k], n * 8));
-            A(dalloc(&c->hx[k], n * 4)); A(dalloc(&c->lx[k], n * 4));
         }
     }
     A(dalloc(&c->sV, n * 8)); A(dalloc(&c->sP, n * 8)); A(dalloc(&c->sm, n * 8)); A(dalloc(&c->sid, n * 4));
-    for (int f = 0; f < 5; ++f) { A(dalloc(&c->hf[f], n * 4)); A(dalloc(&c->lf[f], n * 4)); }
     A(dalloc(&c->rec, (size_t)n * REC_F4 * sizeof(float4)));
     A(dalloc(&c->pos4, (size_t)n * 2 * sizeof(float4)));
     A(dalloc(&c->cells, (size_t)c->table_entries * 8));
@@ -452,7 +441,7 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
         c->tables_dirty = tables ? 1 : 0;
     }
     {
-        Phase ph(c, LP_PH_QUERY, c->dc.radius_mode == LP_RADIUS_KSIDE ? 1 : (c->dc.dim == 1 ? 2 : 3), s);
+        Phase ph(c, LP_PH_QUERY, query_launches(c), s);
         LP_CUDA(query_neighbors(c, n, s));
     }
     c->n_lists = n;
@@ -515,10 +504,8 @@ lp_status lp_gfd_derivs(lp_ctx* c, const lp_particles* p, const double* const* f
             {
                 Phase ph(c, LP_PH_GATHER, 1, s);
                 k_split_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-                    n, real, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->hf[0], c->hf[1], c->hf[2], c->hf[3],
-                    c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec);
+                    n, real, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->rec);
             }
-            for (int q = real; q < 5; ++q) { a.fh[q] = c->hf[0]; a.fl[q] = c->lf[0]; }
             LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
             {
                 Phase ph(c, LP_PH_FIT, 1, s);
@@ -556,10 +543,8 @@ lp_status lp_onesided_derivs(lp_ctx* c, const lp_particles* p, const double* con
         {
             Phase ph(c, LP_PH_GATHER, 1, s);
             k_split_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-                n, nfields, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->hf[0], c->hf[1], c->hf[2], c->hf[3],
-                c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec);
+                n, nfields, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->rec);
         }
-        for (int q = nfields; q < 5; ++q) { a.fh[q] = c->hf[0]; a.fl[q] = c->lf[0]; }
         LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
         {
             Phase ph(c, LP_PH_FIT, 1, s);
@@ -639,7 +624,7 @@ lp_status lp_step_batched(lp_ctx* c, lp_particles* p, const int64_t* offsets, in
 
 lp_status lp_set_schedule(lp_ctx* c, int32_t schedule)
 {
-    if (!c || (schedule != LP_SCHED_FUSED && schedule != LP_SCHED_SPLIT)) return LP_ERR_ARG;
+    if (!c || (schedule & ~(LP_SCHED_SPLIT | LP_SCHED_QUERY_WARP)) != 0) return LP_ERR_ARG;
     c->schedule = schedule;
     return LP_OK;
 }
@@ -677,7 +662,7 @@ lp_status lp_autotune(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_
     int64_t n = 0;
     lp_status st = step_prologue(c, p, offsets, nsim, dt, cfl, nullptr, nullptr, s, a, o, &n);
     if (st != LP_OK) return st;
-    double ms[2] = {0.0, 0.0};
+    double ms[4] = {0.0, 0.0, 0.0, 0.0};
     if (n > 0) {
         // the fit pass reads the sorted copies and writes only its outputs, so it
         // can be repeated; outputs go to scratch so that the state is untouched
@@ -696,32 +681,44 @@ lp_status lp_autotune(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_
         o.id = sid;
         cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
         lp_status rs = LP_OK;
-        for (int sched = 0; sched < 2 && rs == LP_OK; ++sched) {
-            rs = run_fit(c, a, o, sched, s);                 // warm-up
-            if (rs != LP_OK) break;
-            if (cudaEventRecord(e0, s) != cudaSuccess) { rs = LP_ERR_CUDA; break; }
-            for (int r = 0; r < reps && rs == LP_OK; ++r) rs = run_fit(c, a, o, sched, s);
-            if (rs != LP_OK) break;
+        auto timed = [&](auto&& body, double& out) {
+            if (body() != LP_OK) return LP_ERR_CUDA;            // warm-up
+            if (cudaEventRecord(e0, s) != cudaSuccess) return LP_ERR_CUDA;
+            for (int r = 0; r < reps; ++r)
+                if (body() != LP_OK) return LP_ERR_CUDA;
             float f = 0.0f;
             if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                cudaEventElapsedTime(&f, e0, e1) != cudaSuccess) {
-                rs = LP_ERR_CUDA;
-                break;
+                cudaEventElapsedTime(&f, e0, e1) != cudaSuccess)
+                return LP_ERR_CUDA;
+            out = f / reps;
+            return LP_OK;
+        };
+        // the query rewrites the same lists whichever schedule runs it
+        const int keep = c->schedule;
+        if (c->dc.radius_mode != LP_RADIUS_KSIDE && c->dc.dim > 1) {
+            for (int q = 0; q < 2 && rs == LP_OK; ++q) {
+                c->schedule = q ? LP_SCHED_QUERY_WARP : 0;
+                rs = timed([&] { return query_neighbors(c, n, s) == cudaSuccess ? LP_OK : LP_ERR_CUDA; }, ms[2 + q]);
             }
-            ms[sched] = f / reps;
         }
+        c->schedule = keep;
+        for (int f = 0; f < 2 && rs == LP_OK; ++f)
+            rs = timed([&] { return run_fit(c, a, o, f ? LP_SCHED_SPLIT : LP_SCHED_FUSED, s); }, ms[f]);
         cudaStreamSynchronize(s);
         cudaFree(scratch);
         cudaFree(sid);
         if (rs != LP_OK) return rs;
-        c->schedule = ms[LP_SCHED_SPLIT] < ms[LP_SCHED_FUSED] ? LP_SCHED_SPLIT : LP_SCHED_FUSED;
+        int sched = ms[1] < ms[0] ? LP_SCHED_SPLIT : LP_SCHED_FUSED;
+        if (ms[3] > 0.0 && ms[3] < ms[2]) sched |= LP_SCHED_QUERY_WARP;
+        c->schedule = sched;
     }
     LP_CUDA(cudaMemcpyAsync(c->counters, saved, sizeof(saved), cudaMemcpyHostToDevice, s));
     LP_CUDA(cudaMemcpyAsync(c->dt_dev, dt_saved, sizeof(double) * c->dc.nsim_max, cudaMemcpyHostToDevice, s));
     LP_CUDA(cudaStreamSynchronize(s));
     c->launches = launches0;
     memcpy(c->phase_launches, ph_launches0, sizeof(ph_launches0));
-    if (out_ms) { out_ms[0] = ms[0]; out_ms[1] = ms[1]; }
+    if (out_ms)
+        for (int q = 0; q < 4; ++q) out_ms[q] = ms[q];
     return LP_OK;
 }
 

@@ -179,11 +179,7 @@ struct FitArgs {
     const uint32_t* idx;
     const double* d2min;
     const double* sx[3];
-    const float* hx[3];
-    const float* lx[3];
     const double* fd[5];      // field values (FP64)
-    const float* fh[5];       // field hi/lo split
-    const float* fl[5];
     const float4* rec;        // packed fit records (positions and fields, hi/lo)
     const uint32_t* sid;
     const double* sm;

@@ -47,8 +47,26 @@ struct DevCfg {
     double box_lo[3], box_hi[3];
     double Lper[3];       // box_hi - box_lo on periodic axes
     float Lper_h[3], Lper_l[3];
+    float radius_f, radius2_f, kappa_f;   // float copies: (float)radius, (float)(radius^2), (float)kappa
     int64_t n_fluid;
 };
+
+// the float query radius of a particle: kappa (m V)^(1/dim) (volume mode) or
+// R (fixed mode); 0 for a non-finite or negative volume.  Written once per build
+// into the fourth component of the particle's float4 position (hi part).
+__device__ inline float query_radius_f(const DevCfg& c, int dim, double m, double V)
+{
+    float Rf;
+    if (c.radius_mode == LP_RADIUS_FIXED) Rf = c.radius_f;
+    else {
+        float wf = (float)m * (float)V;
+        if (!(wf > 0.0f)) wf = 0.0f;
+        const float r = dim == 3 ? cbrtf(wf) : (dim == 2 ? sqrtf(wf) : wf);
+        Rf = c.kappa_f * r;
+    }
+    if (!(Rf >= 0.0f) || isinf(Rf)) Rf = 0.0f;
+    return Rf;
+}
 
 // grid parameters computed on the device every build
 struct Grid {
@@ -187,10 +205,6 @@ struct lp_ctx {
     double* sP;
     double* sm;
     uint32_t* sid;
-    float* hx[3];
-    float* lx[3];
-    float* hf[5];
-    float* lf[5];
     float4* rec;              // packed per-particle fit record, REC_F4 float4 each
     float4* pos4;             // [n][2] position hi / lo as float4 (neighbour query)
     // cell tables, neighbour lists
@@ -253,6 +267,7 @@ cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s);
 cudaError_t fill_tables(lp_ctx* c, int64_t n, bool clear, cudaStream_t s);
 cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s);
 cudaError_t query_init();   // once per context: kernel attributes
+int query_launches(const lp_ctx* c);   // kernels one query launches
 cudaError_t scatter_back(lp_ctx* c, lp_particles* p, cudaStream_t s);
 cudaError_t split_fields(lp_ctx* c, int64_t n, const double* const* f, int nf, cudaStream_t s);
 cudaError_t run_derivs(lp_ctx* c, int64_t n, const double* const* f, int nf, int out_dtype,

@@ -26,9 +26,7 @@ struct QueryArgs {
     const int64_t* level_off;
     const unsigned long long* cells;
     const double* sx[3];
-    const float* hx[3];
-    const float* lx[3];
-    const float4* pos4;       // [n][2]: position hi (xyz, 0), lo (xyz, 0)
+    const float4* pos4;       // [n][2]: position hi (xyz) and float radius (w), lo (xyz, 0)
     const double* sm;
     const double* sV;
     const uint32_t* sid;
@@ -188,21 +186,13 @@ __device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
     // on this part: one occupies a sub-partition's FP64 pipe for ~64 cycles)
     float hxi[3], lxi[3], tq[3];
     const float inv = g.inv_f;
+    const float4 pih = a.pos4[2 * i], pil = a.pos4[2 * i + 1];
+    hxi[0] = pih.x; hxi[1] = pih.y; hxi[2] = pih.z;
+    lxi[0] = pil.x; lxi[1] = pil.y; lxi[2] = pil.z;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        hxi[k] = a.hx[k][i]; lxi[k] = a.lx[k][i];
-        tq[k] = ((hxi[k] - g.lo_h[k]) + (lxi[k] - g.lo_l[k])) * inv;   // quantised units, error < 1
-    }
-    float Rf;
-    if (c.radius_mode == LP_RADIUS_FIXED) Rf = (float)c.radius;
-    else {
-        float wf = (float)a.sm[i] * (float)a.sV[i];
-        if (!(wf > 0.0f)) wf = 0.0f;
-        float r = DIM == 3 ? cbrtf(wf) : (DIM == 2 ? sqrtf(wf) : wf);
-        Rf = (float)c.kappa * r;
-    }
-    if (!(Rf >= 0.0f) || isinf(Rf)) Rf = 0.0f;   // non-finite volume: no neighbours
-    float R2f = (c.radius_mode == LP_RADIUS_FIXED) ? (float)(c.radius * c.radius) : Rf * Rf;
+    for (int k = 0; k < DIM; ++k) tq[k] = ((hxi[k] - g.lo_h[k]) + (lxi[k] - g.lo_l[k])) * inv;   // quantised units, error < 1
+    const float Rf = pih.w;                          // query_radius_f, written by the gather
+    float R2f = (c.radius_mode == LP_RADIUS_FIXED) ? c.radius2_f : Rf * Rf;
     float Rc = Rf * (1.0f + 1e-5f);
     const float Rq = Rc * inv;
     const float Rout = Rf * inv * (1.0f + 2e-5f) + 2.0f;   // boxes beyond: no neighbour
@@ -516,24 +506,16 @@ __device__ inline void tile_lane(const QueryArgs& a, const Grid& g, int64_t i, T
 {
     const DevCfg& c = a.c;
     const float inv = g.inv_f;
+    const float4 ph = a.pos4[2 * i], pl = a.pos4[2 * i + 1];
+    t.hx[0] = ph.x; t.hx[1] = ph.y; t.hx[2] = ph.z;
+    t.lx[0] = pl.x; t.lx[1] = pl.y; t.lx[2] = pl.z;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) { t.hx[k] = 0.0f; t.lx[k] = 0.0f; t.tq[k] = 0.0f; }
+    for (int k = 0; k < 3; ++k) t.tq[k] = 0.0f;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        t.hx[k] = a.hx[k][i]; t.lx[k] = a.lx[k][i];
-        t.tq[k] = ((t.hx[k] - g.lo_h[k]) + (t.lx[k] - g.lo_l[k])) * inv;
-    }
-    float Rf;
-    if (c.radius_mode == LP_RADIUS_FIXED) Rf = (float)c.radius;
-    else {
-        float wf = (float)a.sm[i] * (float)a.sV[i];
-        if (!(wf > 0.0f)) wf = 0.0f;
-        float r = DIM == 3 ? cbrtf(wf) : (DIM == 2 ? sqrtf(wf) : wf);
-        Rf = (float)c.kappa * r;
-    }
-    if (!(Rf >= 0.0f) || isinf(Rf)) Rf = 0.0f;
+    for (int k = 0; k < DIM; ++k) t.tq[k] = ((t.hx[k] - g.lo_h[k]) + (t.lx[k] - g.lo_l[k])) * inv;
+    const float Rf = ph.w;                           // query_radius_f, written by the gather
     t.Rf = Rf;
-    t.R2f = (c.radius_mode == LP_RADIUS_FIXED) ? (float)(c.radius * c.radius) : Rf * Rf;
+    t.R2f = (c.radius_mode == LP_RADIUS_FIXED) ? c.radius2_f : Rf * Rf;
     t.Rq = Rf * (1.0f + 1e-5f) * inv;
     t.Rout = Rf * inv * (1.0f + 2e-5f) + 2.0f;
 }
@@ -552,17 +534,10 @@ __device__ inline float split_offset(const DevCfg& c, int k, float hj, float lj,
     return dh + dl;
 }
 
-// one (key, index) compare-exchange partner step of the bitonic network
-__device__ inline void bitonic_take(uint32_t& key, uint32_t& j, uint32_t pk, uint32_t pj, bool take_min)
-{
-    const bool mine_smaller = key < pk || (key == pk && j < pj);
-    if (take_min != mine_smaller) { key = pk; j = pj; }
-}
-
-// ascending sort of P = 32 * W (W = 1 or 2) (key, index) pairs, element
-// e = lane + 32 s held by lane in (key[s], j[s])
+// ascending sort of P = 32 * W distinct 32-bit keys, element e = lane + 32 s
+// held by lane in key[s]
 template <int W>
-__device__ inline void bitonic_sort(uint32_t (&key)[2], uint32_t (&j)[2])
+__device__ inline void bitonic_keys(uint32_t (&key)[2])
 {
     const unsigned lane = lane_id();
     constexpr int P = 32 * W;
@@ -570,22 +545,17 @@ __device__ inline void bitonic_sort(uint32_t (&key)[2], uint32_t (&j)[2])
     for (int k = 2; k <= P; k <<= 1) {
 #pragma unroll
         for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            if (jj >= 32) {                  // partner in the other register of this lane
-                const bool up = ((lane & (unsigned)k) == 0u);     // k = 64: always ascending
-                const bool sw = (key[0] > key[1] || (key[0] == key[1] && j[0] > j[1])) == up;
-                if (sw) {
-                    uint32_t t = key[0]; key[0] = key[1]; key[1] = t;
-                    t = j[0]; j[0] = j[1]; j[1] = t;
-                }
+            if (jj >= 32) {                  // partner in the other register (k = 64: ascending)
+                const uint32_t lo = min(key[0], key[1]), hi = max(key[0], key[1]);
+                key[0] = lo;
+                key[1] = hi;
             } else {
 #pragma unroll
                 for (int s = 0; s < W; ++s) {
                     const unsigned e = lane + 32u * s;
                     const uint32_t pk = __shfl_xor_sync(0xffffffffu, key[s], jj);
-                    const uint32_t pj = __shfl_xor_sync(0xffffffffu, j[s], jj);
-                    const bool lower = (e & (unsigned)jj) == 0u;
-                    const bool up = (e & (unsigned)k) == 0u;
-                    bitonic_take(key[s], j[s], pk, pj, lower == up);
+                    const bool take_min = ((e & (unsigned)jj) == 0u) == ((e & (unsigned)k) == 0u);
+                    key[s] = take_min ? min(key[s], pk) : max(key[s], pk);
                 }
             }
         }
@@ -594,19 +564,13 @@ __device__ inline void bitonic_sort(uint32_t (&key)[2], uint32_t (&j)[2])
 
 // one group of lanes of the tile (act); all 32 lanes take part
 template <int DIM, bool PER>
-__device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, uint64_t sim)
+__device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, uint64_t sim,
+                           const TileLane<DIM>& me)
 {
     const unsigned lane = lane_id();
     const DevCfg& c = a.c;
     const int mb = c.mbits;
     const Grid& g = a.g[sim];
-    TileLane<DIM> me;
-    if (act) tile_lane<DIM, PER>(a, g, i, me);
-    else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { me.hx[k] = 0.0f; me.lx[k] = 0.0f; me.tq[k] = 0.0f; }
-        me.Rf = me.R2f = me.Rq = me.Rout = 0.0f;
-    }
     if (PER && act) {
 #pragma unroll
         for (int k = 0; k < DIM; ++k)
@@ -658,7 +622,9 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         return;
     }
     const int nct = (int)ncells;
-
+    float rnc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rnc[k] = 1.0f / (float)nc[k];
     // one lane per cell: the key-order range of cell e if it is within reach of the box
     auto cell_range = [&](int e, uint32_t& cs, uint32_t& cn) {
         cs = 0;
@@ -669,8 +635,11 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         float dmin2 = 0.0f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            const int v = clo[k] + u % nc[k];
-            u /= nc[k];
+            int qt = (int)((float)u * rnc[k]);            // u / nc[k], corrected below
+            int rm = u - qt * nc[k];
+            if (rm < 0) { --qt; rm += nc[k]; } else if (rm >= nc[k]) { ++qt; rm -= nc[k]; }
+            const int v = clo[k] + rm;
+            u = qt;
             const int wr = v & (naxis - 1);
             const int sh = (v - wr) >> l0;          // periodic image (0 on other axes)
             const float lo = (float)wr * size + (float)sh * period;
@@ -849,7 +818,13 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
             pl_[k] = __shfl_sync(0xffffffffu, me.lx[k], p);
         }
         const float pR2 = __shfl_sync(0xffffffffu, me.R2f, p);
-        uint32_t key[2] = {0xffffffffu, 0xffffffffu}, jv[2] = {0xffffffffu, 0xffffffffu};
+        // sort keys: float bits of d2 with the low 6 bits replaced by the slot,
+        // so keys are distinct and ordered as the floats up to 2^-17 relative;
+        // the slot brings index and exact float d2 back after the sort
+        uint32_t key[2], jv[2] = {0xffffffffu, 0xffffffffu};
+        float dv[2] = {INFINITY, INFINITY};
+        key[0] = 0xffffffc0u | lane;
+        key[1] = 0xffffffc0u | (lane + 32u);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const int e = (int)lane + 32 * s;
@@ -867,23 +842,45 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                 bool in = d2f <= pR2 * (1.0f - TOL_R);
                 if (!in && d2f <= pR2 * (1.0f + TOL_R))
                     in = inside64(c, DIM, exact_d2<DIM>(a, ip, j), __dmul_rn(a.sm[ip], a.sV[ip]));
-                if (in) { key[s] = __float_as_uint(d2f); jv[s] = j; }
+                if (in) {
+                    key[s] = (__float_as_uint(d2f) & ~63u) | (uint32_t)e;
+                    jv[s] = j;
+                    dv[s] = d2f;
+                }
             }
         }
-        const uint32_t nin = (uint32_t)(__popc(__ballot_sync(0xffffffffu, key[0] != 0xffffffffu)) +
-                                        __popc(__ballot_sync(0xffffffffu, key[1] != 0xffffffffu)));
-        if (m <= 32) bitonic_sort<1>(key, jv);
-        else bitonic_sort<2>(key, jv);
-        // runs of entries within rounding of their predecessor: exact order
+        const uint32_t nin = (uint32_t)(__popc(__ballot_sync(0xffffffffu, key[0] < 0xffffffc0u)) +
+                                        __popc(__ballot_sync(0xffffffffu, key[1] < 0xffffffc0u)));
+        if (m <= 32) bitonic_keys<1>(key);
+        else bitonic_keys<2>(key);
+        {
+            uint32_t js[2];
+            float ds[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const unsigned slot = key[s] & 63u;
+                const uint32_t j0 = __shfl_sync(0xffffffffu, jv[0], slot & 31u);
+                const uint32_t j1 = __shfl_sync(0xffffffffu, jv[1], slot & 31u);
+                const float d0 = __shfl_sync(0xffffffffu, dv[0], slot & 31u);
+                const float d1 = __shfl_sync(0xffffffffu, dv[1], slot & 31u);
+                js[s] = slot < 32u ? j0 : j1;
+                ds[s] = slot < 32u ? d0 : d1;
+            }
+            jv[0] = js[0]; jv[1] = js[1];
+            dv[0] = ds[0]; dv[1] = ds[1];
+        }
+        // runs of entries within rounding of their predecessor (a relative gap
+        // of at most 2^-16, which holds every pair the truncated keys may have
+        // swapped): exact order
         unsigned tie[2];
         {
-            const uint32_t prev0 = __shfl_up_sync(0xffffffffu, key[0], 1);
-            const uint32_t last0 = __shfl_sync(0xffffffffu, key[0], 31);
-            const uint32_t prev1 = __shfl_up_sync(0xffffffffu, key[1], 1);
-            const uint32_t pk0 = prev0, pk1 = lane == 0 ? last0 : prev1;
-            const bool t0 = lane > 0 && lane < nin &&
-                            __uint_as_float(key[0]) <= __uint_as_float(pk0) * (1.0f + TOL_T);
-            const bool t1 = lane + 32 < nin && __uint_as_float(key[1]) <= __uint_as_float(pk1) * (1.0f + TOL_T);
+            const float TOL_P = 1.52587890625e-05f;    // 2^-16
+            const float prev0 = __shfl_up_sync(0xffffffffu, dv[0], 1);
+            const float last0 = __shfl_sync(0xffffffffu, dv[0], 31);
+            const float prev1 = __shfl_up_sync(0xffffffffu, dv[1], 1);
+            const float pk1 = lane == 0 ? last0 : prev1;
+            const bool t0 = lane > 0 && lane < nin && dv[0] <= prev0 * (1.0f + TOL_P);
+            const bool t1 = lane + 32 < nin && dv[1] <= pk1 * (1.0f + TOL_P);
             tie[0] = __ballot_sync(0xffffffffu, t0);
             tie[1] = __ballot_sync(0xffffffffu, t1);
         }
@@ -955,14 +952,15 @@ __global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile(QueryArgs a)
     const uint64_t mysim = (valid && a.c.nsim_max > 1) ? (a.keys[i] >> (DIM * mb)) : 0ull;
     // groups: a new one starts at lane 0, at a change of simulation, and after
     // a jump of more than TQ_GAP radii between consecutive particles
-    float tq[3] = {0.0f, 0.0f, 0.0f}, Rq = 0.0f;
-    if (valid) {
-        TileLane<DIM> t;
-        tile_lane<DIM, PER>(a, a.g[mysim], i, t);
+    TileLane<DIM> t;
+    if (valid) tile_lane<DIM, PER>(a, a.g[mysim], i, t);
+    else {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) tq[k] = t.tq[k];
-        Rq = t.Rq;
+        for (int k = 0; k < 3; ++k) { t.hx[k] = 0.0f; t.lx[k] = 0.0f; t.tq[k] = 0.0f; }
+        t.Rf = t.R2f = t.Rq = t.Rout = 0.0f;
     }
+    float tq[3] = {t.tq[0], t.tq[1], t.tq[2]};
+    const float Rq = t.Rq;
     const uint64_t psim = __shfl_up_sync(0xffffffffu, mysim, 1);
     const float pRq = __shfl_up_sync(0xffffffffu, Rq, 1);
     float gap2 = 0.0f;
@@ -981,7 +979,7 @@ __global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile(QueryArgs a)
         const int s1 = rest ? __ffs(rest) - 1 : 32;
         const unsigned grp = vmask & ((s1 == 32 ? 0xffffffffu : ((1u << s1) - 1u)) & ~((1u << s0) - 1u));
         const uint64_t sim = __shfl_sync(0xffffffffu, mysim, s0);
-        tile_group<DIM, PER>(a, b, i, ((grp >> lane) & 1u) != 0u, sim);
+        tile_group<DIM, PER>(a, b, i, ((grp >> lane) & 1u) != 0u, sim, t);
     }
 }
 
@@ -1064,7 +1062,7 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     a.cells = c->cells;
     for (int k = 0; k < 3; ++k) {
         int kk = k < c->dc.dim ? k : 0;
-        a.sx[k] = c->sx[kk]; a.hx[k] = c->hx[kk]; a.lx[k] = c->lx[kk];
+        a.sx[k] = c->sx[kk];
     }
     a.pos4 = c->pos4;
     a.sm = c->sm; a.sV = c->sV; a.sid = c->sid;
@@ -1085,9 +1083,15 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
         k_d2min<1><<<tb, 256, 0, s>>>(a);
         return cudaGetLastError();
     }
-    // tiles first; the particles they leave go to the per-particle kernel
     cudaError_t e = cudaMemsetAsync(c->counters + C_QFB_LEN, 0, 8, s);
     if (e != cudaSuccess) return e;
+    if (c->schedule & LP_SCHED_QUERY_WARP) {   // one warp per particle for every particle
+        const unsigned wb = (unsigned)((n + NB_WARPS - 1) / NB_WARPS);
+        if (dim == 3) { k_query<3><<<wb, NB_WARPS * 32, 0, s>>>(a); k_d2min<3><<<tb, 256, 0, s>>>(a); }
+        else { k_query<2><<<wb, NB_WARPS * 32, 0, s>>>(a); k_d2min<2><<<tb, 256, 0, s>>>(a); }
+        return cudaGetLastError();
+    }
+    // tiles first; the particles they leave go to the per-particle kernel
     const bool per = c->dc.periodic[0] || c->dc.periodic[1] || c->dc.periodic[2];
     const int64_t tiles = (n + 31) / 32;
     const unsigned tblocks = (unsigned)((tiles + TQ_WARPS - 1) / TQ_WARPS);
@@ -1105,6 +1109,13 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     if (dim == 3) { k_query<3><<<fblocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<3><<<tb, 256, 0, s>>>(a); }
     else { k_query<2><<<fblocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<2><<<tb, 256, 0, s>>>(a); }
     return cudaGetLastError();
+}
+
+int query_launches(const lp_ctx* c)
+{
+    if (c->dc.radius_mode == LP_RADIUS_KSIDE) return 1;
+    if (c->dc.dim == 1 || (c->schedule & LP_SCHED_QUERY_WARP)) return 2;
+    return 3;
 }
 
 cudaError_t query_init()

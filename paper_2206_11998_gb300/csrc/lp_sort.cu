@@ -24,10 +24,24 @@ __device__ inline double from_order_key(unsigned long long k)
     return __longlong_as_double((long long)b);
 }
 
+constexpr int EXT_ITEMS = 16;
+
+__device__ inline void flush_extent(int dim, unsigned long long* e, const double (&lo)[3], const double (&hi)[3],
+                                    double wlo, double whi)
+{
+    for (int k = 0; k < dim; ++k) {
+        atomic_min_d(e + k, lo[k]);
+        atomic_max_d(e + 3 + k, hi[k]);
+    }
+    atomic_min_d(e + 6, wlo);
+    atomic_max_d(e + 7, whi);
+}
+
 // ext[8 s + 0..2] min x_k, [8 s + 3..5] max x_k, [8 s + 6] min w, [8 s + 7] max w
 // (order keys) of simulation s.  One simulation: grid-stride accumulation and a
-// warp reduction; several: one particle per thread, reduced over the warp when
-// the warp's particles share a simulation (they are stored by simulation).
+// warp reduction; several: EXT_ITEMS particles per thread, reduced over the
+// warp when the warp's particles share a simulation (they are stored by
+// simulation), with atomics per run otherwise.
 __global__ void k_reduce_extent(int dim, int64_t n, const double* __restrict__ x0,
                                 const double* __restrict__ x1, const double* __restrict__ x2,
                                 const double* __restrict__ m, const double* __restrict__ V,
@@ -49,13 +63,29 @@ __global__ void k_reduce_extent(int dim, int64_t n, const double* __restrict__ x
             whi = fmax(whi, w);
         }
     } else {
-        int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        if (i < n) {
-            sim = sim_of[i];
-            for (int k = 0; k < dim; ++k) { lo[k] = xs[k][i]; hi[k] = lo[k]; }
-            wlo = whi = __dmul_rn(m[i], V[i]);
-        } else {
-            sim = 0xffffffffu;
+        // EXT_ITEMS particles per thread (strided by the block size, so loads
+        // stay coalesced); a change of simulation flushes the running extent
+        sim = 0xffffffffu;
+        const int64_t base = (int64_t)blockIdx.x * blockDim.x * EXT_ITEMS + threadIdx.x;
+        for (int r = 0; r < EXT_ITEMS; ++r) {
+            const int64_t i = base + (int64_t)r * blockDim.x;
+            if (i >= n) break;
+            const uint32_t si = sim_of[i];
+            const double w = __dmul_rn(m[i], V[i]);
+            if (si != sim) {
+                if (sim != 0xffffffffu) flush_extent(dim, ext + 8 * (int64_t)sim, lo, hi, wlo, whi);
+                sim = si;
+                for (int k = 0; k < dim; ++k) { lo[k] = xs[k][i]; hi[k] = lo[k]; }
+                wlo = whi = w;
+            } else {
+                for (int k = 0; k < dim; ++k) {
+                    const double v = xs[k][i];
+                    lo[k] = fmin(lo[k], v);
+                    hi[k] = fmax(hi[k], v);
+                }
+                wlo = fmin(wlo, w);
+                whi = fmax(whi, w);
+            }
         }
     }
     uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
@@ -74,13 +104,7 @@ __global__ void k_reduce_extent(int dim, int64_t n, const double* __restrict__ x
     } else if (sim == 0xffffffffu) {
         return;
     }
-    unsigned long long* e = ext + 8 * (int64_t)sim;
-    for (int k = 0; k < dim; ++k) {
-        atomic_min_d(e + k, lo[k]);
-        atomic_max_d(e + 3 + k, hi[k]);
-    }
-    atomic_min_d(e + 6, wlo);
-    atomic_max_d(e + 7, whi);
+    flush_extent(dim, ext + 8 * (int64_t)sim, lo, hi, wlo, whi);
 }
 
 __global__ void k_init_extent(unsigned long long* ext, int nsim)
@@ -310,12 +334,9 @@ k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __re
 
 // gather the state into key order and split it into float hi/lo pairs
 template <int DIM>
-__global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_particles p,
+__global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_particles p, DevCfg c,
                          double* sx0, double* sx1, double* sx2, double* sV, double* su0, double* su1,
-                         double* su2, double* sP, double* sm, uint32_t* sid,
-                         float* hx0, float* hx1, float* hx2, float* lx0, float* lx1, float* lx2,
-                         float* hf0, float* hf1, float* hf2, float* hf3, float* hf4,
-                         float* lf0, float* lf1, float* lf2, float* lf3, float* lf4, float4* rec, float4* pos4)
+                         double* su2, double* sP, double* sm, uint32_t* sid, float4* rec, float4* pos4)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -325,17 +346,11 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_partic
     for (int q = 0; q < 4 * REC_F4; ++q) r[q] = 0.0f;
     double* sx[3] = {sx0, sx1, sx2};
     double* su[3] = {su0, su1, su2};
-    float* hx[3] = {hx0, hx1, hx2};
-    float* lx[3] = {lx0, lx1, lx2};
-    float* hf[5] = {hf0, hf1, hf2, hf3, hf4};
-    float* lf[5] = {lf0, lf1, lf2, lf3, lf4};
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         double v = p.x[k][j];
         sx[k][i] = v;
         split(v, r[REC_XH + k], r[REC_XL + k]);
-        hx[k][i] = r[REC_XH + k];
-        lx[k][i] = r[REC_XL + k];
     }
     double V = p.V[j], P = p.P[j];
     sV[i] = V;
@@ -349,12 +364,11 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_partic
         split(v, r[REC_FH + 1 + k], r[REC_FL + 1 + k]);
     }
 #pragma unroll
-    for (int f = 0; f < DIM + 2; ++f) { hf[f][i] = r[REC_FH + f]; lf[f][i] = r[REC_FL + f]; }
-#pragma unroll
     for (int q = 0; q < REC_F4; ++q) rec[i * REC_F4 + q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-    pos4[2 * i] = make_float4(r[REC_XH], r[REC_XH + 1], r[REC_XH + 2], 0.0f);
+    const double m = p.m[j];
+    pos4[2 * i] = make_float4(r[REC_XH], r[REC_XH + 1], r[REC_XH + 2], query_radius_f(c, DIM, m, V));
     pos4[2 * i + 1] = make_float4(r[REC_XL], r[REC_XL + 1], r[REC_XL + 2], 0.0f);
-    sm[i] = p.m[j];
+    sm[i] = m;
     sid[i] = p.id[j];
 }
 
@@ -429,7 +443,8 @@ cudaError_t build_grid(lp_ctx* c, const lp_particles* p, cudaStream_t s)
     }
     k_init_extent<<<(unsigned)((8 * nsim + 255) / 256), 256, 0, s>>>(c->ext, nsim);
     int64_t nb_ = grid_for(n, 256);
-    unsigned blocks = nsim > 1 ? (unsigned)nb_ : (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
+    unsigned blocks = nsim > 1 ? (unsigned)((n + 256 * EXT_ITEMS - 1) / (256 * EXT_ITEMS))
+                               : (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
     if (blocks == 0) blocks = 1;
     k_reduce_extent<<<blocks, 256, 0, s>>>(c->dc.dim, n, p->x[0], p->x[1] ? p->x[1] : p->x[0],
                                            p->x[2] ? p->x[2] : p->x[0], p->m, p->V, sim_of, c->ext);
@@ -480,9 +495,8 @@ cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s)
     const uint32_t* perm = c->perm_sorted;
     lp_particles q = *p;
     for (int k = dim; k < 3; ++k) { q.x[k] = p->x[0]; q.u[k] = p->u[0]; }
-#define LP_GATHER_ARGS n, perm, q, c->sx[0], c->sx[1], c->sx[2], c->sV, c->su[0], c->su[1], c->su[2], c->sP, \
-        c->sm, c->sid, c->hx[0], c->hx[1], c->hx[2], c->lx[0], c->lx[1], c->lx[2], c->hf[0], c->hf[1],     \
-        c->hf[2], c->hf[3], c->hf[4], c->lf[0], c->lf[1], c->lf[2], c->lf[3], c->lf[4], c->rec, c->pos4
+#define LP_GATHER_ARGS n, perm, q, c->dc, c->sx[0], c->sx[1], c->sx[2], c->sV, c->su[0], c->su[1], c->su[2], \
+        c->sP, c->sm, c->sid, c->rec, c->pos4
     if (dim == 3) k_gather<3><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
     else if (dim == 2) k_gather<2><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
     else k_gather<1><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);

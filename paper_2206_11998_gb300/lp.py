@@ -22,7 +22,7 @@ RADIUS_FIXED, RADIUS_VOLUME, RADIUS_KSIDE = 0, 1, 2
 LIM_FLAGGED, LIM_PAPER, LIM_LW, LIM_UW = 0, 1, 2, 3
 EST_PLAIN, EST_MLP = 0, 1
 OUT_F32, OUT_F64 = 0, 1
-SCHED_FUSED, SCHED_SPLIT = 0, 1
+SCHED_FUSED, SCHED_SPLIT, SCHED_QUERY_WARP = 0, 1, 2
 
 EXPORTED = [
     "lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs", "lp_step",
@@ -348,13 +348,14 @@ class Context:
         return v.value
 
     def autotune(self, ps: ParticleSet, offsets=None, nsim=1, dt=0.0, cfl=0.4, reps=3, stream=None):
-        """Time the fit pass under both schedules on this state and keep the faster;
-        returns (fused_ms, split_ms).  The state is not changed."""
+        """Time the query and the fit pass under each schedule on this state and
+        keep the faster of each; returns {fit_fused, fit_split, query_tile,
+        query_warp} in ms.  The state is not changed."""
         p = ps.struct()
-        out = (C.c_double * 2)()
+        out = (C.c_double * 4)()
         _check(lib().lp_autotune(self.h, C.byref(p), _ptr(offsets), int(nsim), float(dt), float(cfl), int(reps),
                                  out, _stream(stream)), "lp_autotune")
-        return out[0], out[1]
+        return {"fit_fused": out[0], "fit_split": out[1], "query_tile": out[2], "query_warp": out[3]}
 
     def stats(self, stream=None) -> dict:
         s = Stats()

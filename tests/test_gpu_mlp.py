@@ -99,7 +99,7 @@ def test_features_match_oracle(prec, tol):
     ctx.close()
 
 
-def _training_set(n=200_000, steps=3, seed=11):
+def _training_set(n=1_000_000, steps=2, seed=11):
     """Features and plain-estimator flags of the gas cloud's own plain steps."""
     st = inputs.gas_cloud_3d(n, seed=seed)
     cfg = lp.make_config(3, n, kappa=2.2, k_max=64, gamma=5.0 / 3.0, s_ref=inputs.field_scales(st))
@@ -116,7 +116,13 @@ def _training_set(n=200_000, steps=3, seed=11):
     return torch.cat(Xs), torch.cat(ys), st
 
 
-def test_training_reduces_loss_and_separates_flags():
+MISS_TARGET = 0.01    # share of the plain estimator's flags the gate may clear on its training set
+
+
+def _trained_gate():
+    """Train on the cloud's own plain steps; the gate threshold is calibrated
+    on the training set so that at most MISS_TARGET of its flags fall below it.
+    Returns (context, losses, probabilities, labels, tau)."""
     X, y, _ = _training_set()
     g = torch.Generator(device="cuda").manual_seed(0)
     perm = torch.randperm(X.shape[0], device="cuda", generator=g)
@@ -125,13 +131,62 @@ def test_training_reduces_loss_and_separates_flags():
     ctx.mlp_set_params(lp.mlp_init_params(1))
     pos = float((y == 0).sum() / max(1, int((y == 1).sum())))
     losses = ctx.mlp_train(X, y, epochs=30, batch=8192, lr=1e-2, pos_weight=pos)
-    assert losses[-1] < 0.85 * losses[0], losses
     p = ctx.mlp_infer(X).cpu().numpy()
     yy = y.cpu().numpy() > 0.5
-    # skipping below tau drops a large share of particles while missing few flags
-    tau = 0.05
+    tau = float(np.quantile(p[yy], MISS_TARGET))
+    return ctx, losses, p, yy, tau
+
+
+def test_training_reduces_loss_and_separates_flags():
+    ctx, losses, p, yy, tau = _trained_gate()
+    assert losses[-1] < 0.85 * losses[0], losses
+    # at the calibrated threshold the gate clears a large share of particles
     skip = p < tau
     miss = (skip & yy).sum() / max(1, yy.sum())
-    assert skip.mean() > 0.2, skip.mean()
-    assert miss < 0.02, miss
+    print("tau %.4f skip %.3f miss %.4f" % (tau, skip.mean(), miss))
+    assert miss <= MISS_TARGET + 1e-3, miss
+    assert skip.mean() > 0.4, skip.mean()
     ctx.close()
+
+
+def test_learned_gate_gains_over_plain_estimator():
+    """What the trained network buys on a cloud it was not trained on: the
+    gated step skips the one-sided fits of most particles, so its fit pass is
+    faster than the plain estimator's under the same schedule, while it misses
+    few of the flags the plain estimator raises (audit mode)."""
+    ct, _, _, _, tau = _trained_gate()
+    params = ct.mlp_get_params()[0]
+    ct.close()
+
+    n = 1_000_000
+    st = inputs.gas_cloud_3d(n, seed=17)
+
+    def run(est, audit=0, reps=3):
+        cfg = lp.make_config(3, n, kappa=2.2, k_max=64, gamma=5.0 / 3.0, s_ref=inputs.field_scales(st),
+                             estimator=est, mlp_tau_lo=tau, mlp_audit=audit)
+        ctx = lp.Context(cfg)
+        if est == lp.EST_MLP:
+            ctx.mlp_set_params(params)
+        ctx.set_schedule(lp.SCHED_SPLIT)     # the same schedule for both: the comparison isolates the gate
+        ctx.step(lp.ParticleSet.from_state(st), dt=0.0, cfl=0.4)
+        ctx.reset_stats()
+        ctx.phase_times()
+        ctx.set_profiling(True)
+        for _ in range(reps):
+            ctx.step(lp.ParticleSet.from_state(st), dt=0.0, cfl=0.4)
+        ph = ctx.phase_times()
+        ctx.set_profiling(False)
+        s = ctx.stats()
+        ctx.close()
+        fit = (ph["fit+update"][0] + ph["fit+update-fp64"][0]) / reps
+        return fit, s
+
+    plain_ms, sp = run(lp.EST_PLAIN)
+    gated_ms, sg = run(lp.EST_MLP)
+    _, sa = run(lp.EST_MLP, audit=1, reps=1)
+    skip = sg["n_mlp_skip"] / (3 * n)
+    miss = sa["n_mlp_miss"] / max(1, sa["n_flagged"] + sa["n_mlp_miss"])
+    print("fit ms plain %.3f gated %.3f skip %.3f miss %.4f tau %.4f" % (plain_ms, gated_ms, skip, miss, tau))
+    assert skip > 0.4, skip
+    assert miss < 0.05, miss
+    assert gated_ms < 0.85 * plain_ms, (gated_ms, plain_ms)

@@ -110,7 +110,7 @@ def test_default_schedule_follows_estimator():
     assert c1.schedule() == lp.SCHED_FUSED
     assert c2.schedule() == lp.SCHED_SPLIT
     with pytest.raises(lp.LPError):
-        c1.set_schedule(7)
+        c1.set_schedule(4)
     c1.close()
     c2.close()
 
@@ -126,9 +126,11 @@ def test_autotune_keeps_state_and_counters():
     torch.cuda.synchronize()
     before = ps.to_state(N)
     s0 = ctx.stats()
-    fused_ms, split_ms = ctx.autotune(ps, dt=0.0, cfl=0.4, reps=2)
-    assert fused_ms > 0 and split_ms > 0
-    assert ctx.schedule() == (lp.SCHED_SPLIT if split_ms < fused_ms else lp.SCHED_FUSED)
+    t = ctx.autotune(ps, dt=0.0, cfl=0.4, reps=2)
+    assert all(v > 0 for v in t.values()), t
+    want = (lp.SCHED_SPLIT if t["fit_split"] < t["fit_fused"] else lp.SCHED_FUSED) | (
+        lp.SCHED_QUERY_WARP if t["query_warp"] < t["query_tile"] else 0)
+    assert ctx.schedule() == want
     after = ps.to_state(N)
     for f in ("V", "P", "m", "id"):
         assert np.array_equal(before[f], after[f]), f
@@ -142,3 +144,20 @@ def test_autotune_keeps_state_and_counters():
     got = (ps.to_state(N), flag.cpu().numpy(), phi.cpu().numpy(), ctx.stats())
     ctx.close()
     _same(ref, got)
+
+
+def test_query_schedules_give_identical_lists():
+    """Tiles (with the per-particle kernel for the particles they leave) and
+    one warp per particle for every particle: the same lists, bit for bit."""
+    st = _cloud()
+    out = []
+    for sched in (lp.SCHED_FUSED, lp.SCHED_QUERY_WARP):
+        ctx = lp.Context(_cfg(st))
+        ctx.set_schedule(sched)
+        ps = lp.ParticleSet.from_state(st)
+        ctx.build_neighbors(ps)
+        cnt, tot, idx, d2, keys = ctx.export_neighbors(N)
+        out.append([a.cpu().numpy() for a in (cnt, tot, idx, d2, ps.id)])
+        ctx.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
