@@ -3,11 +3,12 @@
 //
 // Schedule: one thread per particle.  The overdetermined GFD system of
 // Eq. linear_system_axb (and its 1D/3D analogues) is reduced to triangular form
-// by Givens rotations applied row by row as the neighbours stream in, so the
-// 9-column R, Q^T b for all fields and the running row live in registers; no
-// stencil is staged and no lane idles.  Columns are scaled by powers of two
-// (exact) so R is well scaled; min|R_kk|/max|R_kk| decides the FP64 redo (FP32)
-// or the first-order fallback (FP64).  The FP32 path forms offsets and field
+// by square-root-free Givens rotations applied row by row as the neighbours
+// stream in, so the 9-column factor, Q^T b for all fields and the running row
+// live in registers; no stencil is staged and no lane idles.  Offsets are
+// scaled by a power of two (exact) so the factor is well scaled;
+// min|R_kk|/max|R_kk| decides the FP64 redo (FP32) or the first-order fallback
+// (FP64).  The FP32 path forms offsets and field
 // differences from split (hi, lo) floats, accurate to a few ulp of the offset
 // itself.
 #pragma once
@@ -30,6 +31,8 @@ template <> struct RN<float> {
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    // the hardware reciprocal (a few ulp), as fast as the square root it replaces
+    static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
 };
 template <> struct RN<double> {
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
@@ -37,115 +40,130 @@ template <> struct RN<double> {
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
 };
 
-template <typename T> __device__ inline T rsqrt_t(T x);
-template <> __device__ inline float rsqrt_t<float>(float x) { return rsqrtf(x); }
-template <> __device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
 
 // ---------------------------------------------------------------------------
 // row-by-row Givens least squares:  min || A x - B ||, A: rows x N, B: rows x F
 // ---------------------------------------------------------------------------
 template <typename T, int N, int F>
 struct Givens {
-    T R[N * (N + 1) / 2];
+    // Square-root-free Givens rotations (Gentleman's form): R = D^{1/2} U with U
+    // unit upper triangular and Q^T B = D^{1/2} Z.  A row (a, b) of weight w,
+    // starting at 1, enters column k as
+    //   d' = d_k + w a_k^2,  s = w a_k / d',  w' = w d_k / d',
+    //   t = a_l - a_k U_kl,  U_kl' = U_kl + s t,  a_l' = t    (l > k; b likewise)
+    // -- two FMAs per element, no square root.  The row's remaining weight w
+    // times its leftover b^2 is its share of the residual sum of squares.
+    T d[N];
+    T U[N * (N - 1) / 2 + 1];   // strict upper part of U, row by row
     T Z[N][F];
 
-    __device__ static constexpr int id(int k, int l) { return k * N - (k * (k - 1)) / 2 + (l - k); }
+    __device__ static constexpr int id(int k, int l) { return k * (N - 1) - (k * (k - 1)) / 2 + (l - k - 1); }
 
     __device__ void zero()
     {
 #pragma unroll
-        for (int q = 0; q < N * (N + 1) / 2; ++q) R[q] = T(0);
+        for (int k = 0; k < N; ++k) d[k] = T(0);
+#pragma unroll
+        for (int q = 0; q < N * (N - 1) / 2 + 1; ++q) U[q] = T(0);
 #pragma unroll
         for (int k = 0; k < N; ++k)
 #pragma unroll
             for (int f = 0; f < F; ++f) Z[k][f] = T(0);
     }
 
-    __device__ void add(T (&a)[N], T (&b)[F])
+    // rotates the row in; returns its remaining weight
+    __device__ T add(T (&a)[N], T (&b)[F])
     {
         using O = RN<T>;
+        T w = T(1);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            T ak = a[k];
-            if (ak != T(0)) {
-                T rkk = R[id(k, k)];
-                T h2 = O::fma(rkk, rkk, O::mul(ak, ak));
-                T inv = rsqrt_t<T>(h2);
-                T cc = O::mul(rkk, inv), ss = O::mul(ak, inv);
-                R[id(k, k)] = O::mul(h2, inv);
+            const T ak = a[k];
+            const T wa = O::mul(w, ak);
+            const T dn = O::fma(wa, ak, d[k]);
+            // a row absorbed by an empty column keeps weight 0: nothing left to rotate
+            if (wa != T(0) && dn > T(0)) {
+                const T inv = O::rcp(dn);
+                const T sk = O::mul(wa, inv);
+                w = O::mul(O::mul(w, d[k]), inv);
+                d[k] = dn;
 #pragma unroll
                 for (int l = k + 1; l < N; ++l) {
-                    T t = R[id(k, l)];
-                    R[id(k, l)] = O::fma(cc, t, O::mul(ss, a[l]));
-                    a[l] = O::fma(cc, a[l], -O::mul(ss, t));
+                    const T t = O::fma(-ak, U[id(k, l)], a[l]);
+                    U[id(k, l)] = O::fma(sk, t, U[id(k, l)]);
+                    a[l] = t;
                 }
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
-                    T t = Z[k][f];
-                    Z[k][f] = O::fma(cc, t, O::mul(ss, b[f]));
-                    b[f] = O::fma(cc, b[f], -O::mul(ss, t));
+                    const T t = O::fma(-ak, Z[k][f], b[f]);
+                    Z[k][f] = O::fma(sk, t, Z[k][f]);
+                    b[f] = t;
                 }
             }
         }
+        return w;
     }
 
+    // min |R_kk| / max |R_kk| = sqrt(min d_k / max d_k)
     __device__ T ratio() const
     {
-        T lo = fabs(R[id(0, 0)]), hi = lo;
+        T lo = d[0], hi = d[0];
 #pragma unroll
         for (int k = 1; k < N; ++k) {
-            T d = fabs(R[id(k, k)]);
-            lo = d < lo ? d : lo;
-            hi = d > hi ? d : hi;
+            lo = d[k] < lo ? d[k] : lo;
+            hi = d[k] > hi ? d[k] : hi;
         }
-        return hi > T(0) ? lo / hi : T(0);
+        return hi > T(0) ? sqrt(RN<T>::div(lo, hi)) : T(0);
     }
 
-    // x = R^{-1} Z
+    // x = R^{-1} Q^T B = U^{-1} Z
     __device__ void solve(T (&x)[N][F]) const
     {
         using O = RN<T>;
 #pragma unroll
         for (int k = N - 1; k >= 0; --k) {
-            T inv = O::div(T(1), R[id(k, k)]);
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 T s = Z[k][f];
 #pragma unroll
-                for (int l = k + 1; l < N; ++l) s = O::fma(-R[id(k, l)], x[l][f], s);
-                x[k][f] = O::mul(s, inv);
+                for (int l = k + 1; l < N; ++l) s = O::fma(-U[id(k, l)], x[l][f], s);
+                x[k][f] = s;
             }
         }
     }
 
-    // d = (R^T R)^{-1} g  (one correction step of the semi-normal equations)
+    // g <- (R^T R)^{-1} g = U^{-1} D^{-1} U^{-T} g  (one correction step of the
+    // semi-normal equations)
     __device__ void solve_normal(T (&g)[N][F]) const
     {
         using O = RN<T>;
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            T inv = O::div(T(1), R[id(k, k)]);
+        for (int k = 0; k < N; ++k)           // U^T y = g (unit lower triangular)
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 T s = g[k][f];
 #pragma unroll
-                for (int l = 0; l < k; ++l) s = O::fma(-R[id(l, k)], g[l][f], s);
-                g[k][f] = O::mul(s, inv);
+                for (int l = 0; l < k; ++l) s = O::fma(-U[id(l, k)], g[l][f], s);
+                g[k][f] = s;
             }
+#pragma unroll
+        for (int k = 0; k < N; ++k) {         // y <- D^{-1} y
+            const T inv = O::rcp(d[k]);
+#pragma unroll
+            for (int f = 0; f < F; ++f) g[k][f] = O::mul(g[k][f], inv);
         }
 #pragma unroll
-        for (int k = N - 1; k >= 0; --k) {
-            T inv = O::div(T(1), R[id(k, k)]);
+        for (int k = N - 1; k >= 0; --k)      // U x = y
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 T s = g[k][f];
 #pragma unroll
-                for (int l = k + 1; l < N; ++l) s = O::fma(-R[id(k, l)], g[l][f], s);
-                g[k][f] = O::mul(s, inv);
+                for (int l = k + 1; l < N; ++l) s = O::fma(-U[id(k, l)], g[l][f], s);
+                g[k][f] = s;
             }
-        }
     }
 };
 
@@ -388,8 +406,8 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
             bmax = bl > bmax ? bl : bmax;
             ssb = RN<T>::fma(bl, bl, ssb);
         }
-        G.add(a, b);
-        if (STATS) ssr = RN<T>::fma(b[F - 1], b[F - 1], ssr);   // the row's leftover after the rotations
+        const T w = G.add(a, b);
+        if (STATS) ssr = RN<T>::fma(RN<T>::mul(w, b[F - 1]), b[F - 1], ssr);   // the row's weighted leftover
         return true;
     });
     if (STATS && st) { st->bmin = bmin; st->bmax = bmax; st->ssb = ssb; st->ssr = ssr; }

@@ -139,8 +139,10 @@ __device__ inline bool step_load(const FitArgs& a, const StepOut& o, int64_t i, 
     return true;
 }
 
-// central stage; false when i went to the FP64 redo list
-template <typename T, int DIM>
+// central stage; false when i went to the FP64 redo list.  GATE: the learned
+// estimator or the feature output is in use (its inputs and code are compiled
+// out otherwise)
+template <typename T, int DIM, bool GATE>
 __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t i, const Loaded<DIM>& L,
                                     const Src<T, DIM, DIM + 2>& src, const uint32_t* nb, int cnt, T invS,
                                     T (&cdf)[DIM][DIM + 2], T (&lw)[DIM + 2], bool& mlp_skip)
@@ -151,7 +153,7 @@ __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t 
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
     T cd[N][F];
     FitStats<T> fst = {T(0), T(0), T(0), T(0)};
-    if (central_fit<T, DIM, F, true>(src, nb, cnt, invS, tau, c.refine != 0, cd, &fst)) {
+    if (central_fit<T, DIM, F, GATE>(src, nb, cnt, invS, tau, c.refine != 0, cd, &fst)) {
         if (IsF32<T>::v) { push_redo(a, i); return false; }
         T lin[DIM][F];
 #pragma unroll
@@ -171,7 +173,7 @@ __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t 
     // learned estimator: below mlp_tau_lo the particle is unflagged and its
     // one-sided fits are skipped (unless auditing against the plain estimator)
     mlp_skip = false;
-    if (o.features || c.estimator == LP_EST_MLP) {
+    if (GATE && (o.features || c.estimator == LP_EST_MLP)) {
         float xf[MLP_IN];
         mlp_features<T, DIM>(cd, fst, (T)sqrt(a.d2min[i]), (T)L.s0[0], (T)L.s0[F - 1], (T)c.gamma, xf);
         if (o.features)
@@ -322,7 +324,7 @@ __device__ inline void skip_plain(const T (&cdf)[DIM][DIM + 2], T (&os)[DIM][2][
 }
 
 // fused schedule: all stages in one thread
-template <typename T, int DIM>
+template <typename T, int DIM, bool GATE>
 __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
 {
     constexpr int F = DIM + 2;
@@ -334,7 +336,7 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     T cdf[DIM][F], lw[F];
     bool mlp_skip;
-    if (!step_central<T, DIM>(a, o, i, L, src, nb, cnt, invS, cdf, lw, mlp_skip)) return;
+    if (!step_central<T, DIM, GATE>(a, o, i, L, src, nb, cnt, invS, cdf, lw, mlp_skip)) return;
     const bool plain = !mlp_skip || a.c.mlp_audit;
     T os[DIM][2][F];
     if (plain) {
@@ -345,17 +347,17 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     step_finish<T, DIM>(a, o, i, L, os, lw, plain, mlp_skip);
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool GATE>
 __global__ void __launch_bounds__(128) k_step(FitArgs a, StepOut o)
 {
     if (a.list) {
         unsigned long long len = *a.list_len;
         for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < len;
              t += (unsigned long long)gridDim.x * blockDim.x)
-            step_one<T, DIM>(a, o, a.list[t]);
+            step_one<T, DIM, GATE>(a, o, a.list[t]);
     } else {
         int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        if (i < a.n) step_one<T, DIM>(a, o, i);
+        if (i < a.n) step_one<T, DIM, GATE>(a, o, i);
     }
 }
 
@@ -376,7 +378,7 @@ __device__ inline unsigned long long warp_append(unsigned long long* len, bool p
     return base + (unsigned long long)__popc(b & ((1u << lane) - 1u));
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool GATE>
 __global__ void __launch_bounds__(128) k_step_central(FitArgs a, StepOut o)
 {
     constexpr int F = DIM + 2;
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(128) k_step_central(FitArgs a, StepOut o)
     const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     T cdf[DIM][F], lw[F];
     bool mlp_skip;
-    if (!step_central<T, DIM>(a, o, i, L, src, nb, cnt, invS, cdf, lw, mlp_skip)) return;
+    if (!step_central<T, DIM, GATE>(a, o, i, L, src, nb, cnt, invS, cdf, lw, mlp_skip)) return;
     const bool plain = !mlp_skip || a.c.mlp_audit;
     unsigned long long t = warp_append(a.plain_len, plain);
     if (plain) {
@@ -594,9 +596,17 @@ inline unsigned fit_blocks(const FitArgs& a)
     {                                                                                           \
         unsigned b = fit_blocks(a);                                                             \
         if (b == 0) return cudaSuccess;                                                         \
-        if (dim == 3) k_step<T, 3><<<b, 128, 0, s>>>(a, o);                                     \
-        else if (dim == 2) k_step<T, 2><<<b, 128, 0, s>>>(a, o);                                \
-        else k_step<T, 1><<<b, 128, 0, s>>>(a, o);                                              \
+        const bool gate = o.features || a.c.estimator == LP_EST_MLP;                           \
+        if (dim == 3) {                                                                         \
+            if (gate) k_step<T, 3, true><<<b, 128, 0, s>>>(a, o);                               \
+            else k_step<T, 3, false><<<b, 128, 0, s>>>(a, o);                                   \
+        } else if (dim == 2) {                                                                  \
+            if (gate) k_step<T, 2, true><<<b, 128, 0, s>>>(a, o);                               \
+            else k_step<T, 2, false><<<b, 128, 0, s>>>(a, o);                                   \
+        } else {                                                                                \
+            if (gate) k_step<T, 1, true><<<b, 128, 0, s>>>(a, o);                               \
+            else k_step<T, 1, false><<<b, 128, 0, s>>>(a, o);                                   \
+        }                                                                                       \
         return cudaGetLastError();                                                              \
     }                                                                                           \
     cudaError_t launch_step_split_##SUF(int dim, const FitArgs& a, const StepOut& o,            \
@@ -604,14 +614,18 @@ inline unsigned fit_blocks(const FitArgs& a)
     {                                                                                           \
         unsigned b = (unsigned)((a.n + 127) / 128);                                             \
         if (b == 0) return cudaSuccess;                                                         \
+        const bool gate = o.features || a.c.estimator == LP_EST_MLP;                           \
         if (dim == 3) {                                                                         \
-            k_step_central<T, 3><<<b, 128, 0, s>>>(a, o);                                       \
+            if (gate) k_step_central<T, 3, true><<<b, 128, 0, s>>>(a, o);                       \
+            else k_step_central<T, 3, false><<<b, 128, 0, s>>>(a, o);                           \
             k_step_plain<T, 3><<<b, 128, 0, s>>>(a, o);                                         \
         } else if (dim == 2) {                                                                  \
-            k_step_central<T, 2><<<b, 128, 0, s>>>(a, o);                                       \
+            if (gate) k_step_central<T, 2, true><<<b, 128, 0, s>>>(a, o);                       \
+            else k_step_central<T, 2, false><<<b, 128, 0, s>>>(a, o);                           \
             k_step_plain<T, 2><<<b, 128, 0, s>>>(a, o);                                         \
         } else {                                                                                \
-            k_step_central<T, 1><<<b, 128, 0, s>>>(a, o);                                       \
+            if (gate) k_step_central<T, 1, true><<<b, 128, 0, s>>>(a, o);                       \
+            else k_step_central<T, 1, false><<<b, 128, 0, s>>>(a, o);                           \
             k_step_plain<T, 1><<<b, 128, 0, s>>>(a, o);                                         \
         }                                                                                       \
         return cudaGetLastError();                                                              \
