@@ -54,11 +54,16 @@ def fit_flops_per_particle(m: float) -> float:
     return central + onesided + 500.0
 
 
+# DRAM bytes per particle of one fit pass (split schedule, FP32), measured by ncu
+# on the 400k-particle cloud for the kernels as they are now; None when the
+# kernels change and the figure has not been re-measured
+FIT_TRAFFIC_BPP = 966.0
+
 # algorithmic DRAM bytes per particle of the memory-bound phases
 BYTES_PER_PARTICLE = {
     "grid+keys": 24 + 8 + 24 + 12,          # extent read, m V read, positions read, key + index write
     "radix-sort": 24,                       # per 8-bit pass: key + index read and written once
-    "gather": 76 + 76 + 64,                 # state read, sorted copy written, hi/lo split written
+    "gather": 76 + 76 + 64 + 32,            # state read; sorted copy, fit record and query positions written
     "cell-tables": 8 * 2,                   # sorted keys read (fill and clear)
 }
 
@@ -312,16 +317,24 @@ def run_ours(args):
             entry.update({"bound": "hbm", "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_peak if gbs else None})
         per_phase[name] = entry
     fit_phase = "fit+update" if args.precision == "fp32" else "fit+update-fp64"
-    fit_ms = phases[fit_phase][0] / args.steps
-    fit_launch_ms = phases[fit_phase][0] / max(1, phases[fit_phase][1])
+    fit_ms = phases[fit_phase][0] / args.steps          # one fit pass over all n particles
     flops = fit_flops_per_particle(m_mean) * n
-    achieved = flops / (fit_launch_ms * 1e-3) / 1e12
+    achieved = flops / (fit_ms * 1e-3) / 1e12
     dominant = max(per_phase, key=lambda k: per_phase[k]["ms_per_step"])
-    roofline = {"kernel": "k_step<float,3> (fit+update)", "dominant_phase": dominant, "bound": "alu",
+    sched = ctx.schedule()
+    fit_kernels = ("k_step_central + k_step_plain" if sched & lp.SCHED_SPLIT else "k_step") + \
+        ("<float,3>" if args.precision == "fp32" else "<double,3>")
+    traffic = None
+    if args.precision == "fp32" and args.estimator == "plain" and sched & lp.SCHED_SPLIT and FIT_TRAFFIC_BPP:
+        traffic = FIT_TRAFFIC_BPP * n
+    roofline = {"kernel": fit_kernels + " (fit+update pass)", "dominant_phase": dominant, "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (sm_max, peak_kind),
                 "flops_per_particle": fit_flops_per_particle(m_mean), "mean_neighbors": m_mean,
-                "traffic": None}
+                "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the fit kernels on the "
+                                  "400k-particle cloud, scaled by particles (profiles/k_step_split_gas_cloud_400k.md)"
+                                  if traffic else None}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, q_n, secs = oracle_sample_rate(state, args.cpu_seconds)

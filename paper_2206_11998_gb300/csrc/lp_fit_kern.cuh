@@ -23,6 +23,12 @@ struct StepOut {
 template <typename T> struct IsF32 { static constexpr bool v = false; };
 template <> struct IsF32<float> { static constexpr bool v = true; };
 
+// resident 128-thread blocks per SM the FP32 step kernels are compiled for
+// (measured on the 2M-particle cloud: 3/4 blocks with a few spilled registers
+// beat 2/3 blocks without spills by 7%); the FP64 kernels keep the default
+template <typename T> struct FitOcc { static constexpr int fused = 1, central = 1, plain = 1; };
+template <> struct FitOcc<float> { static constexpr int fused = 3, central = 3, plain = 4; };
+
 __device__ inline void push_redo(const FitArgs& a, int64_t i)
 {
     unsigned long long pos = atomicAdd(const_cast<unsigned long long*>(a.list_len), 1ull);
@@ -348,7 +354,7 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
 }
 
 template <typename T, int DIM, bool GATE>
-__global__ void __launch_bounds__(128) k_step(FitArgs a, StepOut o)
+__global__ void __launch_bounds__(128, FitOcc<T>::fused) k_step(FitArgs a, StepOut o)
 {
     if (a.list) {
         unsigned long long len = *a.list_len;
@@ -379,7 +385,7 @@ __device__ inline unsigned long long warp_append(unsigned long long* len, bool p
 }
 
 template <typename T, int DIM, bool GATE>
-__global__ void __launch_bounds__(128) k_step_central(FitArgs a, StepOut o)
+__global__ void __launch_bounds__(128, FitOcc<T>::central) k_step_central(FitArgs a, StepOut o)
 {
     constexpr int F = DIM + 2;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -415,7 +421,7 @@ __global__ void __launch_bounds__(128) k_step_central(FitArgs a, StepOut o)
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128) k_step_plain(FitArgs a, StepOut o)
+__global__ void __launch_bounds__(128, FitOcc<T>::plain) k_step_plain(FitArgs a, StepOut o)
 {
     constexpr int F = DIM + 2;
     const unsigned long long len = *a.plain_len;
