@@ -466,7 +466,8 @@ constexpr float TQ_GAP = 2.0f;        // in radii
 struct TileBuf {
     uint32_t kj[TQ_CAP][TQ_PAD];      // prefilter hits, one column per lane
     unsigned long long kc[TQ_KC];     // kept cells: start | count << 32
-    float4 cr[32];                    // staged candidates: relative position, index bits in w
+    float cx[32], cy[32], cz[32];     // staged candidates: position relative to the group's origin
+    uint32_t cj[32];                  // and index
     uint32_t cstart[32], cexcl[32];
 };
 
@@ -722,33 +723,58 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                     const uint32_t j = b.cstart[lo] + (t - b.cexcl[lo]);
                     const float4 ph = __ldg(a.pos4 + 2 * (int64_t)j);
                     const float4 pl = __ldg(a.pos4 + 2 * (int64_t)j + 1);
-                    float4 r;
-                    r.x = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
-                    r.y = DIM > 1 ? split_offset<PER>(c, 1, ph.y, pl.y, oh[1], ol[1]) : 0.0f;
-                    r.z = DIM > 2 ? split_offset<PER>(c, 2, ph.z, pl.z, oh[2], ol[2]) : 0.0f;
-                    r.w = __uint_as_float(j);
-                    b.cr[lane] = r;
+                    b.cx[lane] = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
+                    b.cy[lane] = DIM > 1 ? split_offset<PER>(c, 1, ph.y, pl.y, oh[1], ol[1]) : 0.0f;
+                    b.cz[lane] = DIM > 2 ? split_offset<PER>(c, 2, ph.z, pl.z, oh[2], ol[2]) : 0.0f;
+                    b.cj[lane] = j;
                 }
                 __syncwarp();
                 const int nb = (int)min(32u, T - base);
                 if (act) {
+                    // bit q: staged candidate q passes the prefilter
+                    uint32_t hits = 0;
+                    if (PER) {
 #pragma unroll 4
-                    for (int qq = 0; qq < nb; ++qq) {
-                        const float4 r = b.cr[qq];
-                        float d[3] = {r.x - ri[0], r.y - ri[1], r.z - ri[2]};
-                        if (PER) {
+                        for (int qq = 0; qq < nb; ++qq) {
+                            float d[3] = {b.cx[qq] - ri[0], b.cy[qq] - ri[1], b.cz[qq] - ri[2]};
 #pragma unroll
                             for (int k = 0; k < DIM; ++k)
                                 if (c.periodic[k]) {
                                     if (d[k] > halfL[k]) d[k] -= Lh[k];
                                     else if (d[k] < -halfL[k]) d[k] += Lh[k];
                                 }
+                            float d2 = d[0] * d[0];
+                            if (DIM > 1) d2 = fmaf(d[1], d[1], d2);
+                            if (DIM > 2) d2 = fmaf(d[2], d[2], d2);
+                            hits |= (d2 <= thr ? 1u : 0u) << qq;
                         }
-                        float d2 = d[0] * d[0];
-                        if (DIM > 1) d2 = fmaf(d[1], d[1], d2);
-                        if (DIM > 2) d2 = fmaf(d[2], d[2], d2);
-                        const uint32_t j = __float_as_uint(r.w);
-                        if (d2 <= thr && (int64_t)j != i) {
+                    } else {
+                        // two candidates per packed FP32 instruction (per component
+                        // the same rounding as the scalar form)
+                        const float2 nx = make_float2(-ri[0], -ri[0]);
+                        const float2 ny = make_float2(-ri[1], -ri[1]);
+                        const float2 nz = make_float2(-ri[2], -ri[2]);
+#pragma unroll 4
+                        for (int qq = 0; qq < nb; qq += 2) {
+                            const float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&b.cx[qq]), nx);
+                            float2 d2 = __fmul2_rn(dx, dx);
+                            if (DIM > 1) {
+                                const float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&b.cy[qq]), ny);
+                                d2 = __ffma2_rn(dy, dy, d2);
+                            }
+                            if (DIM > 2) {
+                                const float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&b.cz[qq]), nz);
+                                d2 = __ffma2_rn(dz, dz, d2);
+                            }
+                            hits |= ((d2.x <= thr ? 1u : 0u) | (d2.y <= thr ? 2u : 0u)) << qq;
+                        }
+                        if (nb < 32) hits &= (1u << nb) - 1u;   // the odd last slot holds no candidate
+                    }
+                    while (hits) {
+                        const int q = __ffs(hits) - 1;
+                        hits &= hits - 1;
+                        const uint32_t j = b.cj[q];
+                        if ((int64_t)j != i) {
                             if (cnt < (uint32_t)TQ_CAP) b.kj[cnt][lane] = j;
                             ++cnt;
                         }
