@@ -292,6 +292,7 @@ struct Src<float, DIM, F> {
         for (int f = 0; f < F; ++f)
             b[f] = (r.v[REC_FH + f] - ri[REC_FH + f]) + (r.v[REC_FL + f] - ri[REC_FL + f]);
     }
+    __device__ int side(const Rec& r, uint32_t j, int k) const { return side_rec(r.v, j, k); }
     // side of j along axis k; when non-zero, also its offsets and differences
     __device__ int unpack_side(const Rec& r, uint32_t j, int k, float (&d)[DIM], float (&b)[F]) const
     {
@@ -344,6 +345,11 @@ struct Src<double, DIM, F> {
 #pragma unroll
         for (int f = 0; f < F; ++f) b[f] = r.f[f] - fi[f];
     }
+    __device__ int side(const Rec& r, uint32_t, int k) const
+    {
+        const double dk = offset64(a.c, k, xi[k], r.x[k]);
+        return dk > 0.0 ? 1 : (dk < 0.0 ? -1 : 0);
+    }
     __device__ int unpack_side(const Rec& r, uint32_t, int k, double (&d)[DIM], double (&b)[F]) const
     {
         double dk = offset64(a.c, k, xi[k], r.x[k]);
@@ -387,7 +393,7 @@ __device__ inline float inv_scale(float d2)
 // 1 ill-conditioned (ratio below tau), with x untouched.
 template <typename T, int DIM, int F, bool STATS = false>
 __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau,
-                           bool refine, T (&x)[NU<DIM>::v][F], FitStats<T>* st = nullptr)
+                           const DevCfg& cf, T (&x)[NU<DIM>::v][F], FitStats<T>* st = nullptr)
 {
     constexpr int N = NU<DIM>::v;
     Givens<T, N, F> G;
@@ -411,8 +417,10 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
         return true;
     });
     if (STATS && st) { st->bmin = bmin; st->bmax = bmax; st->ssb = ssb; st->ssr = ssr; }
-    if (!(G.ratio() >= tau) || cnt < N) return 1;
+    const T ratio = G.ratio();
+    if (!(ratio >= tau) || cnt < N) return 1;
     G.solve(x);
+    const bool refine = cf.refine == LP_REFINE_ALWAYS || (cf.refine == LP_REFINE_AUTO && ratio < (T)cf.refine_ratio);
     if (refine) {
         T g[N][F];
 #pragma unroll
@@ -472,47 +480,75 @@ __device__ int linear_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt
     return 0;
 }
 
-// One-sided first derivatives along axis k (Sec. 2.1 left/right derivatives):
-// first k_side list members on each side, first-order fit, component k.
-// ok[s] = false where fewer than DIM members or rank deficient.  ill = true when
-// a system with enough members is below tau (FP32: redo in FP64).
+// One-sided first derivatives (Sec. 2.1 left/right derivatives): along each
+// axis k and on each side, the first k_side list members whose offset along k
+// has that sign; first-order fit; component k.  One pass over the list marks
+// the members of all 2 DIM stencils (bit r of m[k][s]: list position r), then
+// each fit takes exactly its rows in list order.  ok[k][s] = false where fewer
+// than DIM members or rank deficient.  ill = true when a system with enough
+// members is below tau (FP32: redo in FP64).
 template <typename T, int DIM, int F>
-__device__ void onesided_axis(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, int k, int ks, T invS,
-                              T tau, T tau_rank, T (&out)[2][F], bool (&ok)[2], bool& ill)
+__device__ void onesided_all(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, int ks, T invS, T tau,
+                             T tau_rank, T (&out)[DIM][2][F], bool (&ok)[DIM][2], bool& ill)
 {
-    Givens<T, DIM, F> G[2];
-    G[0].zero();
-    G[1].zero();
-    int ns[2] = {0, 0};
+    uint64_t m[DIM][2];
+    int c[DIM][2];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { m[k][0] = m[k][1] = 0ull; c[k][0] = c[k][1] = 0; }
     using Rec = typename Src<T, DIM, F>::Rec;
-    if (ks > 0)
+    if (ks > 0) {
+        int r = 0;
         for_neighbors(src, nb, cnt, [&](uint32_t j, const Rec& rec) {
-            T d[DIM], b[F];
-            int sg = src.unpack_side(rec, j, k, d, b);
-            if (sg != 0) {
-                int s = sg > 0 ? 1 : 0;
-                if (ns[s] < ks) {
+            bool more = false;
 #pragma unroll
-                    for (int q = 0; q < DIM; ++q) d[q] *= invS;
-                    if (s) G[1].add(d, b); else G[0].add(d, b);
-                    ++ns[s];
+            for (int k = 0; k < DIM; ++k) {
+                const int sg = src.side(rec, j, k);
+                if (sg > 0) {
+                    if (c[k][1] < ks) { m[k][1] |= 1ull << r; ++c[k][1]; }
+                } else if (sg < 0) {
+                    if (c[k][0] < ks) { m[k][0] |= 1ull << r; ++c[k][0]; }
                 }
+                more = more || c[k][0] < ks || c[k][1] < ks;
             }
-            return ns[0] < ks || ns[1] < ks;
+            ++r;
+            return more;
         });
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        ok[s] = false;
-        if (ns[s] < DIM) continue;
-        T rt = G[s].ratio();
-        if (!(rt >= tau_rank)) continue;              // rank deficient: central derivative
-        if (!(rt >= tau)) ill = true;                 // usable only in higher precision
-        T x[DIM][F];
-        G[s].solve(x);
-#pragma unroll
-        for (int f = 0; f < F; ++f) out[s][f] = x[k][f] * invS;
-        ok[s] = true;
     }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            ok[k][s] = false;
+            uint64_t mm = m[k][s];
+            if (__popcll(mm) < DIM) continue;
+            Givens<T, DIM, F> G;
+            G.zero();
+            // rows in list order, the next record in flight
+            Rec nxt;
+            uint32_t jn = __ldg(nb + (__ffsll((long long)mm) - 1));
+            src.load_rec(jn, nxt);
+            while (mm) {
+                mm &= mm - 1;
+                const Rec cur = nxt;
+                if (mm) {
+                    jn = __ldg(nb + (__ffsll((long long)mm) - 1));
+                    src.load_rec(jn, nxt);
+                }
+                T d[DIM], b[F];
+                src.unpack(cur, d, b);
+#pragma unroll
+                for (int q = 0; q < DIM; ++q) d[q] *= invS;
+                G.add(d, b);
+            }
+            const T rt = G.ratio();
+            if (!(rt >= tau_rank)) continue;              // rank deficient: central derivative
+            if (!(rt >= tau)) ill = true;                 // usable only in higher precision
+            T x[DIM][F];
+            G.solve(x);
+#pragma unroll
+            for (int f = 0; f < F; ++f) out[k][s][f] = x[k][f] * invS;
+            ok[k][s] = true;
+        }
 }
 
 // ---------------------------------------------------------------------------

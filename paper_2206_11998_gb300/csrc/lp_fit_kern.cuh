@@ -159,7 +159,7 @@ __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t 
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
     T cd[N][F];
     FitStats<T> fst = {T(0), T(0), T(0), T(0)};
-    if (central_fit<T, DIM, F, GATE>(src, nb, cnt, invS, tau, c.refine != 0, cd, &fst)) {
+    if (central_fit<T, DIM, F, GATE>(src, nb, cnt, invS, tau, c, cd, &fst)) {
         if (IsF32<T>::v) { push_redo(a, i); return false; }
         T lin[DIM][F];
 #pragma unroll
@@ -208,16 +208,15 @@ __device__ inline bool step_plain(const FitArgs& a, int64_t i, const Src<T, DIM,
     const DevCfg& c = a.c;
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
     bool ill = false;
+    T out[DIM][2][F];
+    bool ok[DIM][2];
+    onesided_all<T, DIM, F>(src, nb, cnt, c.k_side, invS, tau, (T)c.tau64, out, ok, ill);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        T out[2][F];
-        bool ok[2];
-        onesided_axis<T, DIM, F>(src, nb, cnt, k, c.k_side, invS, tau, (T)c.tau64, out, ok, ill);
+    for (int k = 0; k < DIM; ++k)
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int f = 0; f < F; ++f) os[k][s][f] = ok[s] ? out[s][f] : cdf[k][f];
-    }
+            for (int f = 0; f < F; ++f) os[k][s][f] = ok[k][s] ? out[k][s][f] : cdf[k][f];
     if (IsF32<T>::v && ill) { push_redo(a, i); return false; }
     return true;
 }
@@ -473,7 +472,7 @@ __device__ void derivs_one(const FitArgs& a, const DerivOut& o, int64_t i)
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
     T cd[N][F];
     uint32_t st = IsF32<T>::v ? 0u : (a.list ? FIT_FP64 : 0u);
-    if (central_fit<T, DIM, F>(src, nb, cnt, invS, tau, c.refine != 0, cd)) {
+    if (central_fit<T, DIM, F>(src, nb, cnt, invS, tau, c, cd)) {
         if (IsF32<T>::v) { push_redo(a, i); return; }
         st |= FIT_LINEAR;
 #pragma unroll
@@ -532,7 +531,7 @@ __device__ void onesided_one(const FitArgs& a, double* out, int f_real, int64_t 
     const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
     T cd[N][F];
-    if (central_fit<T, DIM, F>(src, nb, cnt, invS, tau, c.refine != 0, cd)) {
+    if (central_fit<T, DIM, F>(src, nb, cnt, invS, tau, c, cd)) {
         if (IsF32<T>::v) { push_redo(a, i); return; }
 #pragma unroll
         for (int u = 0; u < N; ++u)
@@ -548,15 +547,16 @@ __device__ void onesided_one(const FitArgs& a, double* out, int f_real, int64_t 
     }
     bool ill = false;
     T os[DIM][2][F];
+    {
+        T o2[DIM][2][F];
+        bool ok[DIM][2];
+        onesided_all<T, DIM, F>(src, nb, cnt, c.k_side, invS, tau, (T)c.tau64, o2, ok, ill);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        T o2[2][F];
-        bool ok[2];
-        onesided_axis<T, DIM, F>(src, nb, cnt, k, c.k_side, invS, tau, (T)c.tau64, o2, ok, ill);
+        for (int k = 0; k < DIM; ++k)
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+            for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int f = 0; f < F; ++f) os[k][s][f] = ok[s] ? o2[s][f] : cd[k][f];
+                for (int f = 0; f < F; ++f) os[k][s][f] = ok[k][s] ? o2[k][s][f] : cd[k][f];
     }
     if (IsF32<T>::v && ill) { push_redo(a, i); return; }
 #pragma unroll

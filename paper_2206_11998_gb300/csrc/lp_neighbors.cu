@@ -459,7 +459,7 @@ constexpr int TQ_WARPS = 4;
 constexpr int TQ_CAP = KMAX;          // prefilter hits a lane keeps
 constexpr int TQ_PAD = 33;            // column stride: a row read across lanes is conflict-free
 constexpr int TQ_CELLS_MAX = 4096;    // cells a group's region may span
-constexpr uint32_t TQ_CAND_MAX = 4096;   // candidates a group may test
+constexpr uint32_t TQ_CAND_MAX = 2048;   // candidates a group may test (fastest of 2048, 4096, 8192 on the gas cloud)
 constexpr int TQ_KC = 256;            // non-empty cells a group may keep
 constexpr float TQ_GAP = 2.0f;        // in radii
 

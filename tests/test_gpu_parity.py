@@ -179,13 +179,14 @@ def test_capacity_and_state_errors():
 # GFD derivatives (config-2 shape at reduced size)
 # ---------------------------------------------------------------------------
 
-def _deriv_case(prec, noise, nf, n_side=22):
+def _deriv_case(prec, noise, nf, n_side=22, refine=lp.REFINE_ALWAYS):
     h = 1.0 / n_side
     x, fields, coeffs = inputs.gfd_lattice_workload(n_side, h, noise, nfields=nf)
     n = x[0].shape[0]
     st = {"x": x, "V": np.ones(n), "u": [np.zeros(n)] * 3, "P": np.ones(n), "m": np.ones(n),
           "id": np.arange(n, dtype=np.uint32), "n_fluid": n}
-    cfg = lp.make_config(3, n, precision=prec, radius_mode=lp.RADIUS_FIXED, radius=2.2 * h, k_max=64)
+    cfg = lp.make_config(3, n, precision=prec, radius_mode=lp.RADIUS_FIXED, radius=2.2 * h, k_max=64,
+                         refine=refine)
     ctx = lp.Context(cfg)
     ps = lp.ParticleSet.from_state(st)
     ctx.build_neighbors(ps)
@@ -228,6 +229,19 @@ def test_gfd_derivs_fp32_matches_oracle(nf):
         e2 = max(normwise(gd[f][:, u], od[f][:, u]) for u in range(3, 9))
         assert e1 < FP32_GRAD_TOL, (f, e1)
         assert e2 < FP32_HESS_TOL, (f, e2)
+
+
+def test_refinement_step_buys_fp32_accuracy():
+    """The refinement step of the central fit (on by default) is what brings the
+    FP32 gradients inside the 1e-5 bound; without it (NEVER) and when only
+    ill-conditioned stencils are refined (AUTO) the error is larger but bounded."""
+    errs = {}
+    for mode in (lp.REFINE_ALWAYS, lp.REFINE_AUTO, lp.REFINE_NEVER):
+        gd, od, _, _ = _deriv_case(lp.PREC_FP32, 1e-6, 1, refine=mode)
+        errs[mode] = max(normwise(gd[0][:, u], od[0][:, u]) for u in range(3))
+    assert errs[lp.REFINE_ALWAYS] < FP32_GRAD_TOL
+    assert errs[lp.REFINE_ALWAYS] < errs[lp.REFINE_AUTO] <= errs[lp.REFINE_NEVER] < 1e-2, errs
+    assert errs[lp.REFINE_NEVER] > 10 * errs[lp.REFINE_ALWAYS], errs
 
 
 def test_gfd_derivs_fp32_noise_free_vs_analytic():
