@@ -84,24 +84,23 @@ struct Givens {
             const T ak = a[k];
             const T wa = O::mul(w, ak);
             const T dn = O::fma(wa, ak, d[k]);
-            // a row absorbed by an empty column keeps weight 0: nothing left to rotate
-            if (wa != T(0) && dn > T(0)) {
-                const T inv = O::rcp(dn);
-                const T sk = O::mul(wa, inv);
-                w = O::mul(O::mul(w, d[k]), inv);
-                d[k] = dn;
+            // a row absorbed by an empty column keeps weight 0 (live = false: no change)
+            const bool live = wa != T(0) && dn > T(0);
+            const T inv = live ? O::rcp(dn) : T(0);
+            const T sk = O::mul(wa, inv);
+            w = live ? O::mul(O::mul(w, d[k]), inv) : w;
+            d[k] = live ? dn : d[k];
 #pragma unroll
-                for (int l = k + 1; l < N; ++l) {
-                    const T t = O::fma(-ak, U[id(k, l)], a[l]);
-                    U[id(k, l)] = O::fma(sk, t, U[id(k, l)]);
-                    a[l] = t;
-                }
+            for (int l = k + 1; l < N; ++l) {
+                const T t = O::fma(-ak, U[id(k, l)], a[l]);
+                U[id(k, l)] = O::fma(sk, t, U[id(k, l)]);
+                a[l] = t;
+            }
 #pragma unroll
-                for (int f = 0; f < F; ++f) {
-                    const T t = O::fma(-ak, Z[k][f], b[f]);
-                    Z[k][f] = O::fma(sk, t, Z[k][f]);
-                    b[f] = t;
-                }
+            for (int f = 0; f < F; ++f) {
+                const T t = O::fma(-ak, Z[k][f], b[f]);
+                Z[k][f] = O::fma(sk, t, Z[k][f]);
+                b[f] = t;
             }
         }
         return w;

@@ -656,20 +656,30 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
             cn = ce > cs ? ce - cs : 0;
         }
     };
-    // ---- 1. the group's candidate count; a dense region under a wide group
-    // is cheaper per particle
+    // ---- 1. the group's candidate count (a dense region under a wide group is
+    // cheaper per particle) and, while they fit, its non-empty cells compacted
+    const unsigned lt = (1u << lane) - 1u;
+    int nk = 0;                       // compacted cells in b.kc
+    bool spill = false;               // more non-empty cells than b.kc holds
     {
         uint32_t ncand = 0;
         for (int base0 = 0; base0 < nct && ncand <= TQ_CAND_MAX; base0 += 32) {
             uint32_t cs, cn;
             cell_range(base0 + (int)lane, cs, cn);
             ncand += __reduce_add_sync(0xffffffffu, cn);
+            const unsigned km = __ballot_sync(0xffffffffu, cn > 0);
+            if (!spill && nk + __popc(km) > TQ_KC) spill = true;
+            if (!spill) {
+                if (cn > 0) b.kc[nk + __popc(km & lt)] = (unsigned long long)cs | ((unsigned long long)cn << 32);
+                nk += __popc(km);
+            }
         }
         if (ncand > TQ_CAND_MAX) {
             list_append(a, act, (uint32_t)i);
             return;
         }
     }
+    __syncwarp();
 
     // ---- 2. prefilter: candidates relative to the group's first particle
     const int lead = __ffs(__ballot_sync(0xffffffffu, act)) - 1;
@@ -784,11 +794,12 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
             }
         }
     };
-    // classify again, compacting the non-empty cells; scan whenever the
-    // buffer of kept cells would overflow, and at the end
-    {
-        const unsigned lt = (1u << lane) - 1u;
-        int nk = 0;
+    if (!spill) {
+        scan_kept(nk);                // every kept cell is already in b.kc
+    } else {
+        // classify again, compacting the non-empty cells; scan whenever the
+        // buffer of kept cells would overflow, and at the end
+        nk = 0;
         for (int base0 = 0; base0 < nct; base0 += 32) {
             uint32_t cs, cn;
             cell_range(base0 + (int)lane, cs, cn);
