@@ -236,9 +236,11 @@ struct Src<float, DIM, F> {
     {
         const float4* p = a.rec + j * REC_F4;
 #pragma unroll
-        for (int q = 0; q < REC_F4; ++q) {
-            float4 v = __ldg(p + q);
+        for (int q = 0; q < REC_F4; q += 2) {
+            float4 v, w;
+            ldg256(p + q, v, w);
             r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+            r[4 * q + 4] = w.x; r[4 * q + 5] = w.y; r[4 * q + 6] = w.z; r[4 * q + 7] = w.w;
         }
     }
     __device__ void off_rec(const float (&r)[4 * REC_F4], float (&d)[DIM]) const

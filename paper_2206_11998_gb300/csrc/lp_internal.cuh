@@ -162,6 +162,17 @@ __device__ inline void split(double x, float& h, float& l)
     l = __double2float_rn(__dsub_rn(x, (double)h));
 }
 
+// 32 bytes (two float4) from a 32-byte-aligned global address that the kernel
+// only reads, as one 256-bit load: a lane gathering a record from a random
+// address costs the L1 one wavefront per load instruction, so one wide load
+// instead of two halves that cost
+__device__ __forceinline__ void ldg256(const float4* p, float4& lo, float4& hi)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+        : "l"(p));
+}
+
 // ---------------------------------------------------------------------------
 // warp helpers
 // ---------------------------------------------------------------------------

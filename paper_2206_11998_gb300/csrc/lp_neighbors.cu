@@ -367,7 +367,8 @@ __device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
                     j = b.cstart[lo] + (t - b.cexcl[lo]);
                     bool count_only = (co >> lo) & 1u;
                     if ((int64_t)j != i) {
-                        float4 ph = __ldg(a.pos4 + 2 * (int64_t)j), pl = __ldg(a.pos4 + 2 * (int64_t)j + 1);
+                        float4 ph, pl;
+                        ldg256(a.pos4 + 2 * (int64_t)j, ph, pl);
                         float hj[3] = {ph.x, ph.y, ph.z}, lj[3] = {pl.x, pl.y, pl.z};
 #pragma unroll
                         for (int k = 0; k < DIM; ++k) {
@@ -731,8 +732,8 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                         if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
                     }
                     const uint32_t j = b.cstart[lo] + (t - b.cexcl[lo]);
-                    const float4 ph = __ldg(a.pos4 + 2 * (int64_t)j);
-                    const float4 pl = __ldg(a.pos4 + 2 * (int64_t)j + 1);
+                    float4 ph, pl;
+                    ldg256(a.pos4 + 2 * (int64_t)j, ph, pl);
                     b.cx[lane] = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
                     b.cy[lane] = DIM > 1 ? split_offset<PER>(c, 1, ph.y, pl.y, oh[1], ol[1]) : 0.0f;
                     b.cz[lane] = DIM > 2 ? split_offset<PER>(c, 2, ph.z, pl.z, oh[2], ol[2]) : 0.0f;
@@ -831,8 +832,7 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
             const int e = (int)lane + 32 * s;
             if (e < m) {
                 fj[s] = b.kj[e][p];
-                fh[s] = __ldg(a.pos4 + 2 * (int64_t)fj[s]);
-                fl[s] = __ldg(a.pos4 + 2 * (int64_t)fj[s] + 1);
+                ldg256(a.pos4 + 2 * (int64_t)fj[s], fh[s], fl[s]);
             }
         }
     };
