@@ -20,6 +20,10 @@ namespace lp {
 
 template <int DIM> struct NU { static constexpr int v = DIM == 1 ? 2 : (DIM == 2 ? 5 : 9); };
 
+// threads per block of every fit kernel (the FP32 correction pass keeps one
+// shared-memory column per thread)
+constexpr int FIT_THREADS = 128;
+
 // Explicit round-to-nearest operations.  The fit and rate arithmetic is inlined
 // into more than one kernel (fused and split schedules, the FP64 redo); with
 // explicit operations the compiler cannot contract a*b + c into an FMA in one
@@ -423,6 +427,18 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
     G.solve(x);
     const bool refine = cf.refine == LP_REFINE_ALWAYS || (cf.refine == LP_REFINE_AUTO && ratio < (T)cf.refine_ratio);
     if (refine) {
+        // The FP32 3D factor (d and U, 45 values) waits in shared memory during
+        // the correction pass, which holds the solution and the correction sums:
+        // without that the pass spills.
+        constexpr bool STASH = sizeof(T) == 4 && DIM == 3;
+        constexpr int NS = N + N * (N - 1) / 2;
+        __shared__ T stash[STASH ? NS : 1][FIT_THREADS];
+        if (STASH) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) stash[k][threadIdx.x] = G.d[k];
+#pragma unroll
+            for (int q = 0; q < N * (N - 1) / 2; ++q) stash[N + q][threadIdx.x] = G.U[q];
+        }
         T g[N][F];
 #pragma unroll
         for (int u = 0; u < N; ++u)
@@ -444,6 +460,13 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
             }
             return true;
         });
+        if (STASH) {
+            volatile T* sv = &stash[0][0];      // volatile: reloaded, not kept live
+#pragma unroll
+            for (int k = 0; k < N; ++k) G.d[k] = sv[k * FIT_THREADS + threadIdx.x];
+#pragma unroll
+            for (int q = 0; q < N * (N - 1) / 2; ++q) G.U[q] = sv[(N + q) * FIT_THREADS + threadIdx.x];
+        }
         G.solve_normal(g);
 #pragma unroll
         for (int u = 0; u < N; ++u)

@@ -23,9 +23,10 @@ struct StepOut {
 template <typename T> struct IsF32 { static constexpr bool v = false; };
 template <> struct IsF32<float> { static constexpr bool v = true; };
 
-// resident 128-thread blocks per SM the FP32 step kernels are compiled for
-// (measured on the 2M-particle cloud: 3/4 blocks with a few spilled registers
-// beat 2/3 blocks without spills by 7%); the FP64 kernels keep the default
+// resident blocks per SM the FP32 step kernels are compiled for (measured on
+// the 2M-particle cloud: the central kernel at 3 blocks, 168 registers, runs 5%
+// faster than at 2 and 30% faster than at 4, where it spills; the plain kernel
+// at 4 beats 3); the FP64 kernels keep the default
 template <typename T> struct FitOcc { static constexpr int fused = 1, central = 1, plain = 1; };
 template <> struct FitOcc<float> { static constexpr int fused = 3, central = 3, plain = 4; };
 
@@ -353,7 +354,7 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
 }
 
 template <typename T, int DIM, bool GATE>
-__global__ void __launch_bounds__(128, FitOcc<T>::fused) k_step(FitArgs a, StepOut o)
+__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::fused) k_step(FitArgs a, StepOut o)
 {
     if (a.list) {
         unsigned long long len = *a.list_len;
@@ -384,7 +385,7 @@ __device__ inline unsigned long long warp_append(unsigned long long* len, bool p
 }
 
 template <typename T, int DIM, bool GATE>
-__global__ void __launch_bounds__(128, FitOcc<T>::central) k_step_central(FitArgs a, StepOut o)
+__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_central(FitArgs a, StepOut o)
 {
     constexpr int F = DIM + 2;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(128, FitOcc<T>::central) k_step_central(FitArg
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128, FitOcc<T>::plain) k_step_plain(FitArgs a, StepOut o)
+__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain(FitArgs a, StepOut o)
 {
     constexpr int F = DIM + 2;
     const unsigned long long len = *a.plain_len;
@@ -504,7 +505,7 @@ __device__ void derivs_one(const FitArgs& a, const DerivOut& o, int64_t i)
 }
 
 template <typename T, int DIM, int F>
-__global__ void __launch_bounds__(128) k_derivs(FitArgs a, DerivOut o)
+__global__ void __launch_bounds__(FIT_THREADS) k_derivs(FitArgs a, DerivOut o)
 {
     if (a.list) {
         unsigned long long len = *a.list_len;
@@ -569,7 +570,7 @@ __device__ void onesided_one(const FitArgs& a, double* out, int f_real, int64_t 
 }
 
 template <typename T, int DIM, int F>
-__global__ void __launch_bounds__(128) k_onesided(FitArgs a, double* out, int f_real)
+__global__ void __launch_bounds__(FIT_THREADS) k_onesided(FitArgs a, double* out, int f_real)
 {
     if (a.list) {
         unsigned long long len = *a.list_len;
@@ -594,7 +595,7 @@ cudaError_t launch_onesided_f64(int dim, const FitArgs& a, double* out, int f_re
 
 inline unsigned fit_blocks(const FitArgs& a)
 {
-    return a.list ? 152u * 4u : (unsigned)((a.n + 127) / 128);
+    return a.list ? 152u * 4u : (unsigned)((a.n + FIT_THREADS - 1) / FIT_THREADS);
 }
 
 #define LP_DEFINE_FIT_LAUNCHERS(T, SUF)                                                         \
@@ -604,35 +605,35 @@ inline unsigned fit_blocks(const FitArgs& a)
         if (b == 0) return cudaSuccess;                                                         \
         const bool gate = o.features || a.c.estimator == LP_EST_MLP;                           \
         if (dim == 3) {                                                                         \
-            if (gate) k_step<T, 3, true><<<b, 128, 0, s>>>(a, o);                               \
-            else k_step<T, 3, false><<<b, 128, 0, s>>>(a, o);                                   \
+            if (gate) k_step<T, 3, true><<<b, FIT_THREADS, 0, s>>>(a, o);                               \
+            else k_step<T, 3, false><<<b, FIT_THREADS, 0, s>>>(a, o);                                   \
         } else if (dim == 2) {                                                                  \
-            if (gate) k_step<T, 2, true><<<b, 128, 0, s>>>(a, o);                               \
-            else k_step<T, 2, false><<<b, 128, 0, s>>>(a, o);                                   \
+            if (gate) k_step<T, 2, true><<<b, FIT_THREADS, 0, s>>>(a, o);                               \
+            else k_step<T, 2, false><<<b, FIT_THREADS, 0, s>>>(a, o);                                   \
         } else {                                                                                \
-            if (gate) k_step<T, 1, true><<<b, 128, 0, s>>>(a, o);                               \
-            else k_step<T, 1, false><<<b, 128, 0, s>>>(a, o);                                   \
+            if (gate) k_step<T, 1, true><<<b, FIT_THREADS, 0, s>>>(a, o);                               \
+            else k_step<T, 1, false><<<b, FIT_THREADS, 0, s>>>(a, o);                                   \
         }                                                                                       \
         return cudaGetLastError();                                                              \
     }                                                                                           \
     cudaError_t launch_step_split_##SUF(int dim, const FitArgs& a, const StepOut& o,            \
                                         cudaStream_t s)                                         \
     {                                                                                           \
-        unsigned b = (unsigned)((a.n + 127) / 128);                                             \
+        unsigned b = (unsigned)((a.n + FIT_THREADS - 1) / FIT_THREADS);                                             \
         if (b == 0) return cudaSuccess;                                                         \
         const bool gate = o.features || a.c.estimator == LP_EST_MLP;                           \
         if (dim == 3) {                                                                         \
-            if (gate) k_step_central<T, 3, true><<<b, 128, 0, s>>>(a, o);                       \
-            else k_step_central<T, 3, false><<<b, 128, 0, s>>>(a, o);                           \
-            k_step_plain<T, 3><<<b, 128, 0, s>>>(a, o);                                         \
+            if (gate) k_step_central<T, 3, true><<<b, FIT_THREADS, 0, s>>>(a, o);                       \
+            else k_step_central<T, 3, false><<<b, FIT_THREADS, 0, s>>>(a, o);                           \
+            k_step_plain<T, 3><<<b, FIT_THREADS, 0, s>>>(a, o);                                         \
         } else if (dim == 2) {                                                                  \
-            if (gate) k_step_central<T, 2, true><<<b, 128, 0, s>>>(a, o);                       \
-            else k_step_central<T, 2, false><<<b, 128, 0, s>>>(a, o);                           \
-            k_step_plain<T, 2><<<b, 128, 0, s>>>(a, o);                                         \
+            if (gate) k_step_central<T, 2, true><<<b, FIT_THREADS, 0, s>>>(a, o);                       \
+            else k_step_central<T, 2, false><<<b, FIT_THREADS, 0, s>>>(a, o);                           \
+            k_step_plain<T, 2><<<b, FIT_THREADS, 0, s>>>(a, o);                                         \
         } else {                                                                                \
-            if (gate) k_step_central<T, 1, true><<<b, 128, 0, s>>>(a, o);                       \
-            else k_step_central<T, 1, false><<<b, 128, 0, s>>>(a, o);                           \
-            k_step_plain<T, 1><<<b, 128, 0, s>>>(a, o);                                         \
+            if (gate) k_step_central<T, 1, true><<<b, FIT_THREADS, 0, s>>>(a, o);                       \
+            else k_step_central<T, 1, false><<<b, FIT_THREADS, 0, s>>>(a, o);                           \
+            k_step_plain<T, 1><<<b, FIT_THREADS, 0, s>>>(a, o);                                         \
         }                                                                                       \
         return cudaGetLastError();                                                              \
     }                                                                                           \
@@ -641,10 +642,10 @@ inline unsigned fit_blocks(const FitArgs& a)
     {                                                                                           \
         unsigned b = fit_blocks(a);                                                             \
         if (b == 0) return cudaSuccess;                                                         \
-        if (dim == 3 && F == 1) k_derivs<T, 3, 1><<<b, 128, 0, s>>>(a, o);                     \
-        else if (dim == 3) k_derivs<T, 3, 5><<<b, 128, 0, s>>>(a, o);                          \
-        else if (dim == 2) k_derivs<T, 2, 5><<<b, 128, 0, s>>>(a, o);                          \
-        else k_derivs<T, 1, 5><<<b, 128, 0, s>>>(a, o);                                        \
+        if (dim == 3 && F == 1) k_derivs<T, 3, 1><<<b, FIT_THREADS, 0, s>>>(a, o);                     \
+        else if (dim == 3) k_derivs<T, 3, 5><<<b, FIT_THREADS, 0, s>>>(a, o);                          \
+        else if (dim == 2) k_derivs<T, 2, 5><<<b, FIT_THREADS, 0, s>>>(a, o);                          \
+        else k_derivs<T, 1, 5><<<b, FIT_THREADS, 0, s>>>(a, o);                                        \
         return cudaGetLastError();                                                              \
     }                                                                                           \
     cudaError_t launch_onesided_##SUF(int dim, const FitArgs& a, double* out, int f_real,       \
@@ -652,9 +653,9 @@ inline unsigned fit_blocks(const FitArgs& a)
     {                                                                                           \
         unsigned b = fit_blocks(a);                                                             \
         if (b == 0) return cudaSuccess;                                                         \
-        if (dim == 3) k_onesided<T, 3, 5><<<b, 128, 0, s>>>(a, out, f_real);                   \
-        else if (dim == 2) k_onesided<T, 2, 5><<<b, 128, 0, s>>>(a, out, f_real);              \
-        else k_onesided<T, 1, 5><<<b, 128, 0, s>>>(a, out, f_real);                            \
+        if (dim == 3) k_onesided<T, 3, 5><<<b, FIT_THREADS, 0, s>>>(a, out, f_real);                   \
+        else if (dim == 2) k_onesided<T, 2, 5><<<b, FIT_THREADS, 0, s>>>(a, out, f_real);              \
+        else k_onesided<T, 1, 5><<<b, FIT_THREADS, 0, s>>>(a, out, f_real);                            \
         return cudaGetLastError();                                                              \
     }
 
