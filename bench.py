@@ -57,7 +57,10 @@ def fit_flops_per_particle(m: float) -> float:
 # DRAM bytes per particle of one fit pass (split schedule, FP32), measured by ncu
 # on the 400k-particle cloud for the kernels as they are now; None when the
 # kernels change and the figure has not been re-measured
-FIT_TRAFFIC_BPP = 966.0
+FIT_TRAFFIC_BPP = 942.0
+
+# nominal FP64 rate of a GB300 (TFLOP/s): the roofline of the FP64 fit
+FP64_PEAK_TFLOPS = 1.25
 
 # algorithmic DRAM bytes per particle of the memory-bound phases
 BYTES_PER_PARTICLE = {
@@ -272,12 +275,15 @@ def run_ours(args):
         sampler.start()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         wall0 = time.perf_counter()
+        marked = nvtx_push("timed_steps", torch)      # lets ncu list the timed launches alone
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
             ctx.step(ps, dt=0.0, cfl=CFL, t=t_dev, stream=stream)
             ev[k][1].record(stream)
         stream.synchronize()
+        if marked:
+            torch.cuda.nvtx.range_pop()
         wall = time.perf_counter() - wall0
         barrier()
         clocks = sampler.stop()
@@ -327,9 +333,15 @@ def run_ours(args):
     traffic = None
     if args.precision == "fp32" and args.estimator == "plain" and sched & lp.SCHED_SPLIT and FIT_TRAFFIC_BPP:
         traffic = FIT_TRAFFIC_BPP * n
+    if args.precision == "fp32":
+        alu_peak = fp32_peak
+        alu_source = "FP32 CUDA cores: 152 SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (sm_max, peak_kind)
+    else:
+        alu_peak = FP64_PEAK_TFLOPS
+        alu_source = "nominal GB300 FP64 rate (the FP64 fit runs on the FP64 units)"
     roofline = {"kernel": fit_kernels + " (fit+update pass)", "dominant_phase": dominant, "bound": "alu",
-                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (sm_max, peak_kind),
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "peak_source": alu_source,
                 "flops_per_particle": fit_flops_per_particle(m_mean), "mean_neighbors": m_mean,
                 "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the fit kernels on the "
@@ -415,6 +427,14 @@ def audit_gate(lp, inputs, ps, n, cfg, params, stream, torch):
     cfg.mlp_audit = 0
     return {"audit_skipped": st["n_mlp_skip"], "audit_missed_flags": st["n_mlp_miss"],
             "audit_flagged": st["n_flagged"]}
+
+
+def nvtx_push(name, torch):
+    try:
+        torch.cuda.nvtx.range_push(name)
+        return True
+    except Exception:
+        return False
 
 
 def run_e2e(ctx, state, n, args, stream, lp, torch, flush):
