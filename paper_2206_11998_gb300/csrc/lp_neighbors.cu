@@ -703,6 +703,23 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
     float halfL[3], Lh[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) { Lh[k] = c.Lper_h[k]; halfL[k] = 0.5f * c.Lper_h[k]; }
+    // the group's box in the relative coordinates, and a bound on a candidate's
+    // squared distance to it above every lane's threshold (the distance to the
+    // box is at most the distance to any lane's particle; the margin covers the
+    // rounding of both): candidates beyond it are not staged (open domains;
+    // the minimum image of a periodic axis has no such box)
+    float rlo[3] = {0.0f, 0.0f, 0.0f}, rhi[3] = {0.0f, 0.0f, 0.0f};
+    float thr_box = INFINITY;
+    if (!PER) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            rlo[k] = warp_minf(act ? ri[k] : INFINITY);
+            rhi[k] = warp_maxf(act ? ri[k] : -INFINITY);
+        }
+        const float thm = warp_maxf(act ? thr : 0.0f);
+        const float Rm = warp_maxf(act ? me.Rf : 0.0f);
+        thr_box = thm + ldexpf(thm + 4.0f * E * Rm, -18);
+    }
     uint32_t cnt = 0;                 // prefilter hits of this lane
     // candidates of the compacted cells b.kc[0..nk), 32 cells at a time
     auto scan_kept = [&](int nk) {
@@ -725,23 +742,41 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
             __syncwarp();
             for (uint32_t base = 0; base < T; base += 32) {
                 const uint32_t t = base + lane;
+                bool keep = false;
+                float p[3] = {0.0f, 0.0f, 0.0f};
+                uint32_t j = 0;
                 if (t < T) {
                     int lo = 0, hi = 31;                  // the last cell with cexcl <= t
                     while (lo < hi) {
                         int mid = (lo + hi + 1) >> 1;
                         if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
                     }
-                    const uint32_t j = b.cstart[lo] + (t - b.cexcl[lo]);
+                    j = b.cstart[lo] + (t - b.cexcl[lo]);
                     float4 ph, pl;
                     ldg256(a.pos4 + 2 * (int64_t)j, ph, pl);
-                    b.cx[lane] = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
-                    b.cy[lane] = DIM > 1 ? split_offset<PER>(c, 1, ph.y, pl.y, oh[1], ol[1]) : 0.0f;
-                    b.cz[lane] = DIM > 2 ? split_offset<PER>(c, 2, ph.z, pl.z, oh[2], ol[2]) : 0.0f;
-                    b.cj[lane] = j;
+                    p[0] = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
+                    if (DIM > 1) p[1] = split_offset<PER>(c, 1, ph.y, pl.y, oh[1], ol[1]);
+                    if (DIM > 2) p[2] = split_offset<PER>(c, 2, ph.z, pl.z, oh[2], ol[2]);
+                    float d2b = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) {
+                        const float dk = fmaxf(0.0f, fmaxf(rlo[k] - p[k], p[k] - rhi[k]));
+                        d2b = fmaf(dk, dk, d2b);
+                    }
+                    keep = PER || d2b <= thr_box;
+                }
+                // the kept candidates, compacted
+                const unsigned km = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int sl = __popc(km & lt);
+                    b.cx[sl] = p[0];
+                    b.cy[sl] = p[1];
+                    b.cz[sl] = p[2];
+                    b.cj[sl] = j;
                 }
                 __syncwarp();
-                const int nb = (int)min(32u, T - base);
-                if (act) {
+                const int nb = __popc(km);
+                if (act && nb > 0) {
                     // bit q: staged candidate q passes the prefilter
                     uint32_t hits = 0;
                     if (PER) {
