@@ -170,6 +170,70 @@ struct Givens {
     }
 };
 
+// Normal equations of the same least-squares problem, accumulated row by row:
+// the Gram matrix A^T A (upper triangle) and A^T B -- one FMA per element and
+// row, against two for a rotation.  factor() turns the Gram matrix into the
+// form the Givens factor has (A^T A = U^T D U, U unit upper triangular), so
+// the ratio, the semi-normal solves and the correction pass are shared; the
+// factor it gives is R^T R of the same R up to rounding, accurate to about
+// cond(A)^2 u relative, which the correction pass then removes.
+template <typename T, int N, int F>
+struct NormalEq {
+    T Gm[N * (N + 1) / 2];      // upper triangle of A^T A, row by row
+    T c[N][F];                  // A^T B
+
+    __device__ static constexpr int id(int k, int l) { return k * N - (k * (k - 1)) / 2 + (l - k); }
+
+    __device__ void zero()
+    {
+#pragma unroll
+        for (int q = 0; q < N * (N + 1) / 2; ++q) Gm[q] = T(0);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+#pragma unroll
+            for (int f = 0; f < F; ++f) c[k][f] = T(0);
+    }
+
+    __device__ void add(const T (&a)[N], const T (&b)[F])
+    {
+        using O = RN<T>;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+#pragma unroll
+            for (int l = k; l < N; ++l) Gm[id(k, l)] = O::fma(a[k], a[l], Gm[id(k, l)]);
+#pragma unroll
+            for (int f = 0; f < F; ++f) c[k][f] = O::fma(a[k], b[f], c[k][f]);
+        }
+    }
+
+    // A^T A = U^T D U by rows (square-root-free Cholesky); a pivot that is not
+    // positive leaves d_k = 0, which the ratio test then rejects
+    template <int NF>
+    __device__ void factor(Givens<T, N, NF>& G)
+    {
+        using O = RN<T>;
+        T inv[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            // row k of D U: Gm[k][l] - sum_{j<k} U_jk (D U)_jl, with U_jk = (D U)_jk / d_j
+#pragma unroll
+            for (int j = 0; j < k; ++j) {
+                const T ujk = O::mul(Gm[id(j, k)], inv[j]);
+#pragma unroll
+                for (int l = k; l < N; ++l) Gm[id(k, l)] = O::fma(-ujk, Gm[id(j, l)], Gm[id(k, l)]);
+            }
+            const T dk = Gm[id(k, k)];
+            const bool pos = dk > T(0);
+            G.d[k] = pos ? dk : T(0);
+            inv[k] = pos ? O::rcp(dk) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+#pragma unroll
+            for (int l = k + 1; l < N; ++l) G.U[Givens<T, N, NF>::id(k, l)] = O::mul(Gm[id(k, l)], inv[k]);
+    }
+};
+
 // GFD row for scaled offset e (Eq. linear_system_axb order, 1D/3D analogues)
 template <typename T, int DIM>
 __device__ inline void gfd_row(const T (&e)[DIM], T (&a)[NU<DIM>::v])
@@ -394,39 +458,94 @@ __device__ inline float inv_scale(float d2)
     return ldexpf(1.0f, -e);
 }
 
+// Below this ratio the FP32 fit factors the rows by rotations instead of
+// through the normal equations: there cond(A)^2 u is no longer small enough
+// for one correction pass to remove the error of the Gram matrix.
+constexpr float NE_RATIO_MIN = 0.02f;
+
 // Central second-order fit.  x[u][f] unscaled derivatives.  Returns 0 ok,
 // 1 ill-conditioned (ratio below tau), with x untouched.
+//
+// FP32: the normal equations, factored as U^T D U, then one correction pass
+// (semi-normal equations with the residual of the first solution); when the
+// factor's ratio is below NE_RATIO_MIN, the rows again through square-root-
+// free Givens rotations (the FP64 path's only form).  The correction pass runs
+// in the modes that ask for it, and for the gate's residual sum when the
+// rotations did not give it.
 template <typename T, int DIM, int F, bool STATS = false>
 __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau,
                            const DevCfg& cf, T (&x)[NU<DIM>::v][F], FitStats<T>* st = nullptr)
 {
     constexpr int N = NU<DIM>::v;
+    constexpr bool NE = sizeof(T) == 4;
     Givens<T, N, F> G;
-    G.zero();
     T bmin = T(0), bmax = T(0), ssb = T(0), ssr = T(0);
+    bool have_ssr = false;            // ssr already holds the residual sum
+    bool solved = false;
+    T ratio = T(0);
     using Rec = typename Src<T, DIM, F>::Rec;
-    for_neighbors(src, nb, cnt, [&](uint32_t, const Rec& rec) {
-        T d[DIM], a[N], b[F];
-        src.unpack(rec, d, b);
+    if (NE) {
+        NormalEq<T, N, F> E;
+        E.zero();
+        for_neighbors(src, nb, cnt, [&](uint32_t, const Rec& rec) {
+            T d[DIM], a[N], b[F];
+            src.unpack(rec, d, b);
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) d[k] *= invS;
-        gfd_row<T, DIM>(d, a);
-        if (STATS) {
-            T bl = b[F - 1];
-            bmin = bl < bmin ? bl : bmin;
-            bmax = bl > bmax ? bl : bmax;
-            ssb = RN<T>::fma(bl, bl, ssb);
+            for (int k = 0; k < DIM; ++k) d[k] *= invS;
+            gfd_row<T, DIM>(d, a);
+            if (STATS) {
+                T bl = b[F - 1];
+                bmin = bl < bmin ? bl : bmin;
+                bmax = bl > bmax ? bl : bmax;
+                ssb = RN<T>::fma(bl, bl, ssb);
+            }
+            E.add(a, b);
+            return true;
+        });
+        E.factor(G);
+        ratio = G.ratio();
+        if (ratio >= T(NE_RATIO_MIN)) {
+            if (!(ratio >= tau) || cnt < N) {
+                if (STATS && st) { st->bmin = bmin; st->bmax = bmax; st->ssb = ssb; st->ssr = T(0); }
+                return 1;
+            }
+#pragma unroll
+            for (int u = 0; u < N; ++u)
+#pragma unroll
+                for (int f = 0; f < F; ++f) x[u][f] = E.c[u][f];
+            G.solve_normal(x);
+            solved = true;
         }
-        const T w = G.add(a, b);
-        if (STATS) ssr = RN<T>::fma(RN<T>::mul(w, b[F - 1]), b[F - 1], ssr);   // the row's weighted leftover
-        return true;
-    });
-    if (STATS && st) { st->bmin = bmin; st->bmax = bmax; st->ssb = ssb; st->ssr = ssr; }
-    const T ratio = G.ratio();
-    if (!(ratio >= tau) || cnt < N) return 1;
-    G.solve(x);
+    }
+    if (!solved) {
+        G.zero();
+        bmin = bmax = ssb = T(0);
+        for_neighbors(src, nb, cnt, [&](uint32_t, const Rec& rec) {
+            T d[DIM], a[N], b[F];
+            src.unpack(rec, d, b);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) d[k] *= invS;
+            gfd_row<T, DIM>(d, a);
+            if (STATS) {
+                T bl = b[F - 1];
+                bmin = bl < bmin ? bl : bmin;
+                bmax = bl > bmax ? bl : bmax;
+                ssb = RN<T>::fma(bl, bl, ssb);
+            }
+            const T w = G.add(a, b);
+            if (STATS) ssr = RN<T>::fma(RN<T>::mul(w, b[F - 1]), b[F - 1], ssr);   // the row's weighted leftover
+            return true;
+        });
+        have_ssr = true;
+        ratio = G.ratio();
+        if (!(ratio >= tau) || cnt < N) {
+            if (STATS && st) { st->bmin = bmin; st->bmax = bmax; st->ssb = ssb; st->ssr = ssr; }
+            return 1;
+        }
+        G.solve(x);
+    }
     const bool refine = cf.refine == LP_REFINE_ALWAYS || (cf.refine == LP_REFINE_AUTO && ratio < (T)cf.refine_ratio);
-    if (refine) {
+    if (refine || (STATS && !have_ssr)) {
         // The FP32 3D factor (d and U, 45 values) waits in shared memory during
         // the correction pass, which holds the solution and the correction sums:
         // without that the pass spills.
@@ -444,6 +563,7 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
         for (int u = 0; u < N; ++u)
 #pragma unroll
             for (int f = 0; f < F; ++f) g[u][f] = T(0);
+        const bool sum_res = STATS && !have_ssr;
         for_neighbors(src, nb, cnt, [&](uint32_t, const Rec& rec) {
             T d[DIM], a[N], b[F];
             src.unpack(rec, d, b);
@@ -455,24 +575,28 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
                 T res = b[f];
 #pragma unroll
                 for (int u = 0; u < N; ++u) res = RN<T>::fma(-a[u], x[u][f], res);
+                if (STATS && f == F - 1 && sum_res) ssr = RN<T>::fma(res, res, ssr);
 #pragma unroll
                 for (int u = 0; u < N; ++u) g[u][f] = RN<T>::fma(a[u], res, g[u][f]);
             }
             return true;
         });
-        if (STASH) {
-            volatile T* sv = &stash[0][0];      // volatile: reloaded, not kept live
+        if (refine) {
+            if (STASH) {
+                volatile T* sv = &stash[0][0];      // volatile: reloaded, not kept live
 #pragma unroll
-            for (int k = 0; k < N; ++k) G.d[k] = sv[k * FIT_THREADS + threadIdx.x];
+                for (int k = 0; k < N; ++k) G.d[k] = sv[k * FIT_THREADS + threadIdx.x];
 #pragma unroll
-            for (int q = 0; q < N * (N - 1) / 2; ++q) G.U[q] = sv[(N + q) * FIT_THREADS + threadIdx.x];
+                for (int q = 0; q < N * (N - 1) / 2; ++q) G.U[q] = sv[(N + q) * FIT_THREADS + threadIdx.x];
+            }
+            G.solve_normal(g);
+#pragma unroll
+            for (int u = 0; u < N; ++u)
+#pragma unroll
+                for (int f = 0; f < F; ++f) x[u][f] += g[u][f];
         }
-        G.solve_normal(g);
-#pragma unroll
-        for (int u = 0; u < N; ++u)
-#pragma unroll
-            for (int f = 0; f < F; ++f) x[u][f] += g[u][f];
     }
+    if (STATS && st) { st->bmin = bmin; st->bmax = bmax; st->ssb = ssb; st->ssr = ssr; }
     T s2 = invS * invS;
 #pragma unroll
     for (int u = 0; u < N; ++u)

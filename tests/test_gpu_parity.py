@@ -232,15 +232,18 @@ def test_gfd_derivs_fp32_matches_oracle(nf):
 
 
 def test_refinement_step_buys_fp32_accuracy():
-    """The refinement step of the central fit (on by default) is what brings the
-    FP32 gradients inside the 1e-5 bound; without it (NEVER) and when only
-    ill-conditioned stencils are refined (AUTO) the error is larger but bounded."""
+    """The correction pass of the central fit (on by default) is what brings the
+    FP32 gradients inside the 1e-5 bound; without it (NEVER) the error of the
+    normal equations (~cond^2 u) remains.  AUTO corrects only the stencils
+    below the ratio; a well-conditioned stencil's first solution is already
+    within about cond^2 u, so its correction may round to nothing and AUTO
+    may equal ALWAYS."""
     errs = {}
     for mode in (lp.REFINE_ALWAYS, lp.REFINE_AUTO, lp.REFINE_NEVER):
         gd, od, _, _ = _deriv_case(lp.PREC_FP32, 1e-6, 1, refine=mode)
         errs[mode] = max(normwise(gd[0][:, u], od[0][:, u]) for u in range(3))
     assert errs[lp.REFINE_ALWAYS] < FP32_GRAD_TOL
-    assert errs[lp.REFINE_ALWAYS] < errs[lp.REFINE_AUTO] <= errs[lp.REFINE_NEVER] < 1e-2, errs
+    assert errs[lp.REFINE_ALWAYS] <= errs[lp.REFINE_AUTO] <= errs[lp.REFINE_NEVER] < 1e-2, errs
     assert errs[lp.REFINE_NEVER] > 10 * errs[lp.REFINE_ALWAYS], errs
 
 
