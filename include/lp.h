@@ -256,6 +256,21 @@ lp_status lp_step(lp_ctx *ctx, lp_particles *p, double dt, double cfl, double *t
                   const lp_step_diag *diag, lp_stream stream);
 
 /*
+ * lp_step on particles in HOST memory (single-simulation contexts).  The host
+ * arrays of h are copied into a device copy the context owns (allocated at
+ * capacity on the first call): positions, m and V on `stream`, the other
+ * fields on a second stream of the context while the keys are sorted.  When
+ * every array of h is page-locked (cudaHostAlloc / cudaHostRegister), the
+ * step's kernels write the new, Morton-ordered state straight into them, so
+ * no copy back follows the step; otherwise it is copied back on `stream`.
+ * Either way h holds on completion of `stream` what lp_step leaves in p.
+ * h must not be read or written by the host until then.  t and diag are
+ * device pointers as for lp_step.  LP_ERR_STATE for a batched context.
+ */
+lp_status lp_step_host(lp_ctx *ctx, lp_particles *h, double dt, double cfl, double *t,
+                       const lp_step_diag *diag, lp_stream stream);
+
+/*
  * Copy the lists of the last lp_build_neighbors / lp_step into caller-owned
  * device buffers (any may be NULL): count/total uint32 [n], idx uint32
  * [n][k_max], d2min float64 [n], keys uint64 [n] (Morton keys of the permuted

@@ -30,7 +30,7 @@ void free_all(lp_ctx* c)
                     c->sV, c->su[0], c->su[1], c->su[2], c->sP, c->sm, c->sid, c->rec, c->pos4, c->cells, c->nb_count, c->nb_total,
                     c->nb_idx, c->nb_d2min, c->grid, c->dt_dev, c->dt_min, c->counters, c->redo_list,
                     c->plain_list, c->mid, c->ext, c->grange, c->level_off_dev, c->sim_of,
-                    c->mlp_master, c->mlp_bf16, c->mlp_m1, c->mlp_m2, c->mlp_grad, c->mlp_loss};
+                    c->mlp_master, c->mlp_bf16, c->mlp_m1, c->mlp_m2, c->mlp_grad, c->mlp_loss, c->stage_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -408,6 +408,9 @@ lp_status lp_destroy(lp_ctx* c)
     if (c->graph) cudaGraphDestroy(c->graph);
     for (int q = 0; q < 2 * EV_PAIRS; ++q)
         if (c->ev[q]) cudaEventDestroy(c->ev[q]);
+    if (c->ev_host_start) cudaEventDestroy(c->ev_host_start);
+    if (c->ev_host_in) cudaEventDestroy(c->ev_host_in);
+    if (c->aux) cudaStreamDestroy(c->aux);
     free_all(c);
     free(c);
     return LP_OK;
@@ -433,6 +436,7 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
         Phase ph(c, LP_PH_SORT, 3 * radix_passes(c), s);
         LP_CUDA(radix_sort(c, n, s));
     }
+    if (c->gather_wait) LP_CUDA(cudaStreamWaitEvent(s, c->gather_wait, 0));
     {
         Phase ph(c, LP_PH_GATHER, 1, s);
         LP_CUDA(gather(c, p, s));
@@ -622,6 +626,93 @@ lp_status lp_step_batched(lp_ctx* c, lp_particles* p, const int64_t* offsets, in
     lp_status st = step_prologue(c, p, offsets, nsim, dt, cfl, t, diag, s, a, o, &n);
     if (st != LP_OK || n == 0) return st;
     return run_fit(c, a, o, c->schedule, s);
+}
+
+lp_status lp_step_host(lp_ctx* c, lp_particles* h, double dt, double cfl, double* t, const lp_step_diag* diag,
+                       lp_stream stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (c->dc.nsim_max > 1) return LP_ERR_STATE;
+    lp_status st = check_particles(c, h);
+    if (st != LP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int dim = c->dc.dim;
+    const int64_t n = h->n;
+    if (!c->stage_buf) {            // first call: the device copy at capacity, the copy stream
+        const size_t cap = (size_t)c->cap;
+        LP_CUDA(cudaMalloc(&c->stage_buf, cap * 8 * (2 * (size_t)dim + 3) + cap * 4));
+        double* q = c->stage_buf;
+        memset(&c->stage, 0, sizeof(c->stage));
+        for (int k = 0; k < dim; ++k) { c->stage.x[k] = q; q += cap; c->stage.u[k] = q; q += cap; }
+        c->stage.V = q; q += cap;
+        c->stage.P = q; q += cap;
+        c->stage.m = q; q += cap;
+        c->stage.id = reinterpret_cast<uint32_t*>(q);
+        LP_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+        LP_CUDA(cudaEventCreateWithFlags(&c->ev_host_start, cudaEventDisableTiming));
+        LP_CUDA(cudaEventCreateWithFlags(&c->ev_host_in, cudaEventDisableTiming));
+    }
+    // pinned (page-locked) host arrays: the step writes the new state straight
+    // into them; otherwise into the device copy, then copied back
+    const void* arrs[9] = {h->V, h->P, h->m, h->id, nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < dim; ++k) { arrs[4 + k] = h->x[k]; arrs[4 + dim + k] = h->u[k]; }
+    bool direct = true;
+    for (int q = 0; q < 4 + 2 * dim; ++q) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, arrs[q]) != cudaSuccess) { cudaGetLastError(); direct = false; break; }
+        if (at.type != cudaMemoryTypeHost || !at.devicePointer) { direct = false; break; }
+    }
+    lp_particles g = c->stage;
+    g.n = n;
+    const size_t b8 = (size_t)n * 8;
+    if (n > 0) {
+        // what the keys need, on the caller's stream; the rest on the copy
+        // stream, after everything before this step, overlapping the sort
+        for (int k = 0; k < dim; ++k) LP_CUDA(cudaMemcpyAsync(g.x[k], h->x[k], b8, cudaMemcpyHostToDevice, s));
+        LP_CUDA(cudaMemcpyAsync(g.m, h->m, b8, cudaMemcpyHostToDevice, s));
+        LP_CUDA(cudaMemcpyAsync(g.V, h->V, b8, cudaMemcpyHostToDevice, s));
+        LP_CUDA(cudaEventRecord(c->ev_host_start, s));
+        LP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_host_start, 0));
+        for (int k = 0; k < dim; ++k) LP_CUDA(cudaMemcpyAsync(g.u[k], h->u[k], b8, cudaMemcpyHostToDevice, c->aux));
+        LP_CUDA(cudaMemcpyAsync(g.P, h->P, b8, cudaMemcpyHostToDevice, c->aux));
+        LP_CUDA(cudaMemcpyAsync(g.id, h->id, (size_t)n * 4, cudaMemcpyHostToDevice, c->aux));
+        LP_CUDA(cudaEventRecord(c->ev_host_in, c->aux));
+        c->gather_wait = c->ev_host_in;
+    }
+    FitArgs a;
+    StepOut o;
+    int64_t nn = 0;
+    st = step_prologue(c, &g, nullptr, 1, dt, cfl, t, diag, s, a, o, &nn);
+    if (c->gather_wait) {           // (a no-op when the gather already waited for the copies)
+        cudaStreamWaitEvent(s, c->gather_wait, 0);
+        c->gather_wait = nullptr;
+    }
+    if (st != LP_OK || nn == 0) return st;
+    if (direct) {
+        cudaPointerAttributes at;
+        auto dev = [&](const void* hp) -> void* {
+            return cudaPointerGetAttributes(&at, hp) == cudaSuccess ? at.devicePointer : nullptr;
+        };
+        for (int k = 0; k < 3; ++k) {
+            o.x[k] = static_cast<double*>(dev(h->x[k < dim ? k : 0]));
+            o.u[k] = static_cast<double*>(dev(h->u[k < dim ? k : 0]));
+        }
+        o.V = static_cast<double*>(dev(h->V));
+        o.P = static_cast<double*>(dev(h->P));
+        o.m = static_cast<double*>(dev(h->m));
+        o.id = static_cast<uint32_t*>(dev(h->id));
+    }
+    st = run_fit(c, a, o, c->schedule, s);
+    if (st != LP_OK || direct) return st;
+    for (int k = 0; k < dim; ++k) {
+        LP_CUDA(cudaMemcpyAsync(h->x[k], g.x[k], b8, cudaMemcpyDeviceToHost, s));
+        LP_CUDA(cudaMemcpyAsync(h->u[k], g.u[k], b8, cudaMemcpyDeviceToHost, s));
+    }
+    LP_CUDA(cudaMemcpyAsync(h->V, g.V, b8, cudaMemcpyDeviceToHost, s));
+    LP_CUDA(cudaMemcpyAsync(h->P, g.P, b8, cudaMemcpyDeviceToHost, s));
+    LP_CUDA(cudaMemcpyAsync(h->m, g.m, b8, cudaMemcpyDeviceToHost, s));
+    LP_CUDA(cudaMemcpyAsync(h->id, g.id, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    return LP_OK;
 }
 
 lp_status lp_set_schedule(lp_ctx* c, int32_t schedule)

@@ -26,9 +26,10 @@ template <> struct IsF32<float> { static constexpr bool v = true; };
 // resident blocks per SM the FP32 step kernels are compiled for (measured on
 // the 2M-particle cloud: the central kernel at 3 blocks, 168 registers, runs 5%
 // faster than at 2 and 30% faster than at 4, where it spills; the plain kernel
-// at 4 beats 3); the FP64 kernels keep the default
+// at 5 blocks, a few registers spilled, edges out 4 and 3); the FP64 kernels
+// keep the default
 template <typename T> struct FitOcc { static constexpr int fused = 1, central = 1, plain = 1; };
-template <> struct FitOcc<float> { static constexpr int fused = 3, central = 3, plain = 4; };
+template <> struct FitOcc<float> { static constexpr int fused = 3, central = 3, plain = 5; };
 
 __device__ inline void push_redo(const FitArgs& a, int64_t i)
 {

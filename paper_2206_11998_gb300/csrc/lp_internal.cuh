@@ -243,6 +243,13 @@ struct lp_ctx {
     uint32_t* plain_list;
     void* mid;
     int schedule;                 // LP_SCHED_FUSED / LP_SCHED_SPLIT
+    // lp_step_host: device copy of the caller's host particles, a second stream
+    // for the copies that overlap the key sort, and the event the gather waits on
+    lp_particles stage;
+    double* stage_buf;
+    cudaStream_t aux;
+    cudaEvent_t ev_host_start, ev_host_in;
+    cudaEvent_t gather_wait;      // when set, build() waits for it before the gather
     int64_t n_lists;          // n of the last neighbour build (0: none)
     int tables_dirty;         // tables hold entries of the last build
     double reduce_min_w;

@@ -31,7 +31,7 @@ EXPORTED = [
     "lp_status_string", "lp_version", "lp_set_profiling", "lp_phase_times", "lp_phase_name",
     "lp_sort_keys_noalloc", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step",
     "lp_mlp_train", "lp_mlp_infer", "lp_step_batched", "lp_graph_capture", "lp_graph_launch",
-    "lp_set_schedule", "lp_get_schedule", "lp_autotune",
+    "lp_set_schedule", "lp_get_schedule", "lp_autotune", "lp_step_host",
 ]
 MLP_IN, MLP_H = 8, 32
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H + 1
@@ -110,6 +110,8 @@ def lib():
         L.lp_gfd_derivs.argtypes = [P, C.POINTER(Particles), C.POINTER(C.c_void_p), C.c_int32, C.c_int32, P, P, P]
         L.lp_onesided_derivs.argtypes = [P, C.POINTER(Particles), C.POINTER(C.c_void_p), C.c_int32, P, P]
         L.lp_step.argtypes = [P, C.POINTER(Particles), C.c_double, C.c_double, P, C.POINTER(StepDiag), P]
+        L.lp_step_host.argtypes = [P, C.POINTER(Particles), C.c_double, C.c_double, P, C.POINTER(StepDiag), P]
+        L.lp_step_host.restype = C.c_int
         L.lp_step_batched.argtypes = [P, C.POINTER(Particles), P, C.c_int32, C.c_double, C.c_double, P,
                                       C.POINTER(StepDiag), P]
         L.lp_step_batched.restype = C.c_int
@@ -211,6 +213,17 @@ class ParticleSet:
     def from_state(state, device="cuda"):
         import torch
         t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        return ParticleSet([t(a) for a in state["x"]], t(state["V"]), [t(a) for a in state["u"]], t(state["P"]),
+                           t(state["m"]), t(state["id"].astype(np.int32), torch.int32))
+
+    @staticmethod
+    def from_state_host(state, pinned=True):
+        """Host (CPU) copies of a state, page-locked unless pinned=False, for
+        Context.step_host."""
+        import torch
+        def t(a, dt=torch.float64):
+            v = torch.from_numpy(np.array(a, dtype=np.float64 if dt == torch.float64 else np.int32, copy=True))
+            return v.pin_memory() if pinned else v
         return ParticleSet([t(a) for a in state["x"]], t(state["V"]), [t(a) for a in state["u"]], t(state["P"]),
                            t(state["m"]), t(state["id"].astype(np.int32), torch.int32))
 
@@ -321,6 +334,18 @@ class Context:
         d.features = _ptr(features) if features is not None else None
         _check(lib().lp_step(self.h, C.byref(p), float(dt), float(cfl), _ptr(t), C.byref(d), _stream(stream)),
                "lp_step")
+
+    def step_host(self, ps: ParticleSet, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None, features=None,
+                  stream=None):
+        """lp_step on a ParticleSet of host (CPU, ideally pinned) tensors; t and the
+        diagnostics are device tensors as for step."""
+        p = ps.struct()
+        d = StepDiag()
+        d.flag, d.phi, d.r = (_ptr(flag) if flag is not None else None, _ptr(phi) if phi is not None else None,
+                              _ptr(r) if r is not None else None)
+        d.features = _ptr(features) if features is not None else None
+        _check(lib().lp_step_host(self.h, C.byref(p), float(dt), float(cfl), _ptr(t), C.byref(d), _stream(stream)),
+               "lp_step_host")
 
     def step_batched(self, ps: ParticleSet, offsets, nsim, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None,
                      features=None, stream=None):

@@ -53,5 +53,6 @@ def test_host_side_argument_errors_without_gpu():
     assert L.lp_create(None, ctypes.byref(h)) == lp.ERR_ARG
     assert L.lp_set_schedule(None, lp.SCHED_SPLIT) == lp.ERR_ARG
     assert L.lp_autotune(None, None, None, 1, 0.0, 0.4, 1, None, None) == lp.ERR_ARG
+    assert L.lp_step_host(None, None, 0.0, 0.4, None, None, None) == lp.ERR_ARG
     assert L.lp_destroy(None) == lp.OK
     assert L.lp_status_string(lp.ERR_CAPACITY).decode().startswith("particle count")
