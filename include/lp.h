@@ -324,7 +324,11 @@ lp_status lp_mlp_infer(lp_ctx *ctx, const float *X, int64_t n, float *p, lp_stre
  * NULL), then clears them.  lp_phase_name(k) is the phase's static name.
  */
 enum { LP_PH_GRID = 0, LP_PH_SORT = 1, LP_PH_GATHER = 2, LP_PH_TABLES = 3, LP_PH_QUERY = 4,
-       LP_PH_CFL = 5, LP_PH_FIT = 6, LP_PH_FIT64 = 7, LP_NPHASES = 8 };
+       LP_PH_CFL = 5, LP_PH_FIT = 6, LP_PH_FIT64 = 7,
+       LP_PH_HOST_IN = 8,     /* lp_step_host: copies on the caller's stream, and the
+                                 wait for the second stream's copies before the gather */
+       LP_PH_HOST_OUT = 9,    /* lp_step_host on pageable arrays: the copy back */
+       LP_NPHASES = 10 };
 lp_status lp_set_profiling(lp_ctx *ctx, int32_t on);
 lp_status lp_phase_times(lp_ctx *ctx, double *out_ms, int64_t *out_launches, lp_stream stream);
 const char *lp_phase_name(int32_t phase);

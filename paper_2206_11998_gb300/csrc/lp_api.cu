@@ -436,7 +436,10 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
         Phase ph(c, LP_PH_SORT, 3 * radix_passes(c), s);
         LP_CUDA(radix_sort(c, n, s));
     }
-    if (c->gather_wait) LP_CUDA(cudaStreamWaitEvent(s, c->gather_wait, 0));
+    if (c->gather_wait) {
+        Phase ph(c, LP_PH_HOST_IN, 0, s);
+        LP_CUDA(cudaStreamWaitEvent(s, c->gather_wait, 0));
+    }
     {
         Phase ph(c, LP_PH_GATHER, 1, s);
         LP_CUDA(gather(c, p, s));
@@ -654,7 +657,7 @@ lp_status lp_step_host(lp_ctx* c, lp_particles* h, double dt, double cfl, double
     }
     // pinned (page-locked) host arrays: the step writes the new state straight
     // into them; otherwise into the device copy, then copied back
-    const void* arrs[9] = {h->V, h->P, h->m, h->id, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const void* arrs[4 + 2 * 3] = {h->V, h->P, h->m, h->id};
     for (int k = 0; k < dim; ++k) { arrs[4 + k] = h->x[k]; arrs[4 + dim + k] = h->u[k]; }
     bool direct = true;
     for (int q = 0; q < 4 + 2 * dim; ++q) {
@@ -668,9 +671,12 @@ lp_status lp_step_host(lp_ctx* c, lp_particles* h, double dt, double cfl, double
     if (n > 0) {
         // what the keys need, on the caller's stream; the rest on the copy
         // stream, after everything before this step, overlapping the sort
-        for (int k = 0; k < dim; ++k) LP_CUDA(cudaMemcpyAsync(g.x[k], h->x[k], b8, cudaMemcpyHostToDevice, s));
-        LP_CUDA(cudaMemcpyAsync(g.m, h->m, b8, cudaMemcpyHostToDevice, s));
-        LP_CUDA(cudaMemcpyAsync(g.V, h->V, b8, cudaMemcpyHostToDevice, s));
+        {
+            Phase ph(c, LP_PH_HOST_IN, 0, s);
+            for (int k = 0; k < dim; ++k) LP_CUDA(cudaMemcpyAsync(g.x[k], h->x[k], b8, cudaMemcpyHostToDevice, s));
+            LP_CUDA(cudaMemcpyAsync(g.m, h->m, b8, cudaMemcpyHostToDevice, s));
+            LP_CUDA(cudaMemcpyAsync(g.V, h->V, b8, cudaMemcpyHostToDevice, s));
+        }
         LP_CUDA(cudaEventRecord(c->ev_host_start, s));
         LP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_host_start, 0));
         for (int k = 0; k < dim; ++k) LP_CUDA(cudaMemcpyAsync(g.u[k], h->u[k], b8, cudaMemcpyHostToDevice, c->aux));
@@ -704,6 +710,7 @@ lp_status lp_step_host(lp_ctx* c, lp_particles* h, double dt, double cfl, double
     }
     st = run_fit(c, a, o, c->schedule, s);
     if (st != LP_OK || direct) return st;
+    Phase ph(c, LP_PH_HOST_OUT, 0, s);
     for (int k = 0; k < dim; ++k) {
         LP_CUDA(cudaMemcpyAsync(h->x[k], g.x[k], b8, cudaMemcpyDeviceToHost, s));
         LP_CUDA(cudaMemcpyAsync(h->u[k], g.u[k], b8, cudaMemcpyDeviceToHost, s));
@@ -865,7 +872,8 @@ lp_status lp_phase_times(lp_ctx* c, double* out_ms, int64_t* out_launches, lp_st
 const char* lp_phase_name(int32_t ph)
 {
     static const char* names[LP_NPHASES] = {"grid+keys", "radix-sort", "gather", "cell-tables",
-                                            "neighbor-query", "cfl", "fit+update", "fit+update-fp64"};
+                                            "neighbor-query", "cfl", "fit+update", "fit+update-fp64",
+                                            "host-in", "host-out"};
     return (ph >= 0 && ph < LP_NPHASES) ? names[ph] : "unknown";
 }
 

@@ -36,7 +36,7 @@ EXPORTED = [
 MLP_IN, MLP_H = 8, 32
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H + 1
 NOALLOC_MAX_N = 262144
-NPHASES = 8
+NPHASES = 10
 
 
 class LPError(RuntimeError):
