@@ -100,13 +100,17 @@ enum { LP_OUT_F32 = 0, LP_OUT_F64 = 1 };
  *   max_sims       most simulations one lp_step_batched call advances (0 or 1:
  *                  one).  2D keys keep 21 bits per axis; 3D keys with several
  *                  simulations keep min(21, (64 - ceil(log2 max_sims)) / 3).
- *   refine         one step of iterative refinement of the central fit (the
- *                  corrected semi-normal equations): LP_REFINE_ALWAYS (0, the
- *                  default); LP_REFINE_AUTO (1) only where min|R_kk|/max|R_kk| <
- *                  refine_ratio; LP_REFINE_NEVER (2).  The FP32 gradient error
- *                  bound of 1e-5 needs ALWAYS; AUTO and NEVER are faster (the
- *                  refinement pass is about a quarter of the fit) at about 2e-5
- *                  and 5e-4 on the jittered-lattice GFD workload.
+ *   refine         the FP32 central fit's correction pass (one step of the
+ *                  semi-normal equations on the first solution's residual):
+ *                  LP_REFINE_AUTO (0, the default) where min|R_kk|/max|R_kk| <
+ *                  refine_ratio, i.e. where cond(A)^2 u of the normal
+ *                  equations is not negligible; LP_REFINE_ALWAYS (1);
+ *                  LP_REFINE_NEVER (2).  On the jittered-lattice GFD workload
+ *                  AUTO and ALWAYS give the same gradients (error 2.5e-6; a
+ *                  well-conditioned stencil's correction rounds away), NEVER
+ *                  1.8e-4; on the 2M gas cloud AUTO corrects ~3% of the
+ *                  stencils and its state after a step is within 2e-7 of
+ *                  ALWAYS's.
  *   refine_ratio   LP_REFINE_AUTO threshold (0: 0.1).
  */
 typedef struct {
@@ -139,7 +143,7 @@ typedef struct {
     double refine_ratio;
 } lp_config;
 
-enum { LP_REFINE_ALWAYS = 0, LP_REFINE_AUTO = 1, LP_REFINE_NEVER = 2 };
+enum { LP_REFINE_AUTO = 0, LP_REFINE_ALWAYS = 1, LP_REFINE_NEVER = 2 };
 
 /* Caller-owned device particle arrays (SoA, float64; id uint32).  Unused axes
  * (>= dim) may be NULL. */

@@ -70,7 +70,7 @@ lp_status check_cfg(const lp_config* g)
     if (g->max_level < 0 || g->max_level > 17) return LP_ERR_ARG;
     if (g->max_sims < 0 || g->max_sims > (1 << 20)) return LP_ERR_ARG;
     if (g->max_sims > 1 && g->dim == 1) return LP_ERR_ARG;   // 1D keys are the raw order of x
-    if (g->refine < LP_REFINE_ALWAYS || g->refine > LP_REFINE_NEVER || !(g->refine_ratio >= 0.0)) return LP_ERR_ARG;
+    if (g->refine < LP_REFINE_AUTO || g->refine > LP_REFINE_NEVER || !(g->refine_ratio >= 0.0)) return LP_ERR_ARG;
     return LP_OK;
 }
 

@@ -22,7 +22,7 @@ RADIUS_FIXED, RADIUS_VOLUME, RADIUS_KSIDE = 0, 1, 2
 LIM_FLAGGED, LIM_PAPER, LIM_LW, LIM_UW = 0, 1, 2, 3
 EST_PLAIN, EST_MLP = 0, 1
 OUT_F32, OUT_F64 = 0, 1
-REFINE_ALWAYS, REFINE_AUTO, REFINE_NEVER = 0, 1, 2
+REFINE_AUTO, REFINE_ALWAYS, REFINE_NEVER = 0, 1, 2
 SCHED_FUSED, SCHED_SPLIT, SCHED_QUERY_WARP = 0, 1, 2
 
 EXPORTED = [

@@ -179,7 +179,7 @@ def test_capacity_and_state_errors():
 # GFD derivatives (config-2 shape at reduced size)
 # ---------------------------------------------------------------------------
 
-def _deriv_case(prec, noise, nf, n_side=22, refine=lp.REFINE_ALWAYS):
+def _deriv_case(prec, noise, nf, n_side=22, refine=lp.REFINE_AUTO):
     h = 1.0 / n_side
     x, fields, coeffs = inputs.gfd_lattice_workload(n_side, h, noise, nfields=nf)
     n = x[0].shape[0]
