@@ -32,7 +32,6 @@ if ROOT not in sys.path:
 
 METRIC = "particle-updates/s (3D LP step) at 1e-5 rel err vs FP64; % HBM roofline"
 UNIT = "particle-updates/s"
-N_PARTICLES = 2_000_000
 GAMMA = 5.0 / 3.0
 KAPPA = 2.2
 K_MAX = 64
@@ -77,10 +76,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--particles", type=int, default=N_PARTICLES)
+    ap.add_argument("--particles", type=int, default=None,
+                    help="particles (default: 2M for the gas cloud, about 8M for the jet snapshot)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="gas-cloud", choices=["gas-cloud", "kh-ensemble"])
+    ap.add_argument("--workload", default="gas-cloud", choices=["gas-cloud", "jet-snapshot", "kh-ensemble"],
+                    help="jet-snapshot: the static jet-shaped state (density ratio 1e3, gamma 1.4)")
     ap.add_argument("--sims", type=int, default=256)
     ap.add_argument("--estimator", default="plain", choices=["plain", "mlp"],
                     help="mlp: train the learned estimator on this workload's own plain steps, then time "
@@ -98,9 +99,37 @@ def dist_info():
     return rank, world, local
 
 
+# the single-simulation 3D workloads: generator, gamma, default size
+WORKLOADS = {"gas-cloud": ("gas-cloud-3d", 5.0 / 3.0, 2_000_000),
+             "jet-snapshot": ("jet-snapshot-3d", 1.4, 8_000_000)}
+ACTIVE = "gas-cloud"
+
+
+def select_workload(args):
+    """Set the workload's gamma and name, and its default size."""
+    global ACTIVE, GAMMA, WORKLOAD
+    if args.workload in WORKLOADS:
+        ACTIVE = args.workload
+    name, GAMMA, n0 = WORKLOADS[ACTIVE]
+    if args.particles is None:
+        args.particles = n0
+    WORKLOAD = name
+
+
+def size_tag(n):
+    return ("%dM" % (n // 1_000_000)) if n % 1_000_000 == 0 else (
+        "%.2fM" % (n / 1e6) if n >= 1_000_000 else "%dk" % round(n / 1e3))
+
+
 def workload_state(n, seed=SEED):
+    global WORKLOAD
     from paper_2206_11998_gb300 import inputs
-    return inputs.gas_cloud_3d(n, seed=seed, gamma=GAMMA)
+    if ACTIVE == "jet-snapshot":
+        st = inputs.jet_snapshot_3d(n, seed=seed + 6)
+    else:
+        st = inputs.gas_cloud_3d(n, seed=seed, gamma=GAMMA)
+    WORKLOAD = WORKLOADS[ACTIVE][0] + "-" + size_tag(st["V"].shape[0])
+    return st
 
 
 def config_dict(n, extra=None):
@@ -229,8 +258,8 @@ def run_ours(args):
         dist.init_process_group("nccl", rank=rank, world_size=world)
     torch.cuda.set_device(local)
     b.build()
-    n = args.particles
-    state = workload_state(n, seed=SEED + rank)
+    state = workload_state(args.particles, seed=SEED + rank)
+    n = state["V"].shape[0]
     stream = torch.cuda.Stream()
     mlp_info = None
     kw = {}
@@ -475,8 +504,8 @@ def run_reference(args):
     rank, world, local = dist_info()
     if rank != 0:
         return
-    n = args.particles
-    state = workload_state(n)
+    state = workload_state(args.particles)
+    n = state["V"].shape[0]
     import oracle
     oracle.build()
     from paper_2206_11998_gb300 import inputs
@@ -629,6 +658,7 @@ def run_ensemble(args):
 
 def main():
     args = parse()
+    select_workload(args)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "kh-ensemble":

@@ -190,6 +190,56 @@ def kh_2d(n: int, amp: float, seed: int, rho_in: float = 2.0, rho_out: float = 1
     return _state([x, y], 1.0 / rho, [u, v], np.full(n, p0), np.full(n, M / n))
 
 
+JET_GAMMA = 1.4
+
+
+def jet_snapshot_3d(n: int = 8_000_000, seed: int = 10, r_jet: float = 1.0, l_jet: float = 12.0,
+                    half_width: float = 4.0, length: float = 16.0, density_ratio: float = 1e3,
+                    pressure_ratio: float = 100.0, mach: float = 3.0, jitter: float = 0.2):
+    """A static snapshot shaped like the supersonic jet: a dense cylinder of gas
+    (radius r_jet, along z from 0 to l_jet, rho = 1, p = 1, u_z = mach * c)
+    inside an ambient 1/density_ratio as dense at 1/pressure_ratio of the
+    pressure, at rest, filling the box [-w, w]^2 x [0, length].
+
+    Equal-mass particles on two jittered cubic lattices: spacing h in the jet
+    and h * density_ratio^(1/3) in the ambient (ambient lattice sites closer
+    than half their spacing to the cylinder are dropped), with h chosen so that
+    about n particles result.  This stands in for the jet's particle state
+    until inflow and insertion exist: the same density contrast, so the
+    neighbour counts and stencil shapes span the same range.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v_jet = np.pi * r_jet ** 2 * l_jet
+    v_amb = (2.0 * half_width) ** 2 * length - v_jet
+    # particles per unit volume: n_jet / v_jet = 1 / h^3, ambient 1 / (h^3 density_ratio)
+    h = ((v_jet + v_amb / density_ratio) / n) ** (1.0 / 3.0)
+    ha = h * density_ratio ** (1.0 / 3.0)
+
+    def lattice(spacing, lo, hi):
+        axes = [np.arange(lo[k] + 0.5 * spacing, hi[k], spacing) for k in range(3)]
+        g = np.meshgrid(*axes, indexing="ij")
+        return [a.ravel() for a in g]
+
+    jx, jy, jz = lattice(h, (-r_jet, -r_jet, 0.0), (r_jet, r_jet, l_jet))
+    keep = jx * jx + jy * jy <= r_jet * r_jet
+    jx, jy, jz = jx[keep], jy[keep], jz[keep]
+    ax, ay, az = lattice(ha, (-half_width, -half_width, 0.0), (half_width, half_width, length))
+    rr = np.sqrt(ax * ax + ay * ay)
+    dist = np.where(az <= l_jet, np.maximum(rr - r_jet, 0.0), np.hypot(np.maximum(rr - r_jet, 0.0), az - l_jet))
+    keep = dist > 0.5 * ha
+    ax, ay, az = ax[keep], ay[keep], az[keep]
+    nj, na = jx.shape[0], ax.shape[0]
+    x = [np.concatenate([jx, ax]), np.concatenate([jy, ay]), np.concatenate([jz, az])]
+    sp = np.concatenate([np.full(nj, h), np.full(na, ha)])
+    for k in range(3):
+        x[k] = x[k] + sp * rng.uniform(-jitter, jitter, nj + na)
+    rho = np.concatenate([np.full(nj, 1.0), np.full(na, 1.0 / density_ratio)])
+    p = np.concatenate([np.full(nj, 1.0), np.full(na, 1.0 / pressure_ratio)])
+    uz = np.concatenate([np.full(nj, mach * np.sqrt(JET_GAMMA)), np.zeros(na)])
+    zero = np.zeros(nj + na)
+    return _state(x, 1.0 / rho, [zero, zero.copy(), uz], p, np.full(nj + na, h ** 3))
+
+
 def kh_ensemble_sizes(n_sims: int = 256, lo: int = 10_000, hi: int = 200_000, seed: int = 6):
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.integers(lo, hi + 1, size=n_sims)

@@ -57,6 +57,8 @@ CASES_NB = {
     "3d-volume-cloud": lambda: (inputs.gas_cloud_3d(20_037, seed=8), "vol3"),
     "2d-periodic-kh": lambda: (inputs.kh_2d(7_001, 0.03, seed=5), "kh2"),
     "1d-sod": lambda: (inputs.sod_1d(889, 111), "sod1"),
+    # density contrast 1e3: ambient radii ~10x the jet's, lists truncated at k_max
+    "3d-jet-snapshot": lambda: (inputs.jet_snapshot_3d(30_000), "vol3"),
 }
 
 
@@ -351,6 +353,19 @@ def test_step_gas_cloud_cfl(prec, tol):
     cfg = lp.make_config(3, 20_037, precision=prec, kappa=2.2, k_max=64, gamma=5.0 / 3.0,
                          s_ref=inputs.field_scales(st), limiter=lp.LIM_FLAGGED)
     _step_parity(st, cfg, 0.0, tol, cfl=0.4)
+
+
+@pytest.mark.parametrize("prec,tol", [(lp.PREC_FP32, 1e-5), (lp.PREC_FP64, 1e-12)])
+def test_step_jet_snapshot_cfl(prec, tol):
+    """The jet-shaped snapshot: a 1e3 density jump with 10-64 neighbours per
+    particle, truncated lists around the jet, ill-conditioned one-sided and
+    central stencils at the interface (FP64 redo in the FP32 path)."""
+    st = inputs.jet_snapshot_3d(30_000)
+    n = st["V"].shape[0]
+    cfg = lp.make_config(3, n, precision=prec, kappa=2.2, k_max=64, gamma=inputs.JET_GAMMA,
+                         s_ref=inputs.field_scales(st), limiter=lp.LIM_FLAGGED)
+    errs, stats, ndiff = _step_parity(st, cfg, 0.0, tol, cfl=0.4)
+    assert stats["n_overflow"] > 0 and stats["n_flagged"] > 0, stats
 
 
 def test_step_sod_fp64_and_frozen_ghosts():

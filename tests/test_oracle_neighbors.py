@@ -76,6 +76,21 @@ def test_volume_radius_3d_with_truncation(oracle_lib):
     check(cfg, st, b)
 
 
+def test_volume_radius_jet_contrast(oracle_lib):
+    """A 1e3 density jump: ambient radii ~10x the jet's, so ambient particles
+    next to the jet see hundreds of jet particles (truncated to k_max, the
+    count saturating at 4 k_max) while jet particles see few ambient ones."""
+    st = inputs.jet_snapshot_3d(2500, l_jet=4.0, length=6.0, half_width=3.0)
+    n = st["V"].shape[0]
+    jet = st["V"] == 1.0
+    assert 0 < (~jet).sum() < jet.sum()
+    assert np.all(st["m"] == st["m"][0])            # equal masses
+    cfg = oracle.make_config(3, radius_mode=oracle.RADIUS_VOLUME, kappa=2.2, k_max=32)
+    b = brute_lists(st["x"], st["V"], st["m"], st["id"], oracle.RADIUS_VOLUME, 0, 2.2, 32)
+    assert max(t for i, (_, t, _) in enumerate(b) if not jet[i]) == 128   # ambient lists saturate
+    check(cfg, st, b)
+
+
 def test_ties_broken_by_id_on_perfect_lattice(oracle_lib):
     g = (np.arange(6) + 0.5) * 0.25
     X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
