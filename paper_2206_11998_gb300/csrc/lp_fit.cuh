@@ -56,9 +56,13 @@ struct Givens {
     // Square-root-free Givens rotations (Gentleman's form): R = D^{1/2} U with U
     // unit upper triangular and Q^T B = D^{1/2} Z.  A row (a, b) of weight w,
     // starting at 1, enters column k as
-    //   d' = d_k + w a_k^2,  s = w a_k / d',  w' = w d_k / d',
-    //   t = a_l - a_k U_kl,  U_kl' = U_kl + s t,  a_l' = t    (l > k; b likewise)
-    // -- two FMAs per element, no square root.  The row's remaining weight w
+    //   d' = d_k + w a_k^2,  c = d_k / d',  s = w a_k / d',  w' = w c,
+    //   t = a_l - a_k U_kl,  U_kl' = c U_kl + s a_l,  a_l' = t    (l > k; b likewise)
+    // -- no square root.  U_kl' is the weighted mean of U_kl and a_l / a_k, not
+    // U_kl + s t: that shorter form cancels catastrophically when a row much
+    // larger than the column's previous rows meets a column built from tiny
+    // ones (c near 0, U_kl huge), which drifted lattices produce (offsets of
+    // 1e-17 where the lattice had exact zeros).  The row's remaining weight w
     // times its leftover b^2 is its share of the residual sum of squares.
     T d[N];
     T U[N * (N - 1) / 2 + 1];   // strict upper part of U, row by row
@@ -91,19 +95,20 @@ struct Givens {
             // a row absorbed by an empty column keeps weight 0 (live = false: no change)
             const bool live = wa != T(0) && dn > T(0);
             const T inv = live ? O::rcp(dn) : T(0);
-            const T sk = O::mul(wa, inv);
-            w = live ? O::mul(O::mul(w, d[k]), inv) : w;
+            const T sk = O::mul(wa, inv);                     // 0 when not live
+            const T ck = live ? O::mul(d[k], inv) : T(1);     // 1 when not live: U, Z unchanged
+            w = O::mul(w, ck);
             d[k] = live ? dn : d[k];
 #pragma unroll
             for (int l = k + 1; l < N; ++l) {
                 const T t = O::fma(-ak, U[id(k, l)], a[l]);
-                U[id(k, l)] = O::fma(sk, t, U[id(k, l)]);
+                U[id(k, l)] = O::fma(ck, U[id(k, l)], O::mul(sk, a[l]));
                 a[l] = t;
             }
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 const T t = O::fma(-ak, Z[k][f], b[f]);
-                Z[k][f] = O::fma(sk, t, Z[k][f]);
+                Z[k][f] = O::fma(ck, Z[k][f], O::mul(sk, b[f]));
                 b[f] = t;
             }
         }

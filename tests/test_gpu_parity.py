@@ -259,6 +259,39 @@ def test_gfd_derivs_fp32_noise_free_vs_analytic():
     assert np.abs(gd[0][:, 3:] - hess).max() / np.abs(hess).max() < FP32_HESS_TOL
 
 
+def test_fits_on_a_drifted_lattice():
+    """A perfect lattice moved by a tiny amount (offsets of ~1e-16 where the
+    lattice had exact zeros): stencil rows that are almost zero in a column
+    meet rows that are not.  The square-root-free rotations must not lose the
+    column (no fallback to the linear fit, derivatives as the oracle's)."""
+    n_side, h = 12, 1.0 / 12
+    x = inputs.jittered_lattice_3d(n_side, h, 0.0, seed=1)        # the perfect lattice
+    rng = np.random.default_rng(3)
+    x = [a + h * 1e-15 * rng.standard_normal(a.shape[0]) for a in x]
+    c, g0, H = inputs.random_quadratic_3d(2)
+    fields = [inputs.quadratic_values(x, c, g0, H)]
+    n = x[0].shape[0]
+    st = {"x": x, "V": np.ones(n), "u": [np.zeros(n)] * 3, "P": np.ones(n), "m": np.ones(n),
+          "id": np.arange(n, dtype=np.uint32), "n_fluid": n}
+    for prec, tol in ((lp.PREC_FP64, FP64_DERIV_TOL), (lp.PREC_FP32, FP32_GRAD_TOL)):
+        cfg = lp.make_config(3, n, precision=prec, radius_mode=lp.RADIUS_FIXED, radius=2.2 * h, k_max=64)
+        ctx = lp.Context(cfg)
+        ps = lp.ParticleSet.from_state(st)
+        ctx.build_neighbors(ps)
+        ids = ps.id.cpu().numpy().astype(np.int64)
+        status = torch.zeros(n, dtype=torch.int32, device="cuda")
+        out = ctx.gfd_derivs(ps, [torch.as_tensor(fields[0][ids], device="cuda")], lp.OUT_F64, status=status)
+        stt = status.cpu().numpy()
+        assert np.all((stt & 3) == 0), (prec, np.bincount(stt))      # no linear fallback, no failed fit
+        ocfg = _oracle_cfg(cfg)
+        oidx, ocnt, _, _ = oracle.neighbors(ocfg, x, st["V"], st["m"], st["id"])
+        od, _ = oracle.gfd_central(ocfg, x, fields, ocnt, oidx)
+        g = np.stack([by_id(ids, out.cpu().numpy()[0][:, u]) for u in range(9)], axis=1)
+        for u in range(3):
+            assert normwise(g[:, u], od[0][:, u]) < tol, (prec, u)
+        ctx.close()
+
+
 def test_onesided_derivs_match_oracle():
     st = inputs.smooth_wave_3d(14, 1.0 / 14)
     n = st["V"].shape[0]
