@@ -87,14 +87,15 @@ lp_status check_particles(const lp_ctx* c, const lp_particles* p)
     return LP_OK;
 }
 
-__global__ void k_split_fields(int64_t n, int nf, const double* f0, const double* f1, const double* f2,
+// the first nf of the F fields a fit kernel reads, into the fit records
+__global__ void k_split_fields(int64_t n, int nf, int F, const double* f0, const double* f1, const double* f2,
                                const double* f3, const double* f4, float4* rec)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double* f[5] = {f0, f1, f2, f3, f4};
     float* r = reinterpret_cast<float*>(rec + i * REC_F4);
-    for (int q = 0; q < nf; ++q) split(f[q][i], r[REC_FH + q], r[REC_FL + q]);
+    for (int q = 0; q < nf; ++q) split(f[q][i], r[rec_fh(q, F)], r[rec_fl(q, F)]);
 }
 
 // dt_s = cfl * sqrt(min_i d2min_i / (gamma P_i V_i)) over the fluid particles of
@@ -513,7 +514,7 @@ lp_status lp_gfd_derivs(lp_ctx* c, const lp_particles* p, const double* const* f
             {
                 Phase ph(c, LP_PH_GATHER, 1, s);
                 k_split_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-                    n, real, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->rec);
+                    n, F, F, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->rec);
             }
             LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
             {
@@ -552,7 +553,7 @@ lp_status lp_onesided_derivs(lp_ctx* c, const lp_particles* p, const double* con
         {
             Phase ph(c, LP_PH_GATHER, 1, s);
             k_split_fields<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-                n, nfields, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->rec);
+                n, 5, 5, a.fd[0], a.fd[1], a.fd[2], a.fd[3], a.fd[4], c->rec);
         }
         LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
         {

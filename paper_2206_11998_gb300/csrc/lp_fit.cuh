@@ -335,7 +335,8 @@ struct Src<float, DIM, F> {
         load(j, r);
         off_rec(r, d);
 #pragma unroll
-        for (int f = 0; f < F; ++f) b[f] = (r[REC_FH + f] - ri[REC_FH + f]) + (r[REC_FL + f] - ri[REC_FL + f]);
+        for (int f = 0; f < F; ++f)
+            b[f] = (r[rec_fh(f, F)] - ri[rec_fh(f, F)]) + (r[rec_fl(f, F)] - ri[rec_fl(f, F)]);
     }
     __device__ void off(uint32_t j, float (&d)[DIM]) const
     {
@@ -359,12 +360,26 @@ struct Src<float, DIM, F> {
     // a neighbour's record as loaded (the pipelined loops load one ahead)
     struct Rec { float v[4 * REC_F4]; };
     __device__ void load_rec(uint32_t j, Rec& r) const { load(j, r.v); }
+    // the first 32 bytes only: positions and the last field
+    __device__ void load_half(uint32_t j, Rec& r) const
+    {
+        float4 v, w;
+        ldg256(a.rec + (int64_t)j * REC_F4, v, w);
+        r.v[0] = v.x; r.v[1] = v.y; r.v[2] = v.z; r.v[3] = v.w;
+        r.v[4] = w.x; r.v[5] = w.y; r.v[6] = w.z; r.v[7] = w.w;
+    }
+    // offsets and the last field's difference from a half record
+    __device__ void unpack_last(const Rec& r, float (&d)[DIM], float& bl) const
+    {
+        off_rec(r.v, d);
+        bl = (r.v[rec_fh(F - 1, F)] - ri[rec_fh(F - 1, F)]) + (r.v[rec_fl(F - 1, F)] - ri[rec_fl(F - 1, F)]);
+    }
     __device__ void unpack(const Rec& r, float (&d)[DIM], float (&b)[F]) const
     {
         off_rec(r.v, d);
 #pragma unroll
         for (int f = 0; f < F; ++f)
-            b[f] = (r.v[REC_FH + f] - ri[REC_FH + f]) + (r.v[REC_FL + f] - ri[REC_FL + f]);
+            b[f] = (r.v[rec_fh(f, F)] - ri[rec_fh(f, F)]) + (r.v[rec_fl(f, F)] - ri[rec_fl(f, F)]);
     }
     __device__ int side(const Rec& r, uint32_t j, int k) const { return side_rec(r.v, j, k); }
     // side of j along axis k; when non-zero, also its offsets and differences
@@ -419,6 +434,13 @@ struct Src<double, DIM, F> {
 #pragma unroll
         for (int f = 0; f < F; ++f) b[f] = r.f[f] - fi[f];
     }
+    __device__ void load_half(uint32_t j, Rec& r) const { load_rec(j, r); }
+    __device__ void unpack_last(const Rec& r, double (&d)[DIM], double& bl) const
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) d[k] = offset64(a.c, k, xi[k], r.x[k]);
+        bl = r.f[F - 1] - fi[F - 1];
+    }
     __device__ int side(const Rec& r, uint32_t, int k) const
     {
         const double dk = offset64(a.c, k, xi[k], r.x[k]);
@@ -435,20 +457,20 @@ struct Src<double, DIM, F> {
 
 // Visit the neighbour list in order with the next record (and the index after
 // it) already in flight: body(j, rec) returns false to stop early.
-template <class S, class Body>
+template <bool HALF = false, class S, class Body>
 __device__ __forceinline__ void for_neighbors(const S& src, const uint32_t* nb, int cnt, Body&& body)
 {
     if (cnt <= 0) return;
     typename S::Rec nxt;
     uint32_t jn = __ldg(nb);
-    src.load_rec(jn, nxt);
+    if (HALF) src.load_half(jn, nxt); else src.load_rec(jn, nxt);
     uint32_t jn2 = cnt > 1 ? __ldg(nb + 1) : 0u;
     for (int r = 0; r < cnt; ++r) {
         const typename S::Rec cur = nxt;
         const uint32_t j = jn;
         if (r + 1 < cnt) {
             jn = jn2;
-            src.load_rec(jn, nxt);
+            if (HALF) src.load_half(jn, nxt); else src.load_rec(jn, nxt);
             if (r + 2 < cnt) jn2 = __ldg(nb + r + 2);
         }
         if (!body(j, cur)) break;
@@ -550,6 +572,22 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
         G.solve(x);
     }
     const bool refine = cf.refine == LP_REFINE_ALWAYS || (cf.refine == LP_REFINE_AUTO && ratio < (T)cf.refine_ratio);
+    if (STATS && !have_ssr && !refine) {
+        // only the gate's residual sum of the last field: half of each record
+        for_neighbors<true>(src, nb, cnt, [&](uint32_t, const Rec& rec) {
+            T d[DIM], a[N], bl;
+            src.unpack_last(rec, d, bl);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) d[k] *= invS;
+            gfd_row<T, DIM>(d, a);
+            T res = bl;
+#pragma unroll
+            for (int u = 0; u < N; ++u) res = RN<T>::fma(-a[u], x[u][F - 1], res);
+            ssr = RN<T>::fma(res, res, ssr);
+            return true;
+        });
+        have_ssr = true;
+    }
     if (refine || (STATS && !have_ssr)) {
         // The FP32 3D factor (d and U, 45 values) waits in shared memory during
         // the correction pass, which holds the solution and the correction sums:
@@ -667,40 +705,57 @@ __device__ void onesided_all(const Src<T, DIM, F>& src, const uint32_t* nb, int 
             return more;
         });
     }
+    // the 2 DIM fits in one rolled loop (one copy of its code); fit q = 2k + s
+    // leaves its k-component in shared memory and a bit in okb
+    __shared__ T osm[2 * DIM * F][FIT_THREADS];
+    unsigned okb = 0;
+#pragma unroll 1
+    for (int q = 0; q < 2 * DIM; ++q) {
+        const int k = q >> 1;
+        uint64_t mm = m[0][0];
+#pragma unroll
+        for (int qq = 1; qq < 2 * DIM; ++qq) mm = q == qq ? m[qq >> 1][qq & 1] : mm;
+        if (__popcll(mm) < DIM) continue;
+        Givens<T, DIM, F> G;
+        G.zero();
+        // rows in list order, the next record in flight
+        Rec nxt;
+        uint32_t jn = __ldg(nb + (__ffsll((long long)mm) - 1));
+        src.load_rec(jn, nxt);
+        while (mm) {
+            mm &= mm - 1;
+            const Rec cur = nxt;
+            if (mm) {
+                jn = __ldg(nb + (__ffsll((long long)mm) - 1));
+                src.load_rec(jn, nxt);
+            }
+            T d[DIM], b[F];
+            src.unpack(cur, d, b);
+#pragma unroll
+            for (int u = 0; u < DIM; ++u) d[u] *= invS;
+            G.add(d, b);
+        }
+        const T rt = G.ratio();
+        if (!(rt >= tau_rank)) continue;              // rank deficient: central derivative
+        if (!(rt >= tau)) ill = true;                 // usable only in higher precision
+        T x[DIM][F];
+        G.solve(x);
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            T v = x[0][f];
+#pragma unroll
+            for (int u = 1; u < DIM; ++u) v = k == u ? x[u][f] : v;
+            osm[q * F + f][threadIdx.x] = v * invS;
+        }
+        okb |= 1u << q;
+    }
 #pragma unroll
     for (int k = 0; k < DIM; ++k)
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            ok[k][s] = false;
-            uint64_t mm = m[k][s];
-            if (__popcll(mm) < DIM) continue;
-            Givens<T, DIM, F> G;
-            G.zero();
-            // rows in list order, the next record in flight
-            Rec nxt;
-            uint32_t jn = __ldg(nb + (__ffsll((long long)mm) - 1));
-            src.load_rec(jn, nxt);
-            while (mm) {
-                mm &= mm - 1;
-                const Rec cur = nxt;
-                if (mm) {
-                    jn = __ldg(nb + (__ffsll((long long)mm) - 1));
-                    src.load_rec(jn, nxt);
-                }
-                T d[DIM], b[F];
-                src.unpack(cur, d, b);
+            ok[k][s] = (okb >> (2 * k + s)) & 1u;
 #pragma unroll
-                for (int q = 0; q < DIM; ++q) d[q] *= invS;
-                G.add(d, b);
-            }
-            const T rt = G.ratio();
-            if (!(rt >= tau_rank)) continue;              // rank deficient: central derivative
-            if (!(rt >= tau)) ill = true;                 // usable only in higher precision
-            T x[DIM][F];
-            G.solve(x);
-#pragma unroll
-            for (int f = 0; f < F; ++f) out[k][s][f] = x[k][f] * invS;
-            ok[k][s] = true;
+            for (int f = 0; f < F; ++f) out[k][s][f] = ok[k][s] ? osm[(2 * k + s) * F + f][threadIdx.x] : T(0);
         }
 }
 

@@ -14,10 +14,14 @@ constexpr int MORTON_BITS = 21;   // bits per axis of a Morton key (one simulati
 constexpr int MAX_LEVELS = 22;    // cell levels 0..21
 constexpr int NB_WARPS = 6;       // warps per block of the neighbour query (static smem <= 48 KB)
 constexpr int NB_CAP = 2 * KMAX;  // candidate buffer per warp
-// packed fit record: floats [0,3) position hi, [3,6) position lo,
-// [6,11) field hi, [11,16) field lo (fields V, u_1..u_d, P)
+// packed fit record of F <= 5 fields: floats [0,3) position hi, [3,6)
+// position lo, [6,8) hi and lo of the last field (P in a step), then hi, lo of
+// fields 0..F-2 from float 8 on -- so the first 32 bytes hold the positions and
+// the last field
 constexpr int REC_F4 = 4;
-constexpr int REC_XH = 0, REC_XL = 3, REC_FH = 6, REC_FL = 11;
+constexpr int REC_XH = 0, REC_XL = 3;
+__host__ __device__ constexpr int rec_fh(int f, int F) { return f == F - 1 ? 6 : 8 + 2 * f; }
+__host__ __device__ constexpr int rec_fl(int f, int F) { return f == F - 1 ? 7 : 9 + 2 * f; }
 
 // status bits kept in the device status word (1 << lp_status)
 constexpr uint32_t ST_CAPACITY = 1u << LP_ERR_CAPACITY;

@@ -355,13 +355,14 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_partic
     double V = p.V[j], P = p.P[j];
     sV[i] = V;
     sP[i] = P;
-    split(V, r[REC_FH], r[REC_FL]);
-    split(P, r[REC_FH + DIM + 1], r[REC_FL + DIM + 1]);
+    constexpr int F = DIM + 2;
+    split(V, r[rec_fh(0, F)], r[rec_fl(0, F)]);
+    split(P, r[rec_fh(F - 1, F)], r[rec_fl(F - 1, F)]);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         double v = p.u[k][j];
         su[k][i] = v;
-        split(v, r[REC_FH + 1 + k], r[REC_FL + 1 + k]);
+        split(v, r[rec_fh(1 + k, F)], r[rec_fl(1 + k, F)]);
     }
 #pragma unroll
     for (int q = 0; q < REC_F4; ++q) rec[i * REC_F4 + q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
