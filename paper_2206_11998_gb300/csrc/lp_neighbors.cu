@@ -463,6 +463,7 @@ constexpr int TQ_CELLS_MAX = 4096;    // cells a group's region may span
 constexpr uint32_t TQ_CAND_MAX = 2048;   // candidates a group may test (fastest of 2048, 4096, 8192 on the gas cloud)
 constexpr int TQ_KC = 256;            // non-empty cells a group may keep
 constexpr float TQ_GAP = 2.0f;        // in radii
+constexpr int TQ_SPLIT_MIN = 4;       // smallest half a too-large group is split into
 
 struct TileBuf {
     uint32_t kj[TQ_CAP][TQ_PAD];      // prefilter hits, one column per lane
@@ -564,9 +565,11 @@ __device__ inline void bitonic_keys(uint32_t (&key)[2])
     }
 }
 
-// one group of lanes of the tile (act); all 32 lanes take part
+// one group of lanes of the tile (act); all 32 lanes take part.  false: the
+// group's region spans too many cells or candidates, nothing was written (the
+// caller splits the group or hands its particles to the per-particle kernel)
 template <int DIM, bool PER>
-__device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, uint64_t sim,
+__device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, uint64_t sim,
                            const TileLane<DIM>& me)
 {
     const unsigned lane = lane_id();
@@ -619,10 +622,7 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         nc[k] = a1 - a0 + 1;
         ncells = nc[k] < 1 ? 0 : ncells * nc[k];
     }
-    if (ncells > TQ_CELLS_MAX) {      // a scattered group: per particle instead
-        list_append(a, act, (uint32_t)i);
-        return;
-    }
+    if (ncells > TQ_CELLS_MAX) return false;     // a scattered group
     const int nct = (int)ncells;
     float rnc[3];
 #pragma unroll
@@ -675,10 +675,7 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                 nk += __popc(km);
             }
         }
-        if (ncand > TQ_CAND_MAX) {
-            list_append(a, act, (uint32_t)i);
-            return;
-        }
+        if (ncand > TQ_CAND_MAX) return false;
     }
     __syncwarp();
 
@@ -1008,6 +1005,7 @@ __device__ void tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         if (mx) atomicMax(a.counters + C_MAXCOUNT, (unsigned long long)mx);
     }
     __syncwarp();
+    return true;
 }
 
 template <int DIM, bool PER>
@@ -1051,7 +1049,25 @@ __global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile(QueryArgs a)
         const int s1 = rest ? __ffs(rest) - 1 : 32;
         const unsigned grp = vmask & ((s1 == 32 ? 0xffffffffu : ((1u << s1) - 1u)) & ~((1u << s0) - 1u));
         const uint64_t sim = __shfl_sync(0xffffffffu, mysim, s0);
-        tile_group<DIM, PER>(a, b, i, ((grp >> lane) & 1u) != 0u, sim, t);
+        // a group whose region is too large is halved (by key order: the
+        // halves are smaller regions) down to TQ_SPLIT_MIN particles; what is
+        // still too large goes to the per-particle kernel
+        unsigned stk[6];
+        int sp = 0;
+        stk[sp++] = grp;
+        while (sp > 0) {
+            const unsigned g = stk[--sp];
+            if (tile_group<DIM, PER>(a, b, i, ((g >> lane) & 1u) != 0u, sim, t)) continue;
+            const int pc = __popc(g);
+            if (pc >= 2 * TQ_SPLIT_MIN && sp + 2 <= 6) {
+                unsigned lo = 0, gg = g;                // the first pc / 2 members
+                for (int q = 0; q < pc / 2; ++q) { lo |= gg & (0u - gg); gg &= gg - 1; }
+                stk[sp++] = g & ~lo;
+                stk[sp++] = lo;
+            } else {
+                list_append(a, ((g >> lane) & 1u) != 0u, (uint32_t)i);
+            }
+        }
     }
 }
 
