@@ -56,7 +56,7 @@ def fit_flops_per_particle(m: float) -> float:
 # DRAM bytes per particle of one fit pass (split schedule, FP32), measured by ncu
 # on the 400k-particle cloud for the kernels as they are now; None when the
 # kernels change and the figure has not been re-measured
-FIT_TRAFFIC_BPP = 1010.0
+FIT_TRAFFIC_BPP = 972.0
 
 # nominal FP64 rate of a GB300 (TFLOP/s): the roofline of the FP64 fit
 FP64_PEAK_TFLOPS = 1.25
