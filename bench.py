@@ -92,6 +92,21 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(values, world, torch, dist, device):
+    """Each value's maximum over the ranks: the job takes as long as its
+    slowest rank."""
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_rate(world, n, steps, ms):
+    """Particle-updates per second of the whole job: each of the world ranks
+    advances its own n particles per step (replicas)."""
+    return world * n * steps / (ms * 1e-3)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -330,12 +345,9 @@ def run_ours(args):
         # end to end through the same C-ABI call with host buffers
         e2e = run_e2e(ctx, state, n, args, stream, lp, torch, flush)
 
-    tot = torch.tensor([total_ms, e2e["ms"]], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(tot[0]), float(tot[1])
-    value = world * n * args.steps / (total_ms * 1e-3)
-    e2e_value = world * n * args.steps / (e2e_ms * 1e-3)
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e["ms"]], world, torch, dist, "cuda")
+    value = job_rate(world, n, args.steps, total_ms)
+    e2e_value = job_rate(world, n, args.steps, e2e_ms)
 
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))

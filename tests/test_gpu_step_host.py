@@ -81,6 +81,34 @@ def test_host_step_equals_device_step(pinned, sched):
         assert s1[k] == s2[k], k
 
 
+@pytest.mark.parametrize("prec", [lp.PREC_FP32, lp.PREC_FP64])
+def test_host_step_periodic_2d(prec):
+    """The 2D periodic shear layer (minimum-image offsets, positions wrapped by
+    the mover) through the host path, both precisions."""
+    st = inputs.kh_2d(8_000, 0.03, seed=7)
+    n = st["V"].shape[0]
+    cfg = lp.make_config(2, n, precision=prec, kappa=2.2, k_max=40, gamma=1.4, periodic=(1, 1, 0),
+                         box_lo=(0, 0, 0), box_hi=(1, 1, 1), s_ref=inputs.field_scales(st))
+    c1 = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    for _ in range(3):
+        c1.step(ps, dt=0.0, cfl=0.4)
+    torch.cuda.synchronize()
+    c2 = lp.Context(cfg)
+    hs = lp.ParticleSet.from_state_host(st)
+    for _ in range(3):
+        c2.step_host(hs, dt=0.0, cfl=0.4)
+    torch.cuda.synchronize()
+    a, b = ps.to_state(), _host_state(hs)
+    assert np.array_equal(a["id"], b["id"])
+    for f in ("V", "P", "m"):
+        assert np.array_equal(a[f], b[f]), f
+    for d in range(2):
+        assert np.array_equal(a["x"][d], b["x"][d]) and np.array_equal(a["u"][d], b["u"][d]), d
+    c1.close()
+    c2.close()
+
+
 def test_host_step_fixed_dt_and_time():
     st = inputs.gas_cloud_3d(N, seed=32)
     c1 = lp.Context(_cfg(st))
