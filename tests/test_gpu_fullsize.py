@@ -1,7 +1,9 @@
 """Parity at the benchmark's full size and launch configuration.
 
-The 3D gas cloud with 2,000,000 particles (the workload bench.py times) is
-advanced one step on the GPU with the CFL time step computed on the device.
+The 3D gas cloud with 2,000,000 particles (the workload bench.py times) and
+the jet-shaped snapshot with 8.0M are advanced one step on the GPU, under the
+schedule bench.py's autotuner picks, with the CFL time step computed on the
+device.
 The oracle then evaluates, one particle at a time, the neighbour lists and the
 new state of a seeded sample of particles from the same full state, so the
 comparison is element by element on those samples.  Also: the Sod shock tube
@@ -29,13 +31,24 @@ def _built():
     oracle.build()
 
 
-def test_gas_cloud_2m_sampled_parity():
-    n = 2_000_000
-    st = inputs.gas_cloud_3d(n, seed=4)
+FULL = {
+    # the workload bench.py times by default, and its jet-shaped one (both
+    # under the schedule bench.py's autotuner picks: split fit, query tiles)
+    "gas-cloud-2M": (lambda: inputs.gas_cloud_3d(2_000_000, seed=4), 5.0 / 3.0),
+    "jet-snapshot-8M": (lambda: inputs.jet_snapshot_3d(8_000_000, seed=10), inputs.JET_GAMMA),
+}
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_sampled_parity(name):
+    make, gamma = FULL[name]
+    st = make()
+    n = st["V"].shape[0]
     sref = inputs.field_scales(st)
-    cfg = lp.make_config(3, n, precision=lp.PREC_FP32, kappa=2.2, k_max=64, k_side=8, gamma=5.0 / 3.0,
+    cfg = lp.make_config(3, n, precision=lp.PREC_FP32, kappa=2.2, k_max=64, k_side=8, gamma=gamma,
                          limiter=lp.LIM_FLAGGED, s_ref=sref)
     ctx = lp.Context(cfg)
+    ctx.set_schedule(lp.SCHED_SPLIT)
     ps = lp.ParticleSet.from_state(st)
     phi = torch.empty((n, 5), dtype=torch.float32, device="cuda")
     ctx.step(ps, dt=0.0, cfl=0.4, phi=phi)
@@ -48,9 +61,10 @@ def test_gas_cloud_2m_sampled_parity():
     rng = np.random.default_rng(123)
     q = np.sort(rng.choice(n, 400, replace=False))
     # extremes of the distribution too: the outermost particles have the largest radii
+    # (the cloud), the largest specific volumes sit by the density jump (the jet)
     r2 = st["x"][0] ** 2 + st["x"][1] ** 2 + st["x"][2] ** 2
-    q = np.unique(np.concatenate([q, np.argsort(r2)[-20:], np.argsort(r2)[:20]]))
-    ocfg = oracle.make_config(3, gamma=5.0 / 3.0, kappa=2.2, k_max=64, k_side=8, limiter=oracle.LIM_FLAGGED,
+    q = np.unique(np.concatenate([q, np.argsort(r2)[-20:], np.argsort(r2)[:20], np.argsort(st["V"])[-20:]]))
+    ocfg = oracle.make_config(3, gamma=gamma, kappa=2.2, k_max=64, k_side=8, limiter=oracle.LIM_FLAGGED,
                               s_ref=sref)
     # neighbour lists of the samples, bit-exact
     oidx, ocnt, otot, od2 = oracle.neighbors(ocfg, st["x"], st["V"], st["m"], st["id"], query=q)
