@@ -468,10 +468,12 @@ constexpr int TQ_SPLIT_MIN = 4;       // smallest half a too-large group is spli
 struct TileBuf {
     uint32_t kj[TQ_CAP][TQ_PAD];      // prefilter hits, one column per lane
     unsigned long long kc[TQ_KC];     // kept cells: start | count << 32
-    float cx[32], cy[32], cz[32];     // staged candidates: position relative to the group's origin
+    alignas(16) float cx[32];         // staged candidates: position relative to the group's origin,
+    alignas(16) float cy[32];         // read four at a time by the prefilter
+    alignas(16) float cz[32];
     uint32_t cj[32];                  // and index
-    uint32_t cstart[32], cexcl[32];
 };
+static_assert(sizeof(TileBuf) % 16 == 0, "per-warp buffers keep the 16-byte alignment of cx, cy, cz");
 
 __device__ inline float warp_minf(float v)
 {
@@ -734,21 +736,23 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                 if ((int)lane >= o) incl += v;
             }
             const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-            b.cstart[lane] = cs;
-            b.cexcl[lane] = incl - cn;
-            __syncwarp();
+            const uint32_t cex = incl - cn;       // this lane's cell: its first slot among the T
             for (uint32_t base = 0; base < T; base += 32) {
                 const uint32_t t = base + lane;
+                // slot t lies in the last non-empty cell whose first slot is <= t (first
+                // slots of non-empty cells strictly increase): count the cells starting
+                // before this batch, and those starting in it up to t by a bit mask
+                const bool here = cn > 0 && cex >= base && cex - base < 32u;
+                const uint32_t starts = __reduce_or_sync(0xffffffffu, here ? 1u << (cex - base) : 0u);
+                const int before = __popc(__ballot_sync(0xffffffffu, cn > 0 && cex < base));
+                const int cl = before - 1 + __popc(starts & (0xffffffffu >> (31u - lane)));   // in [0, 31]
+                const uint32_t cs_t = __shfl_sync(0xffffffffu, cs, cl);
+                const uint32_t cex_t = __shfl_sync(0xffffffffu, cex, cl);
                 bool keep = false;
                 float p[3] = {0.0f, 0.0f, 0.0f};
                 uint32_t j = 0;
                 if (t < T) {
-                    int lo = 0, hi = 31;                  // the last cell with cexcl <= t
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
-                    }
-                    j = b.cstart[lo] + (t - b.cexcl[lo]);
+                    j = cs_t + (t - cex_t);
                     float4 ph, pl;
                     ldg256(a.pos4 + 2 * (int64_t)j, ph, pl);
                     p[0] = split_offset<PER>(c, 0, ph.x, pl.x, oh[0], ol[0]);
@@ -792,26 +796,50 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                             hits |= (d2 <= thr ? 1u : 0u) << qq;
                         }
                     } else {
-                        // two candidates per packed FP32 instruction (per component
-                        // the same rounding as the scalar form)
+                        // four candidates per iteration, two per packed FP32 instruction
+                        // (per component the same rounding as the scalar form).  The
+                        // test d2 <= thr is the sign bit of RN(thr - d2), which is clear
+                        // exactly when d2 <= thr; a funnel shift appends it to miss, the
+                        // earlier candidate in the higher bit
                         const float2 nx = make_float2(-ri[0], -ri[0]);
                         const float2 ny = make_float2(-ri[1], -ri[1]);
                         const float2 nz = make_float2(-ri[2], -ri[2]);
-#pragma unroll 4
-                        for (int qq = 0; qq < nb; qq += 2) {
-                            const float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&b.cx[qq]), nx);
-                            float2 d2 = __fmul2_rn(dx, dx);
+                        const float2 t2 = make_float2(thr, thr);
+                        const float2 m1 = make_float2(-1.0f, -1.0f);
+                        uint32_t miss = 0;
+#pragma unroll 1
+                        for (int qq = 0; qq < nb; qq += 4) {
+                            const float4 X = *reinterpret_cast<const float4*>(&b.cx[qq]);
+                            const float2 dxa = __fadd2_rn(make_float2(X.x, X.y), nx);
+                            const float2 dxb = __fadd2_rn(make_float2(X.z, X.w), nx);
+                            float2 d2a = __fmul2_rn(dxa, dxa);
+                            float2 d2b = __fmul2_rn(dxb, dxb);
                             if (DIM > 1) {
-                                const float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&b.cy[qq]), ny);
-                                d2 = __ffma2_rn(dy, dy, d2);
+                                const float4 Y = *reinterpret_cast<const float4*>(&b.cy[qq]);
+                                const float2 dya = __fadd2_rn(make_float2(Y.x, Y.y), ny);
+                                const float2 dyb = __fadd2_rn(make_float2(Y.z, Y.w), ny);
+                                d2a = __ffma2_rn(dya, dya, d2a);
+                                d2b = __ffma2_rn(dyb, dyb, d2b);
                             }
                             if (DIM > 2) {
-                                const float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&b.cz[qq]), nz);
-                                d2 = __ffma2_rn(dz, dz, d2);
+                                const float4 Z = *reinterpret_cast<const float4*>(&b.cz[qq]);
+                                const float2 dza = __fadd2_rn(make_float2(Z.x, Z.y), nz);
+                                const float2 dzb = __fadd2_rn(make_float2(Z.z, Z.w), nz);
+                                d2a = __ffma2_rn(dza, dza, d2a);
+                                d2b = __ffma2_rn(dzb, dzb, d2b);
                             }
-                            hits |= ((d2.x <= thr ? 1u : 0u) | (d2.y <= thr ? 2u : 0u)) << qq;
+                            const float2 sa = __ffma2_rn(d2a, m1, t2);
+                            const float2 sb = __ffma2_rn(d2b, m1, t2);
+                            miss = __funnelshift_l(__float_as_uint(sa.x), miss, 1);
+                            miss = __funnelshift_l(__float_as_uint(sa.y), miss, 1);
+                            miss = __funnelshift_l(__float_as_uint(sb.x), miss, 1);
+                            miss = __funnelshift_l(__float_as_uint(sb.y), miss, 1);
                         }
-                        if (nb < 32) hits &= (1u << nb) - 1u;   // the odd last slot holds no candidate
+                        // nq candidates went in (nb rounded up to 4, at most 32): candidate
+                        // q sits at bit nq - 1 - q; reversed and shifted, at bit q
+                        const int nq = (nb + 3) & ~3;
+                        hits = ~(__brev(miss) >> (32 - nq));
+                        if (nb < 32) hits &= (1u << nb) - 1u;   // slots past nb hold no candidate
                     }
                     while (hits) {
                         const int q = __ffs(hits) - 1;
