@@ -841,15 +841,22 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                         hits = ~(__brev(miss) >> (32 - nq));
                         if (nb < 32) hits &= (1u << nb) - 1u;   // slots past nb hold no candidate
                     }
-                    while (hits) {
-                        const int q = __ffs(hits) - 1;
-                        hits &= hits - 1;
-                        const uint32_t j = b.cj[q];
-                        if ((int64_t)j != i) {
-                            if (cnt < (uint32_t)TQ_CAP) b.kj[cnt][lane] = j;
-                            ++cnt;
+                    // append the hits to this lane's column, highest slot first (the
+                    // particle itself is one of them: the exact pass below drops it,
+                    // and sorts by (d2, id), so the column's order is free).  A lane
+                    // whose hits overflow the column goes to the per-particle kernel,
+                    // so then only the count matters
+                    const uint32_t nh = (uint32_t)__popc(hits);
+                    if (cnt + nh <= (uint32_t)TQ_CAP) {
+                        uint32_t* col = &b.kj[cnt][lane];
+                        while (hits) {
+                            const int q = 31 - __clz(hits);
+                            hits ^= 1u << q;
+                            *col = b.cj[q];
+                            col += TQ_PAD;
                         }
                     }
+                    cnt += nh;
                 }
                 __syncwarp();
             }
@@ -925,7 +932,7 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const int e = (int)lane + 32 * s;
-            if (e < m) {
+            if (e < m && (int64_t)cj[s] != ip) {      // every hit but the particle itself
                 const uint32_t j = cj[s];
                 const float4 qh = ch[s];
                 const float4 ql = cl[s];
