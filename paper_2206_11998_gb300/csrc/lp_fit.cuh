@@ -239,6 +239,69 @@ struct NormalEq {
     }
 };
 
+// The FP32 normal equations of NormalEq, accumulated two values per packed
+// FP32 instruction (__ffma2_rn: per component the same rounding as __fmaf_rn,
+// so the sums are bit for bit those of NormalEq::add).  Row k of A^T [A | B]
+// is a[k] times v = (a_0 .. a_{N-1}, b_0 .. b_{F-1}) from v_k on; v is held
+// in VP aligned pairs, and row k accumulates the pairs from k / 2 on, so an
+// odd row also sums the product with v_{k-1}, which is not used.
+template <int N, int F>
+struct NormalEqPacked {
+    static constexpr int L = N + F;                  // values of v
+    static constexpr int VP = (L + 1) / 2;           // pairs (the last one padded when L is odd)
+    static constexpr int off(int k)                  // first pair of row k in P
+    {
+        int o = 0;
+        for (int r = 0; r < k; ++r) o += VP - r / 2;
+        return o;
+    }
+    static constexpr int NP = off(N);
+    float2 P[NP];
+
+    __device__ void zero()
+    {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) P[q] = make_float2(0.0f, 0.0f);
+    }
+
+    __device__ void add(const float (&a)[N], const float (&b)[F])
+    {
+        float2 v[VP];
+#pragma unroll
+        for (int p = 0; p < VP; ++p) {
+            const int j0 = 2 * p, j1 = 2 * p + 1;
+            const float x = j0 < N ? a[j0 < N ? j0 : 0] : b[j0 < N ? 0 : (j0 - N < F ? j0 - N : 0)];
+            const float y = j1 < N ? a[j1 < N ? j1 : 0] : (j1 - N < F ? b[j1 < N ? 0 : (j1 - N < F ? j1 - N : 0)] : 0.0f);
+            v[p] = make_float2(x, y);
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float2 ak = make_float2(a[k], a[k]);
+#pragma unroll
+            for (int p = k / 2; p < VP; ++p) P[off(k) + p - k / 2] = __ffma2_rn(ak, v[p], P[off(k) + p - k / 2]);
+        }
+    }
+
+    // value j (>= k) of row k
+    __device__ float at(int k, int j) const
+    {
+        const float2 q = P[off(k) + j / 2 - k / 2];
+        return (j & 1) ? q.y : q.x;
+    }
+
+    // the sums in NormalEq's layout
+    __device__ void store(NormalEq<float, N, F>& E) const
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+#pragma unroll
+            for (int l = k; l < N; ++l) E.Gm[NormalEq<float, N, F>::id(k, l)] = at(k, l);
+#pragma unroll
+            for (int f = 0; f < F; ++f) E.c[k][f] = at(k, N + f);
+        }
+    }
+};
+
 // GFD row for scaled offset e (Eq. linear_system_axb order, 1D/3D analogues)
 template <typename T, int DIM>
 __device__ inline void gfd_row(const T (&e)[DIM], T (&a)[NU<DIM>::v])
@@ -511,9 +574,9 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
     bool solved = false;
     T ratio = T(0);
     using Rec = typename Src<T, DIM, F>::Rec;
-    if (NE) {
-        NormalEq<T, N, F> E;
-        E.zero();
+    if constexpr (NE) {
+        NormalEqPacked<N, F> EP;
+        EP.zero();
         for_neighbors(src, nb, cnt, [&](uint32_t, const Rec& rec) {
             T d[DIM], a[N], b[F];
             src.unpack(rec, d, b);
@@ -526,9 +589,11 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
                 bmax = bl > bmax ? bl : bmax;
                 ssb = RN<T>::fma(bl, bl, ssb);
             }
-            E.add(a, b);
+            EP.add(a, b);
             return true;
         });
+        NormalEq<T, N, F> E;
+        EP.store(E);
         E.factor(G);
         ratio = G.ratio();
         if (ratio >= T(NE_RATIO_MIN)) {
