@@ -926,7 +926,6 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         // so keys are distinct and ordered as the floats up to 2^-17 relative;
         // the slot brings index and exact float d2 back after the sort
         uint32_t key[2], jv[2] = {0xffffffffu, 0xffffffffu};
-        float dv[2] = {INFINITY, INFINITY};
         key[0] = 0xffffffc0u | lane;
         key[1] = 0xffffffc0u | (lane + 32u);
 #pragma unroll
@@ -949,7 +948,6 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                 if (in) {
                     key[s] = (__float_as_uint(d2f) & ~63u) | (uint32_t)e;
                     jv[s] = j;
-                    dv[s] = d2f;
                 }
             }
         }
@@ -959,25 +957,23 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         else bitonic_keys<2>(key);
         {
             uint32_t js[2];
-            float ds[2];
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const unsigned slot = key[s] & 63u;
                 const uint32_t j0 = __shfl_sync(0xffffffffu, jv[0], slot & 31u);
                 const uint32_t j1 = __shfl_sync(0xffffffffu, jv[1], slot & 31u);
-                const float d0 = __shfl_sync(0xffffffffu, dv[0], slot & 31u);
-                const float d1 = __shfl_sync(0xffffffffu, dv[1], slot & 31u);
                 js[s] = slot < 32u ? j0 : j1;
-                ds[s] = slot < 32u ? d0 : d1;
             }
             jv[0] = js[0]; jv[1] = js[1];
-            dv[0] = ds[0]; dv[1] = ds[1];
         }
-        // runs of entries within rounding of their predecessor (a relative gap
-        // of at most 2^-16, which holds every pair the truncated keys may have
-        // swapped): exact order
+        // runs of entries within rounding of their predecessor: exact order.
+        // The test reads the keys' truncated d2 (below the float d2 by less
+        // than 2^-17 relative).  A pair it leaves out is more than 2^-16 apart
+        // there, so more than 2^-17 apart in float d2, far beyond the float's
+        // error: its order is the exact one
         unsigned tie[2];
         {
+            const float dv[2] = {__uint_as_float(key[0] & ~63u), __uint_as_float(key[1] & ~63u)};
             const float TOL_P = 1.52587890625e-05f;    // 2^-16
             const float prev0 = __shfl_up_sync(0xffffffffu, dv[0], 1);
             const float last0 = __shfl_sync(0xffffffffu, dv[0], 31);
