@@ -429,25 +429,36 @@ __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain(Fi
     const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     if (t >= len) return;
     const int64_t i = a.plain_list[t];
+    Src<T, DIM, F> src(a, i);
+    const int cnt = (int)a.count[i];
+    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
+    const T invS = (T)inv_scale(last_d2(src, nb, cnt));
+    // the one-sided fits first: the central stage's record and the particle's
+    // state are read after them, so they hold no registers during the fits
+    const DevCfg& c = a.c;
+    bool ill = false;
+    T out[DIM][2][F];
+    bool ok[DIM][2];
+    onesided_all<T, DIM, F>(src, nb, cnt, c.k_side, invS, IsF32<T>::v ? (T)c.tau32 : (T)c.tau64, (T)c.tau64,
+                            out, ok, ill);
+    if (IsF32<T>::v && ill) { push_redo(a, i); return; }
     const T* mid = static_cast<const T*>(a.mid);
     const int64_t cap = a.mid_cap;
-    T cdf[DIM][F], lw[F];
+    T os[DIM][2][F], lw[F];
     int q = 0;
 #pragma unroll
     for (int k = 0; k < DIM; ++k)
 #pragma unroll
-        for (int f = 0; f < F; ++f) cdf[k][f] = mid[(q++) * cap + t];
+        for (int f = 0; f < F; ++f) {
+            const T cd = mid[(q++) * cap + t];          // central derivative: where a side has no fit
+            os[k][0][f] = ok[k][0] ? out[k][0][f] : cd;
+            os[k][1][f] = ok[k][1] ? out[k][1][f] : cd;
+        }
 #pragma unroll
     for (int f = 0; f < F; ++f) lw[f] = mid[(q++) * cap + t];
     const bool mlp_skip = mid[q * cap + t] != T(0);
     Loaded<DIM> L;
     step_load<T, DIM>(a, o, i, L);          // never frozen: frozen particles are not listed
-    Src<T, DIM, F> src(a, i);
-    const int cnt = (int)a.count[i];
-    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
-    const T invS = (T)inv_scale(last_d2(src, nb, cnt));
-    T os[DIM][2][F];
-    if (!step_plain<T, DIM>(a, i, src, nb, cnt, invS, cdf, os)) return;
     step_finish<T, DIM>(a, o, i, L, os, lw, true, mlp_skip);
 }
 
