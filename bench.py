@@ -54,9 +54,11 @@ def fit_flops_per_particle(m: float) -> float:
 
 
 # DRAM bytes per particle of one fit pass (split schedule, FP32), measured by ncu
-# on the 400k-particle cloud for the kernels as they are now; None when the
-# kernels change and the figure has not been re-measured
-FIT_TRAFFIC_BPP = 972.0
+# on the 400k-particle gas cloud for the kernels as they are now (dram bytes
+# read + written by k_step_central and k_step_plain, 373.8 MB); None when the
+# kernels change and the figure has not been re-measured.  It describes the
+# gas cloud only: other workloads report no traffic
+FIT_TRAFFIC_BPP = 934.5
 
 # nominal FP64 rate of a GB300 (TFLOP/s): the roofline of the FP64 fit
 FP64_PEAK_TFLOPS = 1.25
@@ -372,7 +374,8 @@ def run_ours(args):
     fit_kernels = ("k_step_central + k_step_plain" if sched & lp.SCHED_SPLIT else "k_step") + \
         ("<float,3>" if args.precision == "fp32" else "<double,3>")
     traffic = None
-    if args.precision == "fp32" and args.estimator == "plain" and sched & lp.SCHED_SPLIT and FIT_TRAFFIC_BPP:
+    if (args.precision == "fp32" and args.estimator == "plain" and sched & lp.SCHED_SPLIT and FIT_TRAFFIC_BPP
+            and ACTIVE == "gas-cloud"):
         traffic = FIT_TRAFFIC_BPP * n
     if args.precision == "fp32":
         alu_peak = fp32_peak
