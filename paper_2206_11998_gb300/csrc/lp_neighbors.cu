@@ -799,8 +799,9 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
                         // four candidates per iteration, two per packed FP32 instruction
                         // (per component the same rounding as the scalar form).  The
                         // test d2 <= thr is the sign bit of RN(thr - d2), which is clear
-                        // exactly when d2 <= thr; a funnel shift appends it to miss, the
-                        // earlier candidate in the higher bit
+                        // exactly when d2 <= thr (a NaN d2, from non-finite positions, may
+                        // only add a hit that the exact pass rejects); a funnel shift
+                        // appends it to miss, the earlier candidate in the higher bit
                         const float2 nx = make_float2(-ri[0], -ri[0]);
                         const float2 ny = make_float2(-ri[1], -ri[1]);
                         const float2 nz = make_float2(-ri[2], -ri[2]);
