@@ -109,6 +109,15 @@ def job_rate(world, n, steps, ms):
     return world * n * steps / (ms * 1e-3)
 
 
+def fit_traffic(precision, estimator, split, workload, n):
+    """DRAM bytes of one fit pass, from the ncu figure per particle, or None
+    where no capture describes the pass: the figure is of the split schedule's
+    FP32 kernels with the plain estimator on the gas cloud."""
+    if precision == "fp32" and estimator == "plain" and split and workload == "gas-cloud" and FIT_TRAFFIC_BPP:
+        return FIT_TRAFFIC_BPP * n
+    return None
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -373,10 +382,7 @@ def run_ours(args):
     sched = ctx.schedule()
     fit_kernels = ("k_step_central + k_step_plain" if sched & lp.SCHED_SPLIT else "k_step") + \
         ("<float,3>" if args.precision == "fp32" else "<double,3>")
-    traffic = None
-    if (args.precision == "fp32" and args.estimator == "plain" and sched & lp.SCHED_SPLIT and FIT_TRAFFIC_BPP
-            and ACTIVE == "gas-cloud"):
-        traffic = FIT_TRAFFIC_BPP * n
+    traffic = fit_traffic(args.precision, args.estimator, bool(sched & lp.SCHED_SPLIT), ACTIVE, n)
     if args.precision == "fp32":
         alu_peak = fp32_peak
         alu_source = "FP32 CUDA cores: 152 SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (sm_max, peak_kind)

@@ -60,3 +60,15 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         workload = "gas-cloud"
     bench.run_reference(A())                       # returns at once: no work, no output
     assert capsys.readouterr().out == ""
+
+
+def test_fit_traffic_only_where_it_was_captured():
+    """The ncu traffic figure describes the split FP32 pass with the plain
+    estimator on the gas cloud; every other configuration reports none."""
+    import bench
+    n = 2_000_000
+    assert bench.fit_traffic("fp32", "plain", True, "gas-cloud", n) == bench.FIT_TRAFFIC_BPP * n
+    assert bench.fit_traffic("fp32", "plain", False, "gas-cloud", n) is None
+    assert bench.fit_traffic("fp64", "plain", True, "gas-cloud", n) is None
+    assert bench.fit_traffic("fp32", "mlp", True, "gas-cloud", n) is None
+    assert bench.fit_traffic("fp32", "plain", True, "jet-snapshot", n) is None
