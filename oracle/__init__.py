@@ -102,6 +102,8 @@ def lib():
             L.lpo_cfl_dt.restype = C.c_double
             L.lpo_phi.argtypes = [C.c_double]
             L.lpo_phi.restype = C.c_double
+            L.lpo_estimator_r.argtypes = [C.c_int32, _P, _P] + [C.c_double] * 5
+            L.lpo_estimator_r.restype = C.c_double
             L.lpo_riemann_star.argtypes = [C.c_double] * 7 + [_P, _P]
             L.lpo_riemann_star.restype = C.c_int
             L.lpo_riemann_exact.argtypes = [C.c_double] * 9 + [C.c_int64, _P, _P, _P, _P]
@@ -273,6 +275,16 @@ def features(cfg: Config, state: dict, query=None):
 
 def phi(r: float) -> float:
     return float(lib().lpo_phi(float(r)))
+
+
+def estimator_r(sl, sr, ell, s_i, s_ref=0.0, flat_eps=1e-6, active_frac=0.5) -> float:
+    """State estimator r of one field from its left/right one-sided derivatives
+    along each axis (sl[k], sr[k]), the nearest-neighbour distance ell and the
+    particle's value s_i."""
+    sl = _c(sl, np.float64); sr = _c(sr, np.float64)
+    assert sl.shape == sr.shape and 1 <= sl.shape[0] <= 3
+    return float(lib().lpo_estimator_r(sl.shape[0], _ptr(sl), _ptr(sr), float(ell), float(s_i), float(s_ref),
+                                       float(flat_eps), float(active_frac)))
 
 
 def riemann_star(gamma, left, right):

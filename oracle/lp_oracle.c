@@ -525,6 +525,13 @@ static double estimator_r(int dim, const double *sl, const double *sr, double el
     return r;
 }
 
+/* estimator_r of one field, exported so that the tests can pin it directly */
+double lpo_estimator_r(int32_t dim, const double *sl, const double *sr, double ell, double s_i,
+                       double s_ref, double flat_eps, double active_frac)
+{
+    return estimator_r(dim, sl, sr, ell, s_i, s_ref, flat_eps, active_frac);
+}
+
 /* ------------------------------------------------------------------------ */
 /* one LP step                                                              */
 /* ------------------------------------------------------------------------ */

@@ -71,3 +71,26 @@ def test_adam_first_step(oracle_lib):
     # first step: m_hat = g, v_hat = g^2, so w moves by lr * g / (|g| + eps)
     ref = np.array([1.0, -2.0, 0.5]) - 0.01 * g / (np.abs(g) + 1e-8)
     assert np.allclose(w, ref, rtol=0, atol=1e-15)
+
+
+def test_adam_later_steps(oracle_lib):
+    """Steps t >= 2, where beta2 and both bias corrections matter.
+    Constant gradient g: m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so the
+    bias-corrected moments are g and g^2 at every t and each step moves w by
+    lr g / (|g| + eps).  Gradient +1 then -1: m_2 = 0.9 * 0.1 - 0.1 = -0.01,
+    m_hat = -0.01 / (1 - 0.81) = -1/19; v_2 = 0.999 * 0.001 + 0.001 = 0.001999,
+    v_hat = 0.001999 / (1 - 0.998001) = 1; so step 2 moves w by +lr/19 / (1 + eps)."""
+    lr, eps = 0.01, 1e-8
+    w = np.array([1.0, -2.0]); g = np.array([0.3, -0.02])
+    mo = np.zeros(2); ve = np.zeros(2)
+    for t in range(1, 6):
+        oracle.adam(w, g, mo, ve, t, lr)
+    ref = np.array([1.0, -2.0]) - 5 * lr * g / (np.abs(g) + eps)
+    assert np.allclose(w, ref, rtol=0, atol=1e-14)
+
+    w = np.array([0.5]); mo = np.zeros(1); ve = np.zeros(1)
+    oracle.adam(w, np.array([1.0]), mo, ve, 1, lr)
+    assert abs(w[0] - (0.5 - lr / (1.0 + eps))) < 1e-15
+    oracle.adam(w, np.array([-1.0]), mo, ve, 2, lr)
+    assert abs(mo[0] + 0.01) < 1e-17 and abs(ve[0] - 0.001999) < 1e-17
+    assert abs(w[0] - (0.5 - lr / (1.0 + eps) + lr / 19.0 / (1.0 + eps))) < 1e-15
