@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -40,25 +41,47 @@ SEED = 4
 WORKLOAD = "gas-cloud-3d-2M"
 L2_FLUSH_BYTES = 256 << 20
 
-# algorithmic work per particle of the fused fit+update kernel (FP32 flops),
-# m = mean neighbour count, n = 9 unknowns, F = 5 fields, 2d = 6 half-spaces of
-# k = 8 rows with 3 unknowns:
-#   central Householder QR 2 m n^2 - 2 n^3 / 3, Q^T b and back substitution
-#   4 m n F, one refinement step 4 m n F, one-sided 6 (2 k 9 - 18 + 4 k 3 F),
-#   rates + estimator + blend ~ 500.
-def fit_flops_per_particle(m: float) -> float:
-    n, F = 9, 5
-    central = 2 * m * n * n - 2 * n ** 3 / 3 + 8 * m * n * F
-    onesided = 6 * (2 * 8 * 9 - 18 + 4 * 8 * 3 * F)
-    return central + onesided + 500.0
+# FP32 flops per particle of the fit + update pass as the kernels compute it
+# (an FMA counts 2; a multiply, add, subtract or reciprocal 1), with N = 9
+# unknowns, F = 5 fields, D = 3 axes and m neighbours:
+#   central fit, per neighbour row: offsets and field differences from the hi/lo
+#     records (2 subtractions and an add each: 3 D + 3 F), scaling (D), the nine
+#     monomials (9), then the normal equations A^T A (45 FMA) and A^T B (N F = 45
+#     FMA); once per particle the U^T D U factor (sum_k k (N - k) = 120 FMA, N
+#     reciprocals, 36 multiplies) and the semi-normal solve of F right-hand
+#     sides (2 x 36 F FMA, N reciprocals, N F multiplies);
+#   correction pass, on the share of particles that ran it (the n_refined
+#     counter): per row the row again, its residual (N F FMA) and A^T r (N F
+#     FMA), then another semi-normal solve;
+#   one-sided fits, on the share of particles that took the plain estimator:
+#     2 D fits of k_side = 8 rows, each row built from its record (3 D + 3 F + D)
+#     and rotated into a 3-unknown square-root-free Givens factor with F
+#     right-hand sides (per column: 7; per later column 5; per right-hand side 5:
+#     111 per row), plus a 3 x 3 back substitution of F right-hand sides per fit;
+#   LW and UW rates, estimator, limiter, blend and mover: about 500.
+FIT_N, FIT_F, FIT_D, FIT_KSIDE = 9, 5, 3, 8
 
 
-# DRAM bytes per particle of one fit pass (split schedule, FP32), measured by ncu
-# on the 400k-particle gas cloud for the kernels as they are now (dram bytes
-# read + written by k_step_central and k_step_plain, 373.8 MB); None when the
-# kernels change and the figure has not been re-measured.  It describes the
-# gas cloud only: other workloads report no traffic
-FIT_TRAFFIC_BPP = 934.5
+def fit_flops_per_particle(m: float, refined_frac: float = 0.0, plain_frac: float = 1.0) -> float:
+    N, F, D = FIT_N, FIT_F, FIT_D
+    row = 3 * D + 3 * F + D + 9
+    gram = 2 * (N * (N + 1) // 2 + N * F)
+    factor = 2 * 120 + N + 36
+    solve = 2 * (2 * 36 * F) + N + N * F
+    central = m * (row + gram) + factor + solve
+    correction = m * (row + 2 * 2 * N * F) + solve
+    givens_row = (3 * D + 3 * F + D) + sum(7 + 5 * (D - 1 - k) + 5 * F for k in range(D))
+    onesided = 2 * D * (FIT_KSIDE * givens_row + 2 * F * (D * (D - 1) // 2))
+    return central + refined_frac * correction + plain_frac * onesided + 500.0
+
+
+# DRAM bytes per particle of one fit pass (split schedule, FP32), measured by
+# ncu (dram bytes read + written by k_step_central and k_step_plain) on the
+# 400k-particle gas cloud; None when the kernels change and the figure has not
+# been re-measured.  At 400k the records the fit gathers (about 38 MB) fit in
+# the 129 MB L2, at 2M (190 MB) they do not, so the figure is that of the
+# 400k cloud and is reported as such, not as the 2M run's traffic.
+FIT_TRAFFIC_BPP_400K = None
 
 # nominal FP64 rate of a GB300 (TFLOP/s): the roofline of the FP64 fit
 FP64_PEAK_TFLOPS = 1.25
@@ -89,6 +112,8 @@ def parse():
                     help="mlp: train the learned estimator on this workload's own plain steps, then time "
                          "steps gated by it")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP64 and learned-estimator forms reported beside the headline")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="fp64: every fit and rate in FP64 (the plain FP64 GPU form)")
     return ap.parse_args()
@@ -109,12 +134,12 @@ def job_rate(world, n, steps, ms):
     return world * n * steps / (ms * 1e-3)
 
 
-def fit_traffic(precision, estimator, split, workload, n):
-    """DRAM bytes of one fit pass, from the ncu figure per particle, or None
-    where no capture describes the pass: the figure is of the split schedule's
-    FP32 kernels with the plain estimator on the gas cloud."""
-    if precision == "fp32" and estimator == "plain" and split and workload == "gas-cloud" and FIT_TRAFFIC_BPP:
-        return FIT_TRAFFIC_BPP * n
+def fit_traffic(precision, estimator, split, workload, n, bpp=None):
+    """DRAM bytes of one fit pass from an ncu figure per particle, or None where
+    no capture describes the pass: the figure is of the split schedule's FP32
+    kernels with the plain estimator on the gas cloud."""
+    if precision == "fp32" and estimator == "plain" and split and workload == "gas-cloud" and bpp:
+        return bpp * n
     return None
 
 
@@ -172,11 +197,38 @@ def config_dict(n, extra=None):
 # CPU oracle timing
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate(state, target_s, seed=0):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_sample_rate(state, target_s, seed=0, threads=None):
     """Time the oracle's step on a bounded random sample of the workload's
-    particles (full state visible).  Returns (updates/s, cores, sample text)."""
+    particles (full state visible), on all host cores or on `threads`.
+    Returns (updates/s, cores used, sample size, seconds)."""
     import oracle
     oracle.build()
+    if threads:
+        saved = oracle.num_threads()
+        oracle.set_num_threads(threads)
+        try:
+            return oracle_sample_rate(state, target_s, seed)
+        finally:
+            oracle.set_num_threads(saved)
     from paper_2206_11998_gb300 import inputs
     cfg = oracle.make_config(3, gamma=GAMMA, radius_mode=oracle.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
                              k_side=8, limiter=oracle.LIM_FLAGGED, s_ref=inputs.field_scales(state))
@@ -207,13 +259,13 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%s.csv" % os.environ.get("RANK", "0"))
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
-            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            fd, self.path = tempfile.mkstemp(prefix="lp_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "50"]
             if self.gpu is not None:
                 cmd += ["-i", str(self.gpu)]
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
@@ -243,6 +295,10 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
@@ -356,6 +412,11 @@ def run_ours(args):
         # end to end through the same C-ABI call with host buffers
         e2e = run_e2e(ctx, state, n, args, stream, lp, torch, flush)
 
+        # the plain FP64 GPU form and the FP32 + learned form of the same step
+        forms = None
+        if world == 1 and not args.no_forms and args.precision == "fp32" and args.estimator == "plain":
+            forms = other_forms(args, state, n, stream, lp, inputs, torch, flush)
+
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e["ms"]], world, torch, dist, "cuda")
     value = job_rate(world, n, args.steps, total_ms)
     e2e_value = job_rate(world, n, args.steps, e2e_ms)
@@ -376,13 +437,17 @@ def run_ours(args):
         per_phase[name] = entry
     fit_phase = "fit+update" if args.precision == "fp32" else "fit+update-fp64"
     fit_ms = phases[fit_phase][0] / args.steps          # one fit pass over all n particles
-    flops = fit_flops_per_particle(m_mean) * n
+    refined_frac = st["n_refined"] / (n * args.steps)
+    plain_frac = 1.0 - st["n_mlp_skip"] / (n * args.steps)
+    fpp = fit_flops_per_particle(m_mean, refined_frac if args.precision == "fp32" else 0.0, plain_frac)
+    flops = fpp * n
     achieved = flops / (fit_ms * 1e-3) / 1e12
     dominant = max(per_phase, key=lambda k: per_phase[k]["ms_per_step"])
     sched = ctx.schedule()
     fit_kernels = ("k_step_central + k_step_plain" if sched & lp.SCHED_SPLIT else "k_step") + \
         ("<float,3>" if args.precision == "fp32" else "<double,3>")
-    traffic = fit_traffic(args.precision, args.estimator, bool(sched & lp.SCHED_SPLIT), ACTIVE, n)
+    traffic = fit_traffic(args.precision, args.estimator, bool(sched & lp.SCHED_SPLIT), ACTIVE, n,
+                          FIT_TRAFFIC_BPP_400K)
     if args.precision == "fp32":
         alu_peak = fp32_peak
         alu_source = "FP32 CUDA cores: 152 SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (sm_max, peak_kind)
@@ -392,16 +457,22 @@ def run_ours(args):
     roofline = {"kernel": fit_kernels + " (fit+update pass)", "dominant_phase": dominant, "bound": "alu",
                 "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                 "peak_source": alu_source,
-                "flops_per_particle": fit_flops_per_particle(m_mean), "mean_neighbors": m_mean,
-                "traffic": traffic,
+                "flops_per_particle": fpp, "flop_model": "the operations the kernels run: normal equations, "
+                "U^T D U factor and solve; correction pass on the refined share; one-sided Givens fits on the "
+                "plain-estimator share", "mean_neighbors": m_mean, "refined_frac": refined_frac,
+                "plain_frac": plain_frac, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the fit kernels on the "
-                                  "400k-particle cloud, scaled by particles (profiles/k_step_split_gas_cloud_400k.md)"
+                                  "400k-particle cloud, scaled by particles (at 400k the gathered records fit in L2)"
                                   if traffic else None}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, q_n, secs = oracle_sample_rate(state, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "oracle step of %d random particles of the 2M cloud (full state visible), %.1f s" % (q_n, secs)}
+        rate1, _, q1, secs1 = oracle_sample_rate(state, max(2.0, args.cpu_seconds / 4), seed=1, threads=1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": "oracle step of %d random particles, %.1f s" % (q1, secs1)},
+               "sample": "oracle step of %d random particles of the %s cloud (full state visible), %.1f s"
+                         % (q_n, size_tag(n), secs)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -419,7 +490,7 @@ def run_ours(args):
                         "d2h_bytes_per_step": e2e["d2h"],
                         "api": "lp_step_host on page-locked host arrays (state copied in; the new state "
                                "written into the host arrays by the step's kernels)"},
-                "gpu_launches": launches, "clocks": clocks, "phases": per_phase}
+                "gpu_launches": launches, "clocks": clocks, "phases": per_phase, "forms": forms}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -463,6 +534,102 @@ def train_gate(lp, inputs, state, n, stream, torch):
     return params, {"train_samples": int(X.shape[0]), "train_epochs": 20, "train_s": secs,
                     "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "tau_lo": tau,
                     "calibrated_miss": MLP_MISS}
+
+
+def other_forms(args, state, n, stream, lp, inputs, torch, flush):
+    """The plain FP64 GPU form and the FP32 + learned-estimator form of the
+    headline's step on the same workload, timed like it (L2 flushed between
+    steps, CUDA events on the stream), and the one-step error of each FP32 form
+    against the FP64 form from the same initial state with the same dt.  The
+    FP64 form is itself within 1e-12 of the FP64 oracle in the parity tests."""
+    sref = inputs.field_scales(state)
+    base = dict(radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX, k_side=8, gamma=GAMMA,
+                limiter=lp.LIM_FLAGGED, s_ref=sref)
+    out = {}
+
+    def timed(ctx, steps, warmup, graph=False):
+        ps = lp.ParticleSet.from_state(state)
+        for _ in range(warmup):
+            ctx.step(ps, dt=0.0, cfl=CFL, stream=stream)
+        if graph:
+            ctx.graph_capture(ps, None, 1, dt=0.0, cfl=CFL, stream=stream)
+            ctx.graph_launch(stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            if graph:
+                ctx.graph_launch(stream=stream)
+            else:
+                ctx.step(ps, dt=0.0, cfl=CFL, stream=stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    def one_step(ctx, dt):
+        ps = lp.ParticleSet.from_state(state)
+        ctx.reset_stats(stream=stream)
+        ctx.step(ps, dt=dt, cfl=CFL, stream=stream)
+        stream.synchronize()
+        idx = ps.id.long()
+        byid = lambda t: torch.empty_like(t).index_copy_(0, idx, t)
+        return {"V": byid(ps.V), "P": byid(ps.P), "u": [byid(a) for a in ps.u]}, ctx.stats(stream=stream)
+
+    s0 = {"V": torch.as_tensor(state["V"], device="cuda"), "P": torch.as_tensor(state["P"], device="cuda"),
+          "u": [torch.as_tensor(a, device="cuda") for a in state["u"]]}
+
+    def errors(g, o, dt):
+        e = {}
+        for nm, a, b, z in [("V", g["V"], o["V"], s0["V"]), ("P", g["P"], o["P"], s0["P"])] + [
+                ("u%d" % k, g["u"][k], o["u"][k], s0["u"][k]) for k in range(3)]:
+            d = float((a - b).abs().max())
+            e[nm] = d / max(float(b.abs().max()), 1e-300)
+            e["rate_" + nm] = d / max(float((b - z).abs().max()), 1e-300)
+        return e
+
+    try:
+        c64 = lp.Context(lp.make_config(3, n, precision=lp.PREC_FP64, **base))
+        ref, st64 = one_step(c64, 0.0)
+        dt = st64["dt"]
+        k64 = max(2, min(args.steps, 3))
+        ms64 = timed(c64, k64, 1)
+        c64.close()
+        out["fp64"] = {"ms_per_step": ms64, "value": n / (ms64 * 1e-3), "steps": k64, "dtype": "f64",
+                       "form": "every fit, rate and the state in FP64 on the GPU"}
+        c32 = lp.Context(lp.make_config(3, n, precision=lp.PREC_FP32, **base))
+        g32, _ = one_step(c32, dt)
+        c32.close()
+        out["accuracy_vs_fp64_form"] = {"fp32": errors(g32, ref, dt), "dt": dt,
+                                        "note": "one step from the initial state with the FP64 form's CFL dt; "
+                                                "per field max|a - b| / max|b| for the state, and for the "
+                                                "rates (s^{n+1} - s^n)/dt"}
+    except Exception as exc:                                  # reported, never fatal to the headline
+        out["fp64_error"] = repr(exc)
+        ref = None
+    try:
+        params, info = train_gate(lp, inputs, state, n, stream, torch)
+        cm = lp.Context(lp.make_config(3, n, precision=lp.PREC_FP32, estimator=lp.EST_MLP,
+                                       mlp_tau_lo=info["tau_lo"], **base))
+        cm.mlp_set_params(params)
+        if ref is not None:
+            gm, stm = one_step(cm, dt)
+            out["accuracy_vs_fp64_form"]["fp32_learned"] = errors(gm, ref, dt)
+            info["skipped"] = stm["n_mlp_skip"]
+        ms_e = timed(cm, args.steps, args.warmup)
+        ms_g = timed(cm, args.steps, 1, graph=True)
+        cm.close()
+        cfg = lp.make_config(3, n, precision=lp.PREC_FP32, estimator=lp.EST_MLP, mlp_tau_lo=info["tau_lo"], **base)
+        ps = lp.ParticleSet.from_state(state)
+        info.update(audit_gate(lp, inputs, ps, n, cfg, params, stream, torch))
+        del ps
+        out["fp32_learned"] = {"ms_per_step": ms_g, "value": n / (ms_g * 1e-3), "steps": args.steps,
+                               "eager_ms_per_step": ms_e, "dtype": "f32",
+                               "form": "FP32 fits, learned state estimator (plain estimator as fallback), "
+                                       "the step replayed from a captured CUDA graph",
+                               "learned_gate": info}
+    except Exception as exc:
+        out["learned_error"] = repr(exc)
+    return out
 
 
 def audit_gate(lp, inputs, ps, n, cfg, params, stream, torch):

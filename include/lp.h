@@ -190,6 +190,7 @@ typedef struct {
     int64_t n_mlp_miss;        /* ... of which the plain estimator flags (audit mode) */
     int64_t n_query_fallback;  /* particles of the last neighbour build listed by the warp-per-particle
                                   query (more than 64 neighbours, or a tile spread over too many cells) */
+    int64_t n_refined;         /* FP32 central fits of lp_step that ran the correction pass */
 } lp_stats;
 
 typedef struct lp_ctx lp_ctx;
@@ -247,13 +248,17 @@ lp_status lp_onesided_derivs(lp_ctx *ctx, const lp_particles *p, const double *c
  *   t      : optional device float64 scalar, incremented by dt on the device.
  *   diag   : optional device outputs (any may be NULL): flag uint8 [n],
  *            phi float32 [n][nf], r float32 [n][nf] (nf = dim + 2),
- *            features float32 [n][8] (see lp_mlp_*).
+ *            features float32 [n][8] (see lp_mlp_*), gate_p float32 [n].
  */
 typedef struct {
     uint8_t *flag;
     float *phi;
     float *r;
     float *features;   /* float32 [n][8]: the learned estimator's inputs */
+    float *gate_p;     /* float32 [n]: LP_EST_MLP only, the learned estimator's
+                          probability that the particle is flagged (a particle
+                          below mlp_tau_lo skips the plain estimator); frozen
+                          boundary particles get 0; not written otherwise */
 } lp_step_diag;
 
 lp_status lp_step(lp_ctx *ctx, lp_particles *p, double dt, double cfl, double *t,
@@ -355,9 +360,12 @@ const char *lp_phase_name(int32_t phase);
  * Scratch: one fixed device array inside the library, sized for
  * LP_NOALLOC_MAX_N particles (about 6 MiB), which every GPU that loads the
  * library holds until the process exits.  n > LP_NOALLOC_MAX_N returns
- * LP_ERR_CAPACITY without enqueuing anything.  The first call on a device looks
- * up the array's device address (a one-time set-up per device, made with that
- * device current); make that first call before any stream capture.  All calls
+ * LP_ERR_CAPACITY without enqueuing anything.  Each call made outside stream
+ * capture looks up the array's device address on the current device (no
+ * allocation; this also follows a cudaDeviceReset); a call on a capturing
+ * stream uses the address of the last call outside capture on that device, so
+ * make one call on each device before any stream capture (LP_ERR_CUDA
+ * otherwise).  All calls
  * share the one array: calls whose work overlaps on the GPU (different streams,
  * or different host threads) race and corrupt each other's results, so
  * serialise them.  No cudaMalloc, cudaFree or allocating library routine is

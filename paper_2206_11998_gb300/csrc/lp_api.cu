@@ -609,7 +609,10 @@ lp_status step_prologue(lp_ctx* c, lp_particles* p, const int64_t* offsets, int3
         o.u[k] = p->u[k < dim ? k : 0];
     }
     o.V = p->V; o.P = p->P; o.m = p->m; o.id = p->id;
-    if (diag) { o.flag = diag->flag; o.phi = diag->phi; o.r = diag->r; o.features = diag->features; }
+    if (diag) {
+        o.flag = diag->flag; o.phi = diag->phi; o.r = diag->r; o.features = diag->features;
+        o.gate_p = diag->gate_p;
+    }
     a.mlp_w = reinterpret_cast<const __nv_bfloat16*>(c->mlp_bf16);
     o.dt = c->dt_dev;
     *n_out = n;
@@ -943,6 +946,7 @@ lp_status lp_get_stats(lp_ctx* c, lp_stats* out, lp_stream stream)
     out->n_mlp_skip = (int64_t)h[C_MLP_SKIP];
     out->n_mlp_miss = (int64_t)h[C_MLP_MISS];
     out->n_query_fallback = (int64_t)h[C_QFB_LEN];
+    out->n_refined = (int64_t)h[C_REFINED];
     return LP_OK;
 }
 

@@ -564,7 +564,8 @@ constexpr float NE_RATIO_MIN = 0.02f;
 // rotations did not give it.
 template <typename T, int DIM, int F, bool STATS = false>
 __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau,
-                           const DevCfg& cf, T (&x)[NU<DIM>::v][F], FitStats<T>* st = nullptr)
+                           const DevCfg& cf, T (&x)[NU<DIM>::v][F], FitStats<T>* st = nullptr,
+                           bool* refined = nullptr)
 {
     constexpr int N = NU<DIM>::v;
     constexpr bool NE = sizeof(T) == 4;
@@ -637,6 +638,7 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
         G.solve(x);
     }
     const bool refine = cf.refine == LP_REFINE_ALWAYS || (cf.refine == LP_REFINE_AUTO && ratio < (T)cf.refine_ratio);
+    if (refined) *refined = refine;
     if (STATS && !have_ssr && !refine) {
         // only the gate's residual sum of the last field: half of each record
         for_neighbors<true>(src, nb, cnt, [&](uint32_t, const Rec& rec) {

@@ -17,6 +17,7 @@ struct StepOut {
     float* phi;
     float* r;
     float* features;
+    float* gate_p;
     const double* dt;
 };
 
@@ -142,6 +143,7 @@ __device__ inline bool step_load(const FitArgs& a, const StepOut& o, int64_t i, 
     o.m[i] = a.sm[i];
     o.id[i] = L.id;
     if (o.flag) o.flag[i] = 0;
+    if (o.gate_p && c.estimator == LP_EST_MLP) o.gate_p[i] = 0.0f;
     if (o.phi) for (int f = 0; f < F; ++f) o.phi[i * F + f] = 1.0f;
     if (o.r) for (int f = 0; f < F; ++f) o.r[i * F + f] = 1.0f;
     return true;
@@ -161,7 +163,10 @@ __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t 
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
     T cd[N][F];
     FitStats<T> fst = {T(0), T(0), T(0), T(0)};
-    if (central_fit<T, DIM, F, GATE>(src, nb, cnt, invS, tau, c, cd, &fst)) {
+    bool refined = false;
+    const int ill = central_fit<T, DIM, F, GATE>(src, nb, cnt, invS, tau, c, cd, &fst, &refined);
+    if (IsF32<T>::v) warp_count(a.counters, C_REFINED, refined);
+    if (ill) {
         if (IsF32<T>::v) { push_redo(a, i); return false; }
         T lin[DIM][F];
 #pragma unroll
@@ -188,7 +193,9 @@ __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t 
 #pragma unroll
             for (int k = 0; k < MLP_IN; ++k) o.features[i * MLP_IN + k] = xf[k];
         if (c.estimator == LP_EST_MLP) {
-            mlp_skip = mlp_prob(xf, a.mlp_w) < c.mlp_tau_lo;
+            const float pg = mlp_prob(xf, a.mlp_w);
+            if (o.gate_p) o.gate_p[i] = pg;
+            mlp_skip = pg < c.mlp_tau_lo;
             warp_count(a.counters, C_MLP_SKIP, mlp_skip);
             warp_count(a.counters, C_MLP_UNCERTAIN, !mlp_skip);
         }

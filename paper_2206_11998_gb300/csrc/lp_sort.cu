@@ -560,19 +560,30 @@ constexpr int NA_MAX_DEVICES = 64;
 std::mutex na_mutex;
 unsigned char* na_ptr[NA_MAX_DEVICES] = {};
 
-// Once per device, with that device current: the device address of the array.
-cudaError_t noalloc_setup(unsigned char** out)
+// The device address of the array on the current device.  Outside stream
+// capture it is looked up again on every call, so an address cached before a
+// cudaDeviceReset (after which the runtime loads the module again, possibly at
+// another address) is never used.  While `s` is capturing, no runtime call that
+// could load the module is made: the address cached by the last call on this
+// device outside capture is used, and a device never set up that way is an
+// error.
+cudaError_t noalloc_setup(cudaStream_t s, unsigned char** out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(na_mutex);
-    if (!na_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, noalloc_scratch);
         if (e != cudaSuccess) return e;
         na_ptr[dev] = static_cast<unsigned char*>(p);
+    } else if (!na_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = na_ptr[dev];
     return cudaSuccess;
@@ -598,8 +609,8 @@ extern "C" lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double* 
     if (n == 0) return LP_OK;
     if (!x0 || (dim > 1 && !x1) || (dim > 2 && !x2)) return LP_ERR_ARG;
     unsigned char* base = nullptr;
-    if (noalloc_setup(&base) != cudaSuccess) return LP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    if (noalloc_setup(s, &base) != cudaSuccess) return LP_ERR_CUDA;
     uint64_t* keys[2] = {reinterpret_cast<uint64_t*>(base + NA_KEYS0), reinterpret_cast<uint64_t*>(base + NA_KEYS1)};
     uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(base + NA_VALS0), reinterpret_cast<uint32_t*>(base + NA_VALS1)};
     uint32_t* hist = reinterpret_cast<uint32_t*>(base + NA_HIST);

@@ -75,14 +75,22 @@ class Stats(C.Structure):
                 ("n_fp64_redo", C.c_int64), ("n_linear", C.c_int64), ("n_nofit", C.c_int64),
                 ("n_overflow", C.c_int64), ("n_nonfinite", C.c_int64), ("n_mlp_uncertain", C.c_int64),
                 ("max_count", C.c_uint32), ("status", C.c_uint32), ("kernel_launches", C.c_int64),
-                ("n_mlp_skip", C.c_int64), ("n_mlp_miss", C.c_int64), ("n_query_fallback", C.c_int64)]
+                ("n_mlp_skip", C.c_int64), ("n_mlp_miss", C.c_int64), ("n_query_fallback", C.c_int64),
+                ("n_refined", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class StepDiag(C.Structure):
-    _fields_ = [("flag", C.c_void_p), ("phi", C.c_void_p), ("r", C.c_void_p), ("features", C.c_void_p)]
+    _fields_ = [("flag", C.c_void_p), ("phi", C.c_void_p), ("r", C.c_void_p), ("features", C.c_void_p),
+                ("gate_p", C.c_void_p)]
+
+
+def _diag(flag, phi, r, features, gate_p):
+    d = StepDiag()
+    d.flag, d.phi, d.r, d.features, d.gate_p = _ptr(flag), _ptr(phi), _ptr(r), _ptr(features), _ptr(gate_p)
+    return d
 
 
 _lib = None
@@ -254,10 +262,28 @@ def mlp_init_params(seed):
 
 
 def sort_keys_noalloc(x, keys_out, perm_out, stream=None):
-    """Morton keys and sort order of positions x (list of device float64 tensors)
-    into caller buffers, with the library's fixed scratch (no allocation)."""
+    """Morton keys and sort order of positions x (list of 1 to 3 contiguous CUDA
+    float64 tensors of one length n) into caller buffers keys_out (CUDA int64,
+    at least n) and perm_out (CUDA int32, at least n), with the library's fixed
+    scratch (no allocation)."""
+    import torch
+    if not 1 <= len(x) <= 3:
+        raise ValueError("sort_keys_noalloc: 1 to 3 position arrays")
+    n = int(x[0].shape[0])
+
+    def need(t, dtype, what, length):
+        if (not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous()
+                or t.dim() != 1 or t.shape[0] < length):
+            raise ValueError("sort_keys_noalloc: %s must be a contiguous 1-D CUDA %s tensor of length >= %d"
+                             % (what, dtype, length))
+    for k, a in enumerate(x):
+        need(a, torch.float64, "x[%d]" % k, n)
+        if a.shape[0] != n:
+            raise ValueError("sort_keys_noalloc: the position arrays differ in length")
+    need(keys_out, torch.int64, "keys_out", n)
+    need(perm_out, torch.int32, "perm_out", n)
     xs = [_ptr(a) for a in x] + [None] * (3 - len(x))
-    _check(lib().lp_sort_keys_noalloc(len(x), int(x[0].shape[0]), xs[0], xs[1], xs[2], _ptr(keys_out),
+    _check(lib().lp_sort_keys_noalloc(len(x), n, xs[0], xs[1], xs[2], _ptr(keys_out),
                                       _ptr(perm_out), _stream(stream)), "lp_sort_keys_noalloc")
 
 
@@ -326,35 +352,26 @@ class Context:
         return out
 
     def step(self, ps: ParticleSet, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None, features=None,
-             stream=None):
+             gate_p=None, stream=None):
         p = ps.struct()
-        d = StepDiag()
-        d.flag, d.phi, d.r = (_ptr(flag) if flag is not None else None, _ptr(phi) if phi is not None else None,
-                              _ptr(r) if r is not None else None)
-        d.features = _ptr(features) if features is not None else None
+        d = _diag(flag, phi, r, features, gate_p)
         _check(lib().lp_step(self.h, C.byref(p), float(dt), float(cfl), _ptr(t), C.byref(d), _stream(stream)),
                "lp_step")
 
     def step_host(self, ps: ParticleSet, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None, features=None,
-                  stream=None):
+                  gate_p=None, stream=None):
         """lp_step on a ParticleSet of host (CPU, ideally pinned) tensors; t and the
         diagnostics are device tensors as for step."""
         p = ps.struct()
-        d = StepDiag()
-        d.flag, d.phi, d.r = (_ptr(flag) if flag is not None else None, _ptr(phi) if phi is not None else None,
-                              _ptr(r) if r is not None else None)
-        d.features = _ptr(features) if features is not None else None
+        d = _diag(flag, phi, r, features, gate_p)
         _check(lib().lp_step_host(self.h, C.byref(p), float(dt), float(cfl), _ptr(t), C.byref(d), _stream(stream)),
                "lp_step_host")
 
     def step_batched(self, ps: ParticleSet, offsets, nsim, dt=0.0, cfl=0.4, t=None, flag=None, phi=None, r=None,
-                     features=None, stream=None):
+                     features=None, gate_p=None, stream=None):
         """One step of nsim simulations stored back to back; offsets: device int64 [nsim + 1]."""
         p = ps.struct()
-        d = StepDiag()
-        d.flag, d.phi, d.r = (_ptr(flag) if flag is not None else None, _ptr(phi) if phi is not None else None,
-                              _ptr(r) if r is not None else None)
-        d.features = _ptr(features) if features is not None else None
+        d = _diag(flag, phi, r, features, gate_p)
         _check(lib().lp_step_batched(self.h, C.byref(p), _ptr(offsets), int(nsim), float(dt), float(cfl), _ptr(t),
                                      C.byref(d), _stream(stream)), "lp_step_batched")
 

@@ -56,3 +56,19 @@ def test_host_side_argument_errors_without_gpu():
     assert L.lp_step_host(None, None, 0.0, 0.4, None, None, None) == lp.ERR_ARG
     assert L.lp_destroy(None) == lp.OK
     assert L.lp_status_string(lp.ERR_CAPACITY).decode().startswith("particle count")
+
+
+def test_noalloc_binding_checks_its_buffers():
+    """The binding refuses buffers the entry point would overrun or misread
+    (wrong dtype, host memory, too short) before calling the library."""
+    torch = pytest.importorskip("torch")
+    from paper_2206_11998_gb300 import lp
+    x = [torch.zeros(10, dtype=torch.float64)]
+    keys = torch.zeros(10, dtype=torch.int64)
+    perm = torch.zeros(10, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        lp.sort_keys_noalloc(x, keys, perm)                      # host tensors
+    with pytest.raises(ValueError):
+        lp.sort_keys_noalloc([torch.zeros(10, dtype=torch.float32)], keys, perm)
+    with pytest.raises(ValueError):
+        lp.sort_keys_noalloc([], keys, perm)

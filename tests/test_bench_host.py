@@ -63,12 +63,32 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
 
 def test_fit_traffic_only_where_it_was_captured():
-    """The ncu traffic figure describes the split FP32 pass with the plain
-    estimator on the gas cloud; every other configuration reports none."""
+    """An ncu traffic figure describes the split FP32 pass with the plain
+    estimator on the gas cloud; every other configuration, and a kernel whose
+    figure is stale (None), reports none."""
     import bench
     n = 2_000_000
-    assert bench.fit_traffic("fp32", "plain", True, "gas-cloud", n) == bench.FIT_TRAFFIC_BPP * n
-    assert bench.fit_traffic("fp32", "plain", False, "gas-cloud", n) is None
-    assert bench.fit_traffic("fp64", "plain", True, "gas-cloud", n) is None
-    assert bench.fit_traffic("fp32", "mlp", True, "gas-cloud", n) is None
-    assert bench.fit_traffic("fp32", "plain", True, "jet-snapshot", n) is None
+    assert bench.fit_traffic("fp32", "plain", True, "gas-cloud", n, 900.0) == 900.0 * n
+    assert bench.fit_traffic("fp32", "plain", True, "gas-cloud", n, None) is None
+    assert bench.fit_traffic("fp32", "plain", False, "gas-cloud", n, 900.0) is None
+    assert bench.fit_traffic("fp64", "plain", True, "gas-cloud", n, 900.0) is None
+    assert bench.fit_traffic("fp32", "mlp", True, "gas-cloud", n, 900.0) is None
+    assert bench.fit_traffic("fp32", "plain", True, "jet-snapshot", n, 900.0) is None
+
+
+def test_fit_flop_model_counts_the_work_the_kernels_do():
+    """The flop model charges the normal equations per neighbour row, the
+    correction pass only on the refined share, and the one-sided fits only on
+    the plain-estimator share; each part by its operation count."""
+    import bench
+    m = 44.7
+    full = bench.fit_flops_per_particle(m, 1.0, 1.0)
+    none = bench.fit_flops_per_particle(m, 0.0, 0.0)
+    # per row of the central fit: 36 to build it, 180 for the 90 FMA of the Gram
+    # matrix and A^T B; factor 285 and solve 774 once
+    assert none == m * 216 + 285 + 774 + 500
+    # the correction pass: the row again (36) and 2 x 45 FMA, and a solve
+    assert bench.fit_flops_per_particle(m, 1.0, 0.0) - none == m * (36 + 180) + 774
+    # one-sided: 6 fits of 8 rows, 138 flops a row, and 30 for each back substitution
+    assert bench.fit_flops_per_particle(m, 0.0, 1.0) - none == 6 * (8 * 138 + 30)
+    assert 17_000 < bench.fit_flops_per_particle(m, 0.03, 1.0) < 20_000 < full

@@ -14,7 +14,8 @@ import pytest
 
 import oracle
 from paper_2206_11998_gb300 import inputs, lp
-from tests.gpu_util import by_id, ensure_built
+from tests import parity
+from tests.gpu_util import by_id, ensure_built, state_by_id
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -193,3 +194,93 @@ def test_learned_gate_gains_over_plain_estimator():
     assert skip > 0.4, skip
     assert miss < 0.05, miss
     assert gated_ms < 0.93 * plain_ms, (gated_ms, plain_ms)
+
+
+_GATE = {}
+
+
+def _gate_params():
+    """(master weights, calibrated tau) of the gate trained as above, once per module."""
+    if not _GATE:
+        ctx, _, _, _, tau = _trained_gate()
+        _GATE["params"] = ctx.mlp_get_params()[0]
+        _GATE["tau"] = tau
+        ctx.close()
+    return _GATE["params"], _GATE["tau"]
+
+
+def test_learned_gate_step_matches_oracle():
+    """The gated FP32 step against the FP64 oracle, on a cloud the gate was not
+    trained on.
+      - the in-kernel features equal the oracle's definition (FP32 fit accuracy);
+      - the in-kernel gate probability equals the oracle's FP64 forward pass of
+        the same BF16 weights on the GPU's features (FP32 accumulation);
+      - the gate's skip decisions equal those the oracle takes from its own
+        features, except within the band the feature error allows around tau;
+      - with the GPU's gate decisions forced (phi = 1 where it skipped), the
+        oracle's new state equals the GPU's within 1e-5 per field, and its rates
+        within the bars of test_gpu_parity.py;
+      - what the learned call costs: the distance of the gated state from the
+        oracle's plain-estimator step is reported (not a parity bar: it is the
+        effect of the flags the gate misses)."""
+    params, tau = _gate_params()
+    st = inputs.gas_cloud_3d(30_011, seed=19)
+    n = st["V"].shape[0]
+    sref = inputs.field_scales(st)
+    cfg = lp.make_config(3, n, kappa=2.2, k_max=64, gamma=5.0 / 3.0, s_ref=sref, estimator=lp.EST_MLP,
+                         mlp_tau_lo=tau)
+    ctx = lp.Context(cfg)
+    ctx.mlp_set_params(params)
+    _, wb = ctx.mlp_get_params()
+    ps = lp.ParticleSet.from_state(st)
+    feats = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    gp = torch.empty(n, dtype=torch.float32, device="cuda")
+    flag = torch.empty(n, dtype=torch.uint8, device="cuda")
+    phi = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+    ctx.step(ps, dt=0.0, cfl=0.4, features=feats, gate_p=gp, flag=flag, phi=phi)
+    torch.cuda.synchronize()
+    dt = ctx.stats()["dt"]
+    ids = ps.id.cpu().numpy().astype(np.int64)
+    gf = by_id(ids, feats.cpu().numpy()).astype(np.float64)
+    gpp = by_id(ids, gp.cpu().numpy()).astype(np.float64)
+    gflag = by_id(ids, flag.cpu().numpy())
+    gphi = by_id(ids, phi.cpu().numpy())
+    ocfg = oracle.make_config(3, gamma=5.0 / 3.0, kappa=2.2, k_max=64, s_ref=sref)
+    W1, b1, w2, b2 = _unpack(wb)
+    # features and the in-kernel forward pass
+    of = oracle.features(ocfg, st)
+    assert (np.abs(gf - of) / (1.0 + np.abs(of))).max() < 2e-3
+    _, p_on_gpu_features = oracle.mlp_forward(gf, W1, b1, w2, b2)
+    assert np.abs(gpp - p_on_gpu_features).max() < 2e-6
+    # skip decisions: the oracle's own features through the same weights
+    _, p_oracle = oracle.mlp_forward(of, W1, b1, w2, b2)
+    skip = gpp < tau
+    oskip = p_oracle < tau
+    differ = np.nonzero(skip != oskip)[0]
+    near = np.abs(p_oracle[differ] - tau) < 1e-3
+    print("gate: skipped %d of %d, decisions differing from the oracle's %d (all within 1e-3 of tau: %s)"
+          % (skip.sum(), n, len(differ), bool(near.all())))
+    assert skip.mean() > 0.3
+    assert near.all() and len(differ) <= max(3, n // 1000)
+    # the state with the GPU's gate decisions forced
+    forced = np.full((n, 5), np.nan)
+    forced[skip] = 1.0
+    q = np.arange(n)
+    o = oracle.step(ocfg, st, dt, forced_phi=forced)
+    assert np.all(gflag[skip] == 0) and np.all(gphi[skip] == 1.0)
+    o, ndiff = parity.resolve(ocfg, st, q, lp.PREC_FP32, gflag, gphi, o, dt, max(3, n // 500), forced=forced)
+    g = state_by_id(ps, None)
+    errs, rates = parity.field_and_rate_errors(3, st, g, o, dt)
+    print("gated step vs oracle (gate forced): ambiguous %d; fields %s; rates %s" % (ndiff, errs, rates))
+    for k, e in errs.items():
+        assert e < 1e-5, (k, errs)
+    for k, e in rates.items():
+        assert e < 1e-4, (k, rates)
+    # the cost of the learned call against the plain estimator (reported)
+    op = oracle.step(ocfg, st, dt)
+    cost, cost_rates = parity.field_and_rate_errors(3, st, g, op, dt)
+    missed = int(((op["flag"] == 1) & skip).sum())
+    print("gated step vs the oracle's plain estimator: missed flags %d of %d; fields %s; rates %s"
+          % (missed, int(op["flag"].sum()), cost, cost_rates))
+    assert max(cost[k] for k in ("V", "u0", "u1", "u2", "P")) < 1e-2
+    ctx.close()

@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from paper_2206_11998_gb300 import inputs, lp
+from tests import parity
 from tests.gpu_util import by_id, ensure_built, gpu_neighbor_ids, normwise, state_by_id
 
 pytestmark = pytest.mark.gpu
@@ -319,6 +320,24 @@ def test_onesided_derivs_match_oracle():
 # one LP step
 # ---------------------------------------------------------------------------
 
+# Rate tolerances.  The state after a step, s + dt rate, hides rate errors
+# behind the size of s, so the rates (s^{n+1} - s^n) / dt are compared too.
+# Each rate is a sum of products of state values and derivatives (LW: s_t from
+# first derivatives, dt/2 s_tt from products of first derivatives and from
+# second derivatives; UW: one-sided first derivatives).  FP64: the derivatives
+# agree to FP64_DERIV_TOL = 1e-11; a product of two such factors and the sums
+# over axes stay within 1e-9.  FP32: where a rate is led by first derivatives
+# (the velocity rates, -V grad P, and every rate of a moving state) its error is
+# that of the gradients, FP32_GRAD_TOL, times at most 2 for a product and 3 for
+# the sum over axes: 6e-5.  The V and P rates of a state at rest have no
+# first-order term (div u = 0) and are led by the Laplacian of P; on these
+# smooth workloads its FP32 error is cond(A) u ~ 30 x 6e-8 times the share of
+# the curvature in b = g.d + d^T H d / 2, at most ~40 at the cloud's edge
+# (|grad P| r / |H| h), i.e. 7e-5.  Bar: 1e-4 for every field.
+RATE_TOL = {lp.PREC_FP64: {"V": 1e-9, "u": 1e-9, "P": 1e-9},
+            lp.PREC_FP32: {"V": 1e-4, "u": 1e-4, "P": 1e-4}}
+
+
 def _step_parity(st, cfg, dt, tol, cfl=0.4, check_dt=False):
     n = st["V"].shape[0]
     nf = cfg.dim + 2
@@ -339,29 +358,23 @@ def _step_parity(st, cfg, dt, tol, cfl=0.4, check_dt=False):
         dt_used = stats["dt"]
     else:
         dt_used = dt
-    o = oracle.step(ocfg, st, dt_used)
+    q = np.arange(n)
+    o = oracle.step(ocfg, st, dt_used, query=q)
     gphi = by_id(ids, phi.cpu().numpy())
     gflag = by_id(ids, flag.cpu().numpy())
-    # particles whose discrete decision differs: re-run the oracle with the GPU's phi
-    diff = np.nonzero((gflag != o["flag"]) | (np.abs(gphi - o["phi"]).max(axis=1) > 1e-3))[0]
-    if len(diff):
-        assert len(diff) <= max(3, n // 500), "%d decisions differ" % len(diff)
-        r_o = o["r"][diff]
-        near = np.any((np.abs(r_o - 1.5) < 1e-3) | ~np.isfinite(r_o) | (r_o > 1e3), axis=1)
-        assert near.all(), "decision differs away from a threshold"
-        forced = np.full((n, nf), np.nan)
-        forced[diff] = gphi[diff]
-        o = oracle.step(ocfg, st, dt_used, forced_phi=forced)
+    # particles whose discrete decision differs must lie in the ambiguity band;
+    # the oracle is re-run with the GPU's phi for them
+    o, ndiff = parity.resolve(ocfg, st, q, cfg.precision, gflag, gphi, o, dt_used, max(3, n // 500))
     g = state_by_id(ps, st.get("n_fluid"))
-    errs = {"V": normwise(g["V"], o["V"]), "P": normwise(g["P"], o["P"])}
-    for k in range(cfg.dim):
-        errs["u%d" % k] = normwise(g["u"][k], o["u"][k])
-        errs["x%d" % k] = normwise(g["x"][k], o["x"][k])
+    errs, rates = parity.field_and_rate_errors(cfg.dim, st, g, o, dt_used)
+    print("ambiguous %d; field errors %s; rate errors %s" % (ndiff, errs, rates))
     ctx.close()
     for k, e in errs.items():
         assert e < tol, (k, e, errs)
+    for k, e in rates.items():
+        assert e < RATE_TOL[cfg.precision][k[0]], (k, e, rates)
     assert np.array_equal(g["m"], st["m"])
-    return errs, stats, len(diff)
+    return errs, stats, ndiff
 
 
 def test_step_fp64_smooth_3d():

@@ -27,9 +27,14 @@ def _built():
 
 
 def _reference(st):
-    """Keys and permutation from the allocating path (lp_build_neighbors)."""
+    """Keys and permutation from the allocating path (lp_build_neighbors) with a
+    default configuration of the state's dimension."""
     n = st["V"].shape[0]
-    cfg = lp.make_config(3, n, radius_mode=lp.RADIUS_VOLUME, kappa=2.2, k_max=64)
+    dim = len(st["x"])
+    if dim == 1:
+        cfg = lp.make_config(1, n, radius_mode=lp.RADIUS_KSIDE, k_max=8, k_per_side=4, k_side=1)
+    else:
+        cfg = lp.make_config(dim, n, radius_mode=lp.RADIUS_VOLUME, kappa=2.2, k_max=64 if dim == 3 else 40)
     ctx = lp.Context(cfg)
     ps = lp.ParticleSet.from_state(st)
     ctx.build_neighbors(ps)
@@ -71,3 +76,26 @@ def test_noalloc_rejects_sizes_above_the_maximum():
     with pytest.raises(lp.LPError) as e:
         lp.sort_keys_noalloc(x, keys, perm)
     assert e.value.code == lp.ERR_CAPACITY
+
+
+def test_noalloc_1d_and_2d_on_two_calls():
+    """1D: the keys are the order-preserving image of x and the sort runs over
+    all 64 bits (eight passes); 2D: Morton keys sorted by their cell bits down
+    to level 13.  Two calls in a row each, the second on the array the first
+    left behind; ties (equal x in 1D) keep the input order."""
+    rng = np.random.default_rng(31)
+    n1 = 100_003
+    x1 = rng.normal(0.0, 1.0, n1)
+    x1[::7] = np.round(x1[::7], 2)                   # many exactly equal positions, negative and positive
+    x1[5] = -0.0
+    x1[6] = 0.0
+    s1 = {"x": [x1], "V": np.full(n1, 1e-3), "u": [np.zeros(n1)], "P": np.ones(n1), "m": np.ones(n1),
+          "id": np.arange(n1, dtype=np.uint32), "n_fluid": n1}
+    s2 = inputs.kh_2d(150_000, 0.03, seed=32)
+    s2 = dict(s2, x=[a - 0.3 for a in s2["x"]])      # not periodic here: a plain bounding cube
+    for st in (s1, s2):
+        ref_keys, ref_perm = _reference(st)
+        for _ in range(2):
+            keys, perm = _noalloc(st)
+            assert np.array_equal(perm, ref_perm)
+            assert np.array_equal(keys, ref_keys)
