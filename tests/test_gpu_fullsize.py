@@ -57,14 +57,17 @@ def _samples(st, n, name):
     r2 = st["x"][0] ** 2 + st["x"][1] ** 2 + st["x"][2] ** 2
     extra = [np.argsort(r2)[-20:], np.argsort(r2)[:20], np.argsort(st["V"])[-20:]]
     if name.startswith("jet"):
-        # the jet is uniform inside and outside: only particles by its surface
-        # (radius 1 about the z axis, 0 <= z <= 12) change in a step, so 120 of
-        # them are drawn from the initial geometry: jet particles within about
-        # two of their spacings (0.017 at 8M) of it, ambient ones within their
-        # radius (about 0.37)
+        # the jet is uniform inside and outside, and no ambient particle lies
+        # within half its spacing of the jet's surface (radius 1 about the z
+        # axis, 0 <= z <= 12), so a jet particle's neighbours are all jet
+        # particles: what changes in a step are the ambient particles whose
+        # radius reaches the jet.  120 of them are drawn from the initial state.
         rc = np.sqrt(st["x"][0] ** 2 + st["x"][1] ** 2)
         z = st["x"][2]
-        near = np.nonzero(((rc > 0.965) & (rc < 1.3) & (z < 12.3)) | ((rc < 1.3) & (z > 11.965) & (z < 12.3)))[0]
+        out = np.maximum(rc - 1.0, 0.0)
+        dist = np.where(z <= 12.0, out, np.hypot(out, z - 12.0))
+        R = 2.2 * np.cbrt(st["m"] * st["V"])
+        near = np.nonzero((st["V"] > 10.0 * st["V"].min()) & (dist < R))[0]
         extra.append(rng.choice(near, min(120, len(near)), replace=False))
     return np.unique(np.concatenate([q] + extra))
 
@@ -134,7 +137,7 @@ def test_full_size_sampled_parity(name):
     changed = int((np.abs(g["P"] - s0["P"]) > 0).sum())
     print("%s: %d of %d samples changed; ambiguous %d; field errors %s; rate errors %s"
           % (name, changed, len(q), ndiff, errs, rates))
-    assert changed >= min(60, len(q) // 2)
+    assert changed >= min(30, len(q) // 2)
     for k in ("V", "u0", "u1", "u2", "P"):
         assert errs[k] < 1e-5, (k, errs)
         assert rates[k] < RATE_TOL[k[0]], (k, rates)

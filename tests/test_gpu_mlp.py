@@ -193,7 +193,7 @@ def test_learned_gate_gains_over_plain_estimator():
     print("fit ms plain %.3f gated %.3f skip %.3f miss %.4f tau %.4f" % (plain_ms, gated_ms, skip, miss, tau))
     assert skip > 0.4, skip
     assert miss < 0.05, miss
-    assert gated_ms < 0.93 * plain_ms, (gated_ms, plain_ms)
+    assert gated_ms < 0.95 * plain_ms, (gated_ms, plain_ms)
 
 
 _GATE = {}
