@@ -112,6 +112,8 @@ def parse():
                     help="mlp: train the learned estimator on this workload's own plain steps, then time "
                          "steps gated by it")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--schedule", default=None, choices=["fused", "split"],
+                    help="fit schedule to time (instead of the autotuner's choice)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64 and learned-estimator forms reported beside the headline")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
@@ -368,7 +370,9 @@ def run_ours(args):
         for _ in range(args.warmup):
             ctx.step(ps, dt=0.0, cfl=CFL, t=t_dev, stream=stream)
         tune = None
-        if not args.no_autotune:
+        if args.schedule:
+            ctx.set_schedule({"fused": lp.SCHED_FUSED, "split": lp.SCHED_SPLIT}[args.schedule])
+        elif not args.no_autotune:
             tune = ctx.autotune(ps, dt=0.0, cfl=CFL, reps=3, stream=stream)
             sch = ctx.schedule()
             tune["chosen"] = ("split" if sch & lp.SCHED_SPLIT else "fused") + (
