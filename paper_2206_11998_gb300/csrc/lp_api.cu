@@ -29,7 +29,7 @@ void free_all(lp_ctx* c)
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist, c->sx[0], c->sx[1], c->sx[2],
                     c->sV, c->su[0], c->su[1], c->su[2], c->sP, c->sm, c->sid, c->rec, c->pos4, c->cells, c->nb_count, c->nb_total,
                     c->nb_idx, c->nb_d2min, c->grid, c->dt_dev, c->dt_min, c->counters, c->redo_list,
-                    c->plain_list, c->mid, c->ext, c->grange, c->level_off_dev, c->sim_of,
+                    c->plain_list, c->refine_list, c->mid, c->ext, c->grange, c->level_off_dev, c->sim_of,
                     c->mlp_master, c->mlp_bf16, c->mlp_m1, c->mlp_m2, c->mlp_grad, c->mlp_loss, c->stage_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -163,6 +163,8 @@ void fill_fit_args(lp_ctx* c, FitArgs& a, int64_t n)
     a.key_shift = c->dc.dim * c->dc.mbits;
     a.plain_list = c->plain_list;
     a.plain_len = c->counters + C_PLAIN_LEN;
+    a.refine_list = c->refine_list;
+    a.refine_len = c->counters + C_REFINE_LEN;
     a.mid = c->mid;
     a.mid_cap = c->cap;
 }
@@ -241,8 +243,10 @@ lp_status run_fit(lp_ctx* c, FitArgs a, const StepOut& o, int sched, cudaStream_
     if (split) LP_CUDA(cudaMemsetAsync(c->counters + C_PLAIN_LEN, 0, 8, s));
     if (c->dc.precision == LP_PREC_FP32) {
         LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
+        const bool defer = split && c->dc.refine == LP_REFINE_AUTO;
+        if (defer) LP_CUDA(cudaMemsetAsync(c->counters + C_REFINE_LEN, 0, 8, s));
         {
-            Phase ph(c, LP_PH_FIT, split ? 2 : 1, s);
+            Phase ph(c, LP_PH_FIT, split ? (defer ? 3 : 2) : 1, s);
             LP_CUDA(split ? launch_step_split_f32(dim, a, o, s) : launch_step_f32(dim, a, o, s));
         }
         a.list = c->redo_list;
@@ -379,6 +383,7 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     A(dalloc(&c->counters, C_COUNT * 8));
     A(dalloc(&c->redo_list, n * 4));
     A(dalloc(&c->plain_list, n * 4));
+    A(dalloc(&c->refine_list, n * 4));
     A(dalloc(&c->mid, (size_t)n * MidN<3>::v * (cfg->precision == LP_PREC_FP32 ? 4 : 8)));
     A(dalloc(&c->mlp_master, MLP_NPARAM * 4)); A(dalloc(&c->mlp_bf16, MLP_NPARAM * 2));
     A(dalloc(&c->mlp_m1, MLP_NPARAM * 4)); A(dalloc(&c->mlp_m2, MLP_NPARAM * 4));

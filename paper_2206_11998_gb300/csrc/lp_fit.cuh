@@ -349,6 +349,10 @@ struct FitArgs {
     unsigned long long* plain_len;
     void* mid;
     int64_t mid_cap;
+    // split schedule, FP32: the central fits that need the correction pass,
+    // listed by the first kernel for a kernel of their own
+    uint32_t* refine_list;
+    unsigned long long* refine_len;
 };
 
 // statistics of the last field's differences b_j = s_j - s_i over the central
@@ -562,7 +566,9 @@ constexpr float NE_RATIO_MIN = 0.02f;
 // free Givens rotations (the FP64 path's only form).  The correction pass runs
 // in the modes that ask for it, and for the gate's residual sum when the
 // rotations did not give it.
-template <typename T, int DIM, int F, bool STATS = false>
+// DEFER: return 2, with x untouched, where the correction pass would run
+// (the caller lists the particle for a kernel that runs it in full warps).
+template <typename T, int DIM, int F, bool STATS = false, bool DEFER = false>
 __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau,
                            const DevCfg& cf, T (&x)[NU<DIM>::v][F], FitStats<T>* st = nullptr,
                            bool* refined = nullptr)
@@ -638,6 +644,7 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
         G.solve(x);
     }
     const bool refine = cf.refine == LP_REFINE_ALWAYS || (cf.refine == LP_REFINE_AUTO && ratio < (T)cf.refine_ratio);
+    if (DEFER && refine) return 2;
     if (refined) *refined = refine;
     if (STATS && !have_ssr && !refine) {
         // only the gate's residual sum of the last field: half of each record
@@ -655,7 +662,7 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
         });
         have_ssr = true;
     }
-    if (refine || (STATS && !have_ssr)) {
+    if (!DEFER && (refine || (STATS && !have_ssr))) {
         // The FP32 3D factor (d and U, 45 values) waits in shared memory during
         // the correction pass, which holds the solution and the correction sums:
         // without that the pass spills.
@@ -746,7 +753,7 @@ __device__ int linear_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt
 // than DIM members or rank deficient.  ill = true when a system with enough
 // members is below tau (FP32: redo in FP64).
 template <typename T, int DIM, int F>
-__device__ void onesided_all(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, int ks, T invS, T tau,
+__device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, int ks, T invS, T tau,
                              T tau_rank, T (&out)[DIM][2][F], bool (&ok)[DIM][2], bool& ill)
 {
     uint64_t m[DIM][2];

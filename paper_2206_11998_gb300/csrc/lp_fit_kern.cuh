@@ -123,7 +123,7 @@ struct Loaded {
 };
 
 template <typename T, int DIM>
-__device__ inline bool step_load(const FitArgs& a, const StepOut& o, int64_t i, Loaded<DIM>& L)
+__device__ __forceinline__ bool step_load(const FitArgs& a, const StepOut& o, int64_t i, Loaded<DIM>& L)
 {
     constexpr int F = DIM + 2;
     const DevCfg& c = a.c;
@@ -149,10 +149,10 @@ __device__ inline bool step_load(const FitArgs& a, const StepOut& o, int64_t i, 
     return true;
 }
 
-// central stage; false when i went to the FP64 redo list.  GATE: the learned
-// estimator or the feature output is in use (its inputs and code are compiled
-// out otherwise)
-template <typename T, int DIM, bool GATE>
+// central stage; false when i went to the FP64 redo list (or, DEFER, to the
+// correction kernel's list).  GATE: the learned estimator or the feature
+// output is in use (its inputs and code are compiled out otherwise)
+template <typename T, int DIM, bool GATE, bool DEFER = false>
 __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t i, const Loaded<DIM>& L,
                                     const Src<T, DIM, DIM + 2>& src, const uint32_t* nb, int cnt, T invS,
                                     T (&cdf)[DIM][DIM + 2], T (&lw)[DIM + 2], bool& mlp_skip)
@@ -164,8 +164,13 @@ __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t 
     T cd[N][F];
     FitStats<T> fst = {T(0), T(0), T(0), T(0)};
     bool refined = false;
-    const int ill = central_fit<T, DIM, F, GATE>(src, nb, cnt, invS, tau, c, cd, &fst, &refined);
+    const int ill = central_fit<T, DIM, F, GATE, DEFER>(src, nb, cnt, invS, tau, c, cd, &fst, &refined);
     if (IsF32<T>::v) warp_count(a.counters, C_REFINED, refined);
+    if (DEFER && ill == 2) {
+        const unsigned long long pos = atomicAdd(a.refine_len, 1ull);
+        a.refine_list[pos] = (uint32_t)i;
+        return false;
+    }
     if (ill) {
         if (IsF32<T>::v) { push_redo(a, i); return false; }
         T lin[DIM][F];
@@ -210,7 +215,7 @@ __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t 
 
 // plain stage; false when i went to the FP64 redo list
 template <typename T, int DIM>
-__device__ inline bool step_plain(const FitArgs& a, int64_t i, const Src<T, DIM, DIM + 2>& src, const uint32_t* nb,
+__device__ __forceinline__ bool step_plain(const FitArgs& a, int64_t i, const Src<T, DIM, DIM + 2>& src, const uint32_t* nb,
                                   int cnt, T invS, const T (&cdf)[DIM][DIM + 2], T (&os)[DIM][2][DIM + 2])
 {
     constexpr int F = DIM + 2;
@@ -231,7 +236,7 @@ __device__ inline bool step_plain(const FitArgs& a, int64_t i, const Src<T, DIM,
 }
 
 template <typename T, int DIM>
-__device__ inline void step_finish(const FitArgs& a, const StepOut& o, int64_t i, const Loaded<DIM>& L,
+__device__ __forceinline__ void step_finish(const FitArgs& a, const StepOut& o, int64_t i, const Loaded<DIM>& L,
                                    const T (&os)[DIM][2][DIM + 2], const T (&lw)[DIM + 2], bool plain, bool mlp_skip)
 {
     constexpr int F = DIM + 2;
@@ -392,21 +397,15 @@ __device__ inline unsigned long long warp_append(unsigned long long* len, bool p
     return base + (unsigned long long)__popc(b & ((1u << lane) - 1u));
 }
 
-template <typename T, int DIM, bool GATE>
-__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_central(FitArgs a, StepOut o)
+// the end of the split schedule's first stage: a particle the learned gate
+// cleared is finished here; the others are appended to the plain-stage list
+// with their central first derivatives and LW rates
+template <typename T, int DIM>
+__device__ __forceinline__ void central_append_or_finish(const FitArgs& a, const StepOut& o, int64_t i,
+                                                         const Loaded<DIM>& L, const T (&cdf)[DIM][DIM + 2],
+                                                         const T (&lw)[DIM + 2], bool mlp_skip)
 {
     constexpr int F = DIM + 2;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    Loaded<DIM> L;
-    if (step_load<T, DIM>(a, o, i, L)) return;
-    Src<T, DIM, F> src(a, i);
-    const int cnt = (int)a.count[i];
-    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
-    const T invS = (T)inv_scale(last_d2(src, nb, cnt));
-    T cdf[DIM][F], lw[F];
-    bool mlp_skip;
-    if (!step_central<T, DIM, GATE>(a, o, i, L, src, nb, cnt, invS, cdf, lw, mlp_skip)) return;
     const bool plain = !mlp_skip || a.c.mlp_audit;
     unsigned long long t = warp_append(a.plain_len, plain);
     if (plain) {
@@ -426,6 +425,48 @@ __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_centra
     T os[DIM][2][F];
     skip_plain<T, DIM>(cdf, os);
     step_finish<T, DIM>(a, o, i, L, os, lw, false, true);
+}
+
+// the central stage of particle i as the split schedule's first kernel runs it
+template <typename T, int DIM, bool GATE, bool DEFER>
+__device__ __forceinline__ void central_one(const FitArgs& a, const StepOut& o, int64_t i)
+{
+    constexpr int F = DIM + 2;
+    Loaded<DIM> L;
+    if (step_load<T, DIM>(a, o, i, L)) return;
+    Src<T, DIM, F> src(a, i);
+    const int cnt = (int)a.count[i];
+    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
+    const T invS = (T)inv_scale(last_d2(src, nb, cnt));
+    T cdf[DIM][F], lw[F];
+    bool mlp_skip;
+    if (!step_central<T, DIM, GATE, DEFER>(a, o, i, L, src, nb, cnt, invS, cdf, lw, mlp_skip)) return;
+    central_append_or_finish<T, DIM>(a, o, i, L, cdf, lw, mlp_skip);
+}
+
+// First kernel of the split schedule.  DEFER (FP32, correction pass where the
+// ratio asks for it): a central fit that needs the correction pass is listed
+// for k_step_central_refine instead, so that this kernel's warps do not run
+// the pass for the few lanes that need it (2-3% of the gas cloud's stencils,
+// in about half of the warps).
+template <typename T, int DIM, bool GATE, bool DEFER>
+__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_central(FitArgs a, StepOut o)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    central_one<T, DIM, GATE, DEFER>(a, o, i);
+}
+
+// The central fits k_step_central deferred, in full warps, with the correction
+// pass on (the caller passes a configuration with refine = LP_REFINE_ALWAYS):
+// the same arithmetic as an inline correction, so the same results.
+template <typename T, int DIM, bool GATE>
+__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_central_refine(FitArgs a, StepOut o)
+{
+    const unsigned long long len = *a.refine_len;
+    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < len;
+         t += (unsigned long long)gridDim.x * blockDim.x)
+        central_one<T, DIM, GATE, false>(a, o, a.refine_list[t]);
 }
 
 template <typename T, int DIM>
@@ -612,6 +653,28 @@ cudaError_t launch_derivs_f64(int dim, int F, const FitArgs& a, const DerivOut& 
 cudaError_t launch_onesided_f32(int dim, const FitArgs& a, double* out, int f_real, cudaStream_t s);
 cudaError_t launch_onesided_f64(int dim, const FitArgs& a, double* out, int f_real, cudaStream_t s);
 
+// k_step_central_refine over the deferred list (FP32; its own translation
+// unit, lp_fit_f32_refine.cu, so that its instantiation does not change how the
+// other fit kernels are compiled)
+template <typename T>
+cudaError_t launch_central_refine(int dim, bool gate, const FitArgs& r, const StepOut& o, cudaStream_t s);
+template <>
+cudaError_t launch_central_refine<float>(int dim, bool gate, const FitArgs& r, const StepOut& o, cudaStream_t s);
+template <>
+inline cudaError_t launch_central_refine<double>(int, bool, const FitArgs&, const StepOut&, cudaStream_t)
+{
+    return cudaErrorNotSupported;
+}
+
+// the split schedule lists the FP32 central fits that need the correction
+// pass for a kernel of their own (where the correction runs only below the
+// ratio; where it always runs, listing every particle would only repeat work)
+template <typename T>
+inline bool split_defers_t(const FitArgs& a)
+{
+    return IsF32<T>::v && a.refine_list && a.c.refine == LP_REFINE_AUTO;
+}
+
 inline unsigned fit_blocks(const FitArgs& a)
 {
     return a.list ? 152u * 4u : (unsigned)((a.n + FIT_THREADS - 1) / FIT_THREADS);
@@ -638,20 +701,42 @@ inline unsigned fit_blocks(const FitArgs& a)
     cudaError_t launch_step_split_##SUF(int dim, const FitArgs& a, const StepOut& o,            \
                                         cudaStream_t s)                                         \
     {                                                                                           \
+        auto split_defers = [](const FitArgs& x) { return split_defers_t<T>(x); };              \
         unsigned b = (unsigned)((a.n + FIT_THREADS - 1) / FIT_THREADS);                                             \
         if (b == 0) return cudaSuccess;                                                         \
         const bool gate = o.features || a.c.estimator == LP_EST_MLP;                           \
+        if (split_defers(a)) {                                                                  \
+            FitArgs r = a;                                                                      \
+            r.c.refine = LP_REFINE_ALWAYS;                                                      \
+            if (dim == 3) {                                                                     \
+                if (gate) k_step_central<T, 3, true, true><<<b, FIT_THREADS, 0, s>>>(a, o);    \
+                else k_step_central<T, 3, false, true><<<b, FIT_THREADS, 0, s>>>(a, o);        \
+                launch_central_refine<T>(3, gate, r, o, s);                             \
+                k_step_plain<T, 3><<<b, FIT_THREADS, 0, s>>>(a, o);                             \
+            } else if (dim == 2) {                                                              \
+                if (gate) k_step_central<T, 2, true, true><<<b, FIT_THREADS, 0, s>>>(a, o);    \
+                else k_step_central<T, 2, false, true><<<b, FIT_THREADS, 0, s>>>(a, o);        \
+                launch_central_refine<T>(2, gate, r, o, s);                             \
+                k_step_plain<T, 2><<<b, FIT_THREADS, 0, s>>>(a, o);                             \
+            } else {                                                                            \
+                if (gate) k_step_central<T, 1, true, true><<<b, FIT_THREADS, 0, s>>>(a, o);    \
+                else k_step_central<T, 1, false, true><<<b, FIT_THREADS, 0, s>>>(a, o);        \
+                launch_central_refine<T>(1, gate, r, o, s);                             \
+                k_step_plain<T, 1><<<b, FIT_THREADS, 0, s>>>(a, o);                             \
+            }                                                                                   \
+            return cudaGetLastError();                                                          \
+        }                                                                                       \
         if (dim == 3) {                                                                         \
-            if (gate) k_step_central<T, 3, true><<<b, FIT_THREADS, 0, s>>>(a, o);                       \
-            else k_step_central<T, 3, false><<<b, FIT_THREADS, 0, s>>>(a, o);                           \
+            if (gate) k_step_central<T, 3, true, false><<<b, FIT_THREADS, 0, s>>>(a, o);               \
+            else k_step_central<T, 3, false, false><<<b, FIT_THREADS, 0, s>>>(a, o);                   \
             k_step_plain<T, 3><<<b, FIT_THREADS, 0, s>>>(a, o);                                         \
         } else if (dim == 2) {                                                                  \
-            if (gate) k_step_central<T, 2, true><<<b, FIT_THREADS, 0, s>>>(a, o);                       \
-            else k_step_central<T, 2, false><<<b, FIT_THREADS, 0, s>>>(a, o);                           \
+            if (gate) k_step_central<T, 2, true, false><<<b, FIT_THREADS, 0, s>>>(a, o);               \
+            else k_step_central<T, 2, false, false><<<b, FIT_THREADS, 0, s>>>(a, o);                   \
             k_step_plain<T, 2><<<b, FIT_THREADS, 0, s>>>(a, o);                                         \
         } else {                                                                                \
-            if (gate) k_step_central<T, 1, true><<<b, FIT_THREADS, 0, s>>>(a, o);                       \
-            else k_step_central<T, 1, false><<<b, FIT_THREADS, 0, s>>>(a, o);                           \
+            if (gate) k_step_central<T, 1, true, false><<<b, FIT_THREADS, 0, s>>>(a, o);               \
+            else k_step_central<T, 1, false, false><<<b, FIT_THREADS, 0, s>>>(a, o);                   \
             k_step_plain<T, 1><<<b, FIT_THREADS, 0, s>>>(a, o);                                         \
         }                                                                                       \
         return cudaGetLastError();                                                              \

@@ -36,7 +36,7 @@ constexpr uint32_t FIT_LINEAR = 1u, FIT_NONE = 2u, FIT_FP64 = 8u;
 enum Counter {
     C_FLAGGED = 0, C_FP64, C_LINEAR, C_NOFIT, C_OVERFLOW, C_NONFINITE, C_MLP_UNCERTAIN,
     C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_MLP_SKIP, C_MLP_MISS, C_PLAIN_LEN, C_QFB_LEN, C_REFINED,
-    C_COUNT
+    C_REFINE_LEN, C_COUNT
 };
 
 // method constants as the kernels see them
@@ -244,8 +244,10 @@ struct lp_ctx {
     int nsim;                     // simulations of the current call
     unsigned long long* counters;
     uint32_t* redo_list;
-    // split fit schedule: compacted plain-stage list and intermediate record
+    // split fit schedule: compacted plain-stage list and intermediate record,
+    // and the list of FP32 central fits deferred to the correction kernel
     uint32_t* plain_list;
+    uint32_t* refine_list;
     void* mid;
     int schedule;                 // LP_SCHED_FUSED / LP_SCHED_SPLIT
     // lp_step_host: device copy of the caller's host particles, a second stream
