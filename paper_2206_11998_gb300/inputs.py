@@ -190,6 +190,55 @@ def kh_2d(n: int, amp: float, seed: int, rho_in: float = 2.0, rho_out: float = 1
     return _state([x, y], 1.0 / rho, [u, v], np.full(n, p0), np.full(n, M / n))
 
 
+YEE_GAMMA = 1.4
+YEE_BETA = 5.0
+
+
+def yee_vortex_fields(x, y, x0, y0, L, beta=YEE_BETA, gamma=YEE_GAMMA):
+    """The isentropic vortex of Sec. 3 (free stream u = 1, v = 0, rho = 1,
+    p = 1) centred at (x0, y0), evaluated at (x, y) with the minimum-image
+    offsets of a periodic square of edge L:
+      T = 1 - (gamma - 1) beta^2 / (8 gamma pi^2) exp(1 - r^2),  rho = T^(1/(gamma-1)),
+      u = 1 - beta / (2 pi) exp((1 - r^2)/2) (y - y0),
+      v =     beta / (2 pi) exp((1 - r^2)/2) (x - x0),
+      p = rho^gamma.
+    The printed u line reads e (1 - r^2)/2; it is taken as exp((1 - r^2)/2),
+    as in the v line.  Returns (rho, u, v, p)."""
+    dx = x - x0
+    dy = y - y0
+    dx = dx - L * np.round(dx / L)
+    dy = dy - L * np.round(dy / L)
+    r2 = dx * dx + dy * dy
+    T = 1.0 - (gamma - 1.0) * beta ** 2 / (8.0 * gamma * np.pi ** 2) * np.exp(1.0 - r2)
+    rho = T ** (1.0 / (gamma - 1.0))
+    e = beta / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+    return rho, 1.0 - e * dy, e * dx, rho ** gamma
+
+
+def yee_vortex_2d(dx: float, L: float = 16.0, x0: float = 4.0, y0: float = 8.0, jitter: float = 0.0, seed: int = 41):
+    """Particles of the Yee vortex problem on the periodic square [0, L)^2: a
+    hexagonal lattice of spacing dx (rows dx sqrt(3)/2 apart, every other row
+    shifted by dx/2), with the row count rounded to an even number so that the
+    lattice is periodic in a square (the rows then lie within 1% of the
+    hexagonal spacing), optionally jittered by U(-jitter, jitter) dx per axis.
+    Each particle carries the mass of its lattice cell at the local density,
+    so V = 1/rho holds at t = 0."""
+    nx = int(round(L / dx))
+    ny = 2 * int(round(L / (dx * np.sqrt(3.0)) ))
+    hx, hy = L / nx, L / ny
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    x = ((i + 0.5 + 0.5 * (j % 2)) * hx).ravel()
+    y = ((j + 0.5) * hy).ravel()
+    if jitter > 0:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        x = x + jitter * hx * rng.uniform(-1.0, 1.0, x.shape[0])
+        y = y + jitter * hy * rng.uniform(-1.0, 1.0, y.shape[0])
+    x = np.mod(x, L)
+    y = np.mod(y, L)
+    rho, u, v, p = yee_vortex_fields(x, y, x0, y0, L)
+    return _state([x, y], 1.0 / rho, [u, v], p, rho * hx * hy)
+
+
 JET_GAMMA = 1.4
 
 
