@@ -105,9 +105,16 @@ def parse():
                     help="particles (default: 2M for the gas cloud, about 8M for the jet snapshot)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="gas-cloud", choices=["gas-cloud", "jet-snapshot", "kh-ensemble"],
-                    help="jet-snapshot: the static jet-shaped state (density ratio 1e3, gamma 1.4)")
+    ap.add_argument("--workload", default="gas-cloud", choices=["gas-cloud", "jet-snapshot", "kh-ensemble", "jet-inflow"],
+                    help="jet-snapshot: the static jet-shaped state (density ratio 1e3, gamma 1.4); jet-inflow: the "
+                         "jet grown through a reservoir inlet to --particles (default 8M), then timed")
     ap.add_argument("--sims", type=int, default=256)
+    ap.add_argument("--density-ratio", type=float, default=1e3,
+                    help="jet-inflow: jet / ambient density ratio")
+    ap.add_argument("--limiter", default="flagged", choices=["flagged", "uw"],
+                    help="jet-inflow: the limiter mode")
+    ap.add_argument("--grow-seconds", type=float, default=240.0,
+                    help="jet-inflow: wall-time budget of the untimed growth phase")
     ap.add_argument("--estimator", default="plain", choices=["plain", "mlp"],
                     help="mlp: train the learned estimator on this workload's own plain steps, then time "
                          "steps gated by it")
@@ -154,7 +161,8 @@ def dist_info():
 
 # the single-simulation 3D workloads: generator, gamma, default size
 WORKLOADS = {"gas-cloud": ("gas-cloud-3d", 5.0 / 3.0, 2_000_000),
-             "jet-snapshot": ("jet-snapshot-3d", 1.4, 8_000_000)}
+             "jet-snapshot": ("jet-snapshot-3d", 1.4, 8_000_000),
+             "jet-inflow": ("jet-inflow-3d", 1.4, 8_000_000)}
 ACTIVE = "gas-cloud"
 
 
@@ -848,6 +856,124 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the jet with reservoir inflow, grown to its end size
+# ---------------------------------------------------------------------------
+
+JET_H = 0.0169          # jet particle spacing: about 8M particles once the jet reaches z ~ 16
+
+
+def run_inflow(args):
+    """The jet grows from a short column above a Mach-3 reservoir inlet (1e3
+    density contrast with the ambient): lp_step and lp_inflow each step, the
+    arrays and the context's scratch doubled as the count grows (untimed).
+    Once the count reaches the target, steps (lp_step + lp_inflow, the latter
+    with its host read of the layer count) are timed."""
+    import torch
+
+    from paper_2206_11998_gb300 import build as b
+    from paper_2206_11998_gb300 import inputs, lp
+
+    b.build()
+    torch.cuda.set_device(0)
+    target = args.particles
+    st, q = inputs.jet_inflow_3d(JET_H, density_ratio=args.density_ratio)
+    n0 = st["V"].shape[0]
+    inlet = lp.make_inlet(q["center"], q["axis"], q["radius"], q["spacing"], q["mass"], q["P_res"], q["rho_res"],
+                          q["sample_depth"], ghost_layers=q["ghost_layers"], first_id=n0, ghost_id=2 ** 31)
+    cap = 2 * n0
+    cfg = lp.make_config(3, cap, kappa=KAPPA, k_max=K_MAX, k_side=8, gamma=inputs.JET_GAMMA, n_fluid=2 ** 31,
+                         s_ref=(1.0, 1.0, 1.0, 3.5, 1.0),
+                         limiter={"flagged": lp.LIM_FLAGGED, "uw": lp.LIM_UW}[args.limiter])
+    ctx = lp.Context(cfg)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    growth = {"steps": 0, "reserves": 0}
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        ps = lp.ParticleSet.with_capacity(st, cap)
+
+        box_lo, box_hi = (-q["box"][0], -q["box"][0], -q["box"][1]), (q["box"][0], q["box"][0], q["box"][2])
+
+        def advance():
+            nonlocal ps
+            ctx.step(ps, dt=0.0, cfl=CFL, stream=stream)
+            growth["removed"] = growth.get("removed", 0) + ctx.remove_outside(ps, box_lo, box_hi, stream=stream)
+            while True:
+                try:
+                    return ctx.inflow(ps, inlet, stream=stream)
+                except lp.LPError as e:
+                    if e.code != lp.ERR_CAPACITY:
+                        raise
+                    ps = ps.grown(2 * ps.capacity)
+                    ctx.reserve(ps.capacity)
+                    growth["reserves"] += 1
+
+        ctx.inflow(ps, inlet, stream=stream)
+        info = None
+        tick = time.perf_counter()
+        while ps.n < target and growth["steps"] < 4000 and time.perf_counter() - t0 < args.grow_seconds:
+            info = advance()
+            growth["steps"] += 1
+            if growth["steps"] % 50 == 0:
+                stream.synchronize()
+                sg = ctx.stats(stream=stream)
+                now = time.perf_counter()
+                sys.stderr.write("grow step %d n %d dt %.3g  %.1f ms/step  layers %d  fp64-redo %d  query-fallback %d  "
+                                 "rejected %d\n" % (growth["steps"], ps.n, sg["dt"], (now - tick) * 20.0,
+                                                     info["layers_total"], sg["n_fp64_redo"], sg["n_query_fallback"],
+                                                     sg["n_nonfinite"]))
+                sys.stderr.flush()
+                ctx.reset_stats(stream=stream)
+                tick = now
+        stream.synchronize()
+        growth["reached_target"] = ps.n >= target
+        growth["wall_s"] = time.perf_counter() - t0
+        growth["start_particles"] = n0
+        for _ in range(args.warmup):
+            advance()
+        ctx.reset_stats(stream=stream)
+        ctx.phase_times(stream=stream)
+        ctx.set_profiling(True)
+        l0 = ctx.stats(stream=stream)["kernel_launches"]
+        sampler = ClockSampler(gpu_index_for(0))
+        sampler.start()
+        ms, counts, infos = [], [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            counts.append(ps.n)
+            a.record(stream)
+            infos.append(advance())
+            e.record(stream)
+            e.synchronize()
+            ms.append(a.elapsed_time(e))
+        clocks = sampler.stop()
+        ctx.set_profiling(False)
+        phases = ctx.phase_times(stream=stream)
+        s = ctx.stats(stream=stream)
+    total_ms = sum(ms)
+    value = sum(counts) / (total_ms * 1e-3)
+    last = infos[-1]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "jet-inflow-3d-%s" % size_tag(counts[0]), "particles_timed": [counts[0], ps.n],
+                       "jet_spacing": JET_H, "inlet": {k: v for k, v in q.items() if k != "center"},
+                       "growth": growth, "flagged_per_step": s["n_flagged"] / args.steps,
+                       "fp64_redo_per_step": s["n_fp64_redo"] / args.steps,
+                       "rejected_updates_per_step": s["n_nonfinite"] / args.steps,
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "inflow": {"P_inf": last["P_inf"], "rho_inf": last["rho_inf"], "u_inf": last["u_inf"],
+                       "mach": last["u_inf"] / last["c_inf"], "layers_per_step": sum(i["layers"] for i in infos) / len(infos),
+                       "particles_per_layer": last["npat"]},
+            "gpu_launches": s["kernel_launches"] - l0, "clocks": clocks,
+            "phases": {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in phases.items() if v[1]}}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     select_workload(args)
@@ -855,6 +981,8 @@ def main():
         run_reference(args)
     elif args.workload == "kh-ensemble":
         run_ensemble(args)
+    elif args.workload == "jet-inflow":
+        run_inflow(args)
     else:
         run_ours(args)
 

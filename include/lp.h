@@ -377,6 +377,84 @@ lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double *x0, const d
                                lp_stream stream);
 
 /*
+ * Reservoir inflow through a nozzle inlet (Sec. 4, "Supersonic jets for
+ * LPWA": a nozzle attached to a high-pressure reservoir, modelled by a
+ * boundary condition at the inlet).  The inflow state follows the three
+ * hypotheses printed there:
+ *   P_inf   the mean pressure of the fluid particles near the inlet (those
+ *           within `radius` of the axis and within `sample_depth` past the
+ *           inlet plane); the reservoir pressure P_res on the first call;
+ *   rho_inf the reservoir's entropy: P_res / rho_res^gamma = P_inf / rho_inf^gamma;
+ *   u_inf   along the axis, from the enthalpy balance with the reservoir at
+ *           rest: u_inf^2 / 2 + c_inf^2 / (gamma - 1) = c_res^2 / (gamma - 1),
+ *           c^2 = gamma P / rho; no transverse component.
+ * Injected particles sit on a square lattice of in-plane spacing `spacing`
+ * clipped to the inlet disk (npat points per layer), each with mass `mass`, so
+ * a layer's axial thickness is h_z = mass / (rho_inf spacing^2).  The axial
+ * distance the inflow has travelled accumulates u_inf dt (dt: the last
+ * lp_step's time step, 0 before the first step); each whole h_z of it
+ * becomes one layer of fluid particles past the inlet, appended at the end of
+ * the particle arrays with ids first_id + (layer index) npat + point.  Each
+ * layer's lattice is shifted in-plane by a counter-based fraction of the
+ * spacing (Weyl sequence of the layer index).  `ghost_layers` layers of frozen
+ * reservoir particles (ids from ghost_id, which must be >= the configuration's
+ * n_fluid) lie behind the inlet plane with the inflow state: appended on the
+ * first call and rewritten (by id) on every call.
+ *
+ * p: device particle arrays with room for `capacity` particles, p->n in use.
+ * On return *n_out = the new count (p->n plus what was appended).  When that
+ * would exceed `capacity`, nothing is appended or advanced and
+ * LP_ERR_CAPACITY is returned (grow the arrays, lp_reserve, call again).
+ * info (host, may be NULL) receives the inflow state of this call.
+ * Synchronises `stream` (the host reads the number of layers decided on the
+ * device).  Every call must pass the same inlet; LP_ERR_ARG otherwise.
+ */
+typedef struct {
+    double center[3];       /* centre of the inlet disk (on the inlet plane) */
+    int32_t axis;           /* the inflow runs along +axis (0, 1, 2; 3D only) */
+    int32_t ghost_layers;   /* reservoir layers behind the inlet, >= 0 */
+    double radius;          /* inlet radius */
+    double spacing;         /* in-plane lattice spacing of injected particles */
+    double mass;            /* mass of each injected particle */
+    double P_res, rho_res;  /* reservoir pressure and density */
+    double sample_depth;    /* depth of the region whose mean pressure is P_inf */
+    uint32_t first_id;      /* ids of injected fluid particles count up from here */
+    uint32_t ghost_id;      /* ids of the reservoir ghosts count up from here */
+} lp_inlet;
+
+typedef struct {
+    double P_inf, rho_inf, u_inf, c_inf;   /* the inflow state of this call */
+    double h_z;                            /* axial thickness of a layer */
+    double travel;                         /* inflow distance not yet a whole layer */
+    int64_t layers;                        /* layers appended by this call */
+    int64_t layers_total;                  /* layers appended since the first call */
+    int64_t npat;                          /* particles per layer */
+    int64_t sampled;                       /* fluid particles averaged into P_inf */
+} lp_inflow_info;
+
+lp_status lp_inflow(lp_ctx *ctx, lp_particles *p, int64_t capacity, const lp_inlet *inlet, int64_t *n_out,
+                    lp_inflow_info *info, lp_stream stream);
+
+/*
+ * Outflow (Sec. 2.2 step 1: outflow boundaries delete particles): removes the
+ * particles whose position is outside [lo_k, hi_k] on some axis k < dim, or
+ * not finite, keeping the others in their order (stable, in place in p's
+ * arrays); *n_out receives the count that remains.  The neighbour lists of the
+ * last build are dropped.  lo, hi: host double[3].  Synchronises `stream`.
+ */
+lp_status lp_remove_outside(lp_ctx *ctx, lp_particles *p, const double *lo, const double *hi, int64_t *n_out,
+                            lp_stream stream);
+
+/*
+ * Grow (or shrink) the context's scratch to `capacity` particles (at least the
+ * n of the last build).  The neighbour lists of the last build are dropped (the
+ * next call that needs them must rebuild) and a captured graph is discarded.
+ * Synchronises the device.  No counterpart in the paper: the capacity growth
+ * that particle insertion needs.
+ */
+lp_status lp_reserve(lp_ctx *ctx, int64_t capacity);
+
+/*
  * One LP step of nsim independent simulations stored back to back in p: the
  * particles of simulation s are [offsets[s], offsets[s+1]) (offsets: device
  * int64 [nsim + 1], offsets[0] = 0, offsets[nsim] = p->n; nsim <= max_sims).

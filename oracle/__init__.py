@@ -103,6 +103,7 @@ def lib():
             L.lpo_phi.argtypes = [C.c_double]
             L.lpo_phi.restype = C.c_double
             L.lpo_estimator_r.argtypes = [C.c_int32, _P, _P] + [C.c_double] * 5
+            L.lpo_inflow_state.argtypes = [C.c_double] * 4 + [_P, _P]
             L.lpo_estimator_r.restype = C.c_double
             L.lpo_riemann_star.argtypes = [C.c_double] * 7 + [_P, _P]
             L.lpo_riemann_star.restype = C.c_int
@@ -285,6 +286,13 @@ def estimator_r(sl, sr, ell, s_i, s_ref=0.0, flat_eps=1e-6, active_frac=0.5) -> 
     assert sl.shape == sr.shape and 1 <= sl.shape[0] <= 3
     return float(lib().lpo_estimator_r(sl.shape[0], _ptr(sl), _ptr(sr), float(ell), float(s_i), float(s_ref),
                                        float(flat_eps), float(active_frac)))
+
+
+def inflow_state(gamma, P_res, rho_res, P_inf):
+    """(rho_inf, u_inf) of particles entering from a reservoir at rest."""
+    r = np.zeros(1); u = np.zeros(1)
+    lib().lpo_inflow_state(float(gamma), float(P_res), float(rho_res), float(P_inf), _ptr(r), _ptr(u))
+    return float(r[0]), float(u[0])
 
 
 def riemann_star(gamma, left, right):

@@ -28,6 +28,7 @@
  *   lpo_cfl_dt          CFL time step (the paper gives none; see the reading below).
  *   lpo_riemann_exact   exact Riemann solution of the ideal-gas shock tube
  *                       (textbook; the Sod check of the full scheme).
+ *   lpo_inflow_state    reservoir inflow state at a nozzle inlet (Sec. 4).
  *   lpo_mlp_*           FP64 forward/backward/Adam of the 8-32-1 estimator MLP.
  *
  * Readings where the paper is silent (the 3D forms are deferred to the 2018
@@ -994,6 +995,28 @@ int lpo_features(const lpo_config *c, int64_t n, const double *const *x, const d
     }
     free(cnt); free(tot); free(nb); free(d2m);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* reservoir inflow state (Sec. 4, the nozzle inlet boundary condition)      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The state of particles entering a nozzle from a reservoir at rest (P_res,
+ * rho_res), given the inflow pressure P_inf (the mean pressure near the
+ * inlet): the reservoir's entropy, P_res / rho_res^gamma = P_inf / rho_inf^gamma,
+ * gives rho_inf; the enthalpy balance u_res^2/2 + c_res^2/(gamma-1) =
+ * u_inf^2/2 + c_inf^2/(gamma-1) with u_res = 0 and c^2 = gamma P / rho gives
+ * u_inf (0 where the inflow pressure is not below the reservoir's).
+ */
+void lpo_inflow_state(double gamma, double P_res, double rho_res, double P_inf, double *rho_inf, double *u_inf)
+{
+    double rho = rho_res * pow(P_inf / P_res, 1.0 / gamma);
+    double c2_res = gamma * P_res / rho_res;
+    double c2 = gamma * P_inf / rho;
+    double w = 2.0 / (gamma - 1.0) * (c2_res - c2);
+    *rho_inf = rho;
+    *u_inf = w > 0.0 ? sqrt(w) : 0.0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -24,13 +24,55 @@ cudaError_t dalloc(P** p, size_t bytes)
     return cudaMalloc(reinterpret_cast<void**>(p), bytes);
 }
 
+// the buffers sized by the particle capacity n (sorted copies, records,
+// neighbour lists, sort ping-pong, fit-schedule lists), allocated at
+// lp_create and again by lp_reserve
+cudaError_t alloc_n_buffers(lp_ctx* c, int64_t n)
+{
+    const int dim = c->dc.dim;
+    c->hist_blocks = (n + 4095) / 4096;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+    A(dalloc(&c->keys[0], n * 8)); A(dalloc(&c->keys[1], n * 8));
+    A(dalloc(&c->vals[0], n * 4)); A(dalloc(&c->vals[1], n * 4));
+    A(dalloc(&c->hist, (size_t)256 * (c->hist_blocks + 1) * 4));   // block counts + digit totals
+    for (int k = 0; k < dim; ++k) { A(dalloc(&c->sx[k], n * 8)); A(dalloc(&c->su[k], n * 8)); }
+    A(dalloc(&c->sV, n * 8)); A(dalloc(&c->sP, n * 8)); A(dalloc(&c->sm, n * 8)); A(dalloc(&c->sid, n * 4));
+    A(dalloc(&c->rec, (size_t)n * REC_F4 * sizeof(float4)));
+    A(dalloc(&c->pos4, (size_t)n * 2 * sizeof(float4)));
+    A(dalloc(&c->nb_count, n * 4)); A(dalloc(&c->nb_total, n * 4));
+    A(dalloc(&c->nb_idx, (size_t)n * c->cfg.k_max * 4)); A(dalloc(&c->nb_d2min, n * 8));
+    A(dalloc(&c->sim_of, c->dc.nsim_max > 1 ? n * 4 : 4));
+    A(dalloc(&c->redo_list, n * 4));
+    A(dalloc(&c->plain_list, n * 4));
+    A(dalloc(&c->refine_list, n * 4));
+    A(dalloc(&c->mid, (size_t)n * MidN<3>::v * (c->cfg.precision == LP_PREC_FP32 ? 4 : 8)));
+    return e;
+}
+
+void free_n_buffers(lp_ctx* c)
+{
+    void** ptrs[] = {(void**)&c->keys[0], (void**)&c->keys[1], (void**)&c->vals[0], (void**)&c->vals[1],
+                     (void**)&c->hist, (void**)&c->sx[0], (void**)&c->sx[1], (void**)&c->sx[2], (void**)&c->su[0],
+                     (void**)&c->su[1], (void**)&c->su[2], (void**)&c->sV, (void**)&c->sP, (void**)&c->sm,
+                     (void**)&c->sid, (void**)&c->rec, (void**)&c->pos4, (void**)&c->nb_count,
+                     (void**)&c->nb_total, (void**)&c->nb_idx, (void**)&c->nb_d2min, (void**)&c->sim_of,
+                     (void**)&c->redo_list, (void**)&c->plain_list, (void**)&c->refine_list, (void**)&c->mid,
+                     (void**)&c->stage_buf};
+    for (void** p : ptrs) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+}
+
 void free_all(lp_ctx* c)
 {
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist, c->sx[0], c->sx[1], c->sx[2],
                     c->sV, c->su[0], c->su[1], c->su[2], c->sP, c->sm, c->sid, c->rec, c->pos4, c->cells, c->nb_count, c->nb_total,
                     c->nb_idx, c->nb_d2min, c->grid, c->dt_dev, c->dt_min, c->counters, c->redo_list,
                     c->plain_list, c->refine_list, c->mid, c->ext, c->grange, c->level_off_dev, c->sim_of,
-                    c->mlp_master, c->mlp_bf16, c->mlp_m1, c->mlp_m2, c->mlp_grad, c->mlp_loss, c->stage_buf};
+                    c->mlp_master, c->mlp_bf16, c->mlp_m1, c->mlp_m2, c->mlp_grad, c->mlp_loss, c->stage_buf,
+                    c->in_pattern, c->in_state, c->in_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -357,34 +399,14 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
         c->sort_lo_bit = top - 8 * passes;
         if (c->sort_lo_bit < 0) c->sort_lo_bit = 0;
     }
-    int64_t n = c->cap;
-    c->hist_blocks = (n + 4095) / 4096;
-    bool ok = true;
+    bool ok = alloc_n_buffers(c, c->cap) == cudaSuccess;
     auto A = [&](cudaError_t e) { if (e != cudaSuccess) ok = false; };
-    A(dalloc(&c->keys[0], n * 8)); A(dalloc(&c->keys[1], n * 8));
-    A(dalloc(&c->vals[0], n * 4)); A(dalloc(&c->vals[1], n * 4));
-    A(dalloc(&c->hist, (size_t)256 * (c->hist_blocks + 1) * 4));   // block counts + digit totals
-    for (int k = 0; k < 3; ++k) {
-        if (k < dim) {
-            A(dalloc(&c->sx[k], n * 8)); A(dalloc(&c->su[k], n * 8));
-        }
-    }
-    A(dalloc(&c->sV, n * 8)); A(dalloc(&c->sP, n * 8)); A(dalloc(&c->sm, n * 8)); A(dalloc(&c->sid, n * 4));
-    A(dalloc(&c->rec, (size_t)n * REC_F4 * sizeof(float4)));
-    A(dalloc(&c->pos4, (size_t)n * 2 * sizeof(float4)));
     A(dalloc(&c->cells, (size_t)c->table_entries * 8));
-    A(dalloc(&c->nb_count, n * 4)); A(dalloc(&c->nb_total, n * 4));
-    A(dalloc(&c->nb_idx, (size_t)n * cfg->k_max * 4)); A(dalloc(&c->nb_d2min, n * 8));
     int ns = d.nsim_max;
     A(dalloc(&c->grid, sizeof(Grid) * ns)); A(dalloc(&c->dt_dev, 8 * ns));
     A(dalloc(&c->dt_min, 8 * ns)); A(dalloc(&c->ext, 64 * (size_t)ns)); A(dalloc(&c->grange, 8));
     A(dalloc(&c->level_off_dev, sizeof(int64_t) * (MAX_LEVELS + 1)));
-    A(dalloc(&c->sim_of, batched ? n * 4 : 4));
     A(dalloc(&c->counters, C_COUNT * 8));
-    A(dalloc(&c->redo_list, n * 4));
-    A(dalloc(&c->plain_list, n * 4));
-    A(dalloc(&c->refine_list, n * 4));
-    A(dalloc(&c->mid, (size_t)n * MidN<3>::v * (cfg->precision == LP_PREC_FP32 ? 4 : 8)));
     A(dalloc(&c->mlp_master, MLP_NPARAM * 4)); A(dalloc(&c->mlp_bf16, MLP_NPARAM * 2));
     A(dalloc(&c->mlp_m1, MLP_NPARAM * 4)); A(dalloc(&c->mlp_m2, MLP_NPARAM * 4));
     A(dalloc(&c->mlp_grad, MLP_NPARAM * 4)); A(dalloc(&c->mlp_loss, 4));
@@ -403,6 +425,28 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
         return LP_ERR_CUDA;
     }
     *out = c;
+    return LP_OK;
+}
+
+lp_status lp_reserve(lp_ctx* c, int64_t capacity)
+{
+    if (!c || capacity < 1 || capacity > (int64_t)0x7fffffff || capacity < c->n_lists) return LP_ERR_ARG;
+    LP_CUDA(cudaDeviceSynchronize());
+    free_n_buffers(c);
+    c->cap = capacity;
+    c->cfg.capacity = capacity;
+    if (alloc_n_buffers(c, capacity) != cudaSuccess) {
+        free_n_buffers(c);
+        c->cap = 0;
+        return LP_ERR_CUDA;
+    }
+    // the tables still hold the last build's entries, whose keys are gone
+    LP_CUDA(cudaMemset(c->cells, 0, (size_t)c->table_entries * 8));
+    c->tables_dirty = 0;
+    c->n_lists = 0;
+    if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    LP_CUDA(cudaDeviceSynchronize());
     return LP_OK;
 }
 
@@ -432,6 +476,7 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
         c->tables_dirty = 0;
     }
     c->n_lists = 0;
+    c->lists_stale = 0;
     if (n == 0) return LP_OK;
     {
         Phase ph(c, LP_PH_GRID, 5 + (c->nsim > 1 ? 1 : 0), s);
@@ -495,7 +540,7 @@ lp_status lp_gfd_derivs(lp_ctx* c, const lp_particles* p, const double* const* f
 {
     if (!c || !p || !fields || !derivs || nfields < 1) return LP_ERR_ARG;
     if (out_dtype != LP_OUT_F32 && out_dtype != LP_OUT_F64) return LP_ERR_ARG;
-    if (c->n_lists != p->n) return LP_ERR_STATE;
+    if (c->n_lists != p->n || c->lists_stale) return LP_ERR_STATE;
     for (int f = 0; f < nfields; ++f)
         if (!fields[f]) return LP_ERR_ARG;
     int64_t n = p->n;
@@ -544,7 +589,7 @@ lp_status lp_onesided_derivs(lp_ctx* c, const lp_particles* p, const double* con
                              double* derivs, lp_stream stream)
 {
     if (!c || !p || !fields || !derivs || nfields < 1 || nfields > 5) return LP_ERR_ARG;
-    if (c->n_lists != p->n) return LP_ERR_STATE;
+    if (c->n_lists != p->n || c->lists_stale) return LP_ERR_STATE;
     for (int f = 0; f < nfields; ++f)
         if (!fields[f]) return LP_ERR_ARG;
     int64_t n = p->n;
@@ -837,6 +882,7 @@ lp_status lp_export_neighbors(lp_ctx* c, uint32_t* count, uint32_t* total, uint3
     if (!c) return LP_ERR_ARG;
     int64_t n = c->n_lists;
     if (n == 0) return LP_OK;
+    if (c->lists_stale) return LP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     if (count) LP_CUDA(cudaMemcpyAsync(count, c->nb_count, n * 4, cudaMemcpyDeviceToDevice, s));
     if (total) LP_CUDA(cudaMemcpyAsync(total, c->nb_total, n * 4, cudaMemcpyDeviceToDevice, s));
@@ -897,7 +943,7 @@ lp_status lp_graph_capture(lp_ctx* c, lp_particles* p, const int64_t* offsets, i
 {
     if (!c || !p || !stream) return LP_ERR_ARG;
     if (c->profiling) return LP_ERR_STATE;
-    if (c->n_lists != p->n || (c->dc.dim > 1 && !c->tables_dirty)) return LP_ERR_STATE;
+    if (c->n_lists != p->n || c->lists_stale || (c->dc.dim > 1 && !c->tables_dirty)) return LP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
     if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }

@@ -258,6 +258,7 @@ struct lp_ctx {
     cudaEvent_t ev_host_start, ev_host_in;
     cudaEvent_t gather_wait;      // when set, build() waits for it before the gather
     int64_t n_lists;          // n of the last neighbour build (0: none)
+    int lists_stale;          // lp_remove_outside ran since: the lists no longer describe the particles
     int tables_dirty;         // tables hold entries of the last build
     double reduce_min_w;
     // learned estimator: FP32 master weights, BF16 copy used by the kernels, Adam
@@ -269,6 +270,15 @@ struct lp_ctx {
     float* mlp_loss;
     int64_t mlp_step;
     int mlp_ready;
+    // reservoir inflow (lp_inflow): the in-plane lattice of a layer [in_npat][2],
+    // the device state (committed and next), the sampling partial sums, and
+    // the inlet of the first call
+    double* in_pattern;
+    int64_t in_npat;
+    double* in_state;
+    double* in_part;
+    int in_ghosts;                // reservoir ghosts were appended
+    lp_inlet in_cfg;
     // captured step
     cudaGraph_t graph;
     cudaGraphExec_t graph_exec;

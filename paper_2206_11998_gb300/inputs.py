@@ -289,6 +289,51 @@ def jet_snapshot_3d(n: int = 8_000_000, seed: int = 10, r_jet: float = 1.0, l_je
     return _state(x, 1.0 / rho, [zero, zero.copy(), uz], p, np.full(nj + na, h ** 3))
 
 
+def jet_inflow_3d(h: float, seed: int = 12, half_width: float = 4.0, length: float = 16.0,
+                  density_ratio: float = 1e3, pressure_ratio: float = 100.0, jitter: float = 0.2, fill: float = 1.0):
+    """The jet workload with inflow: an ambient gas at rest (rho = 1/density_ratio,
+    p = 1/pressure_ratio) filling [-w, w]^2 x [0, length] on a jittered cubic
+    lattice of spacing h density_ratio^(1/3), particle mass h^3; a column of
+    the jet's gas (rho = 1, p = 1, u_z = 3 c) of radius 1 and height `fill`
+    above the inlet on a jittered lattice of spacing h (ambient sites within
+    half their spacing of it are dropped); and the parameters of a reservoir
+    inlet of radius 1 at the origin, flowing along +z, whose injected particles
+    have that same mass on an in-plane lattice of spacing h (a layer of inflow
+    at density 1 is then h thick).
+
+    The reservoir (P_res, rho_res) = (2.8^3.5, 2.8^2.5) is the stagnation state
+    of a Mach-3 stream at p = 1, rho = 1 (gamma = 1.4: 1 + (gamma - 1) 3^2 / 2 =
+    2.8), so an inlet pressure of 1, 100 times the ambient's, draws a Mach-3
+    inflow at density 1, 1e3 times the ambient's.  Returns (state, inlet dict)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ha = h * density_ratio ** (1.0 / 3.0)
+    axes = [np.arange(-half_width + 0.5 * ha, half_width, ha), np.arange(-half_width + 0.5 * ha, half_width, ha),
+            np.arange(0.5 * ha, length, ha)]
+    g = np.meshgrid(*axes, indexing="ij")
+    xa = [a.ravel() + ha * rng.uniform(-jitter, jitter, a.size) for a in g]
+    ra = np.sqrt(xa[0] ** 2 + xa[1] ** 2)
+    out = np.maximum(ra - 1.0, 0.0)
+    dist = np.where(xa[2] <= fill, out, np.hypot(out, xa[2] - fill))
+    keep = dist > 0.5 * ha
+    xa = [a[keep] for a in xa]
+    axes = [np.arange(-1.0 + 0.5 * h, 1.0, h), np.arange(-1.0 + 0.5 * h, 1.0, h), np.arange(0.5 * h, fill, h)]
+    g = np.meshgrid(*axes, indexing="ij")
+    xj = [a.ravel() for a in g]
+    inside = xj[0] ** 2 + xj[1] ** 2 <= 1.0
+    xj = [a[inside] + h * rng.uniform(-jitter, jitter, int(inside.sum())) for a in xj]
+    na, nj = xa[0].shape[0], xj[0].shape[0]
+    x = [np.concatenate([a, b]) for a, b in zip(xa, xj)]
+    n = na + nj
+    rho = np.concatenate([np.full(na, 1.0 / density_ratio), np.ones(nj)])
+    p = np.concatenate([np.full(na, 1.0 / pressure_ratio), np.ones(nj)])
+    uz = np.concatenate([np.zeros(na), np.full(nj, 3.0 * np.sqrt(JET_GAMMA))])
+    st = _state(x, 1.0 / rho, [np.zeros(n), np.zeros(n), uz], p, np.full(n, h ** 3))
+    inlet = {"center": (0.0, 0.0, 0.0), "axis": 2, "radius": 1.0, "spacing": h, "mass": h ** 3,
+             "P_res": 2.8 ** 3.5, "rho_res": 2.8 ** 2.5, "sample_depth": 2.0 * h, "ghost_layers": 3,
+             "box": (half_width, 0.5, length)}       # outflow box: |x|, |y| <= w, -0.5 <= z <= length
+    return st, inlet
+
+
 def kh_ensemble_sizes(n_sims: int = 256, lo: int = 10_000, hi: int = 200_000, seed: int = 6):
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.integers(lo, hi + 1, size=n_sims)

@@ -31,7 +31,8 @@ EXPORTED = [
     "lp_status_string", "lp_version", "lp_set_profiling", "lp_phase_times", "lp_phase_name",
     "lp_sort_keys_noalloc", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step",
     "lp_mlp_train", "lp_mlp_infer", "lp_step_batched", "lp_graph_capture", "lp_graph_launch",
-    "lp_set_schedule", "lp_get_schedule", "lp_autotune", "lp_step_host",
+    "lp_set_schedule", "lp_get_schedule", "lp_autotune", "lp_step_host", "lp_inflow", "lp_reserve",
+    "lp_remove_outside",
 ]
 MLP_IN, MLP_H = 8, 32
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H + 1
@@ -85,6 +86,35 @@ class Stats(C.Structure):
 class StepDiag(C.Structure):
     _fields_ = [("flag", C.c_void_p), ("phi", C.c_void_p), ("r", C.c_void_p), ("features", C.c_void_p),
                 ("gate_p", C.c_void_p)]
+
+
+class Inlet(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("axis", C.c_int32), ("ghost_layers", C.c_int32),
+                ("radius", C.c_double), ("spacing", C.c_double), ("mass", C.c_double),
+                ("P_res", C.c_double), ("rho_res", C.c_double), ("sample_depth", C.c_double),
+                ("first_id", C.c_uint32), ("ghost_id", C.c_uint32)]
+
+
+class InflowInfo(C.Structure):
+    _fields_ = [("P_inf", C.c_double), ("rho_inf", C.c_double), ("u_inf", C.c_double), ("c_inf", C.c_double),
+                ("h_z", C.c_double), ("travel", C.c_double), ("layers", C.c_int64), ("layers_total", C.c_int64),
+                ("npat", C.c_int64), ("sampled", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def make_inlet(center, axis, radius, spacing, mass, P_res, rho_res, sample_depth, ghost_layers=2, first_id=0,
+               ghost_id=2**31) -> Inlet:
+    """A reservoir inlet for Context.inflow (see lp_inflow in lp.h)."""
+    q = Inlet()
+    for k in range(3):
+        q.center[k] = float(center[k])
+    q.axis, q.ghost_layers = int(axis), int(ghost_layers)
+    q.radius, q.spacing, q.mass = float(radius), float(spacing), float(mass)
+    q.P_res, q.rho_res, q.sample_depth = float(P_res), float(rho_res), float(sample_depth)
+    q.first_id, q.ghost_id = int(first_id), int(ghost_id)
+    return q
 
 
 def _diag(flag, phi, r, features, gate_p):
@@ -151,6 +181,13 @@ def lib():
         L.lp_mlp_adam_step.argtypes = [P, P, C.c_double, P]
         L.lp_mlp_train.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_double, P, P]
         L.lp_mlp_infer.argtypes = [P, P, C.c_int64, P, P]
+        L.lp_inflow.argtypes = [P, C.POINTER(Particles), C.c_int64, C.POINTER(Inlet), C.POINTER(C.c_int64),
+                                C.POINTER(InflowInfo), P]
+        L.lp_inflow.restype = C.c_int
+        L.lp_reserve.argtypes = [P, C.c_int64]
+        L.lp_remove_outside.argtypes = [P, C.POINTER(Particles), P, P, C.POINTER(C.c_int64), P]
+        L.lp_remove_outside.restype = C.c_int
+        L.lp_reserve.restype = C.c_int
         for name in ("lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step", "lp_mlp_train",
                      "lp_mlp_infer"):
             getattr(L, name).restype = C.c_int
@@ -208,10 +245,41 @@ class ParticleSet:
     P: object
     m: object
     id: object
+    count: object = None      # particles in use when the arrays hold more room (None: all)
 
     @property
     def n(self):
+        return int(self.V.shape[0]) if self.count is None else int(self.count)
+
+    @property
+    def capacity(self):
         return int(self.V.shape[0])
+
+    @staticmethod
+    def with_capacity(state, capacity, device="cuda"):
+        """Device arrays of `capacity` particles holding `state` in their first n."""
+        import torch
+        n = state["V"].shape[0]
+        assert capacity >= n
+
+        def t(a, dt=torch.float64):
+            v = torch.zeros(capacity, dtype=dt, device=device)
+            v[:n] = torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+            return v
+        return ParticleSet([t(a) for a in state["x"]], t(state["V"]), [t(a) for a in state["u"]], t(state["P"]),
+                           t(state["m"]), t(state["id"].astype(np.int32), torch.int32), count=n)
+
+    def grown(self, capacity):
+        """A copy with room for `capacity` particles (the first n copied)."""
+        import torch
+        n = self.n
+
+        def g(v):
+            w = torch.zeros(capacity, dtype=v.dtype, device=v.device)
+            w[:n] = v[:n]
+            return w
+        return ParticleSet([g(a) for a in self.x], g(self.V), [g(a) for a in self.u], g(self.P), g(self.m),
+                           g(self.id), count=n)
 
     @property
     def dim(self):
@@ -236,7 +304,8 @@ class ParticleSet:
                            t(state["m"]), t(state["id"].astype(np.int32), torch.int32))
 
     def to_state(self, n_fluid=None):
-        g = lambda a: a.detach().cpu().numpy()
+        n = self.n
+        g = lambda a: a[:n].detach().cpu().numpy()
         st = {"x": [g(a) for a in self.x], "V": g(self.V), "u": [g(a) for a in self.u], "P": g(self.P),
               "m": g(self.m), "id": g(self.id).astype(np.uint32)}
         if n_fluid is not None:
@@ -460,3 +529,34 @@ class Context:
 
     def dt_device_ptr(self):
         return lib().lp_dt_device(self.h)
+
+    # ---- reservoir inflow and capacity ---------------------------------------
+    def inflow(self, ps: ParticleSet, inlet: Inlet, stream=None):
+        """Reservoir inflow through `inlet` (lp_inflow): appends the particles
+        that entered into the room of ps (ps.count grows); returns the inflow
+        state of the call.  LPError(ERR_CAPACITY) when ps has no room."""
+        p = ps.struct()
+        n_out = C.c_int64(0)
+        info = InflowInfo()
+        _check(lib().lp_inflow(self.h, C.byref(p), ps.capacity, C.byref(inlet), C.byref(n_out), C.byref(info),
+                               _stream(stream)), "lp_inflow")
+        ps.count = int(n_out.value)
+        return info.as_dict()
+
+    def remove_outside(self, ps: ParticleSet, lo, hi, stream=None):
+        """Outflow: drop the particles outside the box [lo, hi] (lp_remove_outside);
+        ps.count shrinks.  Returns the number removed."""
+        p = ps.struct()
+        n_out = C.c_int64(0)
+        lo_a = (C.c_double * 3)(*[float(v) for v in lo])
+        hi_a = (C.c_double * 3)(*[float(v) for v in hi])
+        _check(lib().lp_remove_outside(self.h, C.byref(p), lo_a, hi_a, C.byref(n_out), _stream(stream)),
+               "lp_remove_outside")
+        removed = ps.n - int(n_out.value)
+        ps.count = int(n_out.value)
+        return removed
+
+    def reserve(self, capacity):
+        """Resize the context's scratch to `capacity` particles (lp_reserve)."""
+        _check(lib().lp_reserve(self.h, int(capacity)), "lp_reserve")
+        self.cfg.capacity = int(capacity)
