@@ -428,6 +428,18 @@ def run_ours(args):
         forms = None
         if world == 1 and not args.no_forms and args.precision == "fp32" and args.estimator == "plain":
             forms = other_forms(args, state, n, stream, lp, inputs, torch, flush)
+            try:
+                del ps
+                r = ensemble_measure(args, args.sims, min(args.steps, 10), args.warmup)
+                forms["fp32_batched_kh_ensemble"] = {
+                    "workload": "kh-ensemble-%d: 2D periodic shear layers of U[10k, 200k] particles" % r["sims"],
+                    "particles": r["particles"], "ms_per_step": r["batched_ms"],
+                    "value": r["particles"] / (r["batched_ms"] * 1e-3), "steps": r["steps"],
+                    "form": "every simulation in one lp_step_batched per step, replayed from a captured CUDA graph",
+                    "unbatched_ms_per_step": r["loop_ms"], "speedup_vs_unbatched": r["loop_ms"] / r["batched_ms"],
+                    "launches_per_step": r["launches"] / r["steps"], "autotune": r["tune"]}
+            except Exception as exc:
+                forms["ensemble_error"] = repr(exc)
 
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e["ms"]], world, torch, dist, "cuda")
     value = job_rate(world, n, args.steps, total_ms)
@@ -759,18 +771,16 @@ def kh_cfg(lp, n, nsim):
                           max_level=8)
 
 
-def run_ensemble(args):
+def ensemble_measure(args, nsim, steps, warmup):
     """Batched: all simulations in one lp_step_batched, replayed from a CUDA
     graph.  Unbatched comparison: one lp_step per simulation, each with its own
-    context, in a loop."""
+    context, in a loop.  Returns the measurements (dict)."""
     import torch
 
     from paper_2206_11998_gb300 import build as b
     from paper_2206_11998_gb300 import lp
 
     b.build()
-    torch.cuda.set_device(0)
-    nsim = args.sims
     sims = kh_states(nsim)
     sizes = np.array([s["V"].shape[0] for s in sims])
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
@@ -794,14 +804,14 @@ def run_ensemble(args):
             tune["chosen"] = ("split" if sch & lp.SCHED_SPLIT else "fused") + (
                 "+query-warp" if sch & lp.SCHED_QUERY_WARP else "+query-tiles")
         ctx.graph_capture(ps, offs_d, nsim, dt=0.0, cfl=CFL, t=t, stream=stream)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             ctx.graph_launch(stream=stream)
         stream.synchronize()
         l0 = ctx.stats(stream=stream)["kernel_launches"]
         sampler = ClockSampler(gpu_index_for(0))
         sampler.start()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for k in range(args.steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
             flush.zero_()
             ev[k][0].record(stream)
             ctx.graph_launch(stream=stream)
@@ -809,7 +819,7 @@ def run_ensemble(args):
         stream.synchronize()
         clocks = sampler.stop()
         launches = ctx.stats(stream=stream)["kernel_launches"] - l0
-        batched_ms = sum(a.elapsed_time(bb) for a, bb in ev) / args.steps
+        batched_ms = sum(a.elapsed_time(bb) for a, bb in ev) / steps
         # per-phase times of one eager batched step
         ctx.phase_times(stream=stream)
         ctx.set_profiling(True)
@@ -819,7 +829,6 @@ def run_ensemble(args):
     ctx.close()
     del ps
     # unbatched: one context per simulation, one lp_step each, in a loop
-    loop_ms = None
     with torch.cuda.stream(stream):
         ctxs, pss = [], []
         for s in sims:
@@ -831,7 +840,7 @@ def run_ensemble(args):
         stream.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         bb = torch.cuda.Event(enable_timing=True)
-        reps = max(1, min(args.steps, 3))
+        reps = max(1, min(steps, 3))
         a.record(stream)
         for _ in range(reps):
             for c, p in zip(ctxs, pss):
@@ -841,18 +850,26 @@ def run_ensemble(args):
         loop_ms = a.elapsed_time(bb) / reps
         for c in ctxs:
             c.close()
-    value = n * args.steps / (batched_ms * args.steps * 1e-3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": batched_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "kh-ensemble-%d" % nsim, "particles": n, "dim": 2, "gamma": KH_GAMMA,
+    return {"particles": n, "sims": nsim, "batched_ms": batched_ms, "loop_ms": loop_ms, "tune": tune,
+            "launches": launches, "clocks": clocks, "steps": steps,
+            "phases": {k: {"ms": v[0], "launches": v[1]} for k, v in phases.items() if v[1]}}
+
+
+def run_ensemble(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = ensemble_measure(args, args.sims, args.steps, args.warmup)
+    n, batched_ms, loop_ms = r["particles"], r["batched_ms"], r["loop_ms"]
+    line = {"metric": METRIC, "value": n / (batched_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": batched_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "kh-ensemble-%d" % r["sims"], "particles": n, "dim": 2, "gamma": KH_GAMMA,
                        "sizes": "U[10k, 200k] per simulation (seed 6)", "schedule": "batched, CUDA graph replay",
-                       "autotune": tune,
-                       "l2": "flushed between timed steps (256 MiB write)"},
+                       "autotune": r["tune"], "l2": "flushed between timed steps (256 MiB write)"},
             "unbatched": {"ms_per_step": loop_ms, "value": n / (loop_ms * 1e-3),
                           "note": "one lp_step per simulation in a loop, one context each"},
-            "speedup_vs_unbatched": loop_ms / batched_ms, "gpu_launches": launches, "clocks": clocks,
-            "phases": {k: {"ms": v[0], "launches": v[1]} for k, v in phases.items() if v[1]}}
+            "speedup_vs_unbatched": loop_ms / batched_ms, "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "phases": r["phases"]}
     print(json.dumps(line), flush=True)
 
 

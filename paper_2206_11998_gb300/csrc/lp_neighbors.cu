@@ -412,6 +412,8 @@ __device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
     if (lane == 0) {
         a.count[i] = (uint32_t)cnt;
         a.total[i] = min(inside_total, total_cap);
+        // the exact squared distance to the nearest entry (the CFL step's ell^2)
+        a.d2min[i] = cnt > 0 ? exact_d2<DIM>(a, i, b.j[0]) : INFINITY;
         if (inside_total > (uint32_t)c.k_max) atomicAdd(a.counters + C_OVERFLOW, 1ull);
         atomicMax(a.counters + C_MAXCOUNT, (unsigned long long)inside_total);
     }
@@ -890,6 +892,7 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
     list_append(a, act && !mine, (uint32_t)i);
     const uint32_t kmax = (uint32_t)c.k_max;
     uint32_t mx = 0, novf = 0;
+    uint32_t near_j = 0xffffffffu;       // this lane's particle: its nearest entry (none: all ones)
     unsigned todo = __ballot_sync(0xffffffffu, mine);
     // the hits of the next particle are loaded while the current one is sorted
     uint32_t fj[2] = {0u, 0u};
@@ -1025,6 +1028,8 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
 #pragma unroll
         for (int s = 0; s < 2; ++s)
             if (lane + 32u * s < keep) a.idx[ip * (int64_t)kmax + lane + 32 * s] = jv[s];
+        const uint32_t j0 = __shfl_sync(0xffffffffu, jv[0], 0);
+        if ((int)lane == p) near_j = keep > 0 ? j0 : 0xffffffffu;
         if (lane == 0) {
             a.count[ip] = keep;
             a.total[ip] = min(nin, 4u * kmax);
@@ -1036,6 +1041,9 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         if (novf) atomicAdd(a.counters + C_OVERFLOW, (unsigned long long)novf);
         if (mx) atomicMax(a.counters + C_MAXCOUNT, (unsigned long long)mx);
     }
+    // the exact squared distance to each particle's nearest entry (the CFL
+    // step's ell^2), every lane its own particle
+    if (mine) a.d2min[i] = near_j != 0xffffffffu ? exact_d2<DIM>(a, i, near_j) : INFINITY;
     __syncwarp();
     return true;
 }
@@ -1101,17 +1109,6 @@ __global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile(QueryArgs a)
             }
         }
     }
-}
-
-// exact FP64 squared distance to the first (nearest) list entry, one thread per
-// particle
-template <int DIM>
-__global__ void k_d2min(QueryArgs a)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    uint32_t cnt = a.count[i];
-    a.d2min[i] = cnt > 0 ? exact_d2<DIM>(a, i, a.idx[i * (int64_t)a.c.k_max]) : INFINITY;
 }
 
 // 1D, k nearest per side on the exactly x-ordered particles
@@ -1197,18 +1194,16 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
         return cudaGetLastError();
     }
     const int dim = c->dc.dim;
-    const unsigned tb = (unsigned)((n + 255) / 256);
     if (dim == 1) {
         k_query<1><<<(unsigned)((n + NB_WARPS - 1) / NB_WARPS), NB_WARPS * 32, 0, s>>>(a);
-        k_d2min<1><<<tb, 256, 0, s>>>(a);
         return cudaGetLastError();
     }
     cudaError_t e = cudaMemsetAsync(c->counters + C_QFB_LEN, 0, 8, s);
     if (e != cudaSuccess) return e;
     if (c->schedule & LP_SCHED_QUERY_WARP) {   // one warp per particle for every particle
         const unsigned wb = (unsigned)((n + NB_WARPS - 1) / NB_WARPS);
-        if (dim == 3) { k_query<3><<<wb, NB_WARPS * 32, 0, s>>>(a); k_d2min<3><<<tb, 256, 0, s>>>(a); }
-        else { k_query<2><<<wb, NB_WARPS * 32, 0, s>>>(a); k_d2min<2><<<tb, 256, 0, s>>>(a); }
+        if (dim == 3) k_query<3><<<wb, NB_WARPS * 32, 0, s>>>(a);
+        else k_query<2><<<wb, NB_WARPS * 32, 0, s>>>(a);
         return cudaGetLastError();
     }
     // tiles first; the particles they leave go to the per-particle kernel
@@ -1226,16 +1221,16 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     a.list = c->redo_list;
     a.list_len = c->counters + C_QFB_LEN;
     const unsigned fblocks = 152u * 4u;
-    if (dim == 3) { k_query<3><<<fblocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<3><<<tb, 256, 0, s>>>(a); }
-    else { k_query<2><<<fblocks, NB_WARPS * 32, 0, s>>>(a); k_d2min<2><<<tb, 256, 0, s>>>(a); }
+    if (dim == 3) k_query<3><<<fblocks, NB_WARPS * 32, 0, s>>>(a);
+    else k_query<2><<<fblocks, NB_WARPS * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 int query_launches(const lp_ctx* c)
 {
     if (c->dc.radius_mode == LP_RADIUS_KSIDE) return 1;
-    if (c->dc.dim == 1 || (c->schedule & LP_SCHED_QUERY_WARP)) return 2;
-    return 3;
+    if (c->dc.dim == 1 || (c->schedule & LP_SCHED_QUERY_WARP)) return 1;
+    return 2;
 }
 
 cudaError_t query_init()
