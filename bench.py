@@ -75,13 +75,19 @@ def fit_flops_per_particle(m: float, refined_frac: float = 0.0, plain_frac: floa
     return central + refined_frac * correction + plain_frac * onesided + 500.0
 
 
-# DRAM bytes per particle of one fit pass (split schedule, FP32), measured by
-# ncu (dram bytes read + written by k_step_central and k_step_plain) on the
-# 400k-particle gas cloud; None when the kernels change and the figure has not
-# been re-measured.  At 400k the records the fit gathers (about 38 MB) fit in
-# the 129 MB L2, at 2M (190 MB) they do not, so the figure is that of the
-# 400k cloud and is reported as such, not as the 2M run's traffic.
-FIT_TRAFFIC_BPP_400K = None
+# DRAM bytes per particle of one fit pass (split schedule, FP32: k_step_central,
+# k_step_central_refine, k_step_plain), measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass, every launch of three timed steps) on the
+# 2M-particle gas cloud this benchmark times: 2,163 MB per pass.  None when the
+# kernels change and the figure has not been re-measured.
+FIT_TRAFFIC_BPP_2M = 1081.4
+
+# warp instructions per particle of one neighbour query (k_query_tile and the
+# per-particle kernel over the particles it leaves; smsp__inst_executed.sum from
+# the same capture): the query is bound by instruction issue (integer, shuffle
+# and shared-memory work), so it is reported against the SM issue peak of
+# 4 warp instructions per clock per SM.
+QUERY_INST_PP_2M = 891.0
 
 # nominal FP64 rate of a GB300 (TFLOP/s): the roofline of the FP64 fit
 FP64_PEAK_TFLOPS = 1.25
@@ -471,7 +477,7 @@ def run_ours(args):
     fit_kernels = ("k_step_central + k_step_plain" if sched & lp.SCHED_SPLIT else "k_step") + \
         ("<float,3>" if args.precision == "fp32" else "<double,3>")
     traffic = fit_traffic(args.precision, args.estimator, bool(sched & lp.SCHED_SPLIT), ACTIVE, n,
-                          FIT_TRAFFIC_BPP_400K)
+                          FIT_TRAFFIC_BPP_2M if n == 2_000_000 else None)
     if args.precision == "fp32":
         alu_peak = fp32_peak
         alu_source = "FP32 CUDA cores: 152 SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (sm_max, peak_kind)
@@ -485,9 +491,19 @@ def run_ours(args):
                 "U^T D U factor and solve; correction pass on the refined share; one-sided Givens fits on the "
                 "plain-estimator share", "mean_neighbors": m_mean, "refined_frac": refined_frac,
                 "plain_frac": plain_frac, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the fit kernels on the "
-                                  "400k-particle cloud, scaled by particles (at 400k the gathered records fit in L2)"
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the fit kernels, every launch "
+                                  "of three timed steps of this 2M workload"
                                   if traffic else None}
+    query_roofline = None
+    if "neighbor-query" in phases and phases["neighbor-query"][0] > 0 and n == 2_000_000 and ACTIVE == "gas-cloud":
+        q_ms = phases["neighbor-query"][0] / args.steps
+        issue_peak = 152 * 4 * sm_max * 1e6
+        q_ach = QUERY_INST_PP_2M * n / (q_ms * 1e-3)
+        query_roofline = {"kernel": "k_query_tile + k_query (neighbour query)", "bound": "issue",
+                          "achieved": q_ach, "peak": issue_peak, "unit": "warp instructions/s",
+                          "frac": q_ach / issue_peak, "inst_per_particle": QUERY_INST_PP_2M,
+                          "peak_source": "152 SM x 4 schedulers x 1 warp instruction per clock x %.0f MHz" % sm_max,
+                          "inst_source": "ncu smsp__inst_executed.sum, every launch of three timed steps of this workload"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, q_n, secs = oracle_sample_rate(state, args.cpu_seconds)
@@ -509,7 +525,7 @@ def run_ours(args):
                                           "fp64_redo_per_step": st["n_fp64_redo"] / args.steps,
                                           "fit_schedule": tune, "estimator": args.estimator,
                                           "learned_gate": mlp_info}),
-                "roofline": roofline, "cpu_baseline": cpu,
+                "roofline": roofline, "query_roofline": query_roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                         "d2h_bytes_per_step": e2e["d2h"],
                         "api": "lp_step_host on page-locked host arrays (state copied in; the new state "
