@@ -1,16 +1,23 @@
 // lp_fit.cuh -- GFD least-squares fits and the LP update (Sec. 2.1), as
-// templates instantiated for FP32 (lp_fit_f32.cu) and FP64 (lp_fit_f64.cu).
+// templates instantiated for FP32 (lp_fit_f32.cu, lp_fit_f32_refine.cu) and
+// FP64 (lp_fit_f64.cu).
 //
-// Schedule: one thread per particle.  The overdetermined GFD system of
-// Eq. linear_system_axb (and its 1D/3D analogues) is reduced to triangular form
-// by square-root-free Givens rotations applied row by row as the neighbours
-// stream in, so the 9-column factor, Q^T b for all fields and the running row
-// live in registers; no stencil is staged and no lane idles.  Offsets are
-// scaled by a power of two (exact) so the factor is well scaled;
+// Schedule: one thread per particle; no stencil is staged and no lane idles.
+// The overdetermined GFD system of Sec. 2.1 (and its 1D/3D analogues) is
+// solved in one of two forms, both with the factor, the right-hand sides of
+// all fields and the running row in registers:
+//  * FP32 central fit: the normal equations A^T [A | B], accumulated row by row
+//    as the neighbours stream in (paired products in packed FP32 FMAs), factored
+//    as U^T D U (square-root-free Cholesky).  Their error grows as cond(A)^2, so
+//    where the factor's diagonal ratio is below refine_ratio one correction step
+//    (semi-normal equations on the residual) follows, and below 0.02 the rows are
+//    streamed again through the rotations below instead.
+//  * FP64 fits, the FP32 fallback and every one-sided fit: square-root-free
+//    Givens rotations applied row by row, which leave the same U^T D U form.
+// Offsets are scaled by a power of two (exact) so the factor is well scaled;
 // min|R_kk|/max|R_kk| decides the FP64 redo (FP32) or the first-order fallback
-// (FP64).  The FP32 path forms offsets and field
-// differences from split (hi, lo) floats, accurate to a few ulp of the offset
-// itself.
+// (FP64).  The FP32 path forms offsets and field differences from split
+// (hi, lo) floats, accurate to a few ulp of the offset itself.
 #pragma once
 
 #include "lp_internal.cuh"
