@@ -95,7 +95,7 @@ FP64_PEAK_TFLOPS = 1.25
 # algorithmic DRAM bytes per particle of the memory-bound phases
 BYTES_PER_PARTICLE = {
     "grid+keys": 24 + 8 + 24 + 12,          # extent read, m V read, positions read, key + index write
-    "radix-sort": 24,                       # per 8-bit pass: key + index read and written once
+    "radix-sort": 24,                       # per digit pass: key + index read and written once
     "gather": 76 + 76 + 64 + 32,            # state read; sorted copy, fit record and query positions written
     "cell-tables": 8 * 2,                   # sorted keys read (fill and clear)
 }
@@ -461,7 +461,9 @@ def run_ours(args):
             continue
         entry = {"ms_per_step": ms / args.steps, "launches": nl, "share": ms / max(1e-9, sum(v[0] for v in phases.values()))}
         if name in BYTES_PER_PARTICLE:
-            byts = BYTES_PER_PARTICLE[name] * n * (4 if name == "radix-sort" else 1)
+            # the sort runs three kernels per digit pass
+            passes = nl / (3 * args.steps) if name == "radix-sort" else 1
+            byts = BYTES_PER_PARTICLE[name] * n * passes
             gbs = byts / (ms / args.steps * 1e-3) / 1e9 if ms > 0 else None
             entry.update({"bound": "hbm", "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_peak if gbs else None})
         per_phase[name] = entry

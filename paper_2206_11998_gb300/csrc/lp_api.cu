@@ -30,12 +30,12 @@ cudaError_t dalloc(P** p, size_t bytes)
 cudaError_t alloc_n_buffers(lp_ctx* c, int64_t n)
 {
     const int dim = c->dc.dim;
-    c->hist_blocks = (n + 4095) / 4096;
+    c->hist_blocks = (n + RS_TILE_KEYS - 1) / RS_TILE_KEYS;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
     A(dalloc(&c->keys[0], n * 8)); A(dalloc(&c->keys[1], n * 8));
     A(dalloc(&c->vals[0], n * 4)); A(dalloc(&c->vals[1], n * 4));
-    A(dalloc(&c->hist, (size_t)256 * (c->hist_blocks + 1) * 4));   // block counts + digit totals
+    A(dalloc(&c->hist, (size_t)RS_BINS * (c->hist_blocks + 1) * 4));   // block counts + digit totals
     for (int k = 0; k < dim; ++k) { A(dalloc(&c->sx[k], n * 8)); A(dalloc(&c->su[k], n * 8)); }
     A(dalloc(&c->sV, n * 8)); A(dalloc(&c->sP, n * 8)); A(dalloc(&c->sm, n * 8)); A(dalloc(&c->sid, n * 4));
     A(dalloc(&c->rec, (size_t)n * REC_F4 * sizeof(float4)));
@@ -390,15 +390,7 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     }
     c->table_entries = dim > 1 ? off : 1;
     // sort bits: the simulation and the cells down to level lmax_cap
-    if (dim == 1) { c->sort_lo_bit = 0; c->sort_hi_bit = 64; }
-    else {
-        int top = dim * d.mbits + simbits;
-        int need = dim * c->lmax_cap + simbits;
-        int passes = (need + 7) / 8;
-        c->sort_hi_bit = top;
-        c->sort_lo_bit = top - 8 * passes;
-        if (c->sort_lo_bit < 0) c->sort_lo_bit = 0;
-    }
+    sort_bit_range(dim, d.mbits, c->lmax_cap, simbits, c->sort_lo_bit, c->sort_hi_bit);
     bool ok = alloc_n_buffers(c, c->cap) == cudaSuccess;
     auto A = [&](cudaError_t e) { if (e != cudaSuccess) ok = false; };
     A(dalloc(&c->cells, (size_t)c->table_entries * 8));

@@ -118,6 +118,23 @@ __host__ __device__ inline uint64_t morton(const uint32_t* q)
 }
 
 // total order of doubles as unsigned integers (-0 is mapped to +0)
+// LSD radix sort of the Morton keys: RS_BITS-bit digits over tiles of
+// RS_TILE_KEYS keys (block counts and digit totals: RS_BINS x (tiles + 1) words)
+constexpr int RS_BITS = 9;
+constexpr int RS_BINS = 1 << RS_BITS;
+constexpr int RS_TILE_KEYS = 4096;
+
+// bits [lo, hi) of a key the sort orders by: the simulation index and the cell
+// bits down to table level lmax_cap (every bit in 1D), in whole digits
+inline void sort_bit_range(int dim, int mbits, int lmax_cap, int simbits, int& lo, int& hi)
+{
+    if (dim == 1) { lo = 0; hi = 64; return; }
+    hi = dim * mbits + simbits;
+    const int need = dim * lmax_cap + simbits;
+    lo = hi - RS_BITS * ((need + RS_BITS - 1) / RS_BITS);
+    if (lo < 0) lo = 0;
+}
+
 __device__ inline uint64_t order_key(double x)
 {
     if (x == 0.0) x = 0.0;

@@ -14,9 +14,10 @@ namespace {
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+static_assert(RS_TILE == RS_TILE_KEYS, "the histogram is sized for this tile");
+static_assert(RS_BINS == 2 * RS_THREADS, "each thread owns two digits of the histogram");
+constexpr uint32_t RS_MASK = RS_BINS - 1;
 
-__device__ inline void atomic_min_d(unsigned long long* a, double v) { atomicMin(a, (unsigned long long)order_key(v)); }
-__device__ inline void atomic_max_d(unsigned long long* a, double v) { atomicMax(a, (unsigned long long)order_key(v)); }
 
 __device__ inline double from_order_key(unsigned long long k)
 {
@@ -26,85 +27,119 @@ __device__ inline double from_order_key(unsigned long long k)
 
 constexpr int EXT_ITEMS = 16;
 
-__device__ inline void flush_extent(int dim, unsigned long long* e, const double (&lo)[3], const double (&hi)[3],
-                                    double wlo, double whi)
+// order key of the double with bit pattern b (order_key without FP64
+// instructions), and whether b is a NaN (NaNs take no part in an extent, as
+// with fmin / fmax)
+__device__ __forceinline__ uint64_t order_key_bits(uint64_t b)
 {
-    for (int k = 0; k < dim; ++k) {
-        atomic_min_d(e + k, lo[k]);
-        atomic_max_d(e + 3 + k, hi[k]);
-    }
-    atomic_min_d(e + 6, wlo);
-    atomic_max_d(e + 7, whi);
+    if ((b << 1) == 0) b = 0;                   // -0 as +0
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
+__device__ __forceinline__ bool is_nan_bits(uint64_t b) { return (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull; }
+
+constexpr uint64_t KEY_POS_INF = 0xfff0000000000000ull;   // order_key(+inf)
+constexpr uint64_t KEY_NEG_INF = 0x000fffffffffffffull;   // order_key(-inf)
+
+// extent of one run of particles, as order keys: lo[k], hi[k] of the
+// coordinates and wlo, whi of m V
+struct ExtKeys {
+    uint64_t lo[3], hi[3], wlo, whi;
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { lo[k] = KEY_POS_INF; hi[k] = KEY_NEG_INF; }
+        wlo = KEY_POS_INF;
+        whi = KEY_NEG_INF;
+    }
+    template <int DIM>
+    __device__ __forceinline__ void add(const double* const (&xs)[3], const double* m, const double* V, int64_t i)
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const uint64_t b = (uint64_t)__double_as_longlong(xs[k][i]);
+            if (is_nan_bits(b)) continue;
+            const uint64_t q = order_key_bits(b);
+            lo[k] = q < lo[k] ? q : lo[k];
+            hi[k] = q > hi[k] ? q : hi[k];
+        }
+        const uint64_t bw = (uint64_t)__double_as_longlong(__dmul_rn(m[i], V[i]));
+        if (!is_nan_bits(bw)) {
+            const uint64_t q = order_key_bits(bw);
+            wlo = q < wlo ? q : wlo;
+            whi = q > whi ? q : whi;
+        }
+    }
+    template <int DIM>
+    __device__ void flush(unsigned long long* e) const
+    {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            atomicMin(e + k, (unsigned long long)lo[k]);
+            atomicMax(e + 3 + k, (unsigned long long)hi[k]);
+        }
+        atomicMin(e + 6, (unsigned long long)wlo);
+        atomicMax(e + 7, (unsigned long long)whi);
+    }
+};
 
 // ext[8 s + 0..2] min x_k, [8 s + 3..5] max x_k, [8 s + 6] min w, [8 s + 7] max w
 // (order keys) of simulation s.  One simulation: grid-stride accumulation and a
 // warp reduction; several: EXT_ITEMS particles per thread, reduced over the
 // warp when the warp's particles share a simulation (they are stored by
-// simulation), with atomics per run otherwise.
-__global__ void k_reduce_extent(int dim, int64_t n, const double* __restrict__ x0,
+// simulation), with atomics per run otherwise.  The comparisons are integer
+// ones on the order keys (FP64 min / max would run on the scarce FP64 units).
+template <int DIM>
+__global__ void k_reduce_extent(int64_t n, const double* __restrict__ x0,
                                 const double* __restrict__ x1, const double* __restrict__ x2,
                                 const double* __restrict__ m, const double* __restrict__ V,
                                 const uint32_t* __restrict__ sim_of, unsigned long long* ext)
 {
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    double wlo = INFINITY, whi = -INFINITY;
-    const double* xs[3] = {x0, x1, x2};
+    ExtKeys r;
+    r.init();
+    const double* const xs[3] = {x0, x1, x2};
     uint32_t sim = 0;
     if (!sim_of) {
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-            for (int k = 0; k < dim; ++k) {
-                double v = xs[k][i];
-                lo[k] = fmin(lo[k], v);
-                hi[k] = fmax(hi[k], v);
-            }
-            double w = __dmul_rn(m[i], V[i]);
-            wlo = fmin(wlo, w);
-            whi = fmax(whi, w);
-        }
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            r.add<DIM>(xs, m, V, i);
     } else {
         // EXT_ITEMS particles per thread (strided by the block size, so loads
         // stay coalesced); a change of simulation flushes the running extent
         sim = 0xffffffffu;
         const int64_t base = (int64_t)blockIdx.x * blockDim.x * EXT_ITEMS + threadIdx.x;
-        for (int r = 0; r < EXT_ITEMS; ++r) {
-            const int64_t i = base + (int64_t)r * blockDim.x;
+        for (int q = 0; q < EXT_ITEMS; ++q) {
+            const int64_t i = base + (int64_t)q * blockDim.x;
             if (i >= n) break;
             const uint32_t si = sim_of[i];
-            const double w = __dmul_rn(m[i], V[i]);
             if (si != sim) {
-                if (sim != 0xffffffffu) flush_extent(dim, ext + 8 * (int64_t)sim, lo, hi, wlo, whi);
+                if (sim != 0xffffffffu) r.flush<DIM>(ext + 8 * (int64_t)sim);
                 sim = si;
-                for (int k = 0; k < dim; ++k) { lo[k] = xs[k][i]; hi[k] = lo[k]; }
-                wlo = whi = w;
-            } else {
-                for (int k = 0; k < dim; ++k) {
-                    const double v = xs[k][i];
-                    lo[k] = fmin(lo[k], v);
-                    hi[k] = fmax(hi[k], v);
-                }
-                wlo = fmin(wlo, w);
-                whi = fmax(whi, w);
+                r.init();
             }
+            r.add<DIM>(xs, m, V, i);
         }
     }
     uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
     bool uniform = __all_sync(0xffffffffu, sim == s0 || sim == 0xffffffffu);
     if (uniform) {
         for (int o = 16; o > 0; o >>= 1) {
-            for (int k = 0; k < 3; ++k) {
-                lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-                hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const uint64_t a = __shfl_xor_sync(0xffffffffu, r.lo[k], o);
+                const uint64_t b = __shfl_xor_sync(0xffffffffu, r.hi[k], o);
+                r.lo[k] = a < r.lo[k] ? a : r.lo[k];
+                r.hi[k] = b > r.hi[k] ? b : r.hi[k];
             }
-            wlo = fmin(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
-            whi = fmax(whi, __shfl_xor_sync(0xffffffffu, whi, o));
+            const uint64_t a = __shfl_xor_sync(0xffffffffu, r.wlo, o);
+            const uint64_t b = __shfl_xor_sync(0xffffffffu, r.whi, o);
+            r.wlo = a < r.wlo ? a : r.wlo;
+            r.whi = b > r.whi ? b : r.whi;
         }
         if (lane_id() != 0 || s0 == 0xffffffffu) return;
         sim = s0;
     } else if (sim == 0xffffffffu) {
         return;
     }
-    flush_extent(dim, ext + 8 * (int64_t)sim, lo, hi, wlo, whi);
+    r.flush<DIM>(ext + 8 * (int64_t)sim);
 }
 
 __global__ void k_init_extent(unsigned long long* ext, int nsim)
@@ -192,16 +227,14 @@ __global__ void k_keys(int64_t n, const double* __restrict__ x0, const double* _
     uint32_t sim = sim_of ? sim_of[i] : 0u;
     const Grid* g = grids + sim;
     double inv = g->inv;
-    const double qmax = (double)((1u << mbits) - 1u);
+    const uint32_t qmax = (1u << mbits) - 1u;
     uint32_t q[3] = {0, 0, 0};
     for (int k = 0; k < DIM; ++k) {
-        double t = __dmul_rn(__dsub_rn(xs[k][i], g->lo[k]), inv);
-        double f = floor(t);
-        uint32_t v;
-        if (!(f > 0.0)) v = 0;
-        else if (f >= qmax) v = (uint32_t)qmax;
-        else v = (uint32_t)f;
-        q[k] = v;
+        // floor(t) clamped to [0, qmax]: the conversion rounds down and
+        // saturates (negative and NaN give 0), so one FP64 conversion replaces
+        // floor and two comparisons
+        const double t = __dmul_rn(__dsub_rn(xs[k][i], g->lo[k]), inv);
+        q[k] = min(__double2uint_rd(t), qmax);
     }
     keys[i] = ((uint64_t)sim << (DIM * mbits)) | morton<DIM>(q);
     vals[i] = (uint32_t)i;
@@ -212,16 +245,18 @@ __global__ void k_keys(int64_t n, const double* __restrict__ x0, const double* _
 __global__ void k_rs_upsweep(int64_t n, const uint64_t* __restrict__ keys, int shift,
                              uint32_t* __restrict__ counts, int64_t nblocks)
 {
-    __shared__ uint32_t h[256];
+    __shared__ uint32_t h[RS_BINS];
     h[threadIdx.x] = 0;
+    h[threadIdx.x + RS_THREADS] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_TILE;
     for (int r = 0; r < RS_ITEMS; ++r) {
         int64_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & RS_MASK], 1u);
     }
     __syncthreads();
     counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    counts[(int64_t)(threadIdx.x + RS_THREADS) * nblocks + blockIdx.x] = h[threadIdx.x + RS_THREADS];
 }
 
 // Per digit d (one block each): exclusive scan of the block counts
@@ -270,12 +305,14 @@ k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __re
                const uint32_t* __restrict__ counts, const uint32_t* __restrict__ totals, int64_t nblocks)
 {
     constexpr int NW = RS_THREADS / 32;
-    __shared__ uint32_t wc[NW][256];
-    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t wc[NW][RS_BINS];
+    __shared__ uint32_t dbase[RS_BINS];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    // digit bases: exclusive scan of the 256 digit totals
+    // digit bases: exclusive scan of the digit totals, thread t owning digits
+    // 2t and 2t + 1, plus this tile's offset within each digit
     {
-        const uint32_t v = totals[t];
+        const uint32_t v0 = totals[2 * t], v1 = totals[2 * t + 1];
+        const uint32_t v = v0 + v1;
         uint32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -286,10 +323,12 @@ k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __re
         __syncthreads();
         uint32_t add = 0;
         for (int ww = 0; ww < w; ++ww) add += wc[0][ww];
-        dbase[t] = add + x - v + counts[(int64_t)t * nblocks + blockIdx.x];
+        const uint32_t b0 = add + x - v;
+        dbase[2 * t] = b0 + counts[(int64_t)(2 * t) * nblocks + blockIdx.x];
+        dbase[2 * t + 1] = b0 + v0 + counts[(int64_t)(2 * t + 1) * nblocks + blockIdx.x];
     }
     __syncthreads();
-    for (int d = lane; d < 256; d += 32) wc[w][d] = 0;
+    for (int d = lane; d < RS_BINS; d += 32) wc[w][d] = 0;
     __syncwarp();
     const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (32 * RS_ITEMS);
     const unsigned lt = (1u << lane) - 1u;
@@ -301,7 +340,7 @@ k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __re
         const bool valid = i < n;
         key[r] = valid ? kin[i] : 0ull;
         val[r] = valid ? vin[i] : 0u;
-        const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & 255u) : 256u + lane;
+        const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & RS_MASK) : RS_BINS + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const bool leader = (__ffs(peers) - 1) == lane;
         loc[r] = valid ? wc[w][d] + __popc(peers & lt) : 0u;
@@ -310,12 +349,15 @@ k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __re
         __syncwarp();
     }
     __syncthreads();
-    {   // per digit: offsets of the warps' runs in tile order
-        uint32_t run = dbase[t];
+    // per digit: offsets of the warps' runs in tile order
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int d = t + h * RS_THREADS;
+        uint32_t run = dbase[d];
 #pragma unroll
         for (int ww = 0; ww < NW; ++ww) {
-            const uint32_t c = wc[ww][t];
-            wc[ww][t] = run;
+            const uint32_t c = wc[ww][d];
+            wc[ww][d] = run;
             run += c;
         }
     }
@@ -324,7 +366,7 @@ k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __re
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t i = base + r * 32 + lane;
         if (i < n) {
-            const uint32_t d = (uint32_t)((key[r] >> shift) & 255u);
+            const uint32_t d = (uint32_t)((key[r] >> shift) & RS_MASK);
             const uint32_t pos = wc[w][d] + loc[r];
             kout[pos] = key[r];
             vout[pos] = val[r];
@@ -447,8 +489,11 @@ cudaError_t build_grid(lp_ctx* c, const lp_particles* p, cudaStream_t s)
     unsigned blocks = nsim > 1 ? (unsigned)((n + 256 * EXT_ITEMS - 1) / (256 * EXT_ITEMS))
                                : (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
     if (blocks == 0) blocks = 1;
-    k_reduce_extent<<<blocks, 256, 0, s>>>(c->dc.dim, n, p->x[0], p->x[1] ? p->x[1] : p->x[0],
-                                           p->x[2] ? p->x[2] : p->x[0], p->m, p->V, sim_of, c->ext);
+    const double* x1 = p->x[1] ? p->x[1] : p->x[0];
+    const double* x2 = p->x[2] ? p->x[2] : p->x[0];
+    if (c->dc.dim == 3) k_reduce_extent<3><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, p->m, p->V, sim_of, c->ext);
+    else if (c->dc.dim == 2) k_reduce_extent<2><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, p->m, p->V, sim_of, c->ext);
+    else k_reduce_extent<1><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, p->m, p->V, sim_of, c->ext);
     k_finalize_grid<<<(unsigned)((nsim + 127) / 128), 128, 0, s>>>(c->dc, c->lmax_cap, nsim, c->ext, c->grid);
     k_grid_range<<<1, 1, 0, s>>>(nsim, c->grid, c->grange);
     return cudaGetLastError();
@@ -469,16 +514,16 @@ cudaError_t make_keys(lp_ctx* c, const lp_particles* p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-int radix_passes(const lp_ctx* c) { return (c->sort_hi_bit - c->sort_lo_bit + 7) / 8; }
+int radix_passes(const lp_ctx* c) { return (c->sort_hi_bit - c->sort_lo_bit + RS_BITS - 1) / RS_BITS; }
 
 cudaError_t radix_sort(lp_ctx* c, int64_t n, cudaStream_t s)
 {
     int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
     int cur = 0;
-    for (int sh = c->sort_lo_bit; sh < c->sort_hi_bit; sh += 8) {
-        uint32_t* totals = c->hist + 256 * nblocks;
+    for (int sh = c->sort_lo_bit; sh < c->sort_hi_bit; sh += RS_BITS) {
+        uint32_t* totals = c->hist + RS_BINS * nblocks;
         k_rs_upsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, c->keys[cur], sh, c->hist, nblocks);
-        k_rs_scan<<<256, 1024, 0, s>>>(c->hist, nblocks, totals);
+        k_rs_scan<<<RS_BINS, 1024, 0, s>>>(c->hist, nblocks, totals);
         k_rs_downsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, c->keys[cur], c->vals[cur], c->keys[cur ^ 1],
                                                                 c->vals[cur ^ 1], sh, c->hist, totals, nblocks);
         cur ^= 1;
@@ -550,7 +595,7 @@ constexpr size_t NA_KEYS1 = NA_KEYS0 + 8 * NOALLOC_MAX_N;
 constexpr size_t NA_VALS0 = NA_KEYS1 + 8 * NOALLOC_MAX_N;
 constexpr size_t NA_VALS1 = NA_VALS0 + 4 * NOALLOC_MAX_N;
 constexpr size_t NA_HIST = NA_VALS1 + 4 * NOALLOC_MAX_N;
-constexpr size_t NA_EXT = NA_HIST + ((256 * (NA_BLOCKS + 1) * 4 + 255) / 256) * 256;   // counts + digit totals
+constexpr size_t NA_EXT = NA_HIST + ((RS_BINS * (NA_BLOCKS + 1) * 4 + 255) / 256) * 256;   // counts + digit totals
 constexpr size_t NA_GRID = NA_EXT + 256;
 constexpr size_t NA_BYTES = NA_GRID + 256;
 
@@ -629,26 +674,25 @@ extern "C" lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double* 
     dc.nsim_max = 1;
     int lmax_cap = dim == 3 ? 9 : (dim == 2 ? 13 : 0);
     int lo_bit = 0, hi_bit = 64;
-    if (dim > 1) {
-        hi_bit = dim * MORTON_BITS;
-        lo_bit = hi_bit - 8 * ((dim * lmax_cap + 7) / 8);
-    }
+    sort_bit_range(dim, MORTON_BITS, lmax_cap, 0, lo_bit, hi_bit);
     unsigned gb = grid_for(n, 256);
     int64_t nb_ = gb;
     unsigned rblocks = (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
     k_init_extent<<<1, 32, 0, s>>>(ext, 1);
-    k_reduce_extent<<<rblocks, 256, 0, s>>>(dim, n, x0, p1, p2, x0, x0, nullptr, ext);
+    if (dim == 3) k_reduce_extent<3><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, x0, x0, nullptr, ext);
+    else if (dim == 2) k_reduce_extent<2><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, x0, x0, nullptr, ext);
+    else k_reduce_extent<1><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, x0, x0, nullptr, ext);
     k_finalize_grid<<<1, 1, 0, s>>>(dc, lmax_cap, 1, ext, grid);
     if (dim == 3) k_keys<3><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
     else if (dim == 2) k_keys<2><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
     else k_keys<1><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
     int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
     int cur = 0;
-    for (int sh = lo_bit; sh < hi_bit; sh += 8) {
+    for (int sh = lo_bit; sh < hi_bit; sh += RS_BITS) {
         k_rs_upsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, keys[cur], sh, hist, nblocks);
-        k_rs_scan<<<256, 1024, 0, s>>>(hist, nblocks, hist + 256 * nblocks);
+        k_rs_scan<<<RS_BINS, 1024, 0, s>>>(hist, nblocks, hist + RS_BINS * nblocks);
         k_rs_downsweep<<<(unsigned)nblocks, RS_THREADS, 0, s>>>(n, keys[cur], vals[cur], keys[cur ^ 1],
-                                                                vals[cur ^ 1], sh, hist, hist + 256 * nblocks, nblocks);
+                                                                vals[cur ^ 1], sh, hist, hist + RS_BINS * nblocks, nblocks);
         cur ^= 1;
     }
     k_copy_sorted<<<gb, 256, 0, s>>>(n, keys[cur], vals[cur], keys_out, perm_out);

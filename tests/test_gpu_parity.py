@@ -103,8 +103,10 @@ def test_neighbor_lists_bit_exact(name):
         g = ctx.grid_info()
         okeys = oracle.morton_keys(st["x"], g[:cfg.dim], g[3], 21)
         assert np.array_equal(keys, okeys[ids])
+        # the sort orders by the cell bits down to table level 9 (3D) or 13
+        # (2D), in whole 9-bit digits
         top = cfg.dim * 21
-        lo_bit = top - 8 * ((cfg.dim * (9 if cfg.dim == 3 else 13) + 7) // 8)
+        lo_bit = top - 9 * ((cfg.dim * (9 if cfg.dim == 3 else 13) + 8) // 9)
         order = np.lexsort((np.arange(len(okeys)), okeys >> np.uint64(max(lo_bit, 0))))
         assert np.array_equal(ids, order)
     ctx.close()
