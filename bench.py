@@ -101,6 +101,14 @@ BYTES_PER_PARTICLE = {
 }
 
 
+def schedule_name(lp, sch: int) -> str:
+    """The autotuner's choice as text: fit schedule + query schedule."""
+    fit = ("split" if sch & lp.SCHED_SPLIT else "fused") + ("-queue" if sch & lp.SCHED_QUEUE_FIT else "")
+    query = "query-warp" if sch & lp.SCHED_QUERY_WARP else (
+        "query-tiles-queue" if sch & lp.SCHED_QUEUE_QUERY else "query-tiles")
+    return fit + "+" + query
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,8 +397,7 @@ def run_ours(args):
         elif not args.no_autotune:
             tune = ctx.autotune(ps, dt=0.0, cfl=CFL, reps=3, stream=stream)
             sch = ctx.schedule()
-            tune["chosen"] = ("split" if sch & lp.SCHED_SPLIT else "fused") + (
-                "+query-warp" if sch & lp.SCHED_QUERY_WARP else "+query-tiles")
+            tune["chosen"] = schedule_name(lp, sch)
         # mean neighbour count of the current lists (algorithmic work per particle)
         cnt = ctx.export_neighbors(n, stream=stream)[0]
         m_mean = float(cnt.double().mean().item())
@@ -819,8 +826,7 @@ def ensemble_measure(args, nsim, steps, warmup):
         if not args.no_autotune:
             tune = ctx.autotune(ps, offs_d, nsim, dt=0.0, cfl=CFL, reps=2, stream=stream)
             sch = ctx.schedule()
-            tune["chosen"] = ("split" if sch & lp.SCHED_SPLIT else "fused") + (
-                "+query-warp" if sch & lp.SCHED_QUERY_WARP else "+query-tiles")
+            tune["chosen"] = schedule_name(lp, sch)
         ctx.graph_capture(ps, offs_d, nsim, dt=0.0, cfl=CFL, t=t, stream=stream)
         for _ in range(warmup):
             ctx.graph_launch(stream=stream)

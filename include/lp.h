@@ -499,12 +499,22 @@ lp_status lp_graph_launch(lp_ctx *ctx, lp_stream stream);
  *                          the per-particle kernel for the particles a tile
  *                          leaves (more than 64 neighbours, scattered groups).
  *     LP_SCHED_QUERY_WARP  one warp per particle for every particle.
+ *   work distribution (same results):
+ *     LP_SCHED_QUEUE_QUERY the tile kernel runs as a grid of resident blocks
+ *                          whose warps take their next tile of 32 particles
+ *                          from a device work counter (a warp work queue)
+ *                          instead of one tile per warp of the launch.
+ *     LP_SCHED_QUEUE_FIT   likewise for the SPLIT schedule's two kernels
+ *                          (32 particles, then 32 list entries, per take);
+ *                          FP32 path.
  * The default is SPLIT with the learned estimator, FUSED otherwise, and tiles.
  * A graph captured by lp_graph_capture keeps the schedule it was captured with.
  */
 #define LP_SCHED_FUSED 0
 #define LP_SCHED_SPLIT 1
 #define LP_SCHED_QUERY_WARP 2
+#define LP_SCHED_QUEUE_QUERY 4
+#define LP_SCHED_QUEUE_FIT 8
 lp_status lp_set_schedule(lp_ctx *ctx, int32_t schedule);   /* LP_ERR_ARG on unknown bits */
 lp_status lp_get_schedule(lp_ctx *ctx, int32_t *schedule);
 
@@ -515,12 +525,17 @@ lp_status lp_get_schedule(lp_ctx *ctx, int32_t *schedule);
  * launches after one warm-up, CUDA events on `stream`), selects the faster of
  * each, and writes the mean times in milliseconds to out_ms[0] (fit FUSED),
  * out_ms[1] (fit SPLIT), out_ms[2] (query tiles), out_ms[3] (query per
- * particle) when out_ms (host, 4 doubles) is not null.  The particle state is
+ * particle), out_ms[4] (query tiles, LP_SCHED_QUEUE_QUERY) and out_ms[5] (fit
+ * SPLIT | LP_SCHED_QUEUE_FIT; 0 on the FP64 path, where it is not offered)
+ * when out_ms (host, LP_AUTOTUNE_TIMES doubles) is not null.  Entries of
+ * schedules that do not apply (the query schedules of 1D and k-per-side
+ * neighbourhoods) are 0.  The particle state is
  * not changed (the timed fit passes write to scratch buffers the call
  * allocates and frees); the counters, the device time steps (lp_dt_device) and
  * the launch tally are restored.  Synchronises `stream`.  LP_ERR_STATE while
  * profiling is on.
  */
+#define LP_AUTOTUNE_TIMES 6
 lp_status lp_autotune(lp_ctx *ctx, lp_particles *p, const int64_t *offsets, int32_t nsim, double dt, double cfl,
                       int32_t reps, double *out_ms, lp_stream stream);
 

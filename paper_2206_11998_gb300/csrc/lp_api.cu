@@ -207,6 +207,7 @@ void fill_fit_args(lp_ctx* c, FitArgs& a, int64_t n)
     a.plain_len = c->counters + C_PLAIN_LEN;
     a.refine_list = c->refine_list;
     a.refine_len = c->counters + C_REFINE_LEN;
+    a.queue = c->counters + C_QUEUE_CENTRAL;      // and C_QUEUE_PLAIN after it
     a.mid = c->mid;
     a.mid_cap = c->cap;
 }
@@ -289,7 +290,8 @@ lp_status run_fit(lp_ctx* c, FitArgs a, const StepOut& o, int sched, cudaStream_
         if (defer) LP_CUDA(cudaMemsetAsync(c->counters + C_REFINE_LEN, 0, 8, s));
         {
             Phase ph(c, LP_PH_FIT, split ? (defer ? 3 : 2) : 1, s);
-            LP_CUDA(split ? launch_step_split_f32(dim, a, o, s) : launch_step_f32(dim, a, o, s));
+            if (split && (sched & LP_SCHED_QUEUE_FIT)) LP_CUDA(launch_step_split_queue_f32(dim, a, o, s));
+            else LP_CUDA(split ? launch_step_split_f32(dim, a, o, s) : launch_step_f32(dim, a, o, s));
         }
         a.list = c->redo_list;
         Phase ph(c, LP_PH_FIT64, 1, s);
@@ -770,7 +772,8 @@ lp_status lp_step_host(lp_ctx* c, lp_particles* h, double dt, double cfl, double
 
 lp_status lp_set_schedule(lp_ctx* c, int32_t schedule)
 {
-    if (!c || (schedule & ~(LP_SCHED_SPLIT | LP_SCHED_QUERY_WARP)) != 0) return LP_ERR_ARG;
+    if (!c || (schedule & ~(LP_SCHED_SPLIT | LP_SCHED_QUERY_WARP | LP_SCHED_QUEUE_QUERY | LP_SCHED_QUEUE_FIT)) != 0)
+        return LP_ERR_ARG;
     c->schedule = schedule;
     return LP_OK;
 }
@@ -808,7 +811,9 @@ lp_status lp_autotune(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_
     int64_t n = 0;
     lp_status st = step_prologue(c, p, offsets, nsim, dt, cfl, nullptr, nullptr, s, a, o, &n);
     if (st != LP_OK) return st;
-    double ms[4] = {0.0, 0.0, 0.0, 0.0};
+    // fit FUSED, fit SPLIT, query tiles, query per particle, query tiles from
+    // the work queue, fit SPLIT from the work queues (FP32)
+    double ms[LP_AUTOTUNE_TIMES] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (n > 0) {
         // the fit pass reads the sorted copies and writes only its outputs, so it
         // can be repeated; outputs go to scratch so that the state is untouched
@@ -842,20 +847,36 @@ lp_status lp_autotune(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_
         // the query rewrites the same lists whichever schedule runs it
         const int keep = c->schedule;
         if (c->dc.radius_mode != LP_RADIUS_KSIDE && c->dc.dim > 1) {
-            for (int q = 0; q < 2 && rs == LP_OK; ++q) {
-                c->schedule = q ? LP_SCHED_QUERY_WARP : 0;
-                rs = timed([&] { return query_neighbors(c, n, s) == cudaSuccess ? LP_OK : LP_ERR_CUDA; }, ms[2 + q]);
+            const int qs[3] = {0, LP_SCHED_QUERY_WARP, LP_SCHED_QUEUE_QUERY};
+            const int qslot[3] = {2, 3, 4};
+            for (int q = 0; q < 3 && rs == LP_OK; ++q) {
+                c->schedule = qs[q];
+                rs = timed([&] { return query_neighbors(c, n, s) == cudaSuccess ? LP_OK : LP_ERR_CUDA; },
+                           ms[qslot[q]]);
             }
         }
         c->schedule = keep;
-        for (int f = 0; f < 2 && rs == LP_OK; ++f)
-            rs = timed([&] { return run_fit(c, a, o, f ? LP_SCHED_SPLIT : LP_SCHED_FUSED, s); }, ms[f]);
+        const bool fp32 = c->dc.precision == LP_PREC_FP32;
+        const int fs[3] = {LP_SCHED_FUSED, LP_SCHED_SPLIT, LP_SCHED_SPLIT | LP_SCHED_QUEUE_FIT};
+        const int fslot[3] = {0, 1, 5};
+        for (int f = 0; f < (fp32 ? 3 : 2) && rs == LP_OK; ++f)
+            rs = timed([&] { return run_fit(c, a, o, fs[f], s); }, ms[fslot[f]]);
         cudaStreamSynchronize(s);
         cudaFree(scratch);
         cudaFree(sid);
         if (rs != LP_OK) return rs;
-        int sched = ms[1] < ms[0] ? LP_SCHED_SPLIT : LP_SCHED_FUSED;
-        if (ms[3] > 0.0 && ms[3] < ms[2]) sched |= LP_SCHED_QUERY_WARP;
+        // the fastest fit schedule, and the fastest query schedule
+        int sched = LP_SCHED_FUSED;
+        double best = ms[0];
+        if (ms[1] < best) { sched = LP_SCHED_SPLIT; best = ms[1]; }
+        if (fp32 && ms[5] > 0.0 && ms[5] < best) sched = LP_SCHED_SPLIT | LP_SCHED_QUEUE_FIT;
+        if (ms[2] > 0.0) {
+            double qbest = ms[2];
+            int qsched = 0;
+            if (ms[3] > 0.0 && ms[3] < qbest) { qsched = LP_SCHED_QUERY_WARP; qbest = ms[3]; }
+            if (ms[4] > 0.0 && ms[4] < qbest) qsched = LP_SCHED_QUEUE_QUERY;
+            sched |= qsched;
+        }
         c->schedule = sched;
     }
     LP_CUDA(cudaMemcpyAsync(c->counters, saved, sizeof(saved), cudaMemcpyHostToDevice, s));
@@ -864,7 +885,7 @@ lp_status lp_autotune(lp_ctx* c, lp_particles* p, const int64_t* offsets, int32_
     c->launches = launches0;
     memcpy(c->phase_launches, ph_launches0, sizeof(ph_launches0));
     if (out_ms)
-        for (int q = 0; q < 4; ++q) out_ms[q] = ms[q];
+        for (int q = 0; q < LP_AUTOTUNE_TIMES; ++q) out_ms[q] = ms[q];
     return LP_OK;
 }
 

@@ -360,6 +360,7 @@ struct FitArgs {
     // listed by the first kernel for a kernel of their own
     uint32_t* refine_list;
     unsigned long long* refine_len;
+    unsigned long long* queue;        // [2] work counters of the persistent split kernels
 };
 
 // statistics of the last field's differences b_j = s_j - s_i over the central

@@ -469,13 +469,11 @@ __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_centra
         central_one<T, DIM, GATE, false>(a, o, a.refine_list[t]);
 }
 
+// the second stage of list entry t of the split schedule
 template <typename T, int DIM>
-__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain(FitArgs a, StepOut o)
+__device__ __forceinline__ void plain_one(const FitArgs& a, const StepOut& o, unsigned long long t)
 {
     constexpr int F = DIM + 2;
-    const unsigned long long len = *a.plain_len;
-    const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    if (t >= len) return;
     const int64_t i = a.plain_list[t];
     Src<T, DIM, F> src(a, i);
     const int cnt = (int)a.count[i];
@@ -508,6 +506,51 @@ __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain(Fi
     Loaded<DIM> L;
     step_load<T, DIM>(a, o, i, L);          // never frozen: frozen particles are not listed
     step_finish<T, DIM>(a, o, i, L, os, lw, true, mlp_skip);
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain(FitArgs a, StepOut o)
+{
+    const unsigned long long len = *a.plain_len;
+    const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    if (t < len) plain_one<T, DIM>(a, o, t);
+}
+
+// Persistent forms of the split schedule's two kernels (LP_SCHED_QUEUE_FIT):
+// a grid of resident blocks whose warps take their next 32 particles (list
+// entries) from a work counter until none are left.  A warp whose particles
+// had short stencils takes more work at once instead of holding its slot
+// until the slowest warp of its block ends.  Every particle is computed by
+// the same code as in the one-thread-per-particle kernels, so the results are
+// identical.
+__device__ __forceinline__ unsigned long long warp_take(unsigned long long* q)
+{
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31u) == 0u) base = atomicAdd(q, 32ull);
+    return __shfl_sync(0xffffffffu, base, 0);
+}
+
+template <typename T, int DIM, bool GATE, bool DEFER>
+__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_central_q(FitArgs a, StepOut o)
+{
+    for (;;) {
+        const unsigned long long base = warp_take(a.queue);
+        if (base >= (unsigned long long)a.n) return;
+        const int64_t i = (int64_t)base + (int64_t)(threadIdx.x & 31u);
+        if (i < a.n) central_one<T, DIM, GATE, DEFER>(a, o, i);
+    }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain_q(FitArgs a, StepOut o)
+{
+    const unsigned long long len = *a.plain_len;
+    for (;;) {
+        const unsigned long long base = warp_take(a.queue + 1);
+        if (base >= len) return;
+        const unsigned long long t = base + (threadIdx.x & 31u);
+        if (t < len) plain_one<T, DIM>(a, o, t);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -665,6 +708,11 @@ inline cudaError_t launch_central_refine<double>(int, bool, const FitArgs&, cons
 {
     return cudaErrorNotSupported;
 }
+
+// the split schedule with its two kernels persistent over work counters
+// (FP32; its own translation unit, lp_fit_f32_queue.cu).  The counters
+// a.queue[0..1] must be zero.
+cudaError_t launch_step_split_queue_f32(int dim, const FitArgs& a, const StepOut& o, cudaStream_t s);
 
 // the split schedule lists the FP32 central fits that need the correction
 // pass for a kernel of their own (where the correction runs only below the

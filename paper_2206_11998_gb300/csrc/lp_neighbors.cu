@@ -9,6 +9,8 @@
 // candidates within a rounding band of the radius, and entries whose order is
 // within rounding of a neighbour's, are decided with the exact FP64 distance
 // ((dx*dx + dy*dy) + dz*dz, no contraction), so the lists are bit-exact.
+#include <algorithm>
+
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -41,6 +43,8 @@ struct QueryArgs {
     // the tile kernel appends the particles it leaves here
     uint32_t* fb_list;
     unsigned long long* fb_len;
+    // the persistent tile kernel's work counter (zero at launch)
+    unsigned long long* queue;
 };
 
 template <int DIM>
@@ -1048,14 +1052,11 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
     return true;
 }
 
+// the tile of 32 key-ordered particles starting at i0 (< n), one warp
 template <int DIM, bool PER>
-__global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile(QueryArgs a)
+__device__ __forceinline__ void tile_tile(const QueryArgs& a, TileBuf& b, int64_t i0)
 {
-    extern __shared__ __align__(16) unsigned char tq_smem[];
-    TileBuf& b = reinterpret_cast<TileBuf*>(tq_smem)[threadIdx.x >> 5];
     const unsigned lane = lane_id();
-    const int64_t i0 = ((int64_t)blockIdx.x * TQ_WARPS + (threadIdx.x >> 5)) * 32;
-    if (i0 >= a.n) return;                      // whole warp
     const int64_t i = i0 + lane;
     const bool valid = i < a.n;
     const int mb = a.c.mbits;
@@ -1108,6 +1109,35 @@ __global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile(QueryArgs a)
                 list_append(a, ((g >> lane) & 1u) != 0u, (uint32_t)i);
             }
         }
+    }
+}
+
+template <int DIM, bool PER>
+__global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile(QueryArgs a)
+{
+    extern __shared__ __align__(16) unsigned char tq_smem[];
+    TileBuf& b = reinterpret_cast<TileBuf*>(tq_smem)[threadIdx.x >> 5];
+    const int64_t i0 = ((int64_t)blockIdx.x * TQ_WARPS + (threadIdx.x >> 5)) * 32;
+    if (i0 >= a.n) return;                      // whole warp
+    tile_tile<DIM, PER>(a, b, i0);
+}
+
+// Persistent form (LP_SCHED_QUEUE_QUERY): a grid of resident blocks whose
+// warps take their next tile from a.queue until none is left, so a warp whose
+// tile was cheap takes another at once instead of holding its slot (and its
+// shared-memory buffer) until the slowest warp of its block ends.
+template <int DIM, bool PER>
+__global__ void __launch_bounds__(TQ_WARPS * 32, 5) k_query_tile_q(QueryArgs a)
+{
+    extern __shared__ __align__(16) unsigned char tq_smem[];
+    TileBuf& b = reinterpret_cast<TileBuf*>(tq_smem)[threadIdx.x >> 5];
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane_id() == 0) base = atomicAdd(a.queue, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)a.n) return;
+        tile_tile<DIM, PER>(a, b, (int64_t)base);
+        __syncwarp();                           // the buffer is reused by the next tile
     }
 }
 
@@ -1189,6 +1219,7 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     a.list_len = nullptr;
     a.fb_list = c->redo_list;                  // capacity n: each particle is appended at most once
     a.fb_len = c->counters + C_QFB_LEN;
+    a.queue = nullptr;
     if (c->dc.radius_mode == LP_RADIUS_KSIDE) {
         k_query_kside<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
         return cudaGetLastError();
@@ -1211,7 +1242,21 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     const int64_t tiles = (n + 31) / 32;
     const unsigned tblocks = (unsigned)((tiles + TQ_WARPS - 1) / TQ_WARPS);
     const size_t smem = sizeof(TileBuf) * TQ_WARPS;
-    if (dim == 3) {
+    if (c->schedule & LP_SCHED_QUEUE_QUERY) {
+        // as many blocks as are resident at once, never more than the tiles need
+        auto kq = dim == 3 ? (per ? k_query_tile_q<3, true> : k_query_tile_q<3, false>)
+                           : (per ? k_query_tile_q<2, true> : k_query_tile_q<2, false>);
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kq, TQ_WARPS * 32, smem)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const unsigned qb = (unsigned)std::min<int64_t>((int64_t)sms * per_sm, (int64_t)tblocks);
+        a.queue = c->counters + C_QUEUE_TILE;
+        if ((e = cudaMemsetAsync(a.queue, 0, 8, s)) != cudaSuccess) return e;
+        kq<<<qb, TQ_WARPS * 32, smem, s>>>(a);
+    } else if (dim == 3) {
         if (per) k_query_tile<3, true><<<tblocks, TQ_WARPS * 32, smem, s>>>(a);
         else k_query_tile<3, false><<<tblocks, TQ_WARPS * 32, smem, s>>>(a);
     } else {
@@ -1240,7 +1285,11 @@ cudaError_t query_init()
     if ((e = cudaFuncSetAttribute(k_query_tile<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_query_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_query_tile<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_query_tile<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if ((e = cudaFuncSetAttribute(k_query_tile<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_query_tile_q<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_query_tile_q<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_query_tile_q<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_query_tile_q<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 }  // namespace lp

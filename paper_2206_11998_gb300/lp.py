@@ -23,7 +23,8 @@ LIM_FLAGGED, LIM_PAPER, LIM_LW, LIM_UW = 0, 1, 2, 3
 EST_PLAIN, EST_MLP = 0, 1
 OUT_F32, OUT_F64 = 0, 1
 REFINE_AUTO, REFINE_ALWAYS, REFINE_NEVER = 0, 1, 2
-SCHED_FUSED, SCHED_SPLIT, SCHED_QUERY_WARP = 0, 1, 2
+SCHED_FUSED, SCHED_SPLIT, SCHED_QUERY_WARP, SCHED_QUEUE_QUERY, SCHED_QUEUE_FIT = 0, 1, 2, 4, 8
+AUTOTUNE_TIMES = 6
 
 EXPORTED = [
     "lp_create", "lp_destroy", "lp_build_neighbors", "lp_gfd_derivs", "lp_onesided_derivs", "lp_step",
@@ -464,12 +465,14 @@ class Context:
     def autotune(self, ps: ParticleSet, offsets=None, nsim=1, dt=0.0, cfl=0.4, reps=3, stream=None):
         """Time the query and the fit pass under each schedule on this state and
         keep the faster of each; returns {fit_fused, fit_split, query_tile,
-        query_warp} in ms.  The state is not changed."""
+        query_warp, query_tile_queue, fit_split_queue} in ms (0: not offered).
+        The state is not changed."""
         p = ps.struct()
-        out = (C.c_double * 4)()
+        out = (C.c_double * AUTOTUNE_TIMES)()
         _check(lib().lp_autotune(self.h, C.byref(p), _ptr(offsets), int(nsim), float(dt), float(cfl), int(reps),
                                  out, _stream(stream)), "lp_autotune")
-        return {"fit_fused": out[0], "fit_split": out[1], "query_tile": out[2], "query_warp": out[3]}
+        return {"fit_fused": out[0], "fit_split": out[1], "query_tile": out[2], "query_warp": out[3],
+                "query_tile_queue": out[4], "fit_split_queue": out[5]}
 
     def stats(self, stream=None) -> dict:
         s = Stats()

@@ -113,15 +113,20 @@ def test_batched_step_matches_oracle_per_simulation():
     ctx.close()
 
 
-def test_graph_replay_equals_eager_steps():
+@pytest.mark.parametrize("queue", [False, True])
+def test_graph_replay_equals_eager_steps(queue):
     """A step captured into a CUDA graph and replayed equals the same steps run
-    eagerly, bit for bit."""
+    eagerly, bit for bit; with queue, the graph replays the persistent kernels
+    that take their work from warp work queues (tiles of the query, particles
+    and list entries of the split fit), whose counters the graph itself resets."""
     sims = _ensemble([2000, 3500, 2800], seed0=90)
     st, offs = _concat(sims)
     n = st["V"].shape[0]
     outs = []
     for mode in ("eager", "graph"):
         ctx = lp.Context(_cfg(n, lp.PREC_FP32, len(sims)))
+        if queue and mode == "graph":
+            ctx.set_schedule(lp.SCHED_SPLIT | lp.SCHED_QUEUE_FIT | lp.SCHED_QUEUE_QUERY)
         ps = lp.ParticleSet.from_state(st)
         offs_d = torch.as_tensor(offs, device="cuda")
         t = torch.zeros(len(sims), dtype=torch.float64, device="cuda")

@@ -75,6 +75,18 @@ def test_split_equals_fused_plain_estimator(prec):
     _same(a, b)
 
 
+@pytest.mark.parametrize("prec", [lp.PREC_FP32, lp.PREC_FP64])
+def test_work_queue_schedules_equal_the_launch_grid(prec):
+    """The persistent kernels with warp work queues (query tiles, and the split
+    fit's two kernels on the FP32 path) compute every particle with the same
+    code as the one-warp-per-tile and one-thread-per-particle launches: the
+    same state, flags and limiter values, bit for bit."""
+    st = _cloud()
+    a = _run(st, lp.SCHED_SPLIT, precision=prec)
+    b = _run(st, lp.SCHED_SPLIT | lp.SCHED_QUEUE_FIT | lp.SCHED_QUEUE_QUERY, precision=prec)
+    _same(a, b)
+
+
 def _gate_threshold(st, params):
     """Median probability of the (untrained) network on the cloud's features:
     about half the particles fall below it."""
@@ -101,6 +113,9 @@ def test_split_equals_fused_learned_estimator(audit):
     if audit:
         assert a[3]["n_mlp_miss"] > 0        # an untrained gate misses flags; the audit sees them
     _same(a, b)
+    # the split kernels from work queues: a list of about half the particles
+    c = _run(st, lp.SCHED_SPLIT | lp.SCHED_QUEUE_FIT, params=params, **kw)
+    _same(a, c)
 
 
 def test_default_schedule_follows_estimator():
@@ -110,7 +125,7 @@ def test_default_schedule_follows_estimator():
     assert c1.schedule() == lp.SCHED_FUSED
     assert c2.schedule() == lp.SCHED_SPLIT
     with pytest.raises(lp.LPError):
-        c1.set_schedule(4)
+        c1.set_schedule(16)                  # no such schedule bit
     c1.close()
     c2.close()
 
@@ -128,9 +143,11 @@ def test_autotune_keeps_state_and_counters():
     s0 = ctx.stats()
     t = ctx.autotune(ps, dt=0.0, cfl=0.4, reps=2)
     assert all(v > 0 for v in t.values()), t
-    want = (lp.SCHED_SPLIT if t["fit_split"] < t["fit_fused"] else lp.SCHED_FUSED) | (
-        lp.SCHED_QUERY_WARP if t["query_warp"] < t["query_tile"] else 0)
-    assert ctx.schedule() == want
+    fits = {lp.SCHED_FUSED: t["fit_fused"], lp.SCHED_SPLIT: t["fit_split"],
+            lp.SCHED_SPLIT | lp.SCHED_QUEUE_FIT: t["fit_split_queue"]}
+    queries = {0: t["query_tile"], lp.SCHED_QUERY_WARP: t["query_warp"], lp.SCHED_QUEUE_QUERY: t["query_tile_queue"]}
+    want = min(fits, key=fits.get) | min(queries, key=queries.get)
+    assert ctx.schedule() == want, (t, ctx.schedule())
     after = ps.to_state(N)
     for f in ("V", "P", "m", "id"):
         assert np.array_equal(before[f], after[f]), f
@@ -147,11 +164,12 @@ def test_autotune_keeps_state_and_counters():
 
 
 def test_query_schedules_give_identical_lists():
-    """Tiles (with the per-particle kernel for the particles they leave) and
-    one warp per particle for every particle: the same lists, bit for bit."""
+    """Tiles (with the per-particle kernel for the particles they leave), one
+    warp per particle for every particle, and tiles taken from a work queue by
+    a persistent grid: the same lists, bit for bit."""
     st = _cloud()
     out = []
-    for sched in (lp.SCHED_FUSED, lp.SCHED_QUERY_WARP):
+    for sched in (lp.SCHED_FUSED, lp.SCHED_QUERY_WARP, lp.SCHED_QUEUE_QUERY):
         ctx = lp.Context(_cfg(st))
         ctx.set_schedule(sched)
         ps = lp.ParticleSet.from_state(st)
@@ -159,5 +177,6 @@ def test_query_schedules_give_identical_lists():
         cnt, tot, idx, d2, keys = ctx.export_neighbors(N)
         out.append([a.cpu().numpy() for a in (cnt, tot, idx, d2, ps.id)])
         ctx.close()
-    for a, b in zip(*out):
-        assert np.array_equal(a, b)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
