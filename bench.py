@@ -485,7 +485,10 @@ def run_ours(args):
     sched = ctx.schedule()
     fit_kernels = ("k_step_central + k_step_plain" if sched & lp.SCHED_SPLIT else "k_step") + \
         ("<float,3>" if args.precision == "fp32" else "<double,3>")
-    traffic = fit_traffic(args.precision, args.estimator, bool(sched & lp.SCHED_SPLIT), ACTIVE, n,
+    # the captured figure is of the launch-grid split kernels (the persistent
+    # ones read and write the same data, but were not captured)
+    traffic = fit_traffic(args.precision, args.estimator,
+                          bool(sched & lp.SCHED_SPLIT) and not (sched & lp.SCHED_QUEUE_FIT), ACTIVE, n,
                           FIT_TRAFFIC_BPP_2M if n == 2_000_000 else None)
     if args.precision == "fp32":
         alu_peak = fp32_peak
@@ -504,11 +507,13 @@ def run_ours(args):
                                   "of three timed steps of this 2M workload"
                                   if traffic else None}
     query_roofline = None
-    if "neighbor-query" in phases and phases["neighbor-query"][0] > 0 and n == 2_000_000 and ACTIVE == "gas-cloud":
+    if ("neighbor-query" in phases and phases["neighbor-query"][0] > 0 and n == 2_000_000
+            and ACTIVE == "gas-cloud" and not (sched & lp.SCHED_QUERY_WARP)):
         q_ms = phases["neighbor-query"][0] / args.steps
         issue_peak = 152 * 4 * sm_max * 1e6
         q_ach = QUERY_INST_PP_2M * n / (q_ms * 1e-3)
-        query_roofline = {"kernel": "k_query_tile + k_query (neighbour query)", "bound": "issue",
+        tile_kernel = "k_query_tile_q (warp work queue)" if sched & lp.SCHED_QUEUE_QUERY else "k_query_tile"
+        query_roofline = {"kernel": tile_kernel + " + k_query (neighbour query)", "bound": "issue",
                           "achieved": q_ach, "peak": issue_peak, "unit": "warp instructions/s",
                           "frac": q_ach / issue_peak, "inst_per_particle": QUERY_INST_PP_2M,
                           "peak_source": "152 SM x 4 schedulers x 1 warp instruction per clock x %.0f MHz" % sm_max,
