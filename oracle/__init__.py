@@ -24,6 +24,7 @@ _lib = None
 
 RADIUS_FIXED, RADIUS_VOLUME, RADIUS_KSIDE = 0, 1, 2
 LIM_FLAGGED, LIM_PAPER, LIM_LW, LIM_UW = 0, 1, 2, 3
+SELECT_NEAREST, SELECT_OCTANT = 0, 1
 ST_LINEAR_FALLBACK, ST_NO_FIT, ST_OVERFLOW = 1, 2, 4
 
 
@@ -54,14 +55,16 @@ class Config(C.Structure):
         ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
         ("rank_tol", C.c_double),
         ("n_fluid", C.c_int64),
+        ("select", C.c_int32), ("pad1", C.c_int32),
     ]
 
 
 def make_config(dim, gamma=1.4, radius_mode=RADIUS_VOLUME, radius=0.0, kappa=2.2, k_max=64,
                 k_side=8, k_per_side=4, limiter=LIM_FLAGGED, flat_eps=1e-6, active_frac=0.5,
                 s_ref=(0, 0, 0, 0, 0), periodic=(0, 0, 0), box_lo=(0, 0, 0), box_hi=(1, 1, 1),
-                rank_tol=1e-12, n_fluid=2**62) -> Config:
+                rank_tol=1e-12, n_fluid=2**62, select=0) -> Config:
     c = Config()
+    c.select = select
     c.dim, c.radius_mode, c.gamma, c.radius, c.kappa = dim, radius_mode, gamma, radius, kappa
     c.k_max, c.k_side, c.k_per_side, c.limiter = k_max, k_side, k_per_side, limiter
     c.flat_eps, c.active_frac, c.rank_tol, c.n_fluid = flat_eps, active_frac, rank_tol, n_fluid

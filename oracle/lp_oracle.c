@@ -15,7 +15,8 @@
  *   lpo_morton_keys     Morton (Z-curve) keys of quantised positions
  *                       (Sec. 2.2, "Space-filling curve").
  *   lpo_neighbors       neighbour set {j != i : |x_j - x_i| <= R_i} ordered by
- *                       (d^2, id) and truncated (Sec. 2.2 steps 3-4).
+ *                       (d^2, id) and truncated to the nearest or to an
+ *                       octant-balanced selection (Sec. 2.2 steps 3-4).
  *   lpo_gfd_central     second-order GFD least-squares fit, Eq. (linear_system_axb)
  *                       generalised to 1D/3D, solved by Householder QR with
  *                       column pivoting (Sec. 2.1).
@@ -69,7 +70,11 @@ typedef struct {
     double box_hi[3];
     double rank_tol;      /* numerical-rank threshold on |R_kk| / |R_00| */
     int64_t n_fluid;      /* particles with id >= n_fluid are frozen boundary particles */
+    int32_t select;       /* LPO_SELECT_*: which k_max are kept when more lie inside the radius */
+    int32_t pad1;
 } lpo_config;
+
+enum { LPO_SELECT_NEAREST = 0, LPO_SELECT_OCTANT = 1 };
 
 #define LPO_MAXN 9      /* unknowns of the 3D second-order fit */
 #define LPO_MAXF 5      /* fields V, u_1..u_d, P */
@@ -165,7 +170,7 @@ static int inside(const lpo_config *c, double d2, double w)
     return d2 <= k2 * ww;
 }
 
-typedef struct { double d2; uint32_t id; int64_t j; } cand_t;
+typedef struct { double d2; uint32_t id; int64_t j; int64_t rank; } cand_t;
 
 static int cand_cmp(const void *a, const void *b)
 {
@@ -175,6 +180,43 @@ static int cand_cmp(const void *a, const void *b)
     if (p->id < q->id) return -1;
     if (p->id > q->id) return 1;
     return 0;
+}
+
+/* (rank, d2, id) order of the octant-balanced selection */
+static int cand_rank_cmp(const void *a, const void *b)
+{
+    const cand_t *p = (const cand_t *)a, *q = (const cand_t *)b;
+    if (p->rank < q->rank) return -1;
+    if (p->rank > q->rank) return 1;
+    return cand_cmp(a, b);
+}
+
+/* octant (quadrant in 2D) of x_j seen from x_i: bit k set when the offset
+ * along axis k (minimum image on a periodic axis) is >= 0 */
+static int octant_of(const lpo_config *c, const double *const *x, int64_t i, int64_t j)
+{
+    int o = 0;
+    for (int k = 0; k < c->dim; ++k)
+        if (offset(c, x, k, i, j) >= 0.0) o |= 1 << k;
+    return o;
+}
+
+/*
+ * Octant-balanced selection (Sec. 2.2 step 4: the top members of a list are
+ * to contain neighbours from all directions, not only the nearest).  Reading:
+ * buf[0..nc) holds the in-radius set in (d2, id) order and nc > k_max.  Each
+ * member gets its rank within its octant in that order; the k_max kept are
+ * the first k_max by (rank, d2, id), i.e. round robin over the octants,
+ * nearest first in each, an octant that runs out giving its turn to the
+ * others.  They are returned in buf[0..k_max) in (d2, id) order.
+ */
+static void select_octant_balanced(const lpo_config *c, const double *const *x, int64_t i,
+                                   cand_t *buf, int64_t nc)
+{
+    int64_t seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t t = 0; t < nc; ++t) buf[t].rank = seen[octant_of(c, x, i, buf[t].j)]++;
+    qsort(buf, (size_t)nc, sizeof(cand_t), cand_rank_cmp);
+    qsort(buf, (size_t)c->k_max, sizeof(cand_t), cand_cmp);
 }
 
 /* index order by (x_0, index), used by the window pre-filter */
@@ -191,7 +233,9 @@ static int idx_cmp_x0(const void *a, const void *b)
  * Neighbour lists of the query particles q[0..nq-1] (indices into the inputs).
  *
  * out_idx[r*k_max + t] holds the t-th neighbour (input index) of query r in
- * (d2, id) order, out_count[r] = min(#inside, k_max),
+ * (d2, id) order, out_count[r] = min(#inside, k_max); when more than k_max lie
+ * inside, the k_max nearest are kept (LPO_SELECT_NEAREST) or the octant-
+ * balanced selection of select_octant_balanced (LPO_SELECT_OCTANT),
  * out_total[r] = min(#inside, 4 k_max) (the count saturates there),
  * out_d2min[r] = d2 of the nearest neighbour (INFINITY if none).
  *
@@ -274,12 +318,15 @@ int lpo_neighbors(const lpo_config *c, int64_t n, const double *const *x,
                 }
             }
             qsort(buf, (size_t)nc, sizeof(cand_t), cand_cmp);
+            const double d2min = nc > 0 ? buf[0].d2 : INFINITY;
+            if (c->select == LPO_SELECT_OCTANT && c->radius_mode != LPO_RADIUS_KSIDE && nc > c->k_max)
+                select_octant_balanced(c, x, i, buf, nc);
             int64_t keep = nc < c->k_max ? nc : c->k_max;
             for (int64_t t = 0; t < keep; ++t) out_idx[r * c->k_max + t] = buf[t].j;
             for (int64_t t = keep; t < c->k_max; ++t) out_idx[r * c->k_max + t] = -1;
             out_count[r] = (uint32_t)keep;
             out_total[r] = (uint32_t)(nc < 4 * (int64_t)c->k_max ? nc : 4 * (int64_t)c->k_max);
-            out_d2min[r] = nc > 0 ? buf[0].d2 : INFINITY;
+            out_d2min[r] = d2min;
         }
         free(buf);
     }
