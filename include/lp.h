@@ -69,8 +69,8 @@ enum { LP_OUT_F32 = 0, LP_OUT_F64 = 1 };
  *   dim            1, 2 or 3.
  *   precision      LP_PREC_*.
  *   radius_mode    LP_RADIUS_*; radius / kappa as the mode needs.
- *   k_max          neighbour capacity per particle, 1..64; nearer neighbours
- *                  (by (d^2, id)) are kept when more lie inside the radius.
+ *   k_max          neighbour capacity per particle, 1..64; which neighbours
+ *                  are kept when more lie inside the radius: see `select`.
  *   k_side         one-sided stencil size per half-space (Sec. 2.2 step 5
  *                  uses 8 in 3D), 1..16.
  *   k_per_side     LP_RADIUS_KSIDE only, 1..8.
@@ -112,6 +112,15 @@ enum { LP_OUT_F32 = 0, LP_OUT_F64 = 1 };
  *                  stencils and its state after a step is within 2e-7 of
  *                  ALWAYS's.
  *   refine_ratio   LP_REFINE_AUTO threshold (0: 0.1).
+ *   select         which k_max neighbours are kept when more lie inside the
+ *                  radius (Sec. 2.2 step 4): LP_SELECT_NEAREST (0) the k_max
+ *                  nearest by (d^2, id); LP_SELECT_OCTANT (1) round robin over
+ *                  the octants (quadrants in 2D) of the offsets, nearest first
+ *                  in each, so that the list covers all directions.  Either way
+ *                  the list is stored in (d^2, id) order, and with at most k_max
+ *                  inside the radius the two agree.  LP_SELECT_OCTANT needs dim
+ *                  2 or 3 and a radius (not LP_RADIUS_KSIDE).
+ *   reserved       0.
  */
 typedef struct {
     int32_t dim;
@@ -141,7 +150,11 @@ typedef struct {
     int32_t max_sims;
     int32_t refine;
     double refine_ratio;
+    int32_t select;
+    int32_t reserved;
 } lp_config;
+
+enum { LP_SELECT_NEAREST = 0, LP_SELECT_OCTANT = 1 };
 
 enum { LP_REFINE_AUTO = 0, LP_REFINE_ALWAYS = 1, LP_REFINE_NEVER = 2 };
 

@@ -113,6 +113,9 @@ lp_status check_cfg(const lp_config* g)
     if (g->max_sims < 0 || g->max_sims > (1 << 20)) return LP_ERR_ARG;
     if (g->max_sims > 1 && g->dim == 1) return LP_ERR_ARG;   // 1D keys are the raw order of x
     if (g->refine < LP_REFINE_AUTO || g->refine > LP_REFINE_NEVER || !(g->refine_ratio >= 0.0)) return LP_ERR_ARG;
+    if (g->select != LP_SELECT_NEAREST && g->select != LP_SELECT_OCTANT) return LP_ERR_ARG;
+    if (g->select == LP_SELECT_OCTANT && (g->dim < 2 || g->radius_mode == LP_RADIUS_KSIDE)) return LP_ERR_ARG;
+    if (g->reserved != 0) return LP_ERR_ARG;
     return LP_OK;
 }
 
@@ -349,6 +352,7 @@ lp_status lp_create(const lp_config* cfg, lp_ctx** out)
     d.estimator = cfg->estimator;
     d.refine = cfg->refine;
     d.refine_ratio = cfg->refine_ratio > 0.0 ? cfg->refine_ratio : 0.1;
+    d.select = cfg->select;
     d.mlp_tau_lo = (float)cfg->mlp_tau_lo;
     d.mlp_audit = cfg->mlp_audit ? 1 : 0;
     d.nsim_max = cfg->max_sims > 1 ? cfg->max_sims : 1;

@@ -42,6 +42,7 @@ enum Counter {
 // method constants as the kernels see them
 struct DevCfg {
     int dim, precision, radius_mode, k_max, k_side, k_per_side, limiter, estimator, refine;
+    int select;           // LP_SELECT_*
     double refine_ratio;
     int mlp_audit;
     float mlp_tau_lo;

@@ -176,31 +176,44 @@ __device__ void sort_exact(const QueryArgs& a, WarpBuf& b, int m, int64_t i)
 //   otherwise                                  -> candidates scanned
 // Split cells go to the next frontier, processed once the current one is done,
 // so the k_max-th distance found so far prunes them.
+// own position and radius terms of particle i, and the start cells of its
+// query (written to b.front[0]): the cells of the finest level whose edge is
+// at least half the radius that meet the radius's box.  Shared by both
+// per-particle queries.
+struct QueryStart {
+    float hxi[3], lxi[3], tq[3];   // position (hi, lo) and quantised position
+    float inv;                     // quantised units per length
+    float R2f, Rq, Rout, Rin;      // squared radius; radius and box margins, quantised units
+    int ncells;                    // start cells in b.front[0]
+    uint64_t sim;
+};
+
 template <int DIM>
-__device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
+__device__ __forceinline__ void query_start(const QueryArgs& a, WarpBuf& b, int64_t i, QueryStart& st)
 {
     unsigned lane = lane_id();
     const DevCfg& c = a.c;
     const int mb = c.mbits;
     const uint64_t sim = c.nsim_max > 1 ? (a.keys[i] >> (DIM * mb)) : 0ull;
+    st.sim = sim;
     const Grid& g = a.g[sim];
-    unsigned lt = (1u << lane) - 1u;
 
     // own position and radius, all in FP32 (FP64 warp instructions are costly
     // on this part: one occupies a sub-partition's FP64 pipe for ~64 cycles)
-    float hxi[3], lxi[3], tq[3];
     const float inv = g.inv_f;
+    st.inv = inv;
     const float4 pih = a.pos4[2 * i], pil = a.pos4[2 * i + 1];
-    hxi[0] = pih.x; hxi[1] = pih.y; hxi[2] = pih.z;
-    lxi[0] = pil.x; lxi[1] = pil.y; lxi[2] = pil.z;
+    st.hxi[0] = pih.x; st.hxi[1] = pih.y; st.hxi[2] = pih.z;
+    st.lxi[0] = pil.x; st.lxi[1] = pil.y; st.lxi[2] = pil.z;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) tq[k] = ((hxi[k] - g.lo_h[k]) + (lxi[k] - g.lo_l[k])) * inv;   // quantised units, error < 1
+    for (int k = 0; k < DIM; ++k) st.tq[k] = ((st.hxi[k] - g.lo_h[k]) + (st.lxi[k] - g.lo_l[k])) * inv;   // quantised units, error < 1
     const float Rf = pih.w;                          // query_radius_f, written by the gather
-    float R2f = (c.radius_mode == LP_RADIUS_FIXED) ? c.radius2_f : Rf * Rf;
+    st.R2f = (c.radius_mode == LP_RADIUS_FIXED) ? c.radius2_f : Rf * Rf;
     float Rc = Rf * (1.0f + 1e-5f);
     const float Rq = Rc * inv;
-    const float Rout = Rf * inv * (1.0f + 2e-5f) + 2.0f;   // boxes beyond: no neighbour
-    const float Rin = Rf * inv * (1.0f - 2e-5f) - 2.0f;    // boxes within: all neighbours
+    st.Rq = Rq;
+    st.Rout = Rf * inv * (1.0f + 2e-5f) + 2.0f;   // boxes beyond: no neighbour
+    st.Rin = Rf * inv * (1.0f - 2e-5f) - 2.0f;    // boxes within: all neighbours
     if (lane == 0) {   // the minimum image needs R < L/2 on periodic axes
 #pragma unroll
         for (int k = 0; k < DIM; ++k)
@@ -220,8 +233,8 @@ __device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
     int nc[3] = {1, 1, 1};
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-        long long a0 = (long long)floorf((tq[k] - Rq - 2.0f) * cell_scale);
-        long long a1 = (long long)floorf((tq[k] + Rq + 2.0f) * cell_scale);
+        long long a0 = (long long)floorf((st.tq[k] - Rq - 2.0f) * cell_scale);
+        long long a1 = (long long)floorf((st.tq[k] + Rq + 2.0f) * cell_scale);
         if (!c.periodic[k]) {
             a0 = max(0ll, min(a0, ncell_axis - 1));
             a1 = max(0ll, min(a1, ncell_axis - 1));
@@ -250,6 +263,26 @@ __device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
         b.front[0][t] = pack_cell(l0, wv, shv);
     }
     __syncwarp();
+    st.ncells = ncells;
+}
+
+template <int DIM>
+__device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
+{
+    unsigned lane = lane_id();
+    const DevCfg& c = a.c;
+    const int mb = c.mbits;
+    const uint64_t sim = c.nsim_max > 1 ? (a.keys[i] >> (DIM * mb)) : 0ull;
+    const Grid& g = a.g[sim];
+    unsigned lt = (1u << lane) - 1u;
+    QueryStart st;
+    query_start<DIM>(a, b, i, st);
+    const float* hxi = st.hxi;
+    const float* lxi = st.lxi;
+    const float* tq = st.tq;
+    const float inv = st.inv;
+    const float R2f = st.R2f, Rout = st.Rout, Rin = st.Rin;
+    const int ncells = st.ncells;
 
     const uint32_t total_cap = 4u * (uint32_t)c.k_max;   // the count before truncation saturates here
     int m = 0;                     // entries in the buffer
@@ -424,6 +457,233 @@ __device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
     __syncwarp();
 }
 
+// octant (quadrant in 2D) of x_j seen from x_i: bit k set when the FP64
+// offset along axis k (minimum image on a periodic axis) is >= 0
+template <int DIM>
+__device__ inline int octant64(const QueryArgs& a, int64_t i, int64_t j)
+{
+    int o = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+        if (offset64(a.c, k, a.sx[k][i], a.sx[k][j]) >= 0.0) o |= 1 << k;
+    return o;
+}
+
+__device__ inline uint32_t warp_sum_u32(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ranks of the entries b.key/b.j[0..m) (sorted by (d2, id)) within their
+// octants; entry e's rank and octant go to the lane e % 32 of chunk e / 32
+// through the callback, called by all lanes once per chunk
+template <int DIM, typename F>
+__device__ inline void octant_ranks(const QueryArgs& a, WarpBuf& b, int m, int64_t i, F&& fn)
+{
+    const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
+    uint32_t carry[1 << DIM];
+#pragma unroll
+    for (int q = 0; q < (1 << DIM); ++q) carry[q] = 0;
+    for (int e0 = 0; e0 < m; e0 += 32) {
+        const int e = e0 + (int)lane;
+        const bool valid = e < m;
+        const int o = valid ? octant64<DIM>(a, i, b.j[e]) : -1;
+        uint32_t rank = 0;
+#pragma unroll
+        for (int q = 0; q < (1 << DIM); ++q) {
+            const unsigned bq = __ballot_sync(0xffffffffu, o == q);
+            if (o == q) rank = carry[q] + (uint32_t)__popc(bq & lt);
+            carry[q] += (uint32_t)__popc(bq);
+        }
+        fn(e0, valid, o, rank);
+    }
+}
+
+// Octant-balanced selection (LP_SELECT_OCTANT; Sec. 2.2 step 4: the top
+// members of a neighbour list cover all directions).  When more than k_max
+// particles lie inside the radius, the k_max kept are the first by (rank, d2,
+// id), the rank of a member being its place in its octant's (d2, id) order:
+// round robin over the octants, nearest first in each.  They are stored in
+// (d2, id) order; with at most k_max inside, the list is the nearest-first one.
+//   1. a pass over the start cells counts the members of each octant (n_o,
+//      saturated at k_max) and in all;
+//   2. R is the smallest rank with sum_o min(n_o, R + 1) >= k_max: ranks below
+//      R are all kept, rank R partly, so each octant needs only its
+//      q_o = min(n_o, R + 1) nearest;
+//   3. a second pass keeps those (compacting the buffer to the quotas whenever
+//      it fills), and the final sorted buffer gives the selection.
+// Membership and order are decided as in query_one (float split distances,
+// FP64 inside the rounding bands), octants on the FP64 offsets.
+template <int DIM>
+__device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
+{
+    const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
+    const DevCfg& c = a.c;
+    const int mb = c.mbits;
+    QueryStart st;
+    query_start<DIM>(a, b, i, st);
+    const Grid& g = a.g[st.sim];
+    const uint32_t kmax = (uint32_t)c.k_max;
+    constexpr int NO = 1 << DIM;
+    // every candidate j != i of the start cells, 32 at a time: fn(in, j, d2f)
+    // is called by all lanes (in: j lies inside the radius, exactly)
+    auto scan = [&](auto&& fn) {
+        for (int base0 = 0; base0 < st.ncells; base0 += 32) {
+            const int e = base0 + (int)lane;
+            uint32_t cs = 0, cn = 0;
+            if (e < st.ncells) {
+                int l, wv[3], shv[3];
+                unpack_cell(b.front[0][e], l, wv, shv);
+                const float size = ldexpf(1.0f, mb - l), period = ldexpf(1.0f, mb);
+                uint32_t q[3] = {0u, 0u, 0u};
+                float dmin2 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) {
+                    q[k] = (uint32_t)wv[k];
+                    const float lo = (float)wv[k] * size + (float)shv[k] * period, hi = lo + size;
+                    const float dn = fmaxf(0.0f, fmaxf(lo - st.tq[k], st.tq[k] - hi));
+                    dmin2 += dn * dn;
+                }
+                if (sqrtf(dmin2) < st.Rout) {
+                    const uint64_t code = (st.sim << (DIM * l)) | morton<DIM>(q);
+                    const unsigned long long ent = a.cells[a.level_off[l] + (int64_t)code];
+                    cs = (uint32_t)ent;
+                    const uint32_t ce = (uint32_t)(ent >> 32);
+                    cn = ce > cs ? ce - cs : 0;
+                }
+            }
+            uint32_t incl = cn;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += v;
+            }
+            const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+            b.cstart[lane] = cs;
+            b.cexcl[lane] = incl - cn;
+            __syncwarp();
+            for (uint32_t base = 0; base < T; base += 32) {
+                const uint32_t t = base + lane;
+                bool in = false;
+                float d2f = 0.0f;
+                uint32_t j = 0;
+                if (t < T) {
+                    int lo = 0, hi = 31;       // the last cell with cexcl <= t
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
+                    }
+                    j = b.cstart[lo] + (t - b.cexcl[lo]);
+                    if ((int64_t)j != i) {
+                        float4 ph, pl;
+                        ldg256(a.pos4 + 2 * (int64_t)j, ph, pl);
+                        const float hj[3] = {ph.x, ph.y, ph.z}, lj[3] = {pl.x, pl.y, pl.z};
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) {
+                            float dh = hj[k] - st.hxi[k];
+                            float dl = lj[k] - st.lxi[k];
+                            if (c.periodic[k]) {
+                                if (dh > 0.5f * c.Lper_h[k]) { dh -= c.Lper_h[k]; dl -= c.Lper_l[k]; }
+                                else if (dh < -0.5f * c.Lper_h[k]) { dh += c.Lper_h[k]; dl += c.Lper_l[k]; }
+                            }
+                            const float d = dh + dl;
+                            d2f = fmaf(d, d, d2f);
+                        }
+                        if (d2f <= st.R2f * (1.0f - TOL_R)) in = true;
+                        else if (d2f <= st.R2f * (1.0f + TOL_R))
+                            in = inside64(c, DIM, exact_d2<DIM>(a, i, j), __dmul_rn(a.sm[i], a.sV[i]));
+                    }
+                }
+                fn(in, j, d2f);
+            }
+            __syncwarp();
+        }
+    };
+    // ---- 1. members per octant (lane o holds octant o's count) and in all
+    uint32_t cnt_o = 0, total = 0;
+    scan([&](bool in, uint32_t j, float) {
+        const int o = in ? octant64<DIM>(a, i, j) : -1;
+        total += (uint32_t)__popc(__ballot_sync(0xffffffffu, in));
+#pragma unroll
+        for (int q = 0; q < NO; ++q) {
+            const unsigned bq = __ballot_sync(0xffffffffu, o == q);
+            if ((int)lane == q) cnt_o += (uint32_t)__popc(bq);
+        }
+    });
+    // ---- 2. the rank threshold and the quotas
+    const uint32_t n_o = (int)lane < NO ? min(cnt_o, kmax) : 0u;
+    uint32_t R = kmax, q_o = n_o, rem = 0;
+    if (total > kmax) {
+        R = 0;
+        while (warp_sum_u32(min(n_o, R + 1)) < kmax) ++R;    // ends at R <= kmax - 1
+        q_o = min(n_o, R + 1);
+        rem = kmax - warp_sum_u32(min(n_o, R));              // rank-R members kept
+    }
+    // ---- 3. the q_o nearest of each octant
+    int m = 0;
+    auto compact = [&]() {
+        sort_exact<DIM>(a, b, m, i);
+        int w = 0;
+        octant_ranks<DIM>(a, b, m, i, [&](int e0, bool valid, int o, uint32_t rank) {
+            const int e = e0 + (int)lane;
+            // every lane takes part in the shuffle (no short circuit before it)
+            const uint32_t qo = __shfl_sync(0xffffffffu, q_o, o & 7);
+            const bool keep = valid && rank < qo;
+            const unsigned long long kk = valid ? b.key[e] : 0ull;
+            const uint32_t jj = valid ? b.j[e] : 0u;
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            __syncwarp();
+            if (keep) {
+                const int pos = w + __popc(km & lt);
+                b.key[pos] = kk;
+                b.j[pos] = jj;
+            }
+            w += __popc(km);
+            __syncwarp();
+        });
+        m = w;
+    };
+    scan([&](bool in, uint32_t j, float d2f) {
+        const int o = in ? octant64<DIM>(a, i, j) : 0;
+        const uint32_t qo = __shfl_sync(0xffffffffu, q_o, o);   // every lane, then the test
+        const bool keep = in && qo > 0u;
+        if (m > NB_CAP - 32) compact();                      // warp-uniform
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int pos = m + __popc(km & lt);
+            b.key[pos] = ((unsigned long long)__float_as_uint(d2f) << 32) | a.sid[j];
+            b.j[pos] = j;
+        }
+        m += __popc(km);
+        __syncwarp();
+    });
+    compact();                                               // m <= sum_o q_o, sorted
+    // ---- the selection, in (d2, id) order: ranks below R, and the first rem of rank R
+    int w = 0;
+    uint32_t taken_r = 0;
+    octant_ranks<DIM>(a, b, m, i, [&](int e0, bool valid, int, uint32_t rank) {
+        const int e = e0 + (int)lane;
+        const bool atR = valid && rank == R;
+        const unsigned bR = __ballot_sync(0xffffffffu, atR);
+        const bool keep = valid && (rank < R || (atR && taken_r + (uint32_t)__popc(bR & lt) < rem));
+        taken_r += (uint32_t)__popc(bR);
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) a.idx[i * (int64_t)kmax + w + __popc(km & lt)] = b.j[e];
+        w += __popc(km);
+    });
+    if (lane == 0) {
+        a.count[i] = (uint32_t)w;
+        a.total[i] = min(total, 4u * kmax);
+        // the nearest member is kept (rank 0, nearest of the rank-0 members)
+        a.d2min[i] = w > 0 ? exact_d2<DIM>(a, i, b.j[0]) : INFINITY;
+        if (total > kmax) atomicAdd(a.counters + C_OVERFLOW, 1ull);
+        atomicMax(a.counters + C_MAXCOUNT, (unsigned long long)total);
+    }
+    __syncwarp();
+}
+
 // warp per particle: every particle, or the particles of a list
 template <int DIM>
 __global__ void __launch_bounds__(NB_WARPS * 32) k_query(QueryArgs a)
@@ -435,10 +695,17 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_query(QueryArgs a)
         const unsigned long long len = *a.list_len;
         for (unsigned long long t = (unsigned long long)blockIdx.x * NB_WARPS + w; t < len;
              t += (unsigned long long)gridDim.x * NB_WARPS)
-            query_one<DIM>(a, b, (int64_t)a.list[t]);
+        {
+            const int64_t i = (int64_t)a.list[t];
+            if (a.c.select == LP_SELECT_OCTANT) query_one_octant<DIM>(a, b, i);
+            else query_one<DIM>(a, b, i);
+        }
     } else {
         const int64_t i = (int64_t)blockIdx.x * NB_WARPS + w;
-        if (i < a.n) query_one<DIM>(a, b, i);
+        if (i < a.n) {
+            if (a.c.select == LP_SELECT_OCTANT) query_one_octant<DIM>(a, b, i);
+            else query_one<DIM>(a, b, i);
+        }
     }
 }
 
@@ -897,6 +1164,7 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
     const uint32_t kmax = (uint32_t)c.k_max;
     uint32_t mx = 0, novf = 0;
     uint32_t near_j = 0xffffffffu;       // this lane's particle: its nearest entry (none: all ones)
+    bool handed = false;                 // this lane's particle went to the per-particle kernel
     unsigned todo = __ballot_sync(0xffffffffu, mine);
     // the hits of the next particle are loaded while the current one is sorted
     uint32_t fj[2] = {0u, 0u};
@@ -961,6 +1229,12 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
         }
         const uint32_t nin = (uint32_t)(__popc(__ballot_sync(0xffffffffu, key[0] < 0xffffffc0u)) +
                                         __popc(__ballot_sync(0xffffffffu, key[1] < 0xffffffc0u)));
+        if (c.select == LP_SELECT_OCTANT && nin > kmax) {
+            // the octant-balanced selection of more than k_max: the per-particle kernel
+            if (lane == 0) a.fb_list[atomicAdd(a.fb_len, 1ull)] = (uint32_t)ip;
+            if ((int)lane == p) handed = true;
+            continue;
+        }
         if (m <= 32) bitonic_keys<1>(key);
         else bitonic_keys<2>(key);
         {
@@ -1047,7 +1321,7 @@ __device__ bool tile_group(const QueryArgs& a, TileBuf& b, int64_t i, bool act, 
     }
     // the exact squared distance to each particle's nearest entry (the CFL
     // step's ell^2), every lane its own particle
-    if (mine) a.d2min[i] = near_j != 0xffffffffu ? exact_d2<DIM>(a, i, near_j) : INFINITY;
+    if (mine && !handed) a.d2min[i] = near_j != 0xffffffffu ? exact_d2<DIM>(a, i, near_j) : INFINITY;
     __syncwarp();
     return true;
 }

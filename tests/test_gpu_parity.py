@@ -38,7 +38,7 @@ def _oracle_cfg(lcfg, n_fluid=2**62):
         k_max=lcfg.k_max, k_side=lcfg.k_side, k_per_side=lcfg.k_per_side, limiter=lcfg.limiter,
         flat_eps=lcfg.flat_eps, active_frac=lcfg.active_frac, s_ref=list(lcfg.s_ref),
         periodic=list(lcfg.periodic), box_lo=list(lcfg.box_lo), box_hi=list(lcfg.box_hi),
-        rank_tol=1e-12, n_fluid=n_fluid)
+        rank_tol=1e-12, n_fluid=n_fluid, select=lcfg.select)
 
 
 def _check_lists(ctx, ps, st, ocfg):
@@ -126,6 +126,89 @@ def test_neighbor_overflow_truncates_exactly():
     # more than 64 in reach: those lists come from the warp-per-particle kernel
     assert s["n_query_fallback"] > 1000
     ctx.close()
+
+
+def _octant_case(name):
+    """States and configurations with octant-balanced selection where many lists
+    are truncated: a dense cloud with a small capacity, the jet snapshot (the
+    ambient particles next to the jet reach hundreds of jet particles), a
+    periodic 2D shear layer with a small capacity, and an exact lattice (many
+    equal distances, so the (d2, id) tie rule decides ranks)."""
+    if name == "3d-cloud-k24":
+        st = inputs.gas_cloud_3d(12_000, seed=9)
+        return st, lp.make_config(3, 12_000, kappa=3.0, k_max=24, select=lp.SELECT_OCTANT)
+    if name == "3d-jet-snapshot":
+        st = inputs.jet_snapshot_3d(30_000)
+        return st, lp.make_config(3, st["V"].shape[0], kappa=2.2, k_max=64, select=lp.SELECT_OCTANT)
+    if name == "2d-periodic-kh-k16":
+        st = inputs.kh_2d(7_001, 0.03, seed=5)
+        return st, lp.make_config(2, st["V"].shape[0], kappa=2.2, k_max=16, periodic=(1, 1, 0),
+                                  box_lo=(0, 0, 0), box_hi=(1, 1, 1), select=lp.SELECT_OCTANT)
+    n = 21 ** 3
+    # an unjittered lattice: shells of equal distance
+    g = np.stack(np.meshgrid(*[np.arange(21) / 21.0] * 3, indexing="ij"), 0).reshape(3, -1)
+    st = {"x": [g[0].copy(), g[1].copy(), g[2].copy()], "V": np.ones(n), "u": [np.zeros(n)] * 3,
+          "P": np.ones(n), "m": np.ones(n), "id": np.arange(n, dtype=np.uint32), "n_fluid": n}
+    return st, lp.make_config(3, n, radius_mode=lp.RADIUS_FIXED, radius=2.2 / 21, k_max=20,
+                              select=lp.SELECT_OCTANT)
+
+
+@pytest.mark.parametrize("sched", [0, lp.SCHED_QUERY_WARP])
+@pytest.mark.parametrize("name", ["3d-cloud-k24", "3d-jet-snapshot", "2d-periodic-kh-k16", "3d-exact-lattice-k20"])
+def test_octant_selection_lists_bit_exact(name, sched):
+    """Octant-balanced selection (Sec. 2.2 step 4): the lists equal the oracle's,
+    bit for bit, whether the tile kernel hands the truncated particles to the
+    per-particle kernel or that kernel runs every particle."""
+    st, cfg = _octant_case(name)
+    ctx = lp.Context(cfg)
+    ctx.set_schedule(sched)
+    ps = lp.ParticleSet.from_state(st)
+    ctx.build_neighbors(ps)
+    torch.cuda.synchronize()
+    _check_lists(ctx, ps, st, _oracle_cfg(cfg))
+    s = ctx.stats()
+    assert s["n_overflow"] > 0, s
+    ctx.close()
+
+
+def test_octant_selection_agrees_with_nearest_within_capacity():
+    """With at most k_max inside the radius the two selections give the same
+    list; where they differ, the octant-balanced list covers more octants."""
+    st = inputs.jet_snapshot_3d(30_000)
+    n = st["V"].shape[0]
+    out = {}
+    for sel in (lp.SELECT_NEAREST, lp.SELECT_OCTANT):
+        cfg = lp.make_config(3, n, kappa=2.2, k_max=64, select=sel)
+        ctx = lp.Context(cfg)
+        ps = lp.ParticleSet.from_state(st)
+        ctx.build_neighbors(ps)
+        ids, lists, tot, d2, _ = gpu_neighbor_ids(ctx, ps)
+        out[sel] = {int(p): (list(l), int(t), float(d)) for p, l, t, d in zip(ids, lists, tot, d2)}
+        ctx.close()
+    x = np.stack(st["x"], 1)
+    more = 0
+    for pid, (ln, tn, dn) in out[lp.SELECT_NEAREST].items():
+        lo, to, do = out[lp.SELECT_OCTANT][pid]
+        assert tn == to and dn == do
+        if tn <= 64:
+            assert ln == lo
+        else:
+            octs = lambda l: len({tuple((x[j] - x[pid]) >= 0.0) for j in l})
+            assert octs(lo) >= octs(ln)
+            more += octs(lo) > octs(ln)
+    assert more > 0
+
+
+@pytest.mark.parametrize("prec,tol", [(lp.PREC_FP32, 1e-5), (lp.PREC_FP64, 1e-12)])
+def test_step_jet_snapshot_octant_selection(prec, tol):
+    """One CFL step of the jet snapshot with octant-balanced lists: the ambient
+    particles next to the jet fit stencils that reach the ambient side too."""
+    st = inputs.jet_snapshot_3d(30_000)
+    n = st["V"].shape[0]
+    cfg = lp.make_config(3, n, precision=prec, kappa=2.2, k_max=64, gamma=inputs.JET_GAMMA,
+                         s_ref=inputs.field_scales(st), limiter=lp.LIM_FLAGGED, select=lp.SELECT_OCTANT)
+    errs, stats, ndiff = _step_parity(st, cfg, 0.0, tol, cfl=0.4)
+    assert stats["n_overflow"] > 0, stats
 
 
 def test_neighbor_lists_scattered_tiles():
