@@ -107,6 +107,9 @@ def lib():
             L.lpo_phi.restype = C.c_double
             L.lpo_estimator_r.argtypes = [C.c_int32, _P, _P] + [C.c_double] * 5
             L.lpo_inflow_state.argtypes = [C.c_double] * 4 + [_P, _P]
+            L.lpo_free_surface_ghosts.argtypes = [C.POINTER(Config), C.c_int64, _PP, _P, _PP, _P, _P, C.c_int32,
+                                                  C.c_double, C.c_uint32, C.c_int64, _PP, _P, _PP, _P, _P, _P]
+            L.lpo_free_surface_ghosts.restype = C.c_int64
             L.lpo_estimator_r.restype = C.c_double
             L.lpo_riemann_star.argtypes = [C.c_double] * 7 + [_P, _P]
             L.lpo_riemann_star.restype = C.c_int
@@ -225,6 +228,29 @@ def cfl_dt(cfg: Config, V, P, ids, d2min, cfl):
     d2min = _c(d2min, np.float64)
     return float(lib().lpo_cfl_dt(C.byref(cfg), V.shape[0], _ptr(V), _ptr(P), _ptr(ids),
                                   _ptr(d2min), float(cfl)))
+
+
+def free_surface_ghosts(cfg: Config, state: dict, min_per_side=1, p_ghost=0.0, ghost_base=2**31):
+    """Ghost particles completing the free-surface neighbourhoods of the fluid
+    particles of ``state`` (Sec. 2.2 step 3; lpo_free_surface_ghosts): a state
+    dict (x, V, u, P, m, id) of the ghosts, in (particle, axis, side) order."""
+    dim = cfg.dim
+    xs = [_c(a, np.float64) for a in state["x"]]
+    us = [_c(a, np.float64) for a in state["u"]]
+    V = _c(state["V"], np.float64); m = _c(state["m"], np.float64); ids = _c(state["id"], np.uint32)
+    n = V.shape[0]
+    cap = 2 * dim * n
+    ox = [np.zeros(cap) for _ in range(dim)]
+    ou = [np.zeros(cap) for _ in range(dim)]
+    oV = np.zeros(cap); oP = np.zeros(cap); om = np.zeros(cap); oid = np.zeros(cap, np.uint32)
+    px, k1 = _ptrs(xs); pu, k2 = _ptrs(us); pox, k3 = _ptrs(ox); pou, k4 = _ptrs(ou)
+    ng = lib().lpo_free_surface_ghosts(C.byref(cfg), n, px, _ptr(V), pu, _ptr(m), _ptr(ids), int(min_per_side),
+                                       float(p_ghost), int(ghost_base), cap, pox, _ptr(oV), pou, _ptr(oP),
+                                       _ptr(om), _ptr(oid))
+    if ng < 0:
+        raise MemoryError("lpo_free_surface_ghosts failed")
+    return {"x": [a[:ng] for a in ox], "V": oV[:ng], "u": [a[:ng] for a in ou], "P": oP[:ng], "m": om[:ng],
+            "id": oid[:ng]}
 
 
 def step(cfg: Config, state: dict, dt: float, query=None, forced_phi=None):

@@ -29,6 +29,8 @@
  *   lpo_cfl_dt          CFL time step (the paper gives none; see the reading below).
  *   lpo_riemann_exact   exact Riemann solution of the ideal-gas shock tube
  *                       (textbook; the Sod check of the full scheme).
+ *   lpo_free_surface_ghosts  ghost particles completing free-surface
+ *                       neighbourhoods (Sec. 2.2 step 3).
  *   lpo_inflow_state    reservoir inflow state at a nozzle inlet (Sec. 4).
  *   lpo_mlp_*           FP64 forward/backward/Adam of the 8-32-1 estimator MLP.
  *
@@ -1047,6 +1049,70 @@ int lpo_features(const lpo_config *c, int64_t n, const double *const *x, const d
 /* ------------------------------------------------------------------------ */
 /* reservoir inflow state (Sec. 4, the nozzle inlet boundary condition)      */
 /* ------------------------------------------------------------------------ */
+
+/*
+ * Free-surface ghost particles (Sec. 2.2 step 3: where the free boundary
+ * condition applies and a particle's neighbourhood is incomplete in one of
+ * the 2 dim axis directions, ghost particles complete it).  The paper leaves
+ * the ghosts' placement and state to the 2018 LP paper; reading:
+ *   - direction (k, s) of fluid particle i (id < n_fluid) is incomplete when
+ *     fewer than min_per_side members of its neighbour list (lpo_neighbors
+ *     with this configuration) have an offset along axis k of sign s (offsets
+ *     exactly 0 count on neither side, as for the one-sided stencils);
+ *     particles with no neighbour at all get no ghosts;
+ *   - the ghost of (i, k, s) sits at x_i + s ell_i e_k, ell_i = sqrt(d2) of
+ *     i's nearest neighbour, with i's mass, specific volume and velocity and
+ *     the pressure p_ghost (0: vacuum), and id ghost_base + 2 dim id_i + 2k +
+ *     (s > 0), so that ids stay distinct and ghosts (ids >= n_fluid) are
+ *     frozen in a step.
+ * Ghosts are written in the order (particle index, k, side -, +) to out_*
+ * (capacity max_out); returns their count, or -1 when max_out is too small
+ * or memory runs out.
+ */
+int64_t lpo_free_surface_ghosts(const lpo_config *c, int64_t n, const double *const *x, const double *V,
+                                const double *const *u, const double *m, const uint32_t *id,
+                                int32_t min_per_side, double p_ghost, uint32_t ghost_base, int64_t max_out,
+                                double *const *out_x, double *out_V, double *const *out_u, double *out_P,
+                                double *out_m, uint32_t *out_id)
+{
+    int64_t *q = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    uint32_t *cnt = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    uint32_t *tot = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *nb = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1) * (size_t)c->k_max);
+    double *d2m = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int64_t ng = -1;
+    if (!q || !cnt || !tot || !nb || !d2m) goto done;
+    for (int64_t i = 0; i < n; ++i) q[i] = i;
+    if (lpo_neighbors(c, n, x, V, m, id, n, q, 1, cnt, tot, nb, d2m) != 0) goto done;
+    ng = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if ((int64_t)id[i] >= c->n_fluid || cnt[i] == 0) continue;
+        const double ell = sqrt(d2m[i]);
+        for (int k = 0; k < c->dim; ++k) {
+            int neg = 0, pos = 0;
+            for (uint32_t t = 0; t < cnt[i]; ++t) {
+                const double dx = offset(c, x, k, i, nb[i * c->k_max + t]);
+                if (dx < 0.0) ++neg;
+                else if (dx > 0.0) ++pos;
+            }
+            for (int side = 0; side < 2; ++side) {
+                if ((side ? pos : neg) >= min_per_side) continue;
+                if (ng >= max_out) { ng = -1; goto done; }
+                for (int a = 0; a < c->dim; ++a) out_x[a][ng] = x[a][i];
+                out_x[k][ng] = side ? x[k][i] + ell : x[k][i] - ell;
+                for (int a = 0; a < c->dim; ++a) out_u[a][ng] = u[a][i];
+                out_V[ng] = V[i];
+                out_P[ng] = p_ghost;
+                out_m[ng] = m[i];
+                out_id[ng] = ghost_base + (uint32_t)(2 * c->dim) * id[i] + (uint32_t)(2 * k + side);
+                ++ng;
+            }
+        }
+    }
+done:
+    free(q); free(cnt); free(tot); free(nb); free(d2m);
+    return ng;
+}
 
 /*
  * The state of particles entering a nozzle from a reservoir at rest (P_res,
