@@ -125,6 +125,8 @@ def parse():
     ap.add_argument("--sims", type=int, default=256)
     ap.add_argument("--density-ratio", type=float, default=1e3,
                     help="jet-inflow: jet / ambient density ratio")
+    ap.add_argument("--select", default="nearest", choices=["nearest", "octant"],
+                    help="neighbours kept beyond k_max (jet-inflow workload): the nearest, or octant-balanced")
     ap.add_argument("--limiter", default="flagged", choices=["flagged", "uw"],
                     help="jet-inflow: the limiter mode")
     ap.add_argument("--grow-seconds", type=float, default=240.0,
@@ -930,7 +932,8 @@ def run_inflow(args):
     cap = 2 * n0
     cfg = lp.make_config(3, cap, kappa=KAPPA, k_max=K_MAX, k_side=8, gamma=inputs.JET_GAMMA, n_fluid=2 ** 31,
                          s_ref=(1.0, 1.0, 1.0, 3.5, 1.0),
-                         limiter={"flagged": lp.LIM_FLAGGED, "uw": lp.LIM_UW}[args.limiter])
+                         limiter={"flagged": lp.LIM_FLAGGED, "uw": lp.LIM_UW}[args.limiter],
+                         select={"nearest": lp.SELECT_NEAREST, "octant": lp.SELECT_OCTANT}[args.select])
     ctx = lp.Context(cfg)
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -1007,6 +1010,7 @@ def run_inflow(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "jet-inflow-3d-%s" % size_tag(counts[0]), "particles_timed": [counts[0], ps.n],
                        "jet_spacing": JET_H, "inlet": {k: v for k, v in q.items() if k != "center"},
+                       "limiter": args.limiter, "select": args.select,
                        "growth": growth, "flagged_per_step": s["n_flagged"] / args.steps,
                        "fp64_redo_per_step": s["n_fp64_redo"] / args.steps,
                        "rejected_updates_per_step": s["n_nonfinite"] / args.steps,

@@ -468,6 +468,39 @@ lp_status lp_remove_outside(lp_ctx *ctx, lp_particles *p, const double *lo, cons
 lp_status lp_reserve(lp_ctx *ctx, int64_t capacity);
 
 /*
+ * Free-surface ghost particles (Sec. 2.2 step 3: where a free boundary
+ * condition applies and a particle's neighbours are incomplete in some of the
+ * axis directions, ghost particles are generated to complete them).  The
+ * paper defers their placement and state; the reading here:
+ *   - the neighbour lists of p are built (as lp_build_neighbors: p is permuted
+ *     into key order);
+ *   - direction (axis k, side s) of a fluid particle (id < n_fluid) with at
+ *     least one neighbour is incomplete when fewer than `min_per_side` list
+ *     members have an FP64 offset along k of sign s (0 counts on neither side);
+ *   - each incomplete direction gets one ghost at x + s sqrt(d2min) e_k (the
+ *     nearest-neighbour distance), with the particle's m, V and u, pressure
+ *     `p_ghost` (0: vacuum) and id ghost_base + 2 dim id + 2k + (s > 0);
+ *   - the ghosts are appended after the p->n particles in (particle, axis,
+ *     side) order; *n_out = p->n + their count.
+ * Ghosts are frozen in lp_step (ghost_base must be >= the configuration's
+ * n_fluid, and ghost_base + 2 dim n_fluid <= 2^32, else LP_ERR_ARG); remove
+ * them after the step with lp_remove_ghosts(ctx, p, ghost_base, ...).
+ * Non-periodic, single-simulation contexts only (LP_ERR_ARG); min_per_side in
+ * 1..k_max.  When p->n + ghosts > capacity (or capacity exceeds the context's)
+ * nothing is appended and LP_ERR_CAPACITY is returned.  Synchronises `stream`
+ * (the ghost count is read back).  The neighbour lists are stale afterwards.
+ */
+lp_status lp_free_surface_ghosts(lp_ctx *ctx, lp_particles *p, int64_t capacity, int32_t min_per_side,
+                                 double p_ghost, uint32_t ghost_base, int64_t *n_out, lp_stream stream);
+
+/*
+ * Deletes the particles with id >= first_id (ghosts), keeping the order of the
+ * others; *n_out = the count kept.  Synchronises `stream`; the neighbour lists
+ * are stale afterwards.  LP_ERR_ARG for batched contexts.
+ */
+lp_status lp_remove_ghosts(lp_ctx *ctx, lp_particles *p, uint32_t first_id, int64_t *n_out, lp_stream stream);
+
+/*
  * One LP step of nsim independent simulations stored back to back in p: the
  * particles of simulation s are [offsets[s], offsets[s+1]) (offsets: device
  * int64 [nsim + 1], offsets[0] = 0, offsets[nsim] = p->n; nsim <= max_sims).

@@ -176,10 +176,13 @@ bool same_inlet(const lp_inlet& a, const lp_inlet& b) { return memcmp(&a, &b, si
 
 constexpr int RM_BLOCK = 1024;          // particles per block of the outflow compaction
 
-struct Box { double lo[3], hi[3]; int dim; };
+// what stays: inside the box (when `box`), and with id < id_end
+struct Box { double lo[3], hi[3]; int dim; int box; uint32_t id_end; };
 
 __device__ inline bool keeps(const Box& b, const lp_particles& p, int64_t i)
 {
+    if (p.id[i] >= b.id_end) return false;
+    if (!b.box) return true;
     for (int k = 0; k < b.dim; ++k) {
         const double x = p.x[k][i];
         if (!(x >= b.lo[k] && x <= b.hi[k])) return false;     // also drops NaN
@@ -340,21 +343,12 @@ extern "C" lp_status lp_inflow(lp_ctx* c, lp_particles* p, int64_t capacity, con
     return LP_OK;
 }
 
-extern "C" lp_status lp_remove_outside(lp_ctx* c, lp_particles* p, const double* lo, const double* hi, int64_t* n_out,
-                                       lp_stream stream)
+namespace {
+
+// delete the particles b does not keep, keeping the order of the others
+lp_status remove_where(lp_ctx* c, lp_particles* p, const Box& b, int64_t* n_out, cudaStream_t s)
 {
-    if (!c || !p || !lo || !hi || !n_out || p->n < 0 || c->dc.nsim_max > 1) return LP_ERR_ARG;
-    if (p->n > c->cap) return LP_ERR_CAPACITY;
     const int dim = c->dc.dim;
-    for (int k = 0; k < dim; ++k)
-        if (!p->x[k] || !p->u[k]) return LP_ERR_ARG;
-    if (!p->V || !p->P || !p->m || !p->id) return LP_ERR_ARG;
-    *n_out = p->n;
-    if (p->n == 0) return LP_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    Box b;
-    b.dim = dim;
-    for (int k = 0; k < 3; ++k) { b.lo[k] = lo[k]; b.hi[k] = hi[k]; }
     const int64_t nb = (p->n + RM_BLOCK - 1) / RM_BLOCK;
     // scratch: block offsets in the redo list, the copies in the sorted state
     uint32_t* bc = c->redo_list;
@@ -376,4 +370,47 @@ extern "C" lp_status lp_remove_outside(lp_ctx* c, lp_particles* p, const double*
     c->lists_stale = 1;          // the lists and sorted copies no longer describe p
     *n_out = (int64_t)kept;
     return LP_OK;
+}
+
+lp_status check_removal_args(const lp_ctx* c, const lp_particles* p)
+{
+    if (p->n > c->cap) return LP_ERR_CAPACITY;
+    for (int k = 0; k < c->dc.dim; ++k)
+        if (!p->x[k] || !p->u[k]) return LP_ERR_ARG;
+    if (!p->V || !p->P || !p->m || !p->id) return LP_ERR_ARG;
+    return LP_OK;
+}
+
+}  // namespace
+
+extern "C" lp_status lp_remove_ghosts(lp_ctx* c, lp_particles* p, uint32_t first_id, int64_t* n_out, lp_stream stream)
+{
+    if (!c || !p || !n_out || p->n < 0 || c->dc.nsim_max > 1) return LP_ERR_ARG;
+    lp_status st = check_removal_args(c, p);
+    if (st != LP_OK) return st;
+    *n_out = p->n;
+    if (p->n == 0) return LP_OK;
+    Box b;
+    memset(&b, 0, sizeof(b));
+    b.dim = c->dc.dim;
+    b.box = 0;
+    b.id_end = first_id;
+    return remove_where(c, p, b, n_out, (cudaStream_t)stream);
+}
+
+extern "C" lp_status lp_remove_outside(lp_ctx* c, lp_particles* p, const double* lo, const double* hi, int64_t* n_out,
+                                       lp_stream stream)
+{
+    if (!c || !p || !lo || !hi || !n_out || p->n < 0 || c->dc.nsim_max > 1) return LP_ERR_ARG;
+    lp_status st = check_removal_args(c, p);
+    if (st != LP_OK) return st;
+    *n_out = p->n;
+    if (p->n == 0) return LP_OK;
+    Box b;
+    memset(&b, 0, sizeof(b));
+    b.dim = c->dc.dim;
+    b.box = 1;
+    b.id_end = 0xffffffffu;
+    for (int k = 0; k < 3; ++k) { b.lo[k] = lo[k]; b.hi[k] = hi[k]; }
+    return remove_where(c, p, b, n_out, (cudaStream_t)stream);
 }

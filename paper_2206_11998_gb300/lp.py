@@ -34,7 +34,7 @@ EXPORTED = [
     "lp_sort_keys_noalloc", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step",
     "lp_mlp_train", "lp_mlp_infer", "lp_step_batched", "lp_graph_capture", "lp_graph_launch",
     "lp_set_schedule", "lp_get_schedule", "lp_autotune", "lp_step_host", "lp_inflow", "lp_reserve",
-    "lp_remove_outside",
+    "lp_remove_outside", "lp_free_surface_ghosts", "lp_remove_ghosts",
 ]
 MLP_IN, MLP_H = 8, 32
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H + 1
@@ -191,6 +191,11 @@ def lib():
         L.lp_remove_outside.argtypes = [P, C.POINTER(Particles), P, P, C.POINTER(C.c_int64), P]
         L.lp_remove_outside.restype = C.c_int
         L.lp_reserve.restype = C.c_int
+        L.lp_free_surface_ghosts.argtypes = [P, C.POINTER(Particles), C.c_int64, C.c_int32, C.c_double, C.c_uint32,
+                                             C.POINTER(C.c_int64), P]
+        L.lp_free_surface_ghosts.restype = C.c_int
+        L.lp_remove_ghosts.argtypes = [P, C.POINTER(Particles), C.c_uint32, C.POINTER(C.c_int64), P]
+        L.lp_remove_ghosts.restype = C.c_int
         for name in ("lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step", "lp_mlp_train",
                      "lp_mlp_infer"):
             getattr(L, name).restype = C.c_int
@@ -558,6 +563,31 @@ class Context:
         hi_a = (C.c_double * 3)(*[float(v) for v in hi])
         _check(lib().lp_remove_outside(self.h, C.byref(p), lo_a, hi_a, C.byref(n_out), _stream(stream)),
                "lp_remove_outside")
+        removed = ps.n - int(n_out.value)
+        ps.count = int(n_out.value)
+        return removed
+
+    def free_surface_ghosts(self, ps: ParticleSet, min_per_side=1, p_ghost=0.0, ghost_base=2 ** 31, stream=None):
+        """Free-surface ghosts (lp_free_surface_ghosts): builds the lists (ps is
+        permuted into key order) and appends a ghost for each incomplete axis
+        direction of each fluid particle into the room of ps (ps.count grows).
+        Returns the number appended.  LPError(ERR_CAPACITY) when ps has no room."""
+        p = ps.struct()
+        n_out = C.c_int64(0)
+        _check(lib().lp_free_surface_ghosts(self.h, C.byref(p), ps.capacity, int(min_per_side), float(p_ghost),
+                                            int(ghost_base), C.byref(n_out), _stream(stream)),
+               "lp_free_surface_ghosts")
+        added = int(n_out.value) - ps.n
+        ps.count = int(n_out.value)
+        return added
+
+    def remove_ghosts(self, ps: ParticleSet, first_id=2 ** 31, stream=None):
+        """Drop the particles with id >= first_id (lp_remove_ghosts); returns the
+        number removed."""
+        p = ps.struct()
+        n_out = C.c_int64(0)
+        _check(lib().lp_remove_ghosts(self.h, C.byref(p), int(first_id), C.byref(n_out), _stream(stream)),
+               "lp_remove_ghosts")
         removed = ps.n - int(n_out.value)
         ps.count = int(n_out.value)
         return removed
