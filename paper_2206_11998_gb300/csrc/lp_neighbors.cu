@@ -507,15 +507,25 @@ __device__ inline void octant_ranks(const QueryArgs& a, WarpBuf& b, int m, int64
 // id), the rank of a member being its place in its octant's (d2, id) order:
 // round robin over the octants, nearest first in each.  They are stored in
 // (d2, id) order; with at most k_max inside, the list is the nearest-first one.
-//   1. a pass over the start cells counts the members of each octant (n_o,
-//      saturated at k_max) and in all;
+//   1. a traversal counts the members of each octant (n_o, needed up to k_max)
+//      and in all (needed up to 4 k_max);
 //   2. R is the smallest rank with sum_o min(n_o, R + 1) >= k_max: ranks below
 //      R are all kept, rank R partly, so each octant needs only its
 //      q_o = min(n_o, R + 1) nearest;
-//   3. a second pass keeps those (compacting the buffer to the quotas whenever
-//      it fills), and the final sorted buffer gives the selection.
-// Membership and order are decided as in query_one (float split distances,
-// FP64 inside the rounding bands), octants on the FP64 offsets.
+//   3. a second traversal keeps those (compacting the buffer to the quotas
+//      whenever it fills and after each level of cells), and the final sorted
+//      buffer gives the selection.
+// Both traversals start at the start cells and split a cell with more than
+// DESC_MIN particles into its children (processed as the next level), so
+// that a dense region is visited only where it matters: the counting pass
+// counts a cell that lies inside the radius and inside one octant without
+// scanning it, and skips cells whose octants are all counted out once the
+// total reached 4 k_max; the collecting pass skips cells farther than the
+// current q_o-th member of each octant they meet.  A cell is in one octant
+// when its box lies, with the quantisation margin, on one side of the
+// particle along every axis.  Membership and order are decided as in
+// query_one (float split distances, FP64 inside the rounding bands), octants
+// on the FP64 offsets.
 template <int DIM>
 __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
 {
@@ -527,91 +537,161 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
     const Grid& g = a.g[st.sim];
     const uint32_t kmax = (uint32_t)c.k_max;
     constexpr int NO = 1 << DIM;
-    // every candidate j != i of the start cells, 32 at a time: fn(in, j, d2f)
-    // is called by all lanes (in: j lies inside the radius, exactly)
-    auto scan = [&](auto&& fn) {
-        for (int base0 = 0; base0 < st.ncells; base0 += 32) {
-            const int e = base0 + (int)lane;
-            uint32_t cs = 0, cn = 0;
-            if (e < st.ncells) {
-                int l, wv[3], shv[3];
-                unpack_cell(b.front[0][e], l, wv, shv);
-                const float size = ldexpf(1.0f, mb - l), period = ldexpf(1.0f, mb);
-                uint32_t q[3] = {0u, 0u, 0u};
-                float dmin2 = 0.0f;
+    constexpr unsigned ALL_O = (1u << NO) - 1u;
+    // octants with bit k set (offset along k >= 0), per axis
+    constexpr unsigned AXIS_SET[3] = {DIM == 3 ? 0xAAu : (DIM == 2 ? 0xAu : 0x2u), DIM == 3 ? 0xCCu : 0xCu, 0xF0u};
+    enum { SKIP = 0, SCAN = 1, SPLIT = 2, WHOLE = 3 };
+    // One traversal from the start cells.  pre() runs (all lanes) before each
+    // batch of 32 cells; cls(dmin, dmax, touched, splittable) classifies a
+    // non-empty cell within reach (one lane, no warp operations); whole(w,
+    // touched, cn) is called by all lanes (w: this lane's cell is counted
+    // whole); fn(in, j, d2f) by all lanes for each scanned candidate;
+    // level_end() by all lanes after each level.
+    auto traverse = [&](auto&& pre, auto&& cls, auto&& whole, auto&& fn, auto&& level_end) {
+        query_start<DIM>(a, b, i, st);
+        int cur = 0, ncur = st.ncells;
+        while (ncur > 0) {
+            int nnext = 0;
+            for (int base0 = 0; base0 < ncur; base0 += 32) {
+                pre();
+                const int e = base0 + (int)lane;
+                uint32_t cs = 0, cn = 0;
+                int act = SKIP, l = 0, wv[3] = {0, 0, 0}, shv[3] = {0, 0, 0};
+                unsigned touched = 0u;
+                if (e < ncur) {
+                    unpack_cell(b.front[cur][e], l, wv, shv);
+                    const float size = ldexpf(1.0f, mb - l), period = ldexpf(1.0f, mb);
+                    uint32_t q[3] = {0u, 0u, 0u};
+                    float dmin2 = 0.0f, dmax2 = 0.0f;
+                    touched = ALL_O;
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    q[k] = (uint32_t)wv[k];
-                    const float lo = (float)wv[k] * size + (float)shv[k] * period, hi = lo + size;
-                    const float dn = fmaxf(0.0f, fmaxf(lo - st.tq[k], st.tq[k] - hi));
-                    dmin2 += dn * dn;
-                }
-                if (sqrtf(dmin2) < st.Rout) {
-                    const uint64_t code = (st.sim << (DIM * l)) | morton<DIM>(q);
-                    const unsigned long long ent = a.cells[a.level_off[l] + (int64_t)code];
-                    cs = (uint32_t)ent;
-                    const uint32_t ce = (uint32_t)(ent >> 32);
-                    cn = ce > cs ? ce - cs : 0;
-                }
-            }
-            uint32_t incl = cn;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((int)lane >= o) incl += v;
-            }
-            const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-            b.cstart[lane] = cs;
-            b.cexcl[lane] = incl - cn;
-            __syncwarp();
-            for (uint32_t base = 0; base < T; base += 32) {
-                const uint32_t t = base + lane;
-                bool in = false;
-                float d2f = 0.0f;
-                uint32_t j = 0;
-                if (t < T) {
-                    int lo = 0, hi = 31;       // the last cell with cexcl <= t
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
+                    for (int k = 0; k < DIM; ++k) {
+                        q[k] = (uint32_t)wv[k];
+                        const float lo = (float)wv[k] * size + (float)shv[k] * period, hi = lo + size;
+                        const float dn = fmaxf(0.0f, fmaxf(lo - st.tq[k], st.tq[k] - hi));
+                        const float df = fmaxf(st.tq[k] - lo, hi - st.tq[k]);
+                        dmin2 += dn * dn;
+                        dmax2 += df * df;
+                        if (lo > st.tq[k] + 2.0f) touched &= AXIS_SET[k];          // every offset > 0
+                        else if (hi < st.tq[k] - 2.0f) touched &= ~AXIS_SET[k];    // every offset < 0
                     }
-                    j = b.cstart[lo] + (t - b.cexcl[lo]);
-                    if ((int64_t)j != i) {
-                        float4 ph, pl;
-                        ldg256(a.pos4 + 2 * (int64_t)j, ph, pl);
-                        const float hj[3] = {ph.x, ph.y, ph.z}, lj[3] = {pl.x, pl.y, pl.z};
-#pragma unroll
-                        for (int k = 0; k < DIM; ++k) {
-                            float dh = hj[k] - st.hxi[k];
-                            float dl = lj[k] - st.lxi[k];
-                            if (c.periodic[k]) {
-                                if (dh > 0.5f * c.Lper_h[k]) { dh -= c.Lper_h[k]; dl -= c.Lper_l[k]; }
-                                else if (dh < -0.5f * c.Lper_h[k]) { dh += c.Lper_h[k]; dl += c.Lper_l[k]; }
-                            }
-                            const float d = dh + dl;
-                            d2f = fmaf(d, d, d2f);
+                    const float dmin = sqrtf(dmin2), dmax = sqrtf(dmax2);
+                    if (dmin < st.Rout) {
+                        const uint64_t code = (st.sim << (DIM * l)) | morton<DIM>(q);
+                        const unsigned long long ent = a.cells[a.level_off[l] + (int64_t)code];
+                        cs = (uint32_t)ent;
+                        const uint32_t ce = (uint32_t)(ent >> 32);
+                        cn = ce > cs ? ce - cs : 0;
+                        if (cn > 0) act = cls(dmin, dmax, touched, cn > DESC_MIN && l < g.lmax);
+                    }
+                }
+                // split cells: children to the next level while there is room,
+                // scanned otherwise
+                constexpr int nchild = 1 << DIM;
+                const unsigned sm = __ballot_sync(0xffffffffu, act == SPLIT);
+                const int room = (FCAP - nnext) / nchild;
+                if (act == SPLIT) {
+                    const int rank = __popc(sm & lt);
+                    if (rank < room) {
+                        const int pos = nnext + rank * nchild;
+                        for (int ch = 0; ch < nchild; ++ch) {
+                            const int cw[3] = {2 * wv[0] + (ch & 1), DIM > 1 ? 2 * wv[1] + ((ch >> 1) & 1) : 0,
+                                               DIM > 2 ? 2 * wv[2] + ((ch >> 2) & 1) : 0};
+                            b.front[cur ^ 1][pos + ch] = pack_cell(l + 1, cw, shv);
                         }
-                        if (d2f <= st.R2f * (1.0f - TOL_R)) in = true;
-                        else if (d2f <= st.R2f * (1.0f + TOL_R))
-                            in = inside64(c, DIM, exact_d2<DIM>(a, i, j), __dmul_rn(a.sm[i], a.sV[i]));
+                        act = SKIP;
+                    } else {
+                        act = SCAN;
                     }
                 }
-                fn(in, j, d2f);
+                nnext += min(__popc(sm), max(room, 0)) * nchild;
+                whole(act == WHOLE, touched, cn);
+                // scanned cells: their candidates over the lanes
+                const uint32_t cnt = act == SCAN ? cn : 0u;
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((int)lane >= o) incl += v;
+                }
+                const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+                b.cstart[lane] = cs;
+                b.cexcl[lane] = incl - cnt;
+                __syncwarp();
+                for (uint32_t base = 0; base < T; base += 32) {
+                    const uint32_t t = base + lane;
+                    bool in = false;
+                    float d2f = 0.0f;
+                    uint32_t j = 0;
+                    if (t < T) {
+                        int lo = 0, hi = 31;       // the last cell with cexcl <= t
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (b.cexcl[mid] <= t) lo = mid; else hi = mid - 1;
+                        }
+                        j = b.cstart[lo] + (t - b.cexcl[lo]);
+                        if ((int64_t)j != i) {
+                            float4 ph, pl;
+                            ldg256(a.pos4 + 2 * (int64_t)j, ph, pl);
+                            const float hj[3] = {ph.x, ph.y, ph.z}, lj[3] = {pl.x, pl.y, pl.z};
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) {
+                                float dh = hj[k] - st.hxi[k];
+                                float dl = lj[k] - st.lxi[k];
+                                if (c.periodic[k]) {
+                                    if (dh > 0.5f * c.Lper_h[k]) { dh -= c.Lper_h[k]; dl -= c.Lper_l[k]; }
+                                    else if (dh < -0.5f * c.Lper_h[k]) { dh += c.Lper_h[k]; dl += c.Lper_l[k]; }
+                                }
+                                const float d = dh + dl;
+                                d2f = fmaf(d, d, d2f);
+                            }
+                            if (d2f <= st.R2f * (1.0f - TOL_R)) in = true;
+                            else if (d2f <= st.R2f * (1.0f + TOL_R))
+                                in = inside64(c, DIM, exact_d2<DIM>(a, i, j), __dmul_rn(a.sm[i], a.sV[i]));
+                        }
+                    }
+                    fn(in, j, d2f);
+                }
+                __syncwarp();
             }
+            level_end();
+            cur ^= 1;
+            ncur = nnext;
             __syncwarp();
         }
     };
     // ---- 1. members per octant (lane o holds octant o's count) and in all
     uint32_t cnt_o = 0, total = 0;
-    scan([&](bool in, uint32_t j, float) {
-        const int o = in ? octant64<DIM>(a, i, j) : -1;
-        total += (uint32_t)__popc(__ballot_sync(0xffffffffu, in));
+    unsigned sat = 0u;             // octants counted up to k_max (warp-uniform)
+    bool total_done = false;       // total >= 4 k_max
+    traverse(
+        [&]() {
+            sat = __ballot_sync(0xffffffffu, (int)lane < NO && cnt_o >= kmax) & ALL_O;
+            total_done = total >= 4u * kmax;
+        },
+        [&](float dmin, float dmax, unsigned touched, bool splittable) -> int {
+            if (total_done && (touched & ~sat) == 0u) return SKIP;
+            if (__popc(touched) == 1 && dmax <= st.Rin) return WHOLE;
+            return splittable ? SPLIT : SCAN;
+        },
+        [&](bool w, unsigned touched, uint32_t cn) {
+            total += __reduce_add_sync(0xffffffffu, w ? cn : 0u);
 #pragma unroll
-        for (int q = 0; q < NO; ++q) {
-            const unsigned bq = __ballot_sync(0xffffffffu, o == q);
-            if ((int)lane == q) cnt_o += (uint32_t)__popc(bq);
-        }
-    });
+            for (int q = 0; q < NO; ++q) {
+                const uint32_t add = __reduce_add_sync(0xffffffffu, (w && touched == (1u << q)) ? cn : 0u);
+                if ((int)lane == q) cnt_o += add;
+            }
+        },
+        [&](bool in, uint32_t j, float) {
+            const int o = in ? octant64<DIM>(a, i, j) : -1;
+            total += (uint32_t)__popc(__ballot_sync(0xffffffffu, in));
+#pragma unroll
+            for (int q = 0; q < NO; ++q) {
+                const unsigned bq = __ballot_sync(0xffffffffu, o == q);
+                if ((int)lane == q) cnt_o += (uint32_t)__popc(bq);
+            }
+        },
+        [&]() {});
     // ---- 2. the rank threshold and the quotas
     const uint32_t n_o = (int)lane < NO ? min(cnt_o, kmax) : 0u;
     uint32_t R = kmax, q_o = n_o, rem = 0;
@@ -621,11 +701,16 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
         q_o = min(n_o, R + 1);
         rem = kmax - warp_sum_u32(min(n_o, R));              // rank-R members kept
     }
+    const unsigned zero_q = __ballot_sync(0xffffffffu, (int)lane < NO && q_o == 0u) & ALL_O;
     // ---- 3. the q_o nearest of each octant
     int m = 0;
+    unsigned full = 0u;            // octants holding q_o members (warp-uniform)
+    float cut_o = INFINITY;        // lane o: float d2 bound of octant o's members, when full
     auto compact = [&]() {
         sort_exact<DIM>(a, b, m, i);
         int w = 0;
+        unsigned nfull = 0u;
+        float ncut = INFINITY;
         octant_ranks<DIM>(a, b, m, i, [&](int e0, bool valid, int o, uint32_t rank) {
             const int e = e0 + (int)lane;
             // every lane takes part in the shuffle (no short circuit before it)
@@ -633,6 +718,17 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
             const bool keep = valid && rank < qo;
             const unsigned long long kk = valid ? b.key[e] : 0ull;
             const uint32_t jj = valid ? b.j[e] : 0u;
+            // the last member an octant keeps sets its bound
+            const bool last = keep && rank + 1u == qo;
+#pragma unroll
+            for (int q = 0; q < NO; ++q) {
+                const unsigned bl = __ballot_sync(0xffffffffu, last && o == q);
+                const float d = __shfl_sync(0xffffffffu, key_d2(kk), bl ? __ffs(bl) - 1 : 0);
+                if (bl) {
+                    nfull |= 1u << q;
+                    if ((int)lane == q) ncut = d * (1.0f + TOL_T);
+                }
+            }
             const unsigned km = __ballot_sync(0xffffffffu, keep);
             __syncwarp();
             if (keep) {
@@ -644,21 +740,45 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
             __syncwarp();
         });
         m = w;
+        full = nfull;
+        cut_o = ncut;
     };
-    scan([&](bool in, uint32_t j, float d2f) {
-        const int o = in ? octant64<DIM>(a, i, j) : 0;
-        const uint32_t qo = __shfl_sync(0xffffffffu, q_o, o);   // every lane, then the test
-        const bool keep = in && qo > 0u;
-        if (m > NB_CAP - 32) compact();                      // warp-uniform
-        const unsigned km = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            const int pos = m + __popc(km & lt);
-            b.key[pos] = ((unsigned long long)__float_as_uint(d2f) << 32) | a.sid[j];
-            b.j[pos] = j;
-        }
-        m += __popc(km);
-        __syncwarp();
-    });
+    float cutq[NO];                // per octant, quantised units (warp-uniform)
+    traverse(
+        [&]() {
+#pragma unroll
+            for (int q = 0; q < NO; ++q) {
+                const float cd = __shfl_sync(0xffffffffu, cut_o, q);
+                cutq[q] = ((full >> q) & 1u) ? sqrtf(cd) * st.inv * (1.0f + 2e-5f) + 1.0f : INFINITY;
+            }
+        },
+        [&](float dmin, float, unsigned touched, bool splittable) -> int {
+            bool need = false;
+#pragma unroll
+            for (int q = 0; q < NO; ++q)
+                if (((touched & ~zero_q) >> q) & 1u) need |= dmin <= cutq[q];
+            if (!need) return SKIP;
+            return splittable ? SPLIT : SCAN;
+        },
+        [&](bool, unsigned, uint32_t) {},
+        [&](bool in, uint32_t j, float d2f) {
+            const int o = in ? octant64<DIM>(a, i, j) : 0;
+            const uint32_t qo = __shfl_sync(0xffffffffu, q_o, o);   // every lane, then the test
+            const float co = __shfl_sync(0xffffffffu, cut_o, o);
+            const bool keep = in && qo > 0u && d2f <= co;
+            if (m > NB_CAP - 32) compact();                      // warp-uniform
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int pos = m + __popc(km & lt);
+                b.key[pos] = ((unsigned long long)__float_as_uint(d2f) << 32) | a.sid[j];
+                b.j[pos] = j;
+            }
+            m += __popc(km);
+            __syncwarp();
+        },
+        [&]() {
+            if (m > 0) compact();          // bounds for the next level
+        });
     compact();                                               // m <= sum_o q_o, sorted
     // ---- the selection, in (d2, id) order: ranks below R, and the first rem of rank R
     int w = 0;
@@ -695,17 +815,30 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_query(QueryArgs a)
         const unsigned long long len = *a.list_len;
         for (unsigned long long t = (unsigned long long)blockIdx.x * NB_WARPS + w; t < len;
              t += (unsigned long long)gridDim.x * NB_WARPS)
-        {
-            const int64_t i = (int64_t)a.list[t];
-            if (a.c.select == LP_SELECT_OCTANT) query_one_octant<DIM>(a, b, i);
-            else query_one<DIM>(a, b, i);
-        }
+            query_one<DIM>(a, b, (int64_t)a.list[t]);
     } else {
         const int64_t i = (int64_t)blockIdx.x * NB_WARPS + w;
-        if (i < a.n) {
-            if (a.c.select == LP_SELECT_OCTANT) query_one_octant<DIM>(a, b, i);
-            else query_one<DIM>(a, b, i);
-        }
+        if (i < a.n) query_one<DIM>(a, b, i);
+    }
+}
+
+// the octant-balanced selection (LP_SELECT_OCTANT), warp per particle: every
+// particle, or the particles of a list.  A kernel of its own so that the
+// nearest-first kernel keeps its register budget.
+template <int DIM>
+__global__ void __launch_bounds__(NB_WARPS * 32) k_query_octant(QueryArgs a)
+{
+    __shared__ WarpBuf bufs[NB_WARPS];
+    const int w = threadIdx.x >> 5;
+    WarpBuf& b = bufs[w];
+    if (a.list) {
+        const unsigned long long len = *a.list_len;
+        for (unsigned long long t = (unsigned long long)blockIdx.x * NB_WARPS + w; t < len;
+             t += (unsigned long long)gridDim.x * NB_WARPS)
+            query_one_octant<DIM>(a, b, (int64_t)a.list[t]);
+    } else {
+        const int64_t i = (int64_t)blockIdx.x * NB_WARPS + w;
+        if (i < a.n) query_one_octant<DIM>(a, b, i);
     }
 }
 
@@ -1505,10 +1638,16 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     }
     cudaError_t e = cudaMemsetAsync(c->counters + C_QFB_LEN, 0, 8, s);
     if (e != cudaSuccess) return e;
+    const bool octant = c->dc.select == LP_SELECT_OCTANT;
     if (c->schedule & LP_SCHED_QUERY_WARP) {   // one warp per particle for every particle
         const unsigned wb = (unsigned)((n + NB_WARPS - 1) / NB_WARPS);
-        if (dim == 3) k_query<3><<<wb, NB_WARPS * 32, 0, s>>>(a);
-        else k_query<2><<<wb, NB_WARPS * 32, 0, s>>>(a);
+        if (octant) {
+            if (dim == 3) k_query_octant<3><<<wb, NB_WARPS * 32, 0, s>>>(a);
+            else k_query_octant<2><<<wb, NB_WARPS * 32, 0, s>>>(a);
+        } else {
+            if (dim == 3) k_query<3><<<wb, NB_WARPS * 32, 0, s>>>(a);
+            else k_query<2><<<wb, NB_WARPS * 32, 0, s>>>(a);
+        }
         return cudaGetLastError();
     }
     // tiles first; the particles they leave go to the per-particle kernel
@@ -1540,8 +1679,13 @@ cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
     a.list = c->redo_list;
     a.list_len = c->counters + C_QFB_LEN;
     const unsigned fblocks = 152u * 4u;
-    if (dim == 3) k_query<3><<<fblocks, NB_WARPS * 32, 0, s>>>(a);
-    else k_query<2><<<fblocks, NB_WARPS * 32, 0, s>>>(a);
+    if (octant) {
+        if (dim == 3) k_query_octant<3><<<fblocks, NB_WARPS * 32, 0, s>>>(a);
+        else k_query_octant<2><<<fblocks, NB_WARPS * 32, 0, s>>>(a);
+    } else {
+        if (dim == 3) k_query<3><<<fblocks, NB_WARPS * 32, 0, s>>>(a);
+        else k_query<2><<<fblocks, NB_WARPS * 32, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
