@@ -125,8 +125,10 @@ def parse():
     ap.add_argument("--sims", type=int, default=256)
     ap.add_argument("--density-ratio", type=float, default=1e3,
                     help="jet-inflow: jet / ambient density ratio")
-    ap.add_argument("--select", default="nearest", choices=["nearest", "octant"],
-                    help="neighbours kept beyond k_max (jet-inflow workload): the nearest, or octant-balanced")
+    ap.add_argument("--select", default="octant", choices=["nearest", "octant"],
+                    help="neighbours kept beyond k_max (jet-inflow workload): octant-balanced (the default: with "
+                         "the nearest only, the ambient particles next to the jet lose their one-sided stencils "
+                         "and the run stalls), or the nearest")
     ap.add_argument("--limiter", default="flagged", choices=["flagged", "uw"],
                     help="jet-inflow: the limiter mode")
     ap.add_argument("--grow-seconds", type=float, default=240.0,
