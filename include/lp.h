@@ -302,6 +302,19 @@ lp_status lp_export_neighbors(lp_ctx *ctx, uint32_t *count, uint32_t *total, uin
                               double *d2min, uint64_t *keys, lp_stream stream);
 
 /*
+ * All-octant coverage check of the central stencils (Sec. 2.1: the
+ * second-order stencils are meant to include particles from all 8 octants).
+ * For every particle of the last neighbour build (key order, as
+ * lp_export_neighbors), gap[i] = 1 when its list misses one of the 2^dim
+ * sign patterns of the offsets x_j - x_i (an offset of exactly 0 counted as
+ * positive), else 0; gap (device, n bytes) may be null.  *n_gap (host) = the
+ * number of such particles.  The signs come from the float hi/lo offsets the
+ * fits use.  Synchronises `stream`.  LP_ERR_STATE when the lists are stale,
+ * LP_ERR_ARG in the k-per-side mode.
+ */
+lp_status lp_octant_coverage(lp_ctx *ctx, uint8_t *gap, int64_t *n_gap, lp_stream stream);
+
+/*
  * Synchronise `stream` and read the quantisation cube of the last build into
  * host out[5] = {lo_0, lo_1, lo_2, L, finest level}: Morton coordinates are
  * q_k = floor((x_k - lo_k) * 2^21 / L), clamped to [0, 2^21 - 1].

@@ -36,7 +36,7 @@ constexpr uint32_t FIT_LINEAR = 1u, FIT_NONE = 2u, FIT_FP64 = 8u;
 enum Counter {
     C_FLAGGED = 0, C_FP64, C_LINEAR, C_NOFIT, C_OVERFLOW, C_NONFINITE, C_MLP_UNCERTAIN,
     C_MAXCOUNT, C_STATUS, C_REDO_LEN, C_STEPS, C_MLP_SKIP, C_MLP_MISS, C_PLAIN_LEN, C_QFB_LEN, C_REFINED,
-    C_REFINE_LEN, C_QUEUE_TILE, C_QUEUE_CENTRAL, C_QUEUE_PLAIN, C_COUNT
+    C_REFINE_LEN, C_QUEUE_TILE, C_QUEUE_CENTRAL, C_QUEUE_PLAIN, C_OCT_GAP, C_COUNT
 };
 
 // method constants as the kernels see them

@@ -1604,6 +1604,41 @@ __global__ void k_query_kside(QueryArgs a)
 
 }  // namespace
 
+// The all-octant coverage check of the central stencils (Sec. 2.1: the
+// second-order stencils are meant to include particles from all 8 octants):
+// per particle of the last build, whether its list misses one of the 2^dim
+// sign patterns of the offsets (an offset of exactly 0 counted as positive),
+// from the same float hi/lo offsets the fits use.  Thread per particle.
+template <int DIM, bool PER>
+__global__ void k_octant_coverage(int64_t n, DevCfg c, const float4* __restrict__ pos4,
+                                  const uint32_t* __restrict__ count, const uint32_t* __restrict__ idx,
+                                  uint8_t* gap, unsigned long long* ngap)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool g = false;
+    if (i < n) {
+        const float4 ih = pos4[2 * i], il = pos4[2 * i + 1];
+        const float hi[3] = {ih.x, ih.y, ih.z}, li[3] = {il.x, il.y, il.z};
+        const uint32_t cnt = count[i];
+        unsigned mask = 0u;
+        for (uint32_t t = 0; t < cnt; ++t) {
+            const uint32_t j = idx[i * (int64_t)c.k_max + t];
+            float4 qh, ql;
+            ldg256(pos4 + 2 * (int64_t)j, qh, ql);
+            const float hj[3] = {qh.x, qh.y, qh.z}, lj[3] = {ql.x, ql.y, ql.z};
+            unsigned o = 0u;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k)
+                o |= (split_offset<PER>(c, k, hj[k], lj[k], hi[k], li[k]) >= 0.0f ? 1u : 0u) << k;
+            mask |= 1u << o;
+        }
+        g = __popc(mask) < (1 << DIM);
+        if (gap) gap[i] = g ? 1 : 0;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, g);
+    if ((threadIdx.x & 31u) == 0u && b) atomicAdd(ngap, (unsigned long long)__popc(b));
+}
+
 cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
@@ -1711,3 +1746,32 @@ cudaError_t query_init()
 }
 
 }  // namespace lp
+
+using namespace lp;
+
+extern "C" lp_status lp_octant_coverage(lp_ctx* c, uint8_t* gap, int64_t* n_gap, lp_stream stream)
+{
+    if (!c || !n_gap || c->dc.radius_mode == LP_RADIUS_KSIDE) return LP_ERR_ARG;
+    if (c->lists_stale) return LP_ERR_STATE;
+    *n_gap = 0;
+    const int64_t n = c->n_lists;
+    if (n == 0) return LP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long* ctr = c->counters + C_OCT_GAP;
+    if (cudaMemsetAsync(ctr, 0, 8, s) != cudaSuccess) return LP_ERR_CUDA;
+    const bool per = c->dc.periodic[0] || c->dc.periodic[1] || c->dc.periodic[2];
+    const unsigned gb = (unsigned)((n + 255) / 256);
+    const int dim = c->dc.dim;
+#define LP_COV_ARGS n, c->dc, c->pos4, c->nb_count, c->nb_idx, gap, ctr
+    if (dim == 3) { if (per) k_octant_coverage<3, true><<<gb, 256, 0, s>>>(LP_COV_ARGS); else k_octant_coverage<3, false><<<gb, 256, 0, s>>>(LP_COV_ARGS); }
+    else if (dim == 2) { if (per) k_octant_coverage<2, true><<<gb, 256, 0, s>>>(LP_COV_ARGS); else k_octant_coverage<2, false><<<gb, 256, 0, s>>>(LP_COV_ARGS); }
+    else { if (per) k_octant_coverage<1, true><<<gb, 256, 0, s>>>(LP_COV_ARGS); else k_octant_coverage<1, false><<<gb, 256, 0, s>>>(LP_COV_ARGS); }
+#undef LP_COV_ARGS
+    c->launches += 1;
+    unsigned long long h = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&h, ctr, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LP_ERR_CUDA;
+    *n_gap = (int64_t)h;
+    return LP_OK;
+}

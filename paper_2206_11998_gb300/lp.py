@@ -34,7 +34,7 @@ EXPORTED = [
     "lp_sort_keys_noalloc", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step",
     "lp_mlp_train", "lp_mlp_infer", "lp_step_batched", "lp_graph_capture", "lp_graph_launch",
     "lp_set_schedule", "lp_get_schedule", "lp_autotune", "lp_step_host", "lp_inflow", "lp_reserve",
-    "lp_remove_outside", "lp_free_surface_ghosts", "lp_remove_ghosts",
+    "lp_remove_outside", "lp_free_surface_ghosts", "lp_remove_ghosts", "lp_octant_coverage",
 ]
 MLP_IN, MLP_H = 8, 32
 MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H + 1
@@ -196,6 +196,8 @@ def lib():
         L.lp_free_surface_ghosts.restype = C.c_int
         L.lp_remove_ghosts.argtypes = [P, C.POINTER(Particles), C.c_uint32, C.POINTER(C.c_int64), P]
         L.lp_remove_ghosts.restype = C.c_int
+        L.lp_octant_coverage.argtypes = [P, P, C.POINTER(C.c_int64), P]
+        L.lp_octant_coverage.restype = C.c_int
         for name in ("lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_grad", "lp_mlp_adam_step", "lp_mlp_train",
                      "lp_mlp_infer"):
             getattr(L, name).restype = C.c_int
@@ -591,6 +593,14 @@ class Context:
         removed = ps.n - int(n_out.value)
         ps.count = int(n_out.value)
         return removed
+
+    def octant_coverage(self, gap=None, stream=None):
+        """All-octant coverage of the last build's lists (lp_octant_coverage):
+        the number of particles whose list misses an octant; gap (device uint8
+        tensor of n, optional) receives the per-particle flags in key order."""
+        n_gap = C.c_int64(0)
+        _check(lib().lp_octant_coverage(self.h, _ptr(gap), C.byref(n_gap), _stream(stream)), "lp_octant_coverage")
+        return int(n_gap.value)
 
     def reserve(self, capacity):
         """Resize the context's scratch to `capacity` particles (lp_reserve)."""

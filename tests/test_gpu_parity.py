@@ -211,6 +211,31 @@ def test_step_jet_snapshot_octant_selection(prec, tol):
     assert stats["n_overflow"] > 0, stats
 
 
+def test_octant_coverage_check():
+    """The all-octant coverage check of the central stencils
+    (lp_octant_coverage): the particles whose list misses one of the 8 sign
+    patterns of the offsets (exactly 0 counted as positive) are the ones the
+    CPU finds on the oracle's lists (the cloud's edge particles, whose lists
+    have no outward members)."""
+    st = inputs.gas_cloud_3d(20_037, seed=4)
+    n = st["V"].shape[0]
+    cfg = lp.make_config(3, n, kappa=2.2, k_max=64)
+    ctx = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    ctx.build_neighbors(ps)
+    gap = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    ngap = ctx.octant_coverage(gap)
+    ids = ps.id.cpu().numpy().astype(np.int64)
+    g = by_id(ids, gap.cpu().numpy())
+    ctx.close()
+    oidx, ocnt, _, _ = oracle.neighbors(_oracle_cfg(cfg), st["x"], st["V"], st["m"], st["id"])
+    x = np.stack(st["x"], 1)
+    want = np.array([len(set(map(tuple, (x[oidx[i, :ocnt[i]]] - x[i]) >= 0.0))) < 8 for i in range(n)])
+    print("octant gaps: %d of %d" % (ngap, n))
+    assert ngap == int(want.sum()) > 0
+    assert np.array_equal(g.astype(bool), want)
+
+
 def test_neighbor_lists_scattered_tiles():
     """Two far-apart clusters and a sprinkle of isolated points: tiles of 32
     consecutive particles that straddle them span too many cells and are left
