@@ -121,6 +121,10 @@ enum { LP_OUT_F32 = 0, LP_OUT_F64 = 1 };
  *                  inside the radius the two agree.  LP_SELECT_OCTANT needs dim
  *                  2 or 3 and a radius (not LP_RADIUS_KSIDE).
  *   reserved       0.
+ *   t_end          end time (0: none).  When a step is given the device time t
+ *                  (lp_step's `t`), its time step is clipped to t_end - t, so the
+ *                  last step ends at t_end; a simulation already at t_end takes
+ *                  a step of 0 (its state does not change).
  */
 typedef struct {
     int32_t dim;
@@ -152,6 +156,7 @@ typedef struct {
     double refine_ratio;
     int32_t select;
     int32_t reserved;
+    double t_end;
 } lp_config;
 
 enum { LP_SELECT_NEAREST = 0, LP_SELECT_OCTANT = 1 };

@@ -116,6 +116,7 @@ lp_status check_cfg(const lp_config* g)
     if (g->select != LP_SELECT_NEAREST && g->select != LP_SELECT_OCTANT) return LP_ERR_ARG;
     if (g->select == LP_SELECT_OCTANT && (g->dim < 2 || g->radius_mode == LP_RADIUS_KSIDE)) return LP_ERR_ARG;
     if (g->reserved != 0) return LP_ERR_ARG;
+    if (!(g->t_end >= 0.0) || isinf(g->t_end)) return LP_ERR_ARG;
     return LP_OK;
 }
 
@@ -168,8 +169,8 @@ __global__ void k_cfl(int64_t n, DevCfg c, const double* d2min, const double* P,
     if (best >= 0.0 && best < INFINITY) atomicMin(dtmin + sim, (unsigned long long)__double_as_longlong(best));
 }
 
-__global__ void k_dt_finalize(int nsim, double cfl, double dt_fixed, const unsigned long long* dtmin, double* dt,
-                              double* t, unsigned long long* counters)
+__global__ void k_dt_finalize(int nsim, double cfl, double dt_fixed, double t_end, const unsigned long long* dtmin,
+                              double* dt, double* t, unsigned long long* counters)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsim) return;
@@ -179,6 +180,16 @@ __global__ void k_dt_finalize(int nsim, double cfl, double dt_fixed, const unsig
     if (!(v > 0.0) || isinf(v) || isnan(v)) {
         atomicOr(reinterpret_cast<unsigned int*>(counters + C_STATUS), ST_NONFINITE);
         v = 0.0;
+    }
+    // the last step ends at t_end (a simulation already there does not move)
+    if (t && t_end > 0.0) {
+        const double rem = fmax(__dsub_rn(t_end, t[s]), 0.0);
+        if (v >= rem) {
+            dt[s] = rem;
+            t[s] = fmax(t[s], t_end);
+            if (s == 0) counters[C_STEPS] += 1;
+            return;
+        }
     }
     dt[s] = v;
     if (t) t[s] += v;
@@ -270,8 +281,8 @@ cudaError_t run_cfl(lp_ctx* c, int64_t n, double cfl, double dt_fixed, double* t
         k_cfl<<<blocks, 256, 0, s>>>(n, c->dc, c->nb_d2min, c->sP, c->sV, c->sid, c->keys_sorted,
                                      c->dc.dim * c->dc.mbits, c->dt_min);
     }
-    k_dt_finalize<<<(unsigned)((nsim + 127) / 128), 128, 0, s>>>(nsim, cfl, dt_fixed, c->dt_min, c->dt_dev, t,
-                                                                c->counters);
+    k_dt_finalize<<<(unsigned)((nsim + 127) / 128), 128, 0, s>>>(nsim, cfl, dt_fixed, c->cfg.t_end, c->dt_min,
+                                                                c->dt_dev, t, c->counters);
     return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ class Config(C.Structure):
         ("n_fluid", C.c_int64), ("capacity", C.c_int64),
         ("mlp_tau_lo", C.c_double), ("mlp_audit", C.c_int32), ("max_sims", C.c_int32),
         ("refine", C.c_int32), ("refine_ratio", C.c_double),
-        ("select", C.c_int32), ("reserved", C.c_int32),
+        ("select", C.c_int32), ("reserved", C.c_int32), ("t_end", C.c_double),
     ]
 
 
@@ -228,9 +228,11 @@ def make_config(dim, capacity, precision=PREC_FP32, radius_mode=RADIUS_VOLUME, r
                 k_max=64, k_side=8, k_per_side=4, gamma=1.4, limiter=LIM_FLAGGED, estimator=EST_PLAIN,
                 flat_eps=1e-6, active_frac=0.5, s_ref=(0, 0, 0, 0, 0), tau32=1e-3, tau64=1e-12,
                 periodic=(0, 0, 0), box_lo=(0, 0, 0), box_hi=(1, 1, 1), n_fluid=2**62, max_level=0,
-                mlp_tau_lo=0.05, mlp_audit=0, max_sims=1, refine=0, refine_ratio=0.1, select=0) -> Config:
+                mlp_tau_lo=0.05, mlp_audit=0, max_sims=1, refine=0, refine_ratio=0.1, select=0,
+                t_end=0.0) -> Config:
     c = Config()
     c.select = select
+    c.t_end = t_end
     c.dim, c.precision, c.radius_mode, c.k_max, c.k_side = dim, precision, radius_mode, k_max, k_side
     c.k_per_side, c.limiter, c.estimator = k_per_side, limiter, estimator
     c.gamma, c.radius, c.kappa, c.flat_eps, c.active_frac = gamma, radius, kappa, flat_eps, active_frac

@@ -574,3 +574,37 @@ def test_multi_step_sod_fp64_tracks_oracle():
     assert normwise(g["P"], ost["P"]) < 1e-10
     assert normwise(g["u"][0], ost["u"][0]) < 1e-10
     ctx.close()
+
+
+def test_last_step_ends_at_t_end():
+    """With t_end set, the CFL step is clipped so that the last step lands on
+    t_end exactly, and a simulation already there does not move."""
+    st = inputs.gas_cloud_3d(5_000, seed=4)
+    n = st["V"].shape[0]
+    base = lp.make_config(3, n, kappa=2.2, k_max=64, gamma=5.0 / 3.0, s_ref=inputs.field_scales(st))
+    ctx = lp.Context(base)
+    ps = lp.ParticleSet.from_state(st)
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.step(ps, dt=0.0, cfl=0.4, t=t)
+    dt0 = ctx.stats()["dt"]
+    ctx.close()
+    t_end = 1.5 * dt0
+    cfg = lp.make_config(3, n, kappa=2.2, k_max=64, gamma=5.0 / 3.0, s_ref=inputs.field_scales(st), t_end=t_end)
+    ctx = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.step(ps, dt=0.0, cfl=0.4, t=t)
+    assert ctx.stats()["dt"] == dt0 and float(t.cpu()[0]) == dt0
+    ctx.step(ps, dt=0.0, cfl=0.4, t=t)
+    assert float(t.cpu()[0]) == t_end
+    before = ps.to_state(n)
+    ctx.step(ps, dt=0.0, cfl=0.4, t=t)
+    after = ps.to_state(n)
+    assert float(t.cpu()[0]) == t_end and ctx.stats()["dt"] == 0.0
+    assert ctx.stats()["status"] == 0
+    o = np.argsort(before["id"]); p = np.argsort(after["id"])
+    for f in ("V", "P"):
+        assert np.array_equal(before[f][o], after[f][p])
+    for k in range(3):
+        assert np.array_equal(before["x"][k][o], after["x"][k][p])
+    ctx.close()
