@@ -94,7 +94,7 @@ FP64_PEAK_TFLOPS = 1.25
 
 # algorithmic DRAM bytes per particle of the memory-bound phases
 BYTES_PER_PARTICLE = {
-    "grid+keys": 24 + 8 + 24 + 12,          # extent read, m V read, positions read, key + index write
+    "grid+keys": 24 + 24 + 12,              # positions read (extent, keys), key + index write
     "radix-sort": 24,                       # per digit pass: key + index read and written once
     "gather": 76 + 76 + 64 + 32,            # state read; sorted copy, fit record and query positions written
     "cell-tables": 8 * 2,                   # sorted keys read (fill and clear)

@@ -469,6 +469,9 @@ lp_status lp_destroy(lp_ctx* c)
         if (c->ev[q]) cudaEventDestroy(c->ev[q]);
     if (c->ev_host_start) cudaEventDestroy(c->ev_host_start);
     if (c->ev_host_in) cudaEventDestroy(c->ev_host_in);
+    if (c->ev_host_fields) cudaEventDestroy(c->ev_host_fields);
+    if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
+    if (c->ev_fields_done) cudaEventDestroy(c->ev_fields_done);
     if (c->aux) cudaStreamDestroy(c->aux);
     free_all(c);
     free(c);
@@ -488,7 +491,7 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
     c->lists_stale = 0;
     if (n == 0) return LP_OK;
     {
-        Phase ph(c, LP_PH_GRID, 5 + (c->nsim > 1 ? 1 : 0), s);
+        Phase ph(c, LP_PH_GRID, 4 + (c->nsim > 1 ? 1 : 0), s);
         LP_CUDA(build_grid(c, p, s));
         LP_CUDA(make_keys(c, p, s));
     }
@@ -501,8 +504,17 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
         LP_CUDA(cudaStreamWaitEvent(s, c->gather_wait, 0));
     }
     {
-        Phase ph(c, LP_PH_GATHER, 1, s);
-        LP_CUDA(gather(c, p, s));
+        Phase ph(c, LP_PH_GATHER, 2, s);
+        LP_CUDA(c->fields_wait ? gather_geometry(c, p, s) : gather(c, p, s));
+    }
+    if (c->fields_wait) {
+        // the fields, gathered on the copy stream behind their copies from the
+        // host, while the tables and the query run here
+        LP_CUDA(cudaEventRecord(c->ev_sorted, s));
+        LP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_sorted, 0));
+        LP_CUDA(gather_fields(c, p, c->aux));
+        LP_CUDA(cudaEventRecord(c->ev_fields_done, c->aux));
+        c->launches += 1;
     }
     {
         Phase ph(c, LP_PH_TABLES, tables ? 1 : 0, s);
@@ -512,6 +524,10 @@ static lp_status build(lp_ctx* c, lp_particles* p, cudaStream_t s)
     {
         Phase ph(c, LP_PH_QUERY, query_launches(c), s);
         LP_CUDA(query_neighbors(c, n, s));
+    }
+    if (c->fields_wait) {          // the fields, gathered while the query ran
+        Phase ph(c, LP_PH_HOST_IN, 0, s);
+        LP_CUDA(cudaStreamWaitEvent(s, c->ev_fields_done, 0));
     }
     c->n_lists = n;
     return LP_OK;
@@ -717,6 +733,9 @@ lp_status lp_step_host(lp_ctx* c, lp_particles* h, double dt, double cfl, double
         LP_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
         LP_CUDA(cudaEventCreateWithFlags(&c->ev_host_start, cudaEventDisableTiming));
         LP_CUDA(cudaEventCreateWithFlags(&c->ev_host_in, cudaEventDisableTiming));
+        LP_CUDA(cudaEventCreateWithFlags(&c->ev_host_fields, cudaEventDisableTiming));
+        LP_CUDA(cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming));
+        LP_CUDA(cudaEventCreateWithFlags(&c->ev_fields_done, cudaEventDisableTiming));
     }
     // pinned (page-locked) host arrays: the step writes the new state straight
     // into them; otherwise into the device copy, then copied back
@@ -732,29 +751,37 @@ lp_status lp_step_host(lp_ctx* c, lp_particles* h, double dt, double cfl, double
     g.n = n;
     const size_t b8 = (size_t)n * 8;
     if (n > 0) {
-        // what the keys need, on the caller's stream; the rest on the copy
-        // stream, after everything before this step, overlapping the sort
+        // what the keys need (the positions) on the caller's stream; on the
+        // copy stream, after everything before this step, what the query needs
+        // next (m, V, id: the gather of the geometry waits for them) and then
+        // what only the fit needs (u, P: gathered after the query)
         {
             Phase ph(c, LP_PH_HOST_IN, 0, s);
             for (int k = 0; k < dim; ++k) LP_CUDA(cudaMemcpyAsync(g.x[k], h->x[k], b8, cudaMemcpyHostToDevice, s));
-            LP_CUDA(cudaMemcpyAsync(g.m, h->m, b8, cudaMemcpyHostToDevice, s));
-            LP_CUDA(cudaMemcpyAsync(g.V, h->V, b8, cudaMemcpyHostToDevice, s));
         }
         LP_CUDA(cudaEventRecord(c->ev_host_start, s));
         LP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_host_start, 0));
-        for (int k = 0; k < dim; ++k) LP_CUDA(cudaMemcpyAsync(g.u[k], h->u[k], b8, cudaMemcpyHostToDevice, c->aux));
-        LP_CUDA(cudaMemcpyAsync(g.P, h->P, b8, cudaMemcpyHostToDevice, c->aux));
+        LP_CUDA(cudaMemcpyAsync(g.m, h->m, b8, cudaMemcpyHostToDevice, c->aux));
+        LP_CUDA(cudaMemcpyAsync(g.V, h->V, b8, cudaMemcpyHostToDevice, c->aux));
         LP_CUDA(cudaMemcpyAsync(g.id, h->id, (size_t)n * 4, cudaMemcpyHostToDevice, c->aux));
         LP_CUDA(cudaEventRecord(c->ev_host_in, c->aux));
         c->gather_wait = c->ev_host_in;
+        for (int k = 0; k < dim; ++k) LP_CUDA(cudaMemcpyAsync(g.u[k], h->u[k], b8, cudaMemcpyHostToDevice, c->aux));
+        LP_CUDA(cudaMemcpyAsync(g.P, h->P, b8, cudaMemcpyHostToDevice, c->aux));
+        LP_CUDA(cudaEventRecord(c->ev_host_fields, c->aux));
+        c->fields_wait = c->ev_host_fields;
     }
     FitArgs a;
     StepOut o;
     int64_t nn = 0;
     st = step_prologue(c, &g, nullptr, 1, dt, cfl, t, diag, s, a, o, &nn);
-    if (c->gather_wait) {           // (a no-op when the gather already waited for the copies)
+    if (c->gather_wait) {           // (a no-op when the gathers already waited for the copies)
         cudaStreamWaitEvent(s, c->gather_wait, 0);
         c->gather_wait = nullptr;
+    }
+    if (c->fields_wait) {
+        cudaStreamWaitEvent(s, c->fields_wait, 0);
+        c->fields_wait = nullptr;
     }
     if (st != LP_OK || nn == 0) return st;
     if (direct) {

@@ -274,7 +274,10 @@ struct lp_ctx {
     double* stage_buf;
     cudaStream_t aux;
     cudaEvent_t ev_host_start, ev_host_in;
-    cudaEvent_t gather_wait;      // when set, build() waits for it before the gather
+    cudaEvent_t gather_wait;      // when set, build() waits for it before the (geometry) gather
+    cudaEvent_t fields_wait;      // when set, build() gathers in two stages and waits for this
+                                  // one before the fields (u, P), after the neighbour query
+    cudaEvent_t ev_host_fields, ev_sorted, ev_fields_done;
     int64_t n_lists;          // n of the last neighbour build (0: none)
     int lists_stale;          // lp_remove_outside ran since: the lists no longer describe the particles
     int tables_dirty;         // tables hold entries of the last build
@@ -318,6 +321,8 @@ cudaError_t make_keys(lp_ctx* c, const lp_particles* p, cudaStream_t s);
 int radix_passes(const lp_ctx* c);
 cudaError_t radix_sort(lp_ctx* c, int64_t n, cudaStream_t s);
 cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s);
+cudaError_t gather_geometry(lp_ctx* c, const lp_particles* p, cudaStream_t s);
+cudaError_t gather_fields(lp_ctx* c, const lp_particles* p, cudaStream_t s);
 cudaError_t fill_tables(lp_ctx* c, int64_t n, bool clear, cudaStream_t s);
 cudaError_t query_neighbors(lp_ctx* c, int64_t n, cudaStream_t s);
 cudaError_t query_init();   // once per context: kernel attributes

@@ -52,7 +52,7 @@ struct ExtKeys {
         whi = KEY_NEG_INF;
     }
     template <int DIM>
-    __device__ __forceinline__ void add(const double* const (&xs)[3], const double* m, const double* V, int64_t i)
+    __device__ __forceinline__ void add(const double* const (&xs)[3], int64_t i)
     {
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
@@ -62,7 +62,10 @@ struct ExtKeys {
             lo[k] = q < lo[k] ? q : lo[k];
             hi[k] = q > hi[k] ? q : hi[k];
         }
-        const uint64_t bw = (uint64_t)__double_as_longlong(__dmul_rn(m[i], V[i]));
+    }
+    __device__ __forceinline__ void add_w(double w)
+    {
+        const uint64_t bw = (uint64_t)__double_as_longlong(w);
         if (!is_nan_bits(bw)) {
             const uint64_t q = order_key_bits(bw);
             wlo = q < wlo ? q : wlo;
@@ -77,21 +80,49 @@ struct ExtKeys {
             atomicMin(e + k, (unsigned long long)lo[k]);
             atomicMax(e + 3 + k, (unsigned long long)hi[k]);
         }
+    }
+    __device__ void flush_w(unsigned long long* e) const
+    {
         atomicMin(e + 6, (unsigned long long)wlo);
         atomicMax(e + 7, (unsigned long long)whi);
     }
 };
 
-// ext[8 s + 0..2] min x_k, [8 s + 3..5] max x_k, [8 s + 6] min w, [8 s + 7] max w
-// (order keys) of simulation s.  One simulation: grid-stride accumulation and a
-// warp reduction; several: EXT_ITEMS particles per thread, reduced over the
-// warp when the warp's particles share a simulation (they are stored by
-// simulation), with atomics per run otherwise.  The comparisons are integer
-// ones on the order keys (FP64 min / max would run on the scarce FP64 units).
+// the m V extent of the particles of a warp (gather order, simulations kept
+// together), to ext[8 s + 6..7] of their simulation s: one warp reduction when
+// the warp's particles share a simulation, atomics per lane otherwise.  Every
+// lane of the warp calls it (valid: this lane has a particle).
+__device__ __forceinline__ void warp_w_extent(bool valid, double w, uint32_t sim, unsigned long long* ext)
+{
+    ExtKeys r;
+    r.init();
+    if (valid) r.add_w(w);
+    else sim = 0xffffffffu;
+    const uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
+    if (__all_sync(0xffffffffu, sim == s0 || sim == 0xffffffffu)) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t a = __shfl_xor_sync(0xffffffffu, r.wlo, o);
+            const uint64_t b = __shfl_xor_sync(0xffffffffu, r.whi, o);
+            r.wlo = a < r.wlo ? a : r.wlo;
+            r.whi = b > r.whi ? b : r.whi;
+        }
+        if (lane_id() == 0 && s0 != 0xffffffffu) r.flush_w(ext + 8 * (int64_t)s0);
+    } else if (sim != 0xffffffffu) {
+        r.flush_w(ext + 8 * (int64_t)sim);
+    }
+}
+
+// ext[8 s + 0..2] min x_k, [8 s + 3..5] max x_k (order keys) of simulation s
+// (the extent of m V, ext[8 s + 6..7], is taken by the gather, which reads m
+// and V anyway: the keys need only the positions).  One simulation:
+// grid-stride accumulation and a warp reduction; several: EXT_ITEMS particles
+// per thread, reduced over the warp when the warp's particles share a
+// simulation (they are stored by simulation), with atomics per run otherwise.
+// The comparisons are integer ones on the order keys (FP64 min / max would
+// run on the scarce FP64 units).
 template <int DIM>
 __global__ void k_reduce_extent(int64_t n, const double* __restrict__ x0,
                                 const double* __restrict__ x1, const double* __restrict__ x2,
-                                const double* __restrict__ m, const double* __restrict__ V,
                                 const uint32_t* __restrict__ sim_of, unsigned long long* ext)
 {
     ExtKeys r;
@@ -100,7 +131,7 @@ __global__ void k_reduce_extent(int64_t n, const double* __restrict__ x0,
     uint32_t sim = 0;
     if (!sim_of) {
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-            r.add<DIM>(xs, m, V, i);
+            r.add<DIM>(xs, i);
     } else {
         // EXT_ITEMS particles per thread (strided by the block size, so loads
         // stay coalesced); a change of simulation flushes the running extent
@@ -115,7 +146,7 @@ __global__ void k_reduce_extent(int64_t n, const double* __restrict__ x0,
                 sim = si;
                 r.init();
             }
-            r.add<DIM>(xs, m, V, i);
+            r.add<DIM>(xs, i);
         }
     }
     uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
@@ -129,10 +160,6 @@ __global__ void k_reduce_extent(int64_t n, const double* __restrict__ x0,
                 r.lo[k] = a < r.lo[k] ? a : r.lo[k];
                 r.hi[k] = b > r.hi[k] ? b : r.hi[k];
             }
-            const uint64_t a = __shfl_xor_sync(0xffffffffu, r.wlo, o);
-            const uint64_t b = __shfl_xor_sync(0xffffffffu, r.whi, o);
-            r.wlo = a < r.wlo ? a : r.wlo;
-            r.whi = b > r.whi ? b : r.whi;
         }
         if (lane_id() != 0 || s0 == 0xffffffffu) return;
         sim = s0;
@@ -151,11 +178,8 @@ __global__ void k_init_extent(unsigned long long* ext, int nsim)
     }
 }
 
-// Bounding cube and the range of cell levels.  lmin is the finest level whose
-// cell edge L / 2^l is at least the largest radius present; lmax the finest
-// whose edge is at least half the smallest radius (the queries use cells down
-// to half a radius).
-__global__ void k_finalize_grid(DevCfg c, int lmax_cap, int nsim, const unsigned long long* ext_all, Grid* grids)
+// Bounding cube of each simulation (what the keys need).
+__global__ void k_finalize_cube(DevCfg c, int nsim, const unsigned long long* ext_all, Grid* grids)
 {
     int sim = blockIdx.x * blockDim.x + threadIdx.x;
     if (sim >= nsim) return;
@@ -176,37 +200,59 @@ __global__ void k_finalize_grid(DevCfg c, int lmax_cap, int nsim, const unsigned
     for (int k = 0; k < 3; ++k) split(g->lo[k], g->lo_h[k], g->lo_l[k]);
     g->inv_f = (float)g->inv;
     g->L_f = (float)L;
-    double rmin, rmax;
-    if (c.radius_mode == LP_RADIUS_FIXED) { rmin = rmax = c.radius; }
-    else {
-        double wlo = from_order_key(ext[6]), whi = from_order_key(ext[7]);
-        rmin = c.kappa * pow(wlo, 1.0 / c.dim);
-        rmax = c.kappa * pow(whi, 1.0 / c.dim);
-    }
-    // margins wider than the per-particle float radius margin (1e-5) keep every
-    // particle's level inside [lmin, lmax]
-    rmin *= 1.0 - 1e-4;
-    rmax *= 1.0 + 1e-4;
-    if (!(rmin > 0.0)) rmin = L * ldexp(1.0, -lmax_cap);   // empty or degenerate simulation
-    if (!(rmax > 0.0) || isinf(rmax)) rmax = L;
-    int lmax = (int)floor(log2(2.0 * L / rmin));
-    int lmin = (int)floor(log2(L / rmax));
-    lmax = max(0, min(lmax, lmax_cap));
-    lmin = max(0, min(lmin, lmax));
-    g->lmax = lmax;
-    g->lmin = lmin;
 }
 
-// table levels in use over all simulations
-__global__ void k_grid_range(int nsim, const Grid* grids, int* grange)
+// The range of cell levels of each simulation, and over all of them (one
+// block).  lmin is the finest level whose cell edge L / 2^l is at least the
+// largest radius present; lmax the finest whose edge is at least half the
+// smallest radius (the queries use cells down to half a radius).
+constexpr int LEVEL_THREADS = 256;
+__global__ void __launch_bounds__(LEVEL_THREADS) k_finalize_levels(DevCfg c, int lmax_cap, int nsim,
+                                                                   const unsigned long long* ext_all, Grid* grids,
+                                                                   int* grange)
 {
-    int lo = 1 << 20, hi = 0;
-    for (int s = 0; s < nsim; ++s) {
-        lo = min(lo, grids[s].lmin);
-        hi = max(hi, grids[s].lmax);
+    __shared__ int slo[LEVEL_THREADS], shi[LEVEL_THREADS];
+    int lo_all = 1 << 20, hi_all = 0;
+    for (int sim = threadIdx.x; sim < nsim; sim += LEVEL_THREADS) {
+        const unsigned long long* ext = ext_all + 8 * sim;
+        Grid* g = grids + sim;
+        const double L = g->L;
+        double rmin, rmax;
+        if (c.radius_mode == LP_RADIUS_FIXED) { rmin = rmax = c.radius; }
+        else {
+            double wlo = from_order_key(ext[6]), whi = from_order_key(ext[7]);
+            rmin = c.kappa * pow(wlo, 1.0 / c.dim);
+            rmax = c.kappa * pow(whi, 1.0 / c.dim);
+        }
+        // margins wider than the per-particle float radius margin (1e-5) keep every
+        // particle's level inside [lmin, lmax]
+        rmin *= 1.0 - 1e-4;
+        rmax *= 1.0 + 1e-4;
+        if (!(rmin > 0.0)) rmin = L * ldexp(1.0, -lmax_cap);   // empty or degenerate simulation
+        if (!(rmax > 0.0) || isinf(rmax)) rmax = L;
+        int lmax = (int)floor(log2(2.0 * L / rmin));
+        int lmin = (int)floor(log2(L / rmax));
+        lmax = max(0, min(lmax, lmax_cap));
+        lmin = max(0, min(lmin, lmax));
+        g->lmax = lmax;
+        g->lmin = lmin;
+        lo_all = min(lo_all, lmin);
+        hi_all = max(hi_all, lmax);
     }
-    grange[0] = lo;
-    grange[1] = hi;
+    slo[threadIdx.x] = lo_all;
+    shi[threadIdx.x] = hi_all;
+    __syncthreads();
+    for (int h = LEVEL_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            slo[threadIdx.x] = min(slo[threadIdx.x], slo[threadIdx.x + h]);
+            shi[threadIdx.x] = max(shi[threadIdx.x], shi[threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        grange[0] = slo[0];
+        grange[1] = shi[0];
+    }
 }
 
 // key = simulation << (DIM mbits) | Morton code of the quantised position
@@ -378,9 +424,14 @@ k_rs_downsweep(int64_t n, const uint64_t* __restrict__ kin, const uint32_t* __re
 template <int DIM>
 __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_particles p, DevCfg c,
                          double* sx0, double* sx1, double* sx2, double* sV, double* su0, double* su1,
-                         double* su2, double* sP, double* sm, uint32_t* sid, float4* rec, float4* pos4)
+                         double* su2, double* sP, double* sm, uint32_t* sid, float4* rec, float4* pos4,
+                         const uint32_t* __restrict__ sim_of, unsigned long long* ext)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    {
+        const uint32_t jw = i < n ? perm[i] : 0u;
+        warp_w_extent(i < n, i < n ? __dmul_rn(p.m[jw], p.V[jw]) : 0.0, (i < n && sim_of) ? sim_of[jw] : 0u, ext);
+    }
     if (i >= n) return;
     uint32_t j = perm[i];
     float r[4 * REC_F4];
@@ -413,6 +464,69 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_partic
     pos4[2 * i + 1] = make_float4(r[REC_XL], r[REC_XL + 1], r[REC_XL + 2], 0.0f);
     sm[i] = m;
     sid[i] = p.id[j];
+}
+
+// The same gather in two kernels, for the end-to-end path (lp_step_host),
+// where the fields are still being copied from the host while the neighbour
+// query runs: the geometry (positions, m, V, id, the query's float positions
+// and radius, the m V extent) before the query, the fields (u, P and the packed
+// fit record) after it.  Together they write what k_gather writes, bit for bit.
+template <int DIM>
+__global__ void k_gather_geom(int64_t n, const uint32_t* __restrict__ perm, lp_particles p, DevCfg c,
+                              double* sx0, double* sx1, double* sx2, double* sV, double* sm, uint32_t* sid,
+                              float4* pos4, const uint32_t* __restrict__ sim_of, unsigned long long* ext)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    {
+        const uint32_t jw = i < n ? perm[i] : 0u;
+        warp_w_extent(i < n, i < n ? __dmul_rn(p.m[jw], p.V[jw]) : 0.0, (i < n && sim_of) ? sim_of[jw] : 0u, ext);
+    }
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    double* sx[3] = {sx0, sx1, sx2};
+    float xh[3] = {0.0f, 0.0f, 0.0f}, xl[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const double v = p.x[k][j];
+        sx[k][i] = v;
+        split(v, xh[k], xl[k]);
+    }
+    const double V = p.V[j], m = p.m[j];
+    sV[i] = V;
+    sm[i] = m;
+    sid[i] = p.id[j];
+    pos4[2 * i] = make_float4(xh[0], xh[1], xh[2], query_radius_f(c, DIM, m, V));
+    pos4[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.0f);
+}
+
+template <int DIM>
+__global__ void k_gather_fields(int64_t n, const uint32_t* __restrict__ perm, lp_particles p,
+                                const double* sx0, const double* sx1, const double* sx2, const double* sV,
+                                double* su0, double* su1, double* su2, double* sP, float4* rec)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    float r[4 * REC_F4];
+#pragma unroll
+    for (int q = 0; q < 4 * REC_F4; ++q) r[q] = 0.0f;
+    const double* sx[3] = {sx0, sx1, sx2};
+    double* su[3] = {su0, su1, su2};
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) split(sx[k][i], r[REC_XH + k], r[REC_XL + k]);
+    constexpr int F = DIM + 2;
+    const double P = p.P[j];
+    sP[i] = P;
+    split(sV[i], r[rec_fh(0, F)], r[rec_fl(0, F)]);
+    split(P, r[rec_fh(F - 1, F)], r[rec_fl(F - 1, F)]);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const double v = p.u[k][j];
+        su[k][i] = v;
+        split(v, r[rec_fh(1 + k, F)], r[rec_fl(1 + k, F)]);
+    }
+#pragma unroll
+    for (int q = 0; q < REC_F4; ++q) rec[i * REC_F4 + q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
 }
 
 // cell tables: entry = start | end << 32 of the key-sorted particles in the cell
@@ -491,11 +605,10 @@ cudaError_t build_grid(lp_ctx* c, const lp_particles* p, cudaStream_t s)
     if (blocks == 0) blocks = 1;
     const double* x1 = p->x[1] ? p->x[1] : p->x[0];
     const double* x2 = p->x[2] ? p->x[2] : p->x[0];
-    if (c->dc.dim == 3) k_reduce_extent<3><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, p->m, p->V, sim_of, c->ext);
-    else if (c->dc.dim == 2) k_reduce_extent<2><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, p->m, p->V, sim_of, c->ext);
-    else k_reduce_extent<1><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, p->m, p->V, sim_of, c->ext);
-    k_finalize_grid<<<(unsigned)((nsim + 127) / 128), 128, 0, s>>>(c->dc, c->lmax_cap, nsim, c->ext, c->grid);
-    k_grid_range<<<1, 1, 0, s>>>(nsim, c->grid, c->grange);
+    if (c->dc.dim == 3) k_reduce_extent<3><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, sim_of, c->ext);
+    else if (c->dc.dim == 2) k_reduce_extent<2><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, sim_of, c->ext);
+    else k_reduce_extent<1><<<blocks, 256, 0, s>>>(n, p->x[0], x1, x2, sim_of, c->ext);
+    k_finalize_cube<<<(unsigned)((nsim + 127) / 128), 128, 0, s>>>(c->dc, nsim, c->ext, c->grid);
     return cudaGetLastError();
 }
 
@@ -541,11 +654,52 @@ cudaError_t gather(lp_ctx* c, const lp_particles* p, cudaStream_t s)
     const uint32_t* perm = c->perm_sorted;
     lp_particles q = *p;
     for (int k = dim; k < 3; ++k) { q.x[k] = p->x[0]; q.u[k] = p->u[0]; }
+    const uint32_t* sim_of = c->nsim > 1 ? c->sim_of : nullptr;
 #define LP_GATHER_ARGS n, perm, q, c->dc, c->sx[0], c->sx[1], c->sx[2], c->sV, c->su[0], c->su[1], c->su[2], \
-        c->sP, c->sm, c->sid, c->rec, c->pos4
+        c->sP, c->sm, c->sid, c->rec, c->pos4, sim_of, c->ext
     if (dim == 3) k_gather<3><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
     else if (dim == 2) k_gather<2><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
     else k_gather<1><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+#undef LP_GATHER_ARGS
+    // the cell levels need the m V extent the gather took
+    k_finalize_levels<<<1, LEVEL_THREADS, 0, s>>>(c->dc, c->lmax_cap, c->nsim, c->ext, c->grid, c->grange);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_geometry(lp_ctx* c, const lp_particles* p, cudaStream_t s)
+{
+    int64_t n = p->n;
+    int dim = c->dc.dim;
+    unsigned gb = grid_for(n, 256);
+    const uint32_t* perm = c->perm_sorted;
+    lp_particles q = *p;
+    for (int k = dim; k < 3; ++k) q.x[k] = p->x[0];
+    const uint32_t* sim_of = c->nsim > 1 ? c->sim_of : nullptr;
+#define LP_GATHER_ARGS n, perm, q, c->dc, c->sx[0], c->sx[1], c->sx[2], c->sV, c->sm, c->sid, c->pos4, sim_of, c->ext
+    if (dim == 3) k_gather_geom<3><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+    else if (dim == 2) k_gather_geom<2><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+    else k_gather_geom<1><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+#undef LP_GATHER_ARGS
+    k_finalize_levels<<<1, LEVEL_THREADS, 0, s>>>(c->dc, c->lmax_cap, c->nsim, c->ext, c->grid, c->grange);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_fields(lp_ctx* c, const lp_particles* p, cudaStream_t s)
+{
+    int64_t n = p->n;
+    int dim = c->dc.dim;
+    unsigned gb = grid_for(n, 256);
+    const uint32_t* perm = c->perm_sorted;
+    lp_particles q = *p;
+    for (int k = dim; k < 3; ++k) q.u[k] = p->u[0];
+    const double* sx1 = c->sx[dim > 1 ? 1 : 0];
+    const double* sx2 = c->sx[dim > 2 ? 2 : 0];
+    double* su1 = c->su[dim > 1 ? 1 : 0];
+    double* su2 = c->su[dim > 2 ? 2 : 0];
+#define LP_GATHER_ARGS n, perm, q, c->sx[0], sx1, sx2, c->sV, c->su[0], su1, su2, c->sP, c->rec
+    if (dim == 3) k_gather_fields<3><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+    else if (dim == 2) k_gather_fields<2><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
+    else k_gather_fields<1><<<gb, 256, 0, s>>>(LP_GATHER_ARGS);
 #undef LP_GATHER_ARGS
     return cudaGetLastError();
 }
@@ -679,10 +833,10 @@ extern "C" lp_status lp_sort_keys_noalloc(int32_t dim, int64_t n, const double* 
     int64_t nb_ = gb;
     unsigned rblocks = (unsigned)(nb_ < 152 * 8 ? nb_ : 152 * 8);
     k_init_extent<<<1, 32, 0, s>>>(ext, 1);
-    if (dim == 3) k_reduce_extent<3><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, x0, x0, nullptr, ext);
-    else if (dim == 2) k_reduce_extent<2><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, x0, x0, nullptr, ext);
-    else k_reduce_extent<1><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, x0, x0, nullptr, ext);
-    k_finalize_grid<<<1, 1, 0, s>>>(dc, lmax_cap, 1, ext, grid);
+    if (dim == 3) k_reduce_extent<3><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, nullptr, ext);
+    else if (dim == 2) k_reduce_extent<2><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, nullptr, ext);
+    else k_reduce_extent<1><<<rblocks, 256, 0, s>>>(n, x0, p1, p2, nullptr, ext);
+    k_finalize_cube<<<1, 1, 0, s>>>(dc, 1, ext, grid);
     if (dim == 3) k_keys<3><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
     else if (dim == 2) k_keys<2><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
     else k_keys<1><<<gb, 256, 0, s>>>(n, x0, p1, p2, grid, nullptr, MORTON_BITS, keys[0], vals[0]);
