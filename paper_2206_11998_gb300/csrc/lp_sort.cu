@@ -88,27 +88,71 @@ struct ExtKeys {
     }
 };
 
-// the m V extent of the particles of a warp (gather order, simulations kept
-// together), to ext[8 s + 6..7] of their simulation s: one warp reduction when
-// the warp's particles share a simulation, atomics per lane otherwise.  Every
-// lane of the warp calls it (valid: this lane has a particle).
-__device__ __forceinline__ void warp_w_extent(bool valid, double w, uint32_t sim, unsigned long long* ext)
+// the m V extent of the particles of a block (gather order, simulations
+// kept together), to ext[8 s + 6..7] of their simulation s: reduced over each
+// warp whose particles share a simulation, then over the block when all its
+// warps do (one pair of atomics per block: the extent words are the same few
+// addresses for every block, so their atomics would otherwise queue);
+// atomics per warp or per lane otherwise.  Every thread of the block calls it
+// (valid: this thread has a particle); blockDim.x <= 32 * EXT_WARPS.
+constexpr int EXT_WARPS = 8;
+__device__ __forceinline__ void block_w_extent(bool valid, double w, uint32_t sim, unsigned long long* ext)
 {
+    __shared__ uint64_t swlo[EXT_WARPS], swhi[EXT_WARPS];
+    __shared__ uint32_t ssim[EXT_WARPS];
     ExtKeys r;
     r.init();
     if (valid) r.add_w(w);
     else sim = 0xffffffffu;
     const uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
-    if (__all_sync(0xffffffffu, sim == s0 || sim == 0xffffffffu)) {
+    const bool uniform = __all_sync(0xffffffffu, sim == s0 || sim == 0xffffffffu);
+    const unsigned wid = threadIdx.x >> 5;
+    if (uniform) {
         for (int o = 16; o > 0; o >>= 1) {
             const uint64_t a = __shfl_xor_sync(0xffffffffu, r.wlo, o);
             const uint64_t b = __shfl_xor_sync(0xffffffffu, r.whi, o);
             r.wlo = a < r.wlo ? a : r.wlo;
             r.whi = b > r.whi ? b : r.whi;
         }
-        if (lane_id() == 0 && s0 != 0xffffffffu) r.flush_w(ext + 8 * (int64_t)s0);
     } else if (sim != 0xffffffffu) {
-        r.flush_w(ext + 8 * (int64_t)sim);
+        r.flush_w(ext + 8 * (int64_t)sim);                  // a warp across simulations
+    }
+    if (lane_id() == 0) {
+        ssim[wid] = uniform ? s0 : 0xfffffffeu;             // 0xfffffffe: flushed already
+        swlo[wid] = r.wlo;
+        swhi[wid] = r.whi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (int)((blockDim.x + 31) / 32);
+        uint32_t sb = 0xffffffffu;
+        bool one = true;
+        for (int q = 0; q < nw; ++q) {
+            const uint32_t sq = ssim[q];
+            if (sq == 0xffffffffu) continue;                // no particle
+            if (sq == 0xfffffffeu || (sb != 0xffffffffu && sq != sb)) { one = false; break; }
+            sb = sq;
+        }
+        if (one) {
+            if (sb != 0xffffffffu) {
+                ExtKeys t;
+                t.init();
+                for (int q = 0; q < nw; ++q)
+                    if (ssim[q] == sb) {
+                        t.wlo = swlo[q] < t.wlo ? swlo[q] : t.wlo;
+                        t.whi = swhi[q] > t.whi ? swhi[q] : t.whi;
+                    }
+                t.flush_w(ext + 8 * (int64_t)sb);
+            }
+        } else {
+            for (int q = 0; q < nw; ++q) {
+                ExtKeys t;
+                t.init();
+                t.wlo = swlo[q];
+                t.whi = swhi[q];
+                if (ssim[q] < 0xfffffffeu) t.flush_w(ext + 8 * (int64_t)ssim[q]);
+            }
+        }
     }
 }
 
@@ -149,8 +193,14 @@ __global__ void k_reduce_extent(int64_t n, const double* __restrict__ x0,
             r.add<DIM>(xs, i);
         }
     }
-    uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
-    bool uniform = __all_sync(0xffffffffu, sim == s0 || sim == 0xffffffffu);
+    // over the warp when its particles share a simulation, then over the
+    // block when all its warps do (one set of atomics per block: the extent
+    // words are the same few addresses for every block); per lane otherwise
+    __shared__ uint64_t slo[EXT_WARPS][3], shi[EXT_WARPS][3];
+    __shared__ uint32_t ssim[EXT_WARPS];
+    const uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
+    const bool uniform = __all_sync(0xffffffffu, sim == s0 || sim == 0xffffffffu);
+    const unsigned wid = threadIdx.x >> 5;
     if (uniform) {
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -161,12 +211,47 @@ __global__ void k_reduce_extent(int64_t n, const double* __restrict__ x0,
                 r.hi[k] = b > r.hi[k] ? b : r.hi[k];
             }
         }
-        if (lane_id() != 0 || s0 == 0xffffffffu) return;
-        sim = s0;
-    } else if (sim == 0xffffffffu) {
-        return;
+    } else if (sim != 0xffffffffu) {
+        r.flush<DIM>(ext + 8 * (int64_t)sim);
     }
-    r.flush<DIM>(ext + 8 * (int64_t)sim);
+    if (lane_id() == 0) {
+        ssim[wid] = uniform ? s0 : 0xfffffffeu;             // 0xfffffffe: flushed already
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { slo[wid][k] = r.lo[k]; shi[wid][k] = r.hi[k]; }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int nw = (int)((blockDim.x + 31) / 32);
+    uint32_t sb = 0xffffffffu;
+    bool one = true;
+    for (int q = 0; q < nw; ++q) {
+        const uint32_t sq = ssim[q];
+        if (sq == 0xffffffffu) continue;                    // no particle
+        if (sq == 0xfffffffeu || (sb != 0xffffffffu && sq != sb)) { one = false; break; }
+        sb = sq;
+    }
+    for (int q = 0; q < nw; ++q) {
+        const uint32_t sq = ssim[q];
+        if (sq >= 0xfffffffeu) continue;
+        ExtKeys t;
+        t.init();
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { t.lo[k] = slo[q][k]; t.hi[k] = shi[q][k]; }
+        if (one) {
+            // merge every warp into the first, flushed once at the end
+            for (int q2 = q + 1; q2 < nw; ++q2) {
+                if (ssim[q2] != sb) continue;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) {
+                    t.lo[k] = slo[q2][k] < t.lo[k] ? slo[q2][k] : t.lo[k];
+                    t.hi[k] = shi[q2][k] > t.hi[k] ? shi[q2][k] : t.hi[k];
+                }
+            }
+            t.flush<DIM>(ext + 8 * (int64_t)sb);
+            break;
+        }
+        t.flush<DIM>(ext + 8 * (int64_t)sq);
+    }
 }
 
 __global__ void k_init_extent(unsigned long long* ext, int nsim)
@@ -430,7 +515,7 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_partic
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     {
         const uint32_t jw = i < n ? perm[i] : 0u;
-        warp_w_extent(i < n, i < n ? __dmul_rn(p.m[jw], p.V[jw]) : 0.0, (i < n && sim_of) ? sim_of[jw] : 0u, ext);
+        block_w_extent(i < n, i < n ? __dmul_rn(p.m[jw], p.V[jw]) : 0.0, (i < n && sim_of) ? sim_of[jw] : 0u, ext);
     }
     if (i >= n) return;
     uint32_t j = perm[i];
@@ -479,7 +564,7 @@ __global__ void k_gather_geom(int64_t n, const uint32_t* __restrict__ perm, lp_p
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     {
         const uint32_t jw = i < n ? perm[i] : 0u;
-        warp_w_extent(i < n, i < n ? __dmul_rn(p.m[jw], p.V[jw]) : 0.0, (i < n && sim_of) ? sim_of[jw] : 0u, ext);
+        block_w_extent(i < n, i < n ? __dmul_rn(p.m[jw], p.V[jw]) : 0.0, (i < n && sim_of) ? sim_of[jw] : 0u, ext);
     }
     if (i >= n) return;
     const uint32_t j = perm[i];
