@@ -126,9 +126,10 @@ def parse():
     ap.add_argument("--density-ratio", type=float, default=1e3,
                     help="jet-inflow: jet / ambient density ratio")
     ap.add_argument("--select", default="octant", choices=["nearest", "octant"],
-                    help="neighbours kept beyond k_max (jet-inflow workload): octant-balanced (the default: with "
-                         "the nearest only, the ambient particles next to the jet lose their one-sided stencils "
-                         "and the run stalls), or the nearest")
+                    help="neighbours kept beyond k_max (the jet workloads; the gas cloud keeps the nearest): "
+                         "octant-balanced (the default: with the nearest only, the ambient particles next to the "
+                         "jet lose their one-sided stencils, and the jet's volumes and radii blow up within a few "
+                         "steps), or the nearest")
     ap.add_argument("--limiter", default="flagged", choices=["flagged", "uw"],
                     help="jet-inflow: the limiter mode")
     ap.add_argument("--grow-seconds", type=float, default=240.0,
@@ -179,19 +180,22 @@ def dist_info():
     return rank, world, local
 
 
-# the single-simulation 3D workloads: generator, gamma, default size
-WORKLOADS = {"gas-cloud": ("gas-cloud-3d", 5.0 / 3.0, 2_000_000),
-             "jet-snapshot": ("jet-snapshot-3d", 1.4, 8_000_000),
-             "jet-inflow": ("jet-inflow-3d", 1.4, 8_000_000)}
+# the single-simulation 3D workloads: generator, gamma, default size, k_max
+# (the jet's neighbour counts run from 20 to 80)
+WORKLOADS = {"gas-cloud": ("gas-cloud-3d", 5.0 / 3.0, 2_000_000, 64),
+             "jet-snapshot": ("jet-snapshot-3d", 1.4, 8_000_000, 80),
+             "jet-inflow": ("jet-inflow-3d", 1.4, 8_000_000, 80)}
 ACTIVE = "gas-cloud"
+SELECT = "nearest"            # neighbours kept beyond k_max: the jet workloads take --select
 
 
 def select_workload(args):
     """Set the workload's gamma and name, and its default size."""
-    global ACTIVE, GAMMA, WORKLOAD
+    global ACTIVE, GAMMA, WORKLOAD, K_MAX, SELECT
     if args.workload in WORKLOADS:
         ACTIVE = args.workload
-    name, GAMMA, n0 = WORKLOADS[ACTIVE]
+    name, GAMMA, n0, K_MAX = WORKLOADS[ACTIVE]
+    SELECT = args.select if ACTIVE != "gas-cloud" else "nearest"
     if args.particles is None:
         args.particles = n0
     WORKLOAD = name
@@ -215,7 +219,7 @@ def workload_state(n, seed=SEED):
 
 def config_dict(n, extra=None):
     d = {"workload": WORKLOAD, "particles": n, "dim": 3, "gamma": GAMMA, "kappa": KAPPA, "k_max": K_MAX,
-         "cfl": CFL, "limiter": "flagged", "precision": "FP32 fits + FP64 state, FP64 redo",
+         "select": SELECT, "cfl": CFL, "limiter": "flagged", "precision": "FP32 fits + FP64 state, FP64 redo",
          "l2": "flushed between timed steps (256 MiB write); inputs also exceed L2",
          "parallelism": "replicas"}
     if extra:
@@ -261,7 +265,8 @@ def oracle_sample_rate(state, target_s, seed=0, threads=None):
             oracle.set_num_threads(saved)
     from paper_2206_11998_gb300 import inputs
     cfg = oracle.make_config(3, gamma=GAMMA, radius_mode=oracle.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
-                             k_side=8, limiter=oracle.LIM_FLAGGED, s_ref=inputs.field_scales(state))
+                             k_side=8, limiter=oracle.LIM_FLAGGED, s_ref=inputs.field_scales(state),
+                             select=oracle.SELECT_OCTANT if SELECT == "octant" else oracle.SELECT_NEAREST)
     n = state["V"].shape[0]
     rng = np.random.default_rng(seed)
     q0 = np.sort(rng.choice(n, 256, replace=False))
@@ -379,6 +384,8 @@ def run_ours(args):
         params, mlp_info = train_gate(lp, inputs, state, n, stream, torch)
         kw = dict(estimator=lp.EST_MLP, mlp_tau_lo=mlp_info["tau_lo"])
     prec = lp.PREC_FP64 if args.precision == "fp64" else lp.PREC_FP32
+    if SELECT == "octant":
+        kw["select"] = lp.SELECT_OCTANT
     cfg = lp.make_config(3, n, precision=prec, radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
                          k_side=8, gamma=GAMMA, limiter=lp.LIM_FLAGGED, s_ref=inputs.field_scales(state), **kw)
     ctx = lp.Context(cfg)
@@ -777,7 +784,8 @@ def run_reference(args):
     oracle.build()
     from paper_2206_11998_gb300 import inputs
     cfg = oracle.make_config(3, gamma=GAMMA, radius_mode=oracle.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX,
-                             k_side=8, limiter=oracle.LIM_FLAGGED, s_ref=inputs.field_scales(state))
+                             k_side=8, limiter=oracle.LIM_FLAGGED, s_ref=inputs.field_scales(state),
+                             select=oracle.SELECT_OCTANT if SELECT == "octant" else oracle.SELECT_NEAREST)
     rng = np.random.default_rng(1)
     # size one step's sample so that the whole run stays within a few minutes
     budget_s = 150.0

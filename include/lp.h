@@ -69,7 +69,7 @@ enum { LP_OUT_F32 = 0, LP_OUT_F64 = 1 };
  *   dim            1, 2 or 3.
  *   precision      LP_PREC_*.
  *   radius_mode    LP_RADIUS_*; radius / kappa as the mode needs.
- *   k_max          neighbour capacity per particle, 1..64; which neighbours
+ *   k_max          neighbour capacity per particle, 1..80; which neighbours
  *                  are kept when more lie inside the radius: see `select`.
  *   k_side         one-sided stencil size per half-space (Sec. 2.2 step 5
  *                  uses 8 in 3D), 1..16.

@@ -756,10 +756,12 @@ __device__ int linear_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt
 // One-sided first derivatives (Sec. 2.1 left/right derivatives): along each
 // axis k and on each side, the first k_side list members whose offset along k
 // has that sign; first-order fit; component k.  One pass over the list marks
-// the members of all 2 DIM stencils (bit r of m[k][s]: list position r), then
-// each fit takes exactly its rows in list order.  ok[k][s] = false where fewer
-// than DIM members or rank deficient.  ill = true when a system with enough
-// members is below tau (FP32: redo in FP64).
+// the members of all 2 DIM stencils (bit r of m[k][s]: list position r < 64),
+// then each fit takes exactly its rows in list order.  A stencil that still
+// takes members past position 63 (lists of k_max > 64) keeps their number in
+// tailn and finds them by a scan of the list's tail.  ok[k][s] = false where
+// fewer than DIM members or rank deficient.  ill = true when a system with
+// enough members is below tau (FP32: redo in FP64).
 template <typename T, int DIM, int F>
 __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, int ks, T invS, T tau,
                              T tau_rank, T (&out)[DIM][2][F], bool (&ok)[DIM][2], bool& ill)
@@ -773,13 +775,14 @@ __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const ui
         int r = 0;
         for_neighbors(src, nb, cnt, [&](uint32_t j, const Rec& rec) {
             bool more = false;
+            const uint64_t bit = r < 64 ? 1ull << (r & 63) : 0ull;
 #pragma unroll
             for (int k = 0; k < DIM; ++k) {
                 const int sg = src.side(rec, j, k);
                 if (sg > 0) {
-                    if (c[k][1] < ks) { m[k][1] |= 1ull << r; ++c[k][1]; }
+                    if (c[k][1] < ks) { m[k][1] |= bit; ++c[k][1]; }
                 } else if (sg < 0) {
-                    if (c[k][0] < ks) { m[k][0] |= 1ull << r; ++c[k][0]; }
+                    if (c[k][0] < ks) { m[k][0] |= bit; ++c[k][0]; }
                 }
                 more = more || c[k][0] < ks || c[k][1] < ks;
             }
@@ -787,6 +790,12 @@ __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const ui
             return more;
         });
     }
+    // members past position 63, 5 bits per stencil (k_side <= 16)
+    unsigned tailn = 0u;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) tailn |= (unsigned)(c[k][s] - __popcll(m[k][s])) << (5 * (2 * k + s));
     // the 2 DIM fits in one rolled loop (one copy of its code); fit q = 2k + s
     // leaves its k-component in shared memory and a bit in okb
     __shared__ T osm[2 * DIM * F][FIT_THREADS];
@@ -797,25 +806,49 @@ __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const ui
         uint64_t mm = m[0][0];
 #pragma unroll
         for (int qq = 1; qq < 2 * DIM; ++qq) mm = q == qq ? m[qq >> 1][qq & 1] : mm;
-        if (__popcll(mm) < DIM) continue;
+        const int ntail = (int)((tailn >> (5 * q)) & 31u);
+        if (__popcll(mm) + ntail < DIM) continue;
         Givens<T, DIM, F> G;
         G.zero();
         // rows in list order, the next record in flight
-        Rec nxt;
-        uint32_t jn = __ldg(nb + (__ffsll((long long)mm) - 1));
-        src.load_rec(jn, nxt);
-        while (mm) {
-            mm &= mm - 1;
-            const Rec cur = nxt;
-            if (mm) {
-                jn = __ldg(nb + (__ffsll((long long)mm) - 1));
-                src.load_rec(jn, nxt);
-            }
-            T d[DIM], b[F];
-            src.unpack(cur, d, b);
+        if (mm) {
+            Rec nxt;
+            uint32_t jn = __ldg(nb + (__ffsll((long long)mm) - 1));
+            src.load_rec(jn, nxt);
+            while (mm) {
+                mm &= mm - 1;
+                const Rec cur = nxt;
+                if (mm) {
+                    jn = __ldg(nb + (__ffsll((long long)mm) - 1));
+                    src.load_rec(jn, nxt);
+                }
+                T d[DIM], b[F];
+                src.unpack(cur, d, b);
 #pragma unroll
-            for (int u = 0; u < DIM; ++u) d[u] *= invS;
-            G.add(d, b);
+                for (int u = 0; u < DIM; ++u) d[u] *= invS;
+                G.add(d, b);
+            }
+        }
+        if (ntail > 0) {
+            // the members past position 63, found again by their side
+            int need = ntail;
+            const int want = (q & 1) ? 1 : -1;
+            for (int r = 64; r < cnt && need > 0; ++r) {
+                const uint32_t j = __ldg(nb + r);
+                Rec rec;
+                src.load_rec(j, rec);
+                int sg = 0;                 // (k is not a compile-time index here)
+#pragma unroll
+                for (int kk = 0; kk < DIM; ++kk)
+                    if (kk == k) sg = src.side(rec, j, kk);
+                if (sg != want) continue;
+                T d[DIM], b[F];
+                src.unpack(rec, d, b);
+#pragma unroll
+                for (int u = 0; u < DIM; ++u) d[u] *= invS;
+                G.add(d, b);
+                --need;
+            }
         }
         const T rt = G.ratio();
         if (!(rt >= tau_rank)) continue;              // rank deficient: central derivative

@@ -9,11 +9,15 @@
 
 namespace lp {
 
-constexpr int KMAX = 64;          // neighbour capacity compiled into the kernels
+constexpr int KMAX = 80;          // largest k_max the kernels accept
 constexpr int MORTON_BITS = 21;   // bits per axis of a Morton key (one simulation)
 constexpr int MAX_LEVELS = 22;    // cell levels 0..21
 constexpr int NB_WARPS = 6;       // warps per block of the neighbour query (static smem <= 48 KB)
-constexpr int NB_CAP = 2 * KMAX;  // candidate buffer per warp
+constexpr int NB_CAP = 128;       // candidate buffer per warp (a power of two: the sort's size)
+// The per-particle query compacts its buffer once more than NB_CAP - 32 entries
+// are held and then appends up to 32: the compacted entries (k_max; with the
+// octant selection fewer than k_max + 8) must leave that room.
+static_assert((NB_CAP & (NB_CAP - 1)) == 0 && KMAX + 8 <= NB_CAP - 32, "per-particle buffer too small for KMAX");
 // packed fit record of F <= 5 fields: floats [0,3) position hi, [3,6)
 // position lo, [6,8) hi and lo of the last field (P in a step), then hi, lo of
 // fields 0..F-2 from float 8 on -- so the first 32 bytes hold the positions and

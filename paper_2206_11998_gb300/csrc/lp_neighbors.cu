@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_query_octant(QueryArgs a)
 // cells or candidates, are left to the per-particle kernel.
 // ---------------------------------------------------------------------------
 constexpr int TQ_WARPS = 4;
-constexpr int TQ_CAP = KMAX;          // prefilter hits a lane keeps
+constexpr int TQ_CAP = 64;            // prefilter hits a lane keeps (two sort keys per lane)
 constexpr int TQ_PAD = 33;            // column stride: a row read across lanes is conflict-free
 constexpr int TQ_CELLS_MAX = 4096;    // cells a group's region may span
 constexpr uint32_t TQ_CAND_MAX = 2048;   // candidates a group may test (fastest of 2048, 4096, 8192 on the gas cloud)

@@ -42,7 +42,7 @@ def test_host_side_argument_errors_without_gpu():
     h = ctypes.c_void_p()
     bad = lp.make_config(4, 100)                    # dim out of range
     assert L.lp_create(ctypes.byref(bad), ctypes.byref(h)) == lp.ERR_ARG
-    bad = lp.make_config(3, 100, k_max=65)          # above the compiled capacity
+    bad = lp.make_config(3, 100, k_max=81)          # above the compiled capacity
     assert L.lp_create(ctypes.byref(bad), ctypes.byref(h)) == lp.ERR_ARG
     bad = lp.make_config(2, 100, periodic=(1, 1, 0), box_hi=(1.0, 2.0, 1.0))   # non-cubic periodic box
     assert L.lp_create(ctypes.byref(bad), ctypes.byref(h)) == lp.ERR_ARG

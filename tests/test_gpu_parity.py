@@ -128,6 +128,56 @@ def test_neighbor_overflow_truncates_exactly():
     ctx.close()
 
 
+def _stencil_tail_count(st, idx, cnt, k_side):
+    """Particles whose one-sided stencils (the first k_side list members on each
+    side of each axis, Sec. 2.1) take a member at list position 64 or later."""
+    x = np.stack(st["x"], 1)
+    K = idx.shape[1]
+    valid = np.arange(K)[None, :] < cnt[:, None]
+    off = x[np.where(valid, idx, 0)] - x[:, None, :]
+    tail = np.zeros(x.shape[0], bool)
+    for k in range(x.shape[1]):
+        for sg in (1.0, -1.0):
+            mem = valid & (np.sign(off[:, :, k]) == sg)
+            tail |= (mem & (np.cumsum(mem, 1) <= k_side))[:, 64:].any(1)
+    return int(tail.sum())
+
+
+@pytest.mark.parametrize("select", [lp.SELECT_NEAREST, lp.SELECT_OCTANT])
+def test_neighbor_lists_k_max_80(select):
+    """k_max = 80 (the jet's 20-80 neighbours): lists of up to 64 prefilter hits
+    come from the tile kernel, longer ones from the per-particle kernel; both
+    bit-exact."""
+    st = inputs.jet_snapshot_3d(30_000)
+    n = st["V"].shape[0]
+    cfg = lp.make_config(3, n, radius_mode=lp.RADIUS_VOLUME, kappa=2.2, k_max=80, select=select)
+    ocfg = _oracle_cfg(cfg)
+    _, ocnt, otot, _ = oracle.neighbors(ocfg, st["x"], st["V"], st["m"], st["id"])
+    assert (ocnt > 64).sum() > 100 and (otot > 80).sum() > 100 and ocnt.max() == 80
+    ctx = lp.Context(cfg)
+    ps = lp.ParticleSet.from_state(st)
+    ctx.build_neighbors(ps)
+    torch.cuda.synchronize()
+    _check_lists(ctx, ps, st, ocfg)
+    assert ctx.stats()["n_overflow"] == (otot > 80).sum()
+    ctx.close()
+
+
+@pytest.mark.parametrize("select", [lp.SELECT_NEAREST, lp.SELECT_OCTANT])
+@pytest.mark.parametrize("prec,tol", [(lp.PREC_FP32, 1e-5), (lp.PREC_FP64, 1e-12)])
+def test_step_jet_snapshot_k_max_80(prec, tol, select):
+    """One step of the jet snapshot with k_max = 80: some one-sided stencils
+    take members past list position 63 (found by the fits' tail scan)."""
+    st = inputs.jet_snapshot_3d(30_000)
+    n = st["V"].shape[0]
+    cfg = lp.make_config(3, n, precision=prec, kappa=2.2, k_max=80, gamma=inputs.JET_GAMMA,
+                         s_ref=inputs.field_scales(st), limiter=lp.LIM_FLAGGED, select=select)
+    ocfg = _oracle_cfg(cfg)
+    oidx, ocnt, _, _ = oracle.neighbors(ocfg, st["x"], st["V"], st["m"], st["id"])
+    assert _stencil_tail_count(st, oidx, ocnt, cfg.k_side) > 20
+    _step_parity(st, cfg, 0.0, tol, cfl=0.4)
+
+
 def _octant_case(name):
     """States and configurations with octant-balanced selection where many lists
     are truncated: a dense cloud with a small capacity, the jet snapshot (the
