@@ -771,8 +771,8 @@ __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const ui
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { m[k][0] = m[k][1] = 0ull; c[k][0] = c[k][1] = 0; }
     using Rec = typename Src<T, DIM, F>::Rec;
+    int r = 0;                      // list positions the marking pass visited
     if (ks > 0) {
-        int r = 0;
         for_neighbors(src, nb, cnt, [&](uint32_t j, const Rec& rec) {
             bool more = false;
             const uint64_t bit = r < 64 ? 1ull << (r & 63) : 0ull;
@@ -792,10 +792,12 @@ __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const ui
     }
     // members past position 63, 5 bits per stencil (k_side <= 16)
     unsigned tailn = 0u;
+    if (r > 64) {
 #pragma unroll
-    for (int k = 0; k < DIM; ++k)
+        for (int k = 0; k < DIM; ++k)
 #pragma unroll
-        for (int s = 0; s < 2; ++s) tailn |= (unsigned)(c[k][s] - __popcll(m[k][s])) << (5 * (2 * k + s));
+            for (int s = 0; s < 2; ++s) tailn |= (unsigned)(c[k][s] - __popcll(m[k][s])) << (5 * (2 * k + s));
+    }
     // the 2 DIM fits in one rolled loop (one copy of its code); fit q = 2k + s
     // leaves its k-component in shared memory and a bit in okb
     __shared__ T osm[2 * DIM * F][FIT_THREADS];
@@ -811,23 +813,22 @@ __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const ui
         Givens<T, DIM, F> G;
         G.zero();
         // rows in list order, the next record in flight
-        if (mm) {
-            Rec nxt;
-            uint32_t jn = __ldg(nb + (__ffsll((long long)mm) - 1));
-            src.load_rec(jn, nxt);
-            while (mm) {
-                mm &= mm - 1;
-                const Rec cur = nxt;
-                if (mm) {
-                    jn = __ldg(nb + (__ffsll((long long)mm) - 1));
-                    src.load_rec(jn, nxt);
-                }
-                T d[DIM], b[F];
-                src.unpack(cur, d, b);
-#pragma unroll
-                for (int u = 0; u < DIM; ++u) d[u] *= invS;
-                G.add(d, b);
+        // (with no member before position 64 the first load reads entry 0, unused)
+        Rec nxt;
+        uint32_t jn = __ldg(nb + (mm ? __ffsll((long long)mm) - 1 : 0));
+        src.load_rec(jn, nxt);
+        while (mm) {
+            mm &= mm - 1;
+            const Rec cur = nxt;
+            if (mm) {
+                jn = __ldg(nb + (__ffsll((long long)mm) - 1));
+                src.load_rec(jn, nxt);
             }
+            T d[DIM], b[F];
+            src.unpack(cur, d, b);
+#pragma unroll
+            for (int u = 0; u < DIM; ++u) d[u] *= invS;
+            G.add(d, b);
         }
         if (ntail > 0) {
             // the members past position 63, found again by their side

@@ -946,28 +946,43 @@ __device__ inline float split_offset(const DevCfg& c, int k, float hj, float lj,
 }
 
 // ascending sort of P = 32 * W distinct 32-bit keys, element e = lane + 32 s
-// held by lane in key[s]
+// held by lane in key[s].  Bitonic merges in the form whose compare-exchanges
+// all point the same way: the first stage of the merge of two sorted runs of
+// k/2 compares each element with its mirror in the k-block (partner e ^ (k-1)),
+// the later stages with e ^ jj; the lower element takes the minimum.  So a
+// lane's direction depends on one lane bit per stage (five predicates in all)
+// instead of two.
 template <int W>
 __device__ inline void bitonic_keys(uint32_t (&key)[2])
 {
     const unsigned lane = lane_id();
-    constexpr int P = 32 * W;
 #pragma unroll
-    for (int k = 2; k <= P; k <<= 1) {
+    for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
         for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            if (jj >= 32) {                  // partner in the other register (k = 64: ascending)
-                const uint32_t lo = min(key[0], key[1]), hi = max(key[0], key[1]);
-                key[0] = lo;
-                key[1] = hi;
-            } else {
+            const int mask = jj == (k >> 1) ? k - 1 : jj;
+            const bool low = (lane & (unsigned)jj) == 0u;
 #pragma unroll
-                for (int s = 0; s < W; ++s) {
-                    const unsigned e = lane + 32u * s;
-                    const uint32_t pk = __shfl_xor_sync(0xffffffffu, key[s], jj);
-                    const bool take_min = ((e & (unsigned)jj) == 0u) == ((e & (unsigned)k) == 0u);
-                    key[s] = take_min ? min(key[s], pk) : max(key[s], pk);
-                }
+            for (int s = 0; s < W; ++s) {
+                const uint32_t pk = __shfl_xor_sync(0xffffffffu, key[s], mask);
+                key[s] = low ? min(key[s], pk) : max(key[s], pk);
+            }
+        }
+    }
+    if (W == 2) {
+        // the merge of the two sorted registers: mirror stage across them
+        // (e ^ 63 is lane ^ 31 of the other register), then within each
+        const uint32_t p0 = __shfl_xor_sync(0xffffffffu, key[1], 31);
+        const uint32_t p1 = __shfl_xor_sync(0xffffffffu, key[0], 31);
+        key[0] = min(key[0], p0);
+        key[1] = max(key[1], p1);
+#pragma unroll
+        for (int jj = 16; jj > 0; jj >>= 1) {
+            const bool low = (lane & (unsigned)jj) == 0u;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const uint32_t pk = __shfl_xor_sync(0xffffffffu, key[s], jj);
+                key[s] = low ? min(key[s], pk) : max(key[s], pk);
             }
         }
     }
