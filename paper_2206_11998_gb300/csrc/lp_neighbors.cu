@@ -457,15 +457,27 @@ __device__ void query_one(const QueryArgs& a, WarpBuf& b, int64_t i)
     __syncwarp();
 }
 
-// octant (quadrant in 2D) of x_j seen from x_i: bit k set when the FP64
-// offset along axis k (minimum image on a periodic axis) is >= 0
+// Octant (quadrant in 2D) of x_j seen from x_i: bit k set when the FP64
+// offset along axis k (minimum image on a periodic axis) is >= 0.  It is read
+// from the split float parts of both positions (h = RN(x), l = RN(x - h)).
+// Both roundings are monotonic, so h_j > h_i implies x_j > x_i, and with equal
+// high parts l_j > l_i implies it too (and < likewise): the offset's sign is
+// read from the first part that differs, exactly.  Where both parts are equal,
+// and on periodic axes, the FP64 offset decides.  The octant query tests many
+// candidates per particle, and FP64 arithmetic is scarce on this GPU.
 template <int DIM>
-__device__ inline int octant64(const QueryArgs& a, int64_t i, int64_t j)
+__device__ inline int octant_split(const QueryArgs& a, int64_t i, int64_t j, const float (&hi)[3],
+                                   const float (&li)[3], const float (&hj)[3], const float (&lj)[3])
 {
     int o = 0;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k)
-        if (offset64(a.c, k, a.sx[k][i], a.sx[k][j]) >= 0.0) o |= 1 << k;
+    for (int k = 0; k < DIM; ++k) {
+        bool ge;
+        if (!a.c.periodic[k] && hj[k] != hi[k]) ge = hj[k] > hi[k];
+        else if (!a.c.periodic[k] && lj[k] != li[k]) ge = lj[k] > li[k];
+        else ge = offset64(a.c, k, a.sx[k][i], a.sx[k][j]) >= 0.0;
+        if (ge) o |= 1 << k;
+    }
     return o;
 }
 
@@ -480,7 +492,8 @@ __device__ inline uint32_t warp_sum_u32(uint32_t v)
 // octants; entry e's rank and octant go to the lane e % 32 of chunk e / 32
 // through the callback, called by all lanes once per chunk
 template <int DIM, typename F>
-__device__ inline void octant_ranks(const QueryArgs& a, WarpBuf& b, int m, int64_t i, F&& fn)
+__device__ inline void octant_ranks(const QueryArgs& a, WarpBuf& b, int m, int64_t i, const float (&hi)[3],
+                                    const float (&li)[3], F&& fn)
 {
     const unsigned lane = lane_id(), lt = (1u << lane) - 1u;
     uint32_t carry[1 << DIM];
@@ -489,7 +502,14 @@ __device__ inline void octant_ranks(const QueryArgs& a, WarpBuf& b, int m, int64
     for (int e0 = 0; e0 < m; e0 += 32) {
         const int e = e0 + (int)lane;
         const bool valid = e < m;
-        const int o = valid ? octant64<DIM>(a, i, b.j[e]) : -1;
+        int o = -1;
+        if (valid) {
+            const uint32_t j = b.j[e];
+            float4 ph, pl;
+            ldg256(a.pos4 + 2 * (int64_t)j, ph, pl);
+            const float hj[3] = {ph.x, ph.y, ph.z}, lj[3] = {pl.x, pl.y, pl.z};
+            o = octant_split<DIM>(a, i, j, hi, li, hj, lj);
+        }
         uint32_t rank = 0;
 #pragma unroll
         for (int q = 0; q < (1 << DIM); ++q) {
@@ -545,7 +565,7 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
     // batch of 32 cells; cls(dmin, dmax, touched, splittable) classifies a
     // non-empty cell within reach (one lane, no warp operations); whole(w,
     // touched, cn) is called by all lanes (w: this lane's cell is counted
-    // whole); fn(in, j, d2f) by all lanes for each scanned candidate;
+    // whole); fn(in, j, d2f, octant) by all lanes for each scanned candidate;
     // level_end() by all lanes after each level.
     auto traverse = [&](auto&& pre, auto&& cls, auto&& whole, auto&& fn, auto&& level_end) {
         query_start<DIM>(a, b, i, st);
@@ -623,6 +643,7 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
                     bool in = false;
                     float d2f = 0.0f;
                     uint32_t j = 0;
+                    int oct = 0;                   // octant of an in-radius candidate
                     if (t < T) {
                         int lo = 0, hi = 31;       // the last cell with cexcl <= t
                         while (lo < hi) {
@@ -648,9 +669,10 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
                             if (d2f <= st.R2f * (1.0f - TOL_R)) in = true;
                             else if (d2f <= st.R2f * (1.0f + TOL_R))
                                 in = inside64(c, DIM, exact_d2<DIM>(a, i, j), __dmul_rn(a.sm[i], a.sV[i]));
+                            if (in) oct = octant_split<DIM>(a, i, j, st.hxi, st.lxi, hj, lj);
                         }
                     }
-                    fn(in, j, d2f);
+                    fn(in, j, d2f, oct);
                 }
                 __syncwarp();
             }
@@ -682,8 +704,8 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
                 if ((int)lane == q) cnt_o += add;
             }
         },
-        [&](bool in, uint32_t j, float) {
-            const int o = in ? octant64<DIM>(a, i, j) : -1;
+        [&](bool in, uint32_t, float, int oct) {
+            const int o = in ? oct : -1;
             total += (uint32_t)__popc(__ballot_sync(0xffffffffu, in));
 #pragma unroll
             for (int q = 0; q < NO; ++q) {
@@ -711,7 +733,7 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
         int w = 0;
         unsigned nfull = 0u;
         float ncut = INFINITY;
-        octant_ranks<DIM>(a, b, m, i, [&](int e0, bool valid, int o, uint32_t rank) {
+        octant_ranks<DIM>(a, b, m, i, st.hxi, st.lxi, [&](int e0, bool valid, int o, uint32_t rank) {
             const int e = e0 + (int)lane;
             // every lane takes part in the shuffle (no short circuit before it)
             const uint32_t qo = __shfl_sync(0xffffffffu, q_o, o & 7);
@@ -761,8 +783,8 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
             return splittable ? SPLIT : SCAN;
         },
         [&](bool, unsigned, uint32_t) {},
-        [&](bool in, uint32_t j, float d2f) {
-            const int o = in ? octant64<DIM>(a, i, j) : 0;
+        [&](bool in, uint32_t j, float d2f, int oct) {
+            const int o = in ? oct : 0;
             const uint32_t qo = __shfl_sync(0xffffffffu, q_o, o);   // every lane, then the test
             const float co = __shfl_sync(0xffffffffu, cut_o, o);
             const bool keep = in && qo > 0u && d2f <= co;
@@ -783,7 +805,7 @@ __device__ void query_one_octant(const QueryArgs& a, WarpBuf& b, int64_t i)
     // ---- the selection, in (d2, id) order: ranks below R, and the first rem of rank R
     int w = 0;
     uint32_t taken_r = 0;
-    octant_ranks<DIM>(a, b, m, i, [&](int e0, bool valid, int, uint32_t rank) {
+    octant_ranks<DIM>(a, b, m, i, st.hxi, st.lxi, [&](int e0, bool valid, int, uint32_t rank) {
         const int e = e0 + (int)lane;
         const bool atR = valid && rank == R;
         const unsigned bR = __ballot_sync(0xffffffffu, atR);
