@@ -224,6 +224,7 @@ void fill_fit_args(lp_ctx* c, FitArgs& a, int64_t n)
     a.queue = c->counters + C_QUEUE_CENTRAL;      // and C_QUEUE_PLAIN after it
     a.mid = c->mid;
     a.mid_cap = c->cap;
+    a.plain_ident = 0;
 }
 
 constexpr int EV_PAIRS = LP_NPHASES * 4;
@@ -298,6 +299,13 @@ lp_status run_fit(lp_ctx* c, FitArgs a, const StepOut& o, int sched, cudaStream_
     const bool split = (sched & LP_SCHED_SPLIT) != 0;
     const int dim = c->dc.dim;
     if (split) LP_CUDA(cudaMemsetAsync(c->counters + C_PLAIN_LEN, 0, 8, s));
+    // with no learned gate every fitted particle takes the plain stage: its
+    // slot is its index, and the plain kernel keeps the key order (slots of
+    // particles without a plain stage stay all ones)
+    if (split && !o.features && c->dc.estimator != LP_EST_MLP && a.n > 0) {
+        a.plain_ident = 1;
+        LP_CUDA(cudaMemsetAsync(c->plain_list, 0xff, (size_t)a.n * 4, s));
+    }
     if (c->dc.precision == LP_PREC_FP32) {
         LP_CUDA(cudaMemsetAsync(c->counters + C_REDO_LEN, 0, 8, s));
         const bool defer = split && c->dc.refine == LP_REFINE_AUTO;

@@ -351,11 +351,16 @@ struct FitArgs {
     const uint64_t* keys;         // key-sorted keys (simulation above bit key_shift)
     int key_shift;
     // split schedule: compacted list of particles that need the plain stage,
-    // its length, and the intermediate record (component-major, mid_cap slots)
+    // its length, and the intermediate record (component-major, mid_cap slots).
+    // plain_ident (no learned gate: every fitted particle takes the plain
+    // stage): slot t is particle t, plain_list[t] = t or all ones where the
+    // particle has no plain stage, and the plain kernel runs over [0, n) in
+    // key order
     uint32_t* plain_list;
     unsigned long long* plain_len;
     void* mid;
     int64_t mid_cap;
+    int plain_ident;
     // split schedule, FP32: the central fits that need the correction pass,
     // listed by the first kernel for a kernel of their own
     uint32_t* refine_list;

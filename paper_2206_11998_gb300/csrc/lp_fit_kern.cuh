@@ -407,7 +407,7 @@ __device__ __forceinline__ void central_append_or_finish(const FitArgs& a, const
 {
     constexpr int F = DIM + 2;
     const bool plain = !mlp_skip || a.c.mlp_audit;
-    unsigned long long t = warp_append(a.plain_len, plain);
+    const unsigned long long t = a.plain_ident ? (unsigned long long)i : warp_append(a.plain_len, plain);
     if (plain) {
         T* mid = static_cast<T*>(a.mid);
         const int64_t cap = a.mid_cap;
@@ -474,7 +474,9 @@ template <typename T, int DIM>
 __device__ __forceinline__ void plain_one(const FitArgs& a, const StepOut& o, unsigned long long t)
 {
     constexpr int F = DIM + 2;
-    const int64_t i = a.plain_list[t];
+    const uint32_t iu = a.plain_list[t];
+    if (iu == 0xffffffffu) return;          // (plain_ident) no plain stage for this slot
+    const int64_t i = iu;
     Src<T, DIM, F> src(a, i);
     const int cnt = (int)a.count[i];
     const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
@@ -511,7 +513,7 @@ __device__ __forceinline__ void plain_one(const FitArgs& a, const StepOut& o, un
 template <typename T, int DIM>
 __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain(FitArgs a, StepOut o)
 {
-    const unsigned long long len = *a.plain_len;
+    const unsigned long long len = a.plain_ident ? (unsigned long long)a.n : *a.plain_len;
     const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     if (t < len) plain_one<T, DIM>(a, o, t);
 }
@@ -544,7 +546,7 @@ __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_centra
 template <typename T, int DIM>
 __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain_q(FitArgs a, StepOut o)
 {
-    const unsigned long long len = *a.plain_len;
+    const unsigned long long len = a.plain_ident ? (unsigned long long)a.n : *a.plain_len;
     for (;;) {
         const unsigned long long base = warp_take(a.queue + 1);
         if (base >= len) return;
