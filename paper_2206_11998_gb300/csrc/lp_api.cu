@@ -150,22 +150,34 @@ __global__ void k_split_fields(int64_t n, int nf, int F, const double* f0, const
 __global__ void k_cfl(int64_t n, DevCfg c, const double* d2min, const double* P, const double* V,
                       const uint32_t* id, const uint64_t* keys, int key_shift, unsigned long long* dtmin)
 {
-    double best = INFINITY;
+    // The smallest quotient d2 / cs2 is kept as the pair (bn, bd) and compared
+    // by cross-multiplication, d2 bd < bn cs2 (both sides positive): two FP64
+    // multiplications per particle instead of a division, which is a sequence
+    // of FP64 operations on a GPU with little FP64 throughput.  The one
+    // division comes at the end, per warp.  (The comparison rounds: between
+    // two quotients within a few ulp either may win, far inside the accuracy
+    // the step's Delta t is held to.)
+    double bn = INFINITY, bd = 1.0;
     uint32_t sim = 0;
     bool many = c.nsim_max > 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (many) sim = (uint32_t)(keys[i] >> key_shift);
         if ((int64_t)id[i] < c.n_fluid && !isinf(d2min[i])) {
-            double cs2 = (c.gamma * P[i]) * V[i];
-            best = fmin(best, d2min[i] / cs2);
+            const double d2 = d2min[i];
+            const double cs2 = (c.gamma * P[i]) * V[i];
+            if (cs2 > 0.0 && d2 >= 0.0 && d2 * bd < bn * cs2) { bn = d2; bd = cs2; }
         }
         if (many) break;
     }
     uint32_t s0 = __shfl_sync(0xffffffffu, sim, 0);
     if (__all_sync(0xffffffffu, sim == s0)) {
-        for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            const double on = __shfl_xor_sync(0xffffffffu, bn, o), od = __shfl_xor_sync(0xffffffffu, bd, o);
+            if (on * bd < bn * od) { bn = on; bd = od; }
+        }
         if ((threadIdx.x & 31) != 0) return;
     }
+    const double best = bn / bd;
     if (best >= 0.0 && best < INFINITY) atomicMin(dtmin + sim, (unsigned long long)__double_as_longlong(best));
 }
 
