@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/lp.h"
+#include "lp_split.h"
 
 namespace lp {
 
@@ -62,15 +63,16 @@ struct DevCfg {
     int64_t n_fluid;
 };
 
-// the float query radius of a particle: kappa (m V)^(1/dim) (volume mode) or
-// R (fixed mode); 0 for a non-finite or negative volume.  Written once per build
-// into the fourth component of the particle's float4 position (hi part).
-__device__ inline float query_radius_f(const DevCfg& c, int dim, double m, double V)
+// the float query radius of a particle from RN(m) and RN(V): kappa (m V)^(1/dim)
+// (volume mode) or R (fixed mode); 0 for a non-finite or negative volume.
+// Written once per build into the fourth component of the particle's float4
+// position (hi part).
+__device__ inline float query_radius_ff(const DevCfg& c, int dim, float mf, float Vf)
 {
     float Rf;
     if (c.radius_mode == LP_RADIUS_FIXED) Rf = c.radius_f;
     else {
-        float wf = (float)m * (float)V;
+        float wf = mf * Vf;
         if (!(wf > 0.0f)) wf = 0.0f;
         const float r = dim == 3 ? cbrtf(wf) : (dim == 2 ? sqrtf(wf) : wf);
         Rf = c.kappa_f * r;
@@ -182,11 +184,21 @@ __device__ inline bool inside64(const DevCfg& c, int dim, double d2, double w)
     return d2 <= __dmul_rn(k2, ww);
 }
 
-// split a double into float hi + float lo (x ~ hi + lo)
+// split a double into float hi + float lo (x ~ hi + lo): h = RN(x), l =
+// RN(x - h), by integer operations where lp_split.h handles the value, by FP64
+// conversions and a subtraction elsewhere (the same results)
 __device__ inline void split(double x, float& h, float& l)
 {
+    if (split_exact(x, h, l)) return;
     h = __double2float_rn(x);
     l = __double2float_rn(__dsub_rn(x, (double)h));
+}
+
+// RN(x) as a float (integer operations where lp_split.h handles the value)
+__device__ inline float to_float_rn(double x)
+{
+    float h;
+    return round_exact(x, h) ? h : __double2float_rn(x);
 }
 
 // 32 bytes (two float4) from a 32-byte-aligned global address that the kernel

@@ -207,7 +207,7 @@ __device__ __forceinline__ void query_start(const QueryArgs& a, WarpBuf& b, int6
     st.lxi[0] = pil.x; st.lxi[1] = pil.y; st.lxi[2] = pil.z;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) st.tq[k] = ((st.hxi[k] - g.lo_h[k]) + (st.lxi[k] - g.lo_l[k])) * inv;   // quantised units, error < 1
-    const float Rf = pih.w;                          // query_radius_f, written by the gather
+    const float Rf = pih.w;                          // query_radius_ff, written by the gather
     st.R2f = (c.radius_mode == LP_RADIUS_FIXED) ? c.radius2_f : Rf * Rf;
     float Rc = Rf * (1.0f + 1e-5f);
     const float Rq = Rc * inv;
@@ -946,7 +946,7 @@ __device__ inline void tile_lane(const QueryArgs& a, const Grid& g, int64_t i, T
     for (int k = 0; k < 3; ++k) t.tq[k] = 0.0f;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) t.tq[k] = ((t.hx[k] - g.lo_h[k]) + (t.lx[k] - g.lo_l[k])) * inv;
-    const float Rf = ph.w;                           // query_radius_f, written by the gather
+    const float Rf = ph.w;                           // query_radius_ff, written by the gather
     t.Rf = Rf;
     t.R2f = (c.radius_mode == LP_RADIUS_FIXED) ? c.radius2_f : Rf * Rf;
     t.Rq = Rf * (1.0f + 1e-5f) * inv;

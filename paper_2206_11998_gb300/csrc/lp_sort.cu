@@ -545,7 +545,9 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm, lp_partic
 #pragma unroll
     for (int q = 0; q < REC_F4; ++q) rec[i * REC_F4 + q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
     const double m = p.m[j];
-    pos4[2 * i] = make_float4(r[REC_XH], r[REC_XH + 1], r[REC_XH + 2], query_radius_f(c, DIM, m, V));
+    // (r[rec_fh(0, F)] is RN(V))
+    pos4[2 * i] = make_float4(r[REC_XH], r[REC_XH + 1], r[REC_XH + 2],
+                              query_radius_ff(c, DIM, to_float_rn(m), r[rec_fh(0, F)]));
     pos4[2 * i + 1] = make_float4(r[REC_XL], r[REC_XL + 1], r[REC_XL + 2], 0.0f);
     sm[i] = m;
     sid[i] = p.id[j];
@@ -580,7 +582,7 @@ __global__ void k_gather_geom(int64_t n, const uint32_t* __restrict__ perm, lp_p
     sV[i] = V;
     sm[i] = m;
     sid[i] = p.id[j];
-    pos4[2 * i] = make_float4(xh[0], xh[1], xh[2], query_radius_f(c, DIM, m, V));
+    pos4[2 * i] = make_float4(xh[0], xh[1], xh[2], query_radius_ff(c, DIM, to_float_rn(m), to_float_rn(V)));
     pos4[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.0f);
 }
 
