@@ -129,7 +129,7 @@ __host__ __device__ inline uint64_t morton(const uint32_t* q)
 // RS_TILE_KEYS keys (block counts and digit totals: RS_BINS x (tiles + 1) words)
 constexpr int RS_BITS = 9;
 constexpr int RS_BINS = 1 << RS_BITS;
-constexpr int RS_TILE_KEYS = 4096;
+constexpr int RS_TILE_KEYS = 2048;
 
 // bits [lo, hi) of a key the sort orders by: the simulation index and the cell
 // bits down to table level lmax_cap (every bit in 1D), in whole digits

@@ -12,7 +12,7 @@ namespace lp {
 namespace {
 
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
+constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 static_assert(RS_TILE == RS_TILE_KEYS, "the histogram is sized for this tile");
 static_assert(RS_BINS == 2 * RS_THREADS, "each thread owns two digits of the histogram");
