@@ -361,11 +361,11 @@ __global__ void k_keys(int64_t n, const double* __restrict__ x0, const double* _
     const uint32_t qmax = (1u << mbits) - 1u;
     uint32_t q[3] = {0, 0, 0};
     for (int k = 0; k < DIM; ++k) {
-        // floor(t) clamped to [0, qmax]: the conversion rounds down and
-        // saturates (negative and NaN give 0), so one FP64 conversion replaces
-        // floor and two comparisons
+        // floor(t) clamped to [0, qmax] (negative and NaN give 0, +inf gives
+        // qmax), read from t's bits: the conversion instruction would run on
+        // the FP64 units, which the subtraction and the product already keep busy
         const double t = __dmul_rn(__dsub_rn(xs[k][i], g->lo[k]), inv);
-        q[k] = min(__double2uint_rd(t), qmax);
+        q[k] = floor_clamped(t, qmax);
     }
     keys[i] = ((uint64_t)sim << (DIM * mbits)) | morton<DIM>(q);
     vals[i] = (uint32_t)i;

@@ -12,6 +12,8 @@
 // ones the plain form gives; the host test (tests/test_split_host.py) checks
 // that bit for bit against the compiler's conversions.
 //
+// Also the floor of an FP64 value as an integer, from its bits (floor_clamped).
+//
 // Plain C++ so that the host test compiles it as well.
 #pragma once
 
@@ -110,6 +112,22 @@ LP_SPLIT_FN bool split_exact(double x, float& h, float& l)
     }
     l = split_float_of(lsgn | split_scaled_bits((uint32_t)rr, e - 52));
     return true;
+}
+
+// floor(t) as an unsigned integer clamped to [0, qmax] (qmax < 2^32), from the
+// bits of t: 0 for t < 1, negative t and NaN; qmax for t >= qmax and +inf
+LP_SPLIT_FN uint32_t floor_clamped(double t, uint32_t qmax)
+{
+    const uint64_t b = split_bits_of(t);
+    if (b >> 63) return 0u;                                   // negative, -0, NaN with the sign set
+    const int E = (int)((b >> 52) & 0x7ffu);
+    const uint64_t mant = b & 0xfffffffffffffull;
+    if (E == 0x7ff) return mant ? 0u : qmax;                  // NaN, +inf
+    const int e = E - 1023;
+    if (e < 0) return 0u;                                     // t < 1 (zero and subnormals included)
+    if (e >= 32) return qmax;
+    const uint32_t q = (uint32_t)((mant | (1ull << 52)) >> (52 - e));
+    return q < qmax ? q : qmax;
 }
 
 // RN(x) as a float, the first half of split_exact; false outside its range

@@ -1,8 +1,9 @@
 """The integer split of an FP64 value into float parts (csrc/lp_split.h), which
 the gather uses for positions and fields: h = RN(x) and l = RN(x - h) bit for
 bit as the host compiler's own conversions give them, over random values,
-rounding midpoints, carries into the exponent, both signs and zero.  Compiled
-with the host C++ compiler; needs no GPU."""
+rounding midpoints, carries into the exponent, both signs and zero; and the
+clamped floor the key kernel reads from an FP64 value's bits, against the
+library floor.  Compiled with the host C++ compiler; needs no GPU."""
 import os
 import shutil
 import subprocess
@@ -55,8 +56,32 @@ int main()
     const double special[] = {0.0, -0.0, 1.0, -1.0, 0.1, -0.1, 1e-22, 5e-23, 3.0e38, 1.7e38,
                               INFINITY, -INFINITY, NAN, 4.9e-324, 2.2250738585072014e-308};
     for (double x : special) check(x);
-    printf("checked %ld skipped %ld bad %ld\n", n, skipped, bad);
-    return bad != 0 || n < 2000000;
+    // floor_clamped against the library floor on the same kind of values
+    long fbad = 0;
+    const uint32_t qmax = (1u << 21) - 1u;
+    for (long t = 0; t < 2000000; ++t) {
+        const uint64_t r = g();
+        const int e = (int)(r % 60) - 20;
+        uint64_t m = g() & 0xfffffffffffffull;
+        if (t % 7 == 0) m = 0;                       // powers of two
+        if (t % 9 == 0) m &= ~((1ull << 40) - 1);    // integers and half-integers
+        const uint64_t b = ((uint64_t)(e + 1023) << 52) | m | ((t % 10 == 0 ? 1ull : 0ull) << 63);
+        double x;
+        memcpy(&x, &b, 8);
+        const double f = std::floor(x);
+        const uint32_t want = !(x >= 0.0) ? 0u : (f >= (double)qmax ? qmax : (uint32_t)f);
+        if (lp::floor_clamped(x, qmax) != want) {
+            if (fbad < 5) printf("floor mismatch %a: %u / %u\n", x, lp::floor_clamped(x, qmax), want);
+            ++fbad;
+        }
+    }
+    const double fs[] = {0.0, -0.0, 0.5, 1.0, 2097151.0, 2097151.5, 2097152.0, 1e300, -1.0, INFINITY, -INFINITY, NAN,
+                         4.9e-324};
+    const uint32_t fw[] = {0u, 0u, 0u, 1u, qmax, qmax, qmax, qmax, 0u, qmax, 0u, 0u, 0u};
+    for (int k = 0; k < 13; ++k)
+        if (lp::floor_clamped(fs[k], qmax) != fw[k]) { printf("floor special %a\n", fs[k]); ++fbad; }
+    printf("checked %ld skipped %ld bad %ld floor-bad %ld\n", n, skipped, bad, fbad);
+    return bad != 0 || fbad != 0 || n < 2000000;
 }
 """
 
