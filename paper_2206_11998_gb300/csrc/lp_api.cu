@@ -157,15 +157,24 @@ __global__ void k_cfl(int64_t n, DevCfg c, const double* d2min, const double* P,
     // division comes at the end, per warp.  (The comparison rounds: between
     // two quotients within a few ulp either may win, far inside the accuracy
     // the step's Delta t is held to.)
+    // The tests compare the bit patterns as integers: for doubles that are
+    // not negative and not NaN the order of the patterns is the order of the
+    // values, and an integer comparison does not occupy the FP64 units
+    // (finite positive values below 2^1024 have patterns below 0x7ff0...).
+    constexpr long long INF_BITS = 0x7ff0000000000000ll;
     double bn = INFINITY, bd = 1.0;
     uint32_t sim = 0;
     bool many = c.nsim_max > 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (many) sim = (uint32_t)(keys[i] >> key_shift);
-        if ((int64_t)id[i] < c.n_fluid && !isinf(d2min[i])) {
-            const double d2 = d2min[i];
+        const double d2 = d2min[i];
+        const long long d2b = __double_as_longlong(d2);
+        // fluid, 0 <= d2 < inf (-0 has the sign bit and is left out with the negatives)
+        if ((int64_t)id[i] < c.n_fluid && d2b >= 0 && d2b < INF_BITS) {
             const double cs2 = (c.gamma * P[i]) * V[i];
-            if (cs2 > 0.0 && d2 >= 0.0 && d2 * bd < bn * cs2) { bn = d2; bd = cs2; }
+            const long long cb = __double_as_longlong(cs2);
+            if (cb > 0 && cb < INF_BITS &&
+                __double_as_longlong(d2 * bd) < __double_as_longlong(bn * cs2)) { bn = d2; bd = cs2; }
         }
         if (many) break;
     }
@@ -173,7 +182,7 @@ __global__ void k_cfl(int64_t n, DevCfg c, const double* d2min, const double* P,
     if (__all_sync(0xffffffffu, sim == s0)) {
         for (int o = 16; o > 0; o >>= 1) {
             const double on = __shfl_xor_sync(0xffffffffu, bn, o), od = __shfl_xor_sync(0xffffffffu, bd, o);
-            if (on * bd < bn * od) { bn = on; bd = od; }
+            if (__double_as_longlong(on * bd) < __double_as_longlong(bn * od)) { bn = on; bd = od; }
         }
         if ((threadIdx.x & 31) != 0) return;
     }
