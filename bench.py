@@ -109,7 +109,7 @@ def schedule_name(lp, sch: int) -> str:
     return fit + "+" + query
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -146,7 +146,11 @@ def parse():
                     help="skip the FP64 and learned-estimator forms reported beside the headline")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="fp64: every fit and rate in FP64 (the plain FP64 GPU form)")
-    return ap.parse_args()
+    ap.add_argument("--compare-estimators", type=int, default=0, metavar="STEPS",
+                    help="gas cloud: advance the same state STEPS steps with the plain and with the learned "
+                         "estimator (the learned run takes the plain run's CFL steps) and report both times "
+                         "and the learned run's drift from the plain one")
+    return ap.parse_args(argv)
 
 
 def max_over_ranks(values, world, torch, dist, device):
@@ -1055,9 +1059,90 @@ def run_inflow(args):
     print(json.dumps(line), flush=True)
 
 
+def estimator_compare(args):
+    """The gas cloud advanced args.compare_estimators steps twice from the same
+    state: with the plain estimator (CFL steps), and with the learned estimator
+    trained on the cloud's own plain steps, taking the same sequence of steps so
+    that both end at the same time.  Reports each run's time per step (CUDA
+    events, eager steps), the flagged and skipped counts, and the learned run's
+    drift from the plain one per field: the relative L2 and max differences of
+    the final states, and the L2 difference relative to the plain run's own
+    change from the initial state."""
+    import torch
+
+    from paper_2206_11998_gb300 import build as b
+    from paper_2206_11998_gb300 import inputs, lp
+
+    b.build()
+    torch.cuda.set_device(0)
+    steps = args.compare_estimators
+    state = workload_state(args.particles)
+    n = state["V"].shape[0]
+    stream = torch.cuda.Stream()
+    params, info = train_gate(lp, inputs, state, n, stream, torch)
+    base = dict(radius_mode=lp.RADIUS_VOLUME, kappa=KAPPA, k_max=K_MAX, k_side=8, gamma=GAMMA,
+                limiter=lp.LIM_FLAGGED, s_ref=inputs.field_scales(state))
+
+    def run(ctx, dts):
+        out_dt, ms, flagged, skipped, nonfinite = [], [], 0, 0, 0
+        with torch.cuda.stream(stream):
+            ps = lp.ParticleSet.from_state(state)
+            ctx.reset_stats(stream=stream)
+            for k in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.step(ps, dt=0.0 if dts is None else dts[k], cfl=CFL, stream=stream)
+                e1.record(stream)
+                if dts is None:
+                    out_dt.append(ctx.stats(stream=stream)["dt"])
+                ms.append((e0, e1))
+            stream.synchronize()
+            st = ctx.stats(stream=stream)
+            idx = ps.id.long()
+            byid = lambda t: torch.empty_like(t).index_copy_(0, idx, t)
+            fields = {"V": byid(ps.V), "P": byid(ps.P)}
+            for k in range(3):
+                fields["u%d" % k] = byid(ps.u[k])
+        t_ms = sum(a.elapsed_time(bb) for a, bb in ms) / steps
+        return fields, out_dt, t_ms, st
+
+    cp = lp.Context(lp.make_config(3, n, precision=lp.PREC_FP32, **base))
+    fp, dts, ms_p, stp = run(cp, None)
+    cp.close()
+    cm = lp.Context(lp.make_config(3, n, precision=lp.PREC_FP32, estimator=lp.EST_MLP, mlp_tau_lo=info["tau_lo"],
+                                   **base))
+    cm.mlp_set_params(params)
+    fm, _, ms_m, stm = run(cm, dts)
+    cm.close()
+    s0 = {"V": state["V"], "P": state["P"], "u0": state["u"][0], "u1": state["u"][1], "u2": state["u"][2]}
+    drift = {}
+    for nm in fp:
+        a, bb = fm[nm].double(), fp[nm].double()
+        z = torch.as_tensor(np.asarray(s0[nm]), device=a.device, dtype=torch.float64)
+        d = a - bb
+        drift[nm] = {"l2": float(d.norm() / max(float(bb.norm()), 1e-300)),
+                     "max": float(d.abs().max() / max(float(bb.abs().max()), 1e-300)),
+                     "l2_of_change": float(d.norm() / max(float((bb - z).norm()), 1e-300))}
+    line = {"metric": "plain vs learned state estimator, %d steps" % steps, "impl": "ours",
+            "config": config_dict(n, {"steps_compared": steps, "t_end": float(sum(dts)),
+                                      "dt_first": dts[0], "dt_last": dts[-1]}),
+            "plain": {"ms_per_step": ms_p, "value": n / (ms_p * 1e-3), "flagged_per_step": stp["n_flagged"] / steps,
+                      "nonfinite": stp["n_nonfinite"], "fp64_redo_per_step": stp["n_fp64_redo"] / steps},
+            "learned": {"ms_per_step": ms_m, "value": n / (ms_m * 1e-3),
+                        "skipped_per_step": stm["n_mlp_skip"] / steps, "flagged_per_step": stm["n_flagged"] / steps,
+                        "nonfinite": stm["n_nonfinite"], "gate": info},
+            "drift_of_learned_from_plain": drift,
+            "note": "eager lp_step calls timed with CUDA events (no L2 flush); the learned run takes the plain "
+                    "run's CFL steps, so both states are at the same time"}
+    return line
+
+
 def main():
     args = parse()
     select_workload(args)
+    if args.compare_estimators > 0 and args.impl != "reference":
+        print(json.dumps(estimator_compare(args)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "kh-ensemble":
