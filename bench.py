@@ -538,7 +538,10 @@ def run_ours(args):
                 "plain_frac": plain_frac, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the fit kernels, every launch "
                                   "of three timed steps of this 2M workload"
-                                  if traffic else None}
+                                  if traffic else None,
+                "limiter": "not the FP32 pipe: the L1 data pipe's wavefronts for the per-lane gathers of neighbour "
+                           "records (ncu, 400k cloud: 76% of peak in k_step_central, 69% in k_step_plain) and the "
+                           "latency of those loads (long_scoreboard the top stall)"}
     query_roofline = None
     if ("neighbor-query" in phases and phases["neighbor-query"][0] > 0 and n == 2_000_000
             and ACTIVE == "gas-cloud" and not (sched & lp.SCHED_QUERY_WARP)):
