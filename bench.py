@@ -493,7 +493,8 @@ def run_ours(args):
 
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s, FP32 CUDA cores
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s, FP32 CUDA cores
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     per_phase = {}
     for name, (ms, nl) in phases.items():
@@ -525,7 +526,7 @@ def run_ours(args):
                           FIT_TRAFFIC_BPP_2M if n == 2_000_000 else None)
     if args.precision == "fp32":
         alu_peak = fp32_peak
-        alu_source = "FP32 CUDA cores: 152 SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (sm_max, peak_kind)
+        alu_source = "FP32 CUDA cores: %d SM x 128 lanes x 2 x %.0f MHz (%s max clock)" % (n_sm, sm_max, peak_kind)
     else:
         alu_peak = FP64_PEAK_TFLOPS
         alu_source = "nominal GB300 FP64 rate (the FP64 fit runs on the FP64 units)"
@@ -546,13 +547,13 @@ def run_ours(args):
     if ("neighbor-query" in phases and phases["neighbor-query"][0] > 0 and n == 2_000_000
             and ACTIVE == "gas-cloud" and not (sched & lp.SCHED_QUERY_WARP)):
         q_ms = phases["neighbor-query"][0] / args.steps
-        issue_peak = 152 * 4 * sm_max * 1e6
+        issue_peak = n_sm * 4 * sm_max * 1e6
         q_ach = QUERY_INST_PP_2M * n / (q_ms * 1e-3)
         tile_kernel = "k_query_tile_q (warp work queue)" if sched & lp.SCHED_QUEUE_QUERY else "k_query_tile"
         query_roofline = {"kernel": tile_kernel + " + k_query (neighbour query)", "bound": "issue",
                           "achieved": q_ach, "peak": issue_peak, "unit": "warp instructions/s",
                           "frac": q_ach / issue_peak, "inst_per_particle": QUERY_INST_PP_2M,
-                          "peak_source": "152 SM x 4 schedulers x 1 warp instruction per clock x %.0f MHz" % sm_max,
+                          "peak_source": "%d SM x 4 schedulers x 1 warp instruction per clock x %.0f MHz" % (n_sm, sm_max),
                           "inst_source": "ncu smsp__inst_executed.sum, every launch of three timed steps of this workload"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
