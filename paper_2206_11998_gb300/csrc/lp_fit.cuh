@@ -535,23 +535,65 @@ struct Src<double, DIM, F> {
     }
 };
 
+// A particle's neighbour list entries, read one at a time by its thread.
+// NbGlobal reads the list row in global memory: each lane of a warp on a line
+// of its own, one L1 wavefront per lane and entry, as many as the record loads
+// the entry leads to.  NbStaged<D> reads the first D entries from a
+// shared-memory copy of the warp's 32 list rows, staged with coalesced loads
+// (stage_rows), where a warp's read of one entry per lane is one wavefront.
+struct NbGlobal {
+    const uint32_t* p;
+    __device__ __forceinline__ uint32_t operator[](int r) const { return __ldg(p + r); }
+};
+constexpr int NB_PITCH = FIT_THREADS + 1;   // entry-major, a column per thread (conflict-free both ways)
+template <int D>
+struct NbStaged {
+    const uint32_t* p;        // the list row in global memory
+    const uint32_t* s;        // this thread's column of the staged copy
+    __device__ __forceinline__ uint32_t operator[](int r) const { return r < D ? s[r * NB_PITCH] : __ldg(p + r); }
+};
+
+// The warp's staging of the first D (32 or 64) entries of the list rows of its
+// lanes' particles (particle i of each lane, none where i < 0) into
+// stage[entry][threadIdx.x]: coalesced reads of 32 entries per instruction.
+// All 32 lanes take part.
+template <int D>
+__device__ __forceinline__ void stage_rows(uint32_t (*stage)[NB_PITCH], const uint32_t* idx, int k_max, int64_t i)
+{
+    static_assert(D == 32 || D == 64, "stage depth");
+    const unsigned lane = threadIdx.x & 31u;
+    const int w0 = (int)(threadIdx.x & ~31u);
+    const int nr = k_max < D ? k_max : D;
+    for (int q = 0; q < 32; ++q) {
+        const long long ip = __shfl_sync(0xffffffffu, (long long)i, q);
+        if (ip < 0) continue;                          // warp-uniform
+        const uint32_t* row = idx + ip * (int64_t)k_max;
+#pragma unroll
+        for (int h = 0; h < D / 32; ++h) {
+            const int e = (int)lane + 32 * h;
+            if (e < nr) stage[e][w0 + q] = __ldg(row + e);
+        }
+    }
+    __syncwarp();
+}
+
 // Visit the neighbour list in order with the next record (and the index after
 // it) already in flight: body(j, rec) returns false to stop early.
-template <bool HALF = false, class S, class Body>
-__device__ __forceinline__ void for_neighbors(const S& src, const uint32_t* nb, int cnt, Body&& body)
+template <bool HALF = false, class S, class NB, class Body>
+__device__ __forceinline__ void for_neighbors(const S& src, const NB& nb, int cnt, Body&& body)
 {
     if (cnt <= 0) return;
     typename S::Rec nxt;
-    uint32_t jn = __ldg(nb);
+    uint32_t jn = nb[0];
     if (HALF) src.load_half(jn, nxt); else src.load_rec(jn, nxt);
-    uint32_t jn2 = cnt > 1 ? __ldg(nb + 1) : 0u;
+    uint32_t jn2 = cnt > 1 ? nb[1] : 0u;
     for (int r = 0; r < cnt; ++r) {
         const typename S::Rec cur = nxt;
         const uint32_t j = jn;
         if (r + 1 < cnt) {
             jn = jn2;
             if (HALF) src.load_half(jn, nxt); else src.load_rec(jn, nxt);
-            if (r + 2 < cnt) jn2 = __ldg(nb + r + 2);
+            if (r + 2 < cnt) jn2 = nb[r + 2];
         }
         if (!body(j, cur)) break;
     }
@@ -581,8 +623,8 @@ constexpr float NE_RATIO_MIN = 0.02f;
 // rotations did not give it.
 // DEFER: return 2, with x untouched, where the correction pass would run
 // (the caller lists the particle for a kernel that runs it in full warps).
-template <typename T, int DIM, int F, bool STATS = false, bool DEFER = false>
-__device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau,
+template <typename T, int DIM, int F, bool STATS = false, bool DEFER = false, class NB>
+__device__ int central_fit(const Src<T, DIM, F>& src, const NB& nb, int cnt, T invS, T tau,
                            const DevCfg& cf, T (&x)[NU<DIM>::v][F], FitStats<T>* st = nullptr,
                            bool* refined = nullptr)
 {
@@ -736,8 +778,8 @@ __device__ int central_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cn
 }
 
 // First-order fit on the whole list (fallback).  Returns 0 ok, 1 rank deficient.
-template <typename T, int DIM, int F>
-__device__ int linear_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, T invS, T tau, T (&x)[DIM][F])
+template <typename T, int DIM, int F, class NB>
+__device__ int linear_fit(const Src<T, DIM, F>& src, const NB& nb, int cnt, T invS, T tau, T (&x)[DIM][F])
 {
     Givens<T, DIM, F> G;
     G.zero();
@@ -767,8 +809,8 @@ __device__ int linear_fit(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt
 // tailn and finds them by a scan of the list's tail.  ok[k][s] = false where
 // fewer than DIM members or rank deficient.  ill = true when a system with
 // enough members is below tau (FP32: redo in FP64).
-template <typename T, int DIM, int F>
-__device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt, int ks, T invS, T tau,
+template <typename T, int DIM, int F, class NB>
+__device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const NB& nb, int cnt, int ks, T invS, T tau,
                              T tau_rank, T (&out)[DIM][2][F], bool (&ok)[DIM][2], bool& ill)
 {
     uint64_t m[DIM][2];
@@ -820,13 +862,13 @@ __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const ui
         // rows in list order, the next record in flight
         // (with no member before position 64 the first load reads entry 0, unused)
         Rec nxt;
-        uint32_t jn = __ldg(nb + (mm ? __ffsll((long long)mm) - 1 : 0));
+        uint32_t jn = nb[mm ? __ffsll((long long)mm) - 1 : 0];
         src.load_rec(jn, nxt);
         while (mm) {
             mm &= mm - 1;
             const Rec cur = nxt;
             if (mm) {
-                jn = __ldg(nb + (__ffsll((long long)mm) - 1));
+                jn = nb[__ffsll((long long)mm) - 1];
                 src.load_rec(jn, nxt);
             }
             T d[DIM], b[F];
@@ -840,7 +882,7 @@ __device__ __forceinline__ void onesided_all(const Src<T, DIM, F>& src, const ui
             int need = ntail;
             const int want = (q & 1) ? 1 : -1;
             for (int r = 64; r < cnt && need > 0; ++r) {
-                const uint32_t j = __ldg(nb + r);
+                const uint32_t j = nb[r];
                 Rec rec;
                 src.load_rec(j, rec);
                 int sg = 0;                 // (k is not a compile-time index here)

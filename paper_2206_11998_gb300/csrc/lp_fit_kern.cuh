@@ -39,8 +39,8 @@ __device__ inline void push_redo(const FitArgs& a, int64_t i)
     atomicAdd(a.counters + C_FP64, 1ull);
 }
 
-template <typename T, int DIM, int F>
-__device__ inline float last_d2(const Src<T, DIM, F>& src, const uint32_t* nb, int cnt)
+template <typename T, int DIM, int F, class NB>
+__device__ inline float last_d2(const Src<T, DIM, F>& src, const NB& nb, int cnt)
 {
     if (cnt <= 0) return 0.0f;
     T d[DIM];
@@ -152,9 +152,9 @@ __device__ __forceinline__ bool step_load(const FitArgs& a, const StepOut& o, in
 // central stage; false when i went to the FP64 redo list (or, DEFER, to the
 // correction kernel's list).  GATE: the learned estimator or the feature
 // output is in use (its inputs and code are compiled out otherwise)
-template <typename T, int DIM, bool GATE, bool DEFER = false>
+template <typename T, int DIM, bool GATE, bool DEFER = false, class NB>
 __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t i, const Loaded<DIM>& L,
-                                    const Src<T, DIM, DIM + 2>& src, const uint32_t* nb, int cnt, T invS,
+                                    const Src<T, DIM, DIM + 2>& src, const NB& nb, int cnt, T invS,
                                     T (&cdf)[DIM][DIM + 2], T (&lw)[DIM + 2], bool& mlp_skip)
 {
     constexpr int F = DIM + 2;
@@ -214,8 +214,8 @@ __device__ inline bool step_central(const FitArgs& a, const StepOut& o, int64_t 
 }
 
 // plain stage; false when i went to the FP64 redo list
-template <typename T, int DIM>
-__device__ __forceinline__ bool step_plain(const FitArgs& a, int64_t i, const Src<T, DIM, DIM + 2>& src, const uint32_t* nb,
+template <typename T, int DIM, class NB>
+__device__ __forceinline__ bool step_plain(const FitArgs& a, int64_t i, const Src<T, DIM, DIM + 2>& src, const NB& nb,
                                   int cnt, T invS, const T (&cdf)[DIM][DIM + 2], T (&os)[DIM][2][DIM + 2])
 {
     constexpr int F = DIM + 2;
@@ -351,7 +351,7 @@ __device__ void step_one(const FitArgs& a, const StepOut& o, int64_t i)
     if (step_load<T, DIM>(a, o, i, L)) return;
     Src<T, DIM, F> src(a, i);
     const int cnt = (int)a.count[i];
-    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
+    const NbGlobal nb{a.idx + i * (int64_t)a.c.k_max};
     const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     T cdf[DIM][F], lw[F];
     bool mlp_skip;
@@ -427,16 +427,16 @@ __device__ __forceinline__ void central_append_or_finish(const FitArgs& a, const
     step_finish<T, DIM>(a, o, i, L, os, lw, false, true);
 }
 
-// the central stage of particle i as the split schedule's first kernel runs it
-template <typename T, int DIM, bool GATE, bool DEFER>
-__device__ __forceinline__ void central_one(const FitArgs& a, const StepOut& o, int64_t i)
+// the central stage of particle i as the split schedule's first kernel runs
+// it, its list entries read through nb (NbGlobal, NbStaged)
+template <typename T, int DIM, bool GATE, bool DEFER, class NB>
+__device__ __forceinline__ void central_one(const FitArgs& a, const StepOut& o, int64_t i, const NB& nb)
 {
     constexpr int F = DIM + 2;
     Loaded<DIM> L;
     if (step_load<T, DIM>(a, o, i, L)) return;
     Src<T, DIM, F> src(a, i);
     const int cnt = (int)a.count[i];
-    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
     const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     T cdf[DIM][F], lw[F];
     bool mlp_skip;
@@ -452,9 +452,11 @@ __device__ __forceinline__ void central_one(const FitArgs& a, const StepOut& o, 
 template <typename T, int DIM, bool GATE, bool DEFER>
 __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_central(FitArgs a, StepOut o)
 {
+    // (list entries from global memory: staging the rows in shared memory, as
+    // the plain kernel does, made this kernel slower, with and without the gate)
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    central_one<T, DIM, GATE, DEFER>(a, o, i);
+    central_one<T, DIM, GATE, DEFER>(a, o, i, NbGlobal{a.idx + i * (int64_t)a.c.k_max});
 }
 
 // The central fits k_step_central deferred, in full warps, with the correction
@@ -466,12 +468,14 @@ __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_centra
     const unsigned long long len = *a.refine_len;
     for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < len;
          t += (unsigned long long)gridDim.x * blockDim.x)
-        central_one<T, DIM, GATE, false>(a, o, a.refine_list[t]);
+        central_one<T, DIM, GATE, false>(a, o, a.refine_list[t],
+                                         NbGlobal{a.idx + (int64_t)a.refine_list[t] * (int64_t)a.c.k_max});
 }
 
 // the second stage of list entry t of the split schedule
 template <typename T, int DIM>
-__device__ __forceinline__ void plain_one(const FitArgs& a, const StepOut& o, unsigned long long t)
+__device__ __forceinline__ void plain_one(const FitArgs& a, const StepOut& o, unsigned long long t,
+                                          const uint32_t* stage_col)
 {
     constexpr int F = DIM + 2;
     const uint32_t iu = a.plain_list[t];
@@ -479,7 +483,7 @@ __device__ __forceinline__ void plain_one(const FitArgs& a, const StepOut& o, un
     const int64_t i = iu;
     Src<T, DIM, F> src(a, i);
     const int cnt = (int)a.count[i];
-    const uint32_t* nb = a.idx + i * (int64_t)a.c.k_max;
+    const NbStaged<32> nb{a.idx + i * (int64_t)a.c.k_max, stage_col};
     const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     // the one-sided fits first: the central stage's record and the particle's
     // state are read after them, so they hold no registers during the fits
@@ -510,12 +514,22 @@ __device__ __forceinline__ void plain_one(const FitArgs& a, const StepOut& o, un
     step_finish<T, DIM>(a, o, i, L, os, lw, true, mlp_skip);
 }
 
+// the particle of plain-stage slot t (or -1: none)
+__device__ __forceinline__ int64_t plain_particle(const FitArgs& a, unsigned long long t, unsigned long long len)
+{
+    if (t >= len) return -1;
+    const uint32_t iu = a.plain_list[t];
+    return iu == 0xffffffffu ? -1 : (int64_t)iu;
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain(FitArgs a, StepOut o)
 {
+    __shared__ uint32_t stage[32][NB_PITCH];
     const unsigned long long len = a.plain_ident ? (unsigned long long)a.n : *a.plain_len;
     const unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    if (t < len) plain_one<T, DIM>(a, o, t);
+    stage_rows<32>(stage, a.idx, a.c.k_max, plain_particle(a, t, len));
+    if (t < len) plain_one<T, DIM>(a, o, t, &stage[0][threadIdx.x]);
 }
 
 // Persistent forms of the split schedule's two kernels (LP_SCHED_QUEUE_FIT):
@@ -539,19 +553,22 @@ __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_centra
         const unsigned long long base = warp_take(a.queue);
         if (base >= (unsigned long long)a.n) return;
         const int64_t i = (int64_t)base + (int64_t)(threadIdx.x & 31u);
-        if (i < a.n) central_one<T, DIM, GATE, DEFER>(a, o, i);
+        if (i < a.n) central_one<T, DIM, GATE, DEFER>(a, o, i, NbGlobal{a.idx + i * (int64_t)a.c.k_max});
     }
 }
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::plain) k_step_plain_q(FitArgs a, StepOut o)
 {
+    __shared__ uint32_t stage[32][NB_PITCH];
     const unsigned long long len = a.plain_ident ? (unsigned long long)a.n : *a.plain_len;
     for (;;) {
         const unsigned long long base = warp_take(a.queue + 1);
         if (base >= len) return;
         const unsigned long long t = base + (threadIdx.x & 31u);
-        if (t < len) plain_one<T, DIM>(a, o, t);
+        stage_rows<32>(stage, a.idx, a.c.k_max, plain_particle(a, t, len));
+        if (t < len) plain_one<T, DIM>(a, o, t, &stage[0][threadIdx.x]);
+        __syncwarp();                               // the staged rows are reused by the next batch
     }
 }
 
@@ -573,7 +590,7 @@ __device__ void derivs_one(const FitArgs& a, const DerivOut& o, int64_t i)
     const DevCfg& c = a.c;
     Src<T, DIM, F> src(a, i);
     const int cnt = (int)a.count[i];
-    const uint32_t* nb = a.idx + i * (int64_t)c.k_max;
+    const NbGlobal nb{a.idx + i * (int64_t)c.k_max};
     const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
     T cd[N][F];
@@ -633,7 +650,7 @@ __device__ void onesided_one(const FitArgs& a, double* out, int f_real, int64_t 
     const DevCfg& c = a.c;
     Src<T, DIM, F> src(a, i);
     const int cnt = (int)a.count[i];
-    const uint32_t* nb = a.idx + i * (int64_t)c.k_max;
+    const NbGlobal nb{a.idx + i * (int64_t)c.k_max};
     const T invS = (T)inv_scale(last_d2(src, nb, cnt));
     const T tau = IsF32<T>::v ? (T)c.tau32 : (T)c.tau64;
     T cd[N][F];
