@@ -564,15 +564,26 @@ __device__ __forceinline__ void stage_rows(uint32_t (*stage)[NB_PITCH], const ui
     const unsigned lane = threadIdx.x & 31u;
     const int w0 = (int)(threadIdx.x & ~31u);
     const int nr = k_max < D ? k_max : D;
-    for (int q = 0; q < 32; ++q) {
-        const long long ip = __shfl_sync(0xffffffffu, (long long)i, q);
-        if (ip < 0) continue;                          // warp-uniform
-        const uint32_t* row = idx + ip * (int64_t)k_max;
+    // eight rows per round, their loads issued before their stores
+#pragma unroll 1
+    for (int q0 = 0; q0 < 32; q0 += 8) {
+        uint32_t v[8][D / 32];
 #pragma unroll
-        for (int h = 0; h < D / 32; ++h) {
-            const int e = (int)lane + 32 * h;
-            if (e < nr) stage[e][w0 + q] = __ldg(row + e);
+        for (int u = 0; u < 8; ++u) {
+            const long long ip = __shfl_sync(0xffffffffu, (long long)i, q0 + u);
+#pragma unroll
+            for (int h = 0; h < D / 32; ++h) {
+                const int e = (int)lane + 32 * h;
+                v[u][h] = (ip >= 0 && e < nr) ? __ldg(idx + ip * (int64_t)k_max + e) : 0u;
+            }
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int h = 0; h < D / 32; ++h) {
+                const int e = (int)lane + 32 * h;
+                if (e < nr) stage[e][w0 + q0 + u] = v[u][h];
+            }
     }
     __syncwarp();
 }

@@ -452,11 +452,16 @@ __device__ __forceinline__ void central_one(const FitArgs& a, const StepOut& o, 
 template <typename T, int DIM, bool GATE, bool DEFER>
 __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_central(FitArgs a, StepOut o)
 {
-    // (list entries from global memory: staging the rows in shared memory, as
-    // the plain kernel does, made this kernel slower, with and without the gate)
+    // the warp's list rows staged in shared memory (their index reads then
+    // cost the L1 one wavefront per warp instead of one per lane); without
+    // DEFER the correction pass's stash takes 23 KB, and 32 staged entries
+    // keep the block below 48 KB of static shared memory
+    constexpr int SD = DEFER ? 64 : 32;
+    __shared__ uint32_t stage[SD][NB_PITCH];
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    stage_rows<SD>(stage, a.idx, a.c.k_max, i < a.n ? i : -1);
     if (i >= a.n) return;
-    central_one<T, DIM, GATE, DEFER>(a, o, i, NbGlobal{a.idx + i * (int64_t)a.c.k_max});
+    central_one<T, DIM, GATE, DEFER>(a, o, i, NbStaged<SD>{a.idx + i * (int64_t)a.c.k_max, &stage[0][threadIdx.x]});
 }
 
 // The central fits k_step_central deferred, in full warps, with the correction
@@ -549,11 +554,17 @@ __device__ __forceinline__ unsigned long long warp_take(unsigned long long* q)
 template <typename T, int DIM, bool GATE, bool DEFER>
 __global__ void __launch_bounds__(FIT_THREADS, FitOcc<T>::central) k_step_central_q(FitArgs a, StepOut o)
 {
+    constexpr int SD = DEFER ? 64 : 32;               // (as in k_step_central)
+    __shared__ uint32_t stage[SD][NB_PITCH];
     for (;;) {
         const unsigned long long base = warp_take(a.queue);
         if (base >= (unsigned long long)a.n) return;
         const int64_t i = (int64_t)base + (int64_t)(threadIdx.x & 31u);
-        if (i < a.n) central_one<T, DIM, GATE, DEFER>(a, o, i, NbGlobal{a.idx + i * (int64_t)a.c.k_max});
+        stage_rows<SD>(stage, a.idx, a.c.k_max, i < a.n ? i : -1);
+        if (i < a.n)
+            central_one<T, DIM, GATE, DEFER>(a, o, i,
+                                             NbStaged<SD>{a.idx + i * (int64_t)a.c.k_max, &stage[0][threadIdx.x]});
+        __syncwarp();                               // the staged rows are reused by the next batch
     }
 }
 
