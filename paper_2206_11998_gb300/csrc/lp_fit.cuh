@@ -564,12 +564,13 @@ __device__ __forceinline__ void stage_rows(uint32_t (*stage)[NB_PITCH], const ui
     const unsigned lane = threadIdx.x & 31u;
     const int w0 = (int)(threadIdx.x & ~31u);
     const int nr = k_max < D ? k_max : D;
-    // eight rows per round, their loads issued before their stores
+    // RR rows per round, their loads issued before their stores
+    constexpr int RR = 16;
 #pragma unroll 1
-    for (int q0 = 0; q0 < 32; q0 += 8) {
-        uint32_t v[8][D / 32];
+    for (int q0 = 0; q0 < 32; q0 += RR) {
+        uint32_t v[RR][D / 32];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < RR; ++u) {
             const long long ip = __shfl_sync(0xffffffffu, (long long)i, q0 + u);
 #pragma unroll
             for (int h = 0; h < D / 32; ++h) {
@@ -578,7 +579,7 @@ __device__ __forceinline__ void stage_rows(uint32_t (*stage)[NB_PITCH], const ui
             }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < RR; ++u)
 #pragma unroll
             for (int h = 0; h < D / 32; ++h) {
                 const int e = (int)lane + 32 * h;
