@@ -565,7 +565,7 @@ __device__ __forceinline__ void stage_rows(uint32_t (*stage)[NB_PITCH], const ui
     const int w0 = (int)(threadIdx.x & ~31u);
     const int nr = k_max < D ? k_max : D;
     // RR rows per round, their loads issued before their stores
-    constexpr int RR = 16;
+    constexpr int RR = 32;
 #pragma unroll 1
     for (int q0 = 0; q0 < 32; q0 += RR) {
         uint32_t v[RR][D / 32];
