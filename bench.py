@@ -78,9 +78,9 @@ def fit_flops_per_particle(m: float, refined_frac: float = 0.0, plain_frac: floa
 # DRAM bytes per particle of one fit pass (split schedule, FP32: k_step_central,
 # k_step_central_refine, k_step_plain), measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass, every launch of three timed steps) on the
-# 2M-particle gas cloud this benchmark times: 2,119 MB per pass.  None when the
+# 2M-particle gas cloud this benchmark times: 2,118 MB per pass.  None when the
 # kernels change and the figure has not been re-measured.
-FIT_TRAFFIC_BPP_2M = 1059.3
+FIT_TRAFFIC_BPP_2M = 1059.0
 
 # warp instructions per particle of one neighbour query (k_query_tile and the
 # per-particle kernel over the particles it leaves; smsp__inst_executed.sum from
