@@ -564,28 +564,25 @@ __device__ __forceinline__ void stage_rows(uint32_t (*stage)[NB_PITCH], const ui
     const unsigned lane = threadIdx.x & 31u;
     const int w0 = (int)(threadIdx.x & ~31u);
     const int nr = k_max < D ? k_max : D;
-    // RR rows per round, their loads issued before their stores
-    constexpr int RR = 32;
-#pragma unroll 1
-    for (int q0 = 0; q0 < 32; q0 += RR) {
-        uint32_t v[RR][D / 32];
+    // the 32 rows' loads all issued before their stores (one at a time, each
+    // waiting for its load, the staging cost more than it saved)
+    uint32_t v[32][D / 32];
 #pragma unroll
-        for (int u = 0; u < RR; ++u) {
-            const long long ip = __shfl_sync(0xffffffffu, (long long)i, q0 + u);
+    for (int u = 0; u < 32; ++u) {
+        const long long ip = __shfl_sync(0xffffffffu, (long long)i, u);
 #pragma unroll
-            for (int h = 0; h < D / 32; ++h) {
-                const int e = (int)lane + 32 * h;
-                v[u][h] = (ip >= 0 && e < nr) ? __ldg(idx + ip * (int64_t)k_max + e) : 0u;
-            }
+        for (int h = 0; h < D / 32; ++h) {
+            const int e = (int)lane + 32 * h;
+            v[u][h] = (ip >= 0 && e < nr) ? __ldg(idx + ip * (int64_t)k_max + e) : 0u;
         }
-#pragma unroll
-        for (int u = 0; u < RR; ++u)
-#pragma unroll
-            for (int h = 0; h < D / 32; ++h) {
-                const int e = (int)lane + 32 * h;
-                if (e < nr) stage[e][w0 + q0 + u] = v[u][h];
-            }
     }
+#pragma unroll
+    for (int u = 0; u < 32; ++u)
+#pragma unroll
+        for (int h = 0; h < D / 32; ++h) {
+            const int e = (int)lane + 32 * h;
+            if (e < nr) stage[e][w0 + u] = v[u][h];
+        }
     __syncwarp();
 }
 
