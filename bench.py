@@ -80,7 +80,7 @@ def fit_flops_per_particle(m: float, refined_frac: float = 0.0, plain_frac: floa
 # dram__bytes_write.sum, one pass, every launch of three timed steps) on the
 # 2M-particle gas cloud this benchmark times: 2,118 MB per pass.  None when the
 # kernels change and the figure has not been re-measured.
-FIT_TRAFFIC_BPP_2M = 1059.0
+FIT_TRAFFIC_BPP_2M = 1058.8
 
 # warp instructions per particle of one neighbour query (k_query_tile and the
 # per-particle kernel over the particles it leaves; smsp__inst_executed.sum from
