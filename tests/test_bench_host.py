@@ -92,3 +92,28 @@ def test_fit_flop_model_counts_the_work_the_kernels_do():
     # one-sided: 6 fits of 8 rows, 138 flops a row, and 30 for each back substitution
     assert bench.fit_flops_per_particle(m, 0.0, 1.0) - none == 6 * (8 * 138 + 30)
     assert 17_000 < bench.fit_flops_per_particle(m, 0.03, 1.0) < 20_000 < full
+
+
+def test_workload_settings():
+    """Each workload's configuration: the gas cloud keeps the nearest k_max = 64
+    neighbours; the jet workloads, whose configuration quotes 20-80
+    neighbours, take k_max = 80 with the octant-balanced selection unless
+    --select says otherwise; the estimator comparison is its own mode."""
+    import bench
+    a = bench.parse([])
+    bench.select_workload(a)
+    assert (bench.K_MAX, bench.SELECT, a.particles) == (64, "nearest", 2_000_000)
+    assert a.compare_estimators == 0
+    for w in ("jet-snapshot", "jet-inflow"):
+        a = bench.parse(["--workload", w])
+        bench.select_workload(a)
+        assert (bench.K_MAX, bench.SELECT, a.particles) == (80, "octant", 8_000_000)
+        cfg = bench.config_dict(a.particles)
+        assert cfg["k_max"] == 80 and cfg["select"] == "octant"
+    a = bench.parse(["--workload", "jet-snapshot", "--select", "nearest"])
+    bench.select_workload(a)
+    assert bench.SELECT == "nearest"
+    a = bench.parse(["--compare-estimators", "200", "--particles", "400000"])
+    bench.select_workload(a)
+    assert (a.compare_estimators, a.particles, bench.K_MAX) == (200, 400_000, 64)
+    bench.select_workload(bench.parse([]))          # back to the default workload for later tests
